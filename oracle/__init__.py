@@ -1,0 +1,154 @@
+"""CPU oracle for the checkerboard spin-lattice sweep -- TEST INFRASTRUCTURE ONLY.
+
+A plain single-threaded restatement (``oracle.c``) of the checkerboard
+Metropolis sweep for spin-S Ising models (Levy, Cohen & Rabani, §III.A,
+Eq. 2) and of the facilitated North-East sweep (§III.B, Eq. 3), used to check
+the CUDA library bit for bit.  Only ``tests/``, ``__graft_entry__.smoke()``
+and ``bench.py``'s CPU baseline may import this package; the library never
+does, and the two share no code.
+
+Parity pins: see the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ISING, NE = 0, 1
+INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared object with gcc (no GPU needed)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+            u8p = ctypes.c_void_p
+            i64p = ctypes.c_void_p
+            u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+            lib.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            lib.oracle_philox4x32_10.restype = None
+            lib.oracle_init.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_uint64, ctypes.c_int, i8p]
+            lib.oracle_init.restype = ctypes.c_int
+            lib.oracle_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_uint64, i8p, u8p, ctypes.c_int64,
+                                         ctypes.c_int64, i64p, i64p, i64p, i64p]
+            lib.oracle_sweep.restype = ctypes.c_int
+            lib.oracle_measure.argtypes = [ctypes.c_int, ctypes.c_int, i8p, u8p,
+                                           i64p, i64p, i64p, i64p]
+            lib.oracle_measure.restype = None
+            lib.oracle_metropolis_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
+                                                        ctypes.POINTER(ctypes.c_uint32)]
+            lib.oracle_metropolis_threshold.restype = ctypes.c_int
+            lib.oracle_probability_threshold.argtypes = [ctypes.c_double,
+                                                         ctypes.POINTER(ctypes.c_uint32)]
+            lib.oracle_probability_threshold.restype = ctypes.c_int
+            lib.oracle_delta_energy.argtypes = [ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_int, ctypes.c_int]
+            lib.oracle_delta_energy.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(counter, key):
+    """Philox4x32-10 (Salmon et al., SC'11) of one 4-word counter and 2-word key."""
+    lib = _load()
+    c = np.ascontiguousarray(counter, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.oracle_philox4x32_10(c, k, out)
+    return out
+
+
+def metropolis_threshold(dE: float, T: float):
+    """(always, thr): Metropolis acceptance min[1, exp(-dE/T)] as an integer threshold."""
+    lib = _load()
+    thr = ctypes.c_uint32(0)
+    always = lib.oracle_metropolis_threshold(float(dE), float(T), ctypes.byref(thr))
+    return bool(always), int(thr.value)
+
+
+def probability_threshold(p: float):
+    lib = _load()
+    thr = ctypes.c_uint32(0)
+    always = lib.oracle_probability_threshold(float(p), ctypes.byref(thr))
+    return bool(always), int(thr.value)
+
+
+def delta_energy(J: float, h: float, ds: int, n: int) -> float:
+    return _load().oracle_delta_energy(float(J), float(h), int(ds), int(n))
+
+
+class Lattice:
+    """A lattice advanced by the oracle: spins (int8, x fastest) + persistence flags."""
+
+    def __init__(self, dims, L, two_S=1, model=ISING, J=1.0, h=0.0, T_or_c=2.269185,
+                 seed=0, init=INIT_COLD):
+        self.dims, self.L, self.two_S, self.model = dims, L, two_S, model
+        self.J, self.h, self.T_or_c, self.seed = float(J), float(h), float(T_or_c), int(seed)
+        self.N = L ** dims
+        self.spins = np.zeros(self.N, dtype=np.int8)
+        self.flags = np.zeros(self.N, dtype=np.uint8)
+        self.sweep_index = 0
+        rc = _load().oracle_init(dims, L, two_S, model, self.J, self.h, self.T_or_c,
+                                 self.seed, init, self.spins)
+        if rc != 0:
+            raise ValueError("oracle_init rejected the parameters")
+
+    def sweep(self, n: int):
+        """Advance n sweeps; returns dict of per-sweep int64 series (bond, mag, up, unflipped)."""
+        out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
+        rc = _load().oracle_sweep(self.dims, self.L, self.two_S, self.model, self.J, self.h,
+                                  self.T_or_c, self.seed, self.spins,
+                                  _ptr(self.flags) if self.model == NE else None,
+                                  self.sweep_index, n, _ptr(out["bond"]), _ptr(out["mag"]),
+                                  _ptr(out["up"]), _ptr(out["unflipped"]))
+        if rc != 0:
+            raise ValueError("oracle_sweep rejected the parameters")
+        self.sweep_index += n
+        return out
+
+    def measure(self):
+        b, m, u, f = (ctypes.c_int64() for _ in range(4))
+        _load().oracle_measure(self.dims, self.L, self.spins,
+                               _ptr(self.flags) if self.model == NE else None,
+                               ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
+                               ctypes.byref(f))
+        return dict(bond=b.value, mag=m.value, up=u.value, unflipped=f.value)
+
+    def energy(self, bond, mag):
+        J, h = self.J, self.h
+        if self.model == NE and J == 0.0 and h == 0.0:
+            J, h = 0.0, -1.0
+        return -J * np.asarray(bond, dtype=np.float64) - h * np.asarray(mag, dtype=np.float64)

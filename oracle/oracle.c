@@ -1,0 +1,346 @@
+/*
+ * oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU restatement of the checkerboard
+ * Metropolis / facilitated sweep of Levy, Cohen & Rabani, "Simulating
+ * lattice spin models on GPUs" (arXiv:1209.0296).  It exists to check the
+ * CUDA library against the paper; nothing in the product path may call it.
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference legs load this file's shared object.
+ *
+ * It shares no code, header, table or constant generator with the CUDA
+ * library: Philox4x32-10, the acceptance rule, the initial state and the
+ * observables are all written out again here, site by site, in the order
+ * the paper's algorithm states them.
+ *
+ * Readings of the paper taken here (the paper is silent or ambiguous):
+ *  - Hamiltonian sign: H = -J sum_<ij> s_i s_j - h sum_i s_i for every model
+ *    (Eq. 2 sign, extended with a field); the North-East model of Eq. 3
+ *    with B = +1 is h = -1 here.  Each bond (i, i+e_d) is counted once per
+ *    direction d, so for L = 2 a pair appears twice, in H and in dE alike.
+ *  - Checkerboard: colour(x,y[,z]) = (x+y[+z]) mod 2; one sweep updates
+ *    colour 0 then colour 1 (the paper's red+blue, then green+white, §III.A
+ *    steps 6-7 and Fig. 2).  Periodic boundaries; L even.
+ *  - Randomness: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) in place
+ *    of the paper's per-thread LCG (§IV, Eqs. 5-7).  key = (seed lo, seed
+ *    hi); counter = (g, sweep lo, sweep hi, colour); g = r*G + (j >> sh),
+ *    r = y + L*z the row, j = x >> 1 the index of the site among the
+ *    same-colour sites of its row, G = ceil((L/2) / 2^sh) groups per row,
+ *    sh = 2 for spin-1/2 (word j & 3 decides acceptance), sh = 1 for
+ *    spin-S > 1/2 (word 2(j&1) decides acceptance, word 2(j&1)+1 picks the
+ *    proposal).  Initial states use counter (i >> 2, 0, 0, 2), word i & 3.
+ *  - Acceptance (§III.A, min[1, exp(-dH/T)]): dE <= 0 accepts without a
+ *    draw; otherwise accept iff u < floor(exp(-dE/T) * 2^32).
+ *  - Spin-S (§III "any spin value"): state k in [0, two_S]; s = 2k - two_S
+ *    for odd two_S, s = k - two_S/2 for even two_S.  Proposal: one of the
+ *    other two_S states, uniformly: k' = (k + 1 + floor(u*two_S/2^32)) mod
+ *    (two_S + 1).
+ *  - North-East (§III.B): north of (x,y) is (x, y-1), east is (x+1, y); a
+ *    site may change only if both are up (+1).  With J = h = 0 the last
+ *    model parameter is the up-spin concentration c and the rates are
+ *    p(down->up) = min(1, c/(1-c)), p(up->down) = min(1, (1-c)/c).
+ *  - Persistence: a site's flag is set the first time its value changes
+ *    (North-East model only).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, as published by Salmon et al. (SC'11, "Parallel random     */
+/* numbers: as easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplies     */
+/* with the round keys bumped by the Weyl constants between rounds.         */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* One Philox draw for (seed, counter words). */
+static uint32_t draw_word(uint64_t seed, uint32_t g, int64_t sweep,
+                          uint32_t colour, int word)
+{
+    uint32_t ctr[4] = {g, (uint32_t)((uint64_t)sweep & 0xffffffffu),
+                       (uint32_t)((uint64_t)sweep >> 32), colour};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[word];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spin values (§III: s_i = +-1, "easily extended to any spin value").      */
+/* ------------------------------------------------------------------------ */
+int oracle_spin_of_state(int two_S, int k)
+{
+    if (two_S & 1) return 2 * k - two_S;
+    return k - two_S / 2;
+}
+
+int oracle_state_of_spin(int two_S, int s)
+{
+    if (two_S & 1) return (s + two_S) / 2;
+    return s + two_S / 2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metropolis acceptance threshold (§III.A: P_acc = min[1, exp(-dH/T)]).    */
+/* Returns 1 when the move is accepted without a draw (dE <= 0); otherwise  */
+/* returns 0 and writes thr = floor(exp(-dE/T) * 2^32), so that a uniform   */
+/* 32-bit draw u accepts with probability exactly thr / 2^32.               */
+/* ------------------------------------------------------------------------ */
+int oracle_metropolis_threshold(double dE, double T, uint32_t *thr)
+{
+    if (dE <= 0.0) {
+        *thr = 0;
+        return 1;
+    }
+    double p = exp(-dE / T);
+    *thr = (uint32_t)floor(ldexp(p, 32));
+    return 0;
+}
+
+/* Same rule when the acceptance probability p itself is given (North-East
+ * model at fixed concentration c, §III.B). */
+int oracle_probability_threshold(double p, uint32_t *thr)
+{
+    if (p >= 1.0) {
+        *thr = 0;
+        return 1;
+    }
+    *thr = (uint32_t)floor(ldexp(p, 32));
+    return 0;
+}
+
+/* Energy change of replacing spin s by s2 at a site whose neighbour spins
+ * sum to n, for H = -J sum s_i s_j - h sum s_i (Eq. 2 plus a field). */
+double oracle_delta_energy(double J, double h, int ds, int n)
+{
+    return -(J * (double)(ds * n)) - h * (double)ds;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lattice geometry.                                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int dims, L, two_S, model;
+    double J, h, T, c;
+    int cmode;
+    uint64_t seed;
+    int64_t N;
+} params_t;
+
+static int64_t site_index(const params_t *p, int x, int y, int z)
+{
+    int L = p->L;
+    x = ((x % L) + L) % L;
+    y = ((y % L) + L) % L;
+    z = ((z % L) + L) % L;
+    return (int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * (int64_t)z);
+}
+
+static int setup(params_t *p, int dims, int L, int two_S, int model, double J,
+                 double h, double T_or_c, uint64_t seed)
+{
+    if (dims != 2 && dims != 3) return -1;
+    if (L < 2 || (L & 1)) return -1;
+    if (two_S < 1 || two_S > 8) return -1;
+    if (model != 0 && model != 1) return -1;
+    if (model == 1 && (dims != 2 || two_S != 1)) return -1;
+    p->dims = dims; p->L = L; p->two_S = two_S; p->model = model;
+    p->J = J; p->h = h; p->seed = seed;
+    p->N = (int64_t)L * L * (dims == 3 ? L : 1);
+    if (p->N >= ((int64_t)1 << 32)) return -1;
+    p->cmode = (model == 1 && J == 0.0 && h == 0.0);
+    if (p->cmode) {
+        if (!(T_or_c > 0.0 && T_or_c < 1.0)) return -1;
+        p->c = T_or_c; p->T = 0.0;
+    } else {
+        if (!(T_or_c > 0.0)) return -1;
+        p->T = T_or_c; p->c = 0.0;
+    }
+    return 0;
+}
+
+/* Sum of the 2*dims nearest-neighbour spins of (x,y,z), periodic. */
+static int neighbour_sum(const params_t *p, const int8_t *s, int x, int y,
+                         int z)
+{
+    int n = s[site_index(p, x - 1, y, z)] + s[site_index(p, x + 1, y, z)] +
+            s[site_index(p, x, y - 1, z)] + s[site_index(p, x, y + 1, z)];
+    if (p->dims == 3)
+        n += s[site_index(p, x, y, z - 1)] + s[site_index(p, x, y, z + 1)];
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial state (§III.A step 1: random lattice; §III.B step 1: each site up */
+/* with probability c).  init: 0 cold (+1 / top state), 1 random, 2          */
+/* equilibrium at concentration c (North-East, c-mode).                      */
+/* ------------------------------------------------------------------------ */
+int oracle_init(int dims, int L, int two_S, int model, double J, double h,
+                double T_or_c, uint64_t seed, int init, int8_t *s)
+{
+    params_t p;
+    if (setup(&p, dims, L, two_S, model, J, h, T_or_c, seed)) return -1;
+    if (init == 2 && !p.cmode) return -1;
+    for (int64_t i = 0; i < p.N; ++i) {
+        uint32_t u = draw_word(seed, (uint32_t)(i >> 2), 0, 2, (int)(i & 3));
+        int k;
+        if (init == 0) {
+            k = two_S;                                 /* all spins up */
+        } else if (init == 1) {
+            if (two_S == 1) k = (u < 0x80000000u) ? 1 : 0;
+            else k = (int)(((uint64_t)u * (uint64_t)(two_S + 1)) >> 32);
+        } else if (init == 2) {
+            uint32_t thr_c = (uint32_t)floor(ldexp(p.c, 32));
+            k = (u < thr_c) ? 1 : 0;
+        } else {
+            return -1;
+        }
+        s[i] = (int8_t)oracle_spin_of_state(two_S, k);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observables of one configuration, straight from their definitions:        */
+/*   bond = sum over sites i and directions d of s_i * s_{i+e_d}             */
+/*   mag  = sum_i s_i;  up = #{s_i > 0};  unflipped = #{flag_i == 0}         */
+/* E = -J*bond - h*mag (Eq. 2 with a field).                                 */
+/* ------------------------------------------------------------------------ */
+void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
+                    int64_t *bond, int64_t *mag, int64_t *up,
+                    int64_t *unflipped)
+{
+    params_t p;
+    memset(&p, 0, sizeof p);
+    p.dims = dims; p.L = L;
+    int Lz = (dims == 3) ? L : 1;
+    int64_t b = 0, m = 0, nu = 0, nf = 0;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int64_t i = site_index(&p, x, y, z);
+                int si = s[i];
+                b += si * s[site_index(&p, x + 1, y, z)];
+                b += si * s[site_index(&p, x, y + 1, z)];
+                if (dims == 3) b += si * s[site_index(&p, x, y, z + 1)];
+                m += si;
+                nu += (si > 0);
+                nf += (flag == NULL) ? 0 : (flag[i] == 0);
+            }
+    *bond = b; *mag = m; *up = nu; *unflipped = nf;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The sweep (§III.A algorithm steps 5-8, Fig. 2; §III.B facilitated rule,   */
+/* Eq. 3).  For each sweep t: all colour-0 sites, then all colour-1 sites;   */
+/* sites of one colour share no bond and no north/east neighbour, so the     */
+/* order inside a colour does not matter and a plain raster loop is used.    */
+/* After each sweep the four observables are recorded (NULL skips one).     */
+/* flag may be NULL for the Ising model.                                     */
+/* ------------------------------------------------------------------------ */
+int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
+                 double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
+                 int64_t sweep0, int64_t nsweeps, int64_t *bond,
+                 int64_t *mag, int64_t *up, int64_t *unflipped)
+{
+    params_t p;
+    if (setup(&p, dims, L, two_S, model, J, h, T_or_c, seed)) return -1;
+    if (model == 1 && flag == NULL) return -1;
+    const int sh = (two_S == 1) ? 2 : 1;               /* sites per draw: 4 or 2 */
+    const int64_t half = L / 2;
+    const int64_t G = (half + (1 << sh) - 1) >> sh;    /* groups per row */
+    const int Lz = (dims == 3) ? L : 1;
+
+    for (int64_t t = sweep0; t < sweep0 + nsweeps; ++t) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int z = 0; z < Lz; ++z)
+                for (int y = 0; y < L; ++y)
+                    for (int x = 0; x < L; ++x) {
+                        if (((x + y + z) & 1) != colour) continue;
+                        int64_t i = site_index(&p, x, y, z);
+                        int64_t r = (int64_t)y + (int64_t)L * z;
+                        int64_t j = x >> 1;
+                        uint32_t g = (uint32_t)(r * G + (j >> sh));
+
+                        int s_old = s[i];
+                        int k_old = oracle_state_of_spin(two_S, s_old);
+                        int k_new;
+                        uint32_t u_acc;
+                        if (two_S == 1) {
+                            k_new = 1 - k_old;                 /* spin flip */
+                            u_acc = draw_word(seed, g, t, (uint32_t)colour,
+                                              (int)(j & 3));
+                        } else {
+                            int w = 2 * (int)(j & 1);
+                            u_acc = draw_word(seed, g, t, (uint32_t)colour, w);
+                            uint32_t u_prop = draw_word(seed, g, t,
+                                                        (uint32_t)colour, w + 1);
+                            int step = 1 + (int)(((uint64_t)u_prop *
+                                                  (uint64_t)two_S) >> 32);
+                            k_new = (k_old + step) % (two_S + 1);
+                        }
+                        int s_new = oracle_spin_of_state(two_S, k_new);
+
+                        /* North-East constraint (§III.B): both the north
+                         * (x, y-1) and the east (x+1, y) neighbours up. */
+                        if (model == 1) {
+                            int north = s[site_index(&p, x, y - 1, z)];
+                            int east = s[site_index(&p, x + 1, y, z)];
+                            if (!(north == 1 && east == 1)) continue;
+                        }
+
+                        int accept;
+                        uint32_t thr;
+                        if (model == 1 && p.cmode) {
+                            double pr = (s_new > s_old) ? p.c / (1.0 - p.c)
+                                                        : (1.0 - p.c) / p.c;
+                            accept = oracle_probability_threshold(pr, &thr);
+                        } else {
+                            int n = neighbour_sum(&p, s, x, y, z);
+                            double dE = oracle_delta_energy(J, h, s_new - s_old, n);
+                            accept = oracle_metropolis_threshold(dE, p.T, &thr);
+                        }
+                        if (!accept) accept = (u_acc < thr);
+                        if (accept) {
+                            s[i] = (int8_t)s_new;
+                            if (flag != NULL && s_new != s_old) flag[i] = 1;
+                        }
+                    }
+        }
+        int64_t b, m, nu, nf;
+        oracle_measure(dims, L, s, flag, &b, &m, &nu, &nf);
+        int64_t k = t - sweep0;
+        if (bond) bond[k] = b;
+        if (mag) mag[k] = m;
+        if (up) up[k] = nu;
+        if (unflipped) unflipped[k] = nf;
+    }
+    return 0;
+}
+
+/* Number of distinct 32-bit words this oracle needs from Philox per call. */
+int oracle_sites_per_draw(int two_S) { return two_S == 1 ? 4 : 2; }
