@@ -1,0 +1,261 @@
+/*
+ * lattice.h -- C ABI of the GB300 checkerboard spin-lattice sweep library.
+ *
+ * Method: Levy, Cohen & Rabani, "Simulating lattice spin models on GPUs"
+ * (arXiv:1209.0296).
+ *   - §III.A, Eq. 2: 2D Ising model H = -J sum_<ij> s_i s_j, Metropolis
+ *     acceptance min[1, exp(-dH/T)], checkerboard (sublattice) parallel
+ *     sweep: one colour of sites is updated while the other is held fixed
+ *     (algorithm steps 5-8, Fig. 2); extended here with a field h, to 3D,
+ *     and to spin-S values (§III: "easily extended to any spin dimension
+ *     and value").
+ *   - §III.B, Eq. 3: the North-East kinetically constrained model: a site
+ *     may change only if its north (upper) and east (right) neighbours are
+ *     up; the initial state is up with probability c (the equilibrium
+ *     concentration).
+ *   - §IV: per-thread random numbers; replaced here by counter-based
+ *     Philox4x32-10 (Salmon et al., SC'11) so results do not depend on the
+ *     thread mapping: every result is bit-exact with a CPU restatement.
+ *
+ * Conventions shared by every entry point:
+ *   - H = -J sum_<ij> s_i s_j - h sum_i s_i for both models; each bond
+ *     (i, i+e_d) is counted once per direction d (so for L = 2 a pair is
+ *     counted twice, in H and in dE alike).  The paper's North-East
+ *     Hamiltonian with B = +1 corresponds to h = -1 here.
+ *   - Sites are stored x fastest: i = x + L*(y + L*z).  colour(i) =
+ *     (x+y+z) mod 2.  One sweep = all colour-0 sites, then all colour-1
+ *     sites.  Periodic boundaries in every direction; L must be even.
+ *   - Spin values (int8): two_S = 1 gives s = +-1; even two_S gives
+ *     s in {-S..S}; odd two_S > 1 gives s in {-two_S, -two_S+2, .., two_S}
+ *     (twice the half-integer value).
+ *   - Randomness: key = (seed lo, seed hi); counter = (g, sweep lo,
+ *     sweep hi, colour), g = row * G + (j >> sh), row = y + L*z,
+ *     j = x >> 1, G = ceil((L/2) / 2^sh); sh = 2 (4 sites per draw, word
+ *     j & 3 decides acceptance) for spin-1/2, sh = 1 (2 sites per draw,
+ *     word 2(j&1) decides acceptance, word 2(j&1)+1 picks the proposal) for
+ *     two_S > 1.  Initial states use counter (i >> 2, 0, 0, 2), word i & 3.
+ *   - Acceptance: dE <= 0 is accepted without a draw; otherwise the move is
+ *     accepted iff u < floor(exp(-dE/T) * 2^32), the threshold being
+ *     computed on the host in double precision.  North-East with
+ *     J = h = 0 reads T_or_c as the concentration c, with
+ *     p(down->up) = min(1, c/(1-c)) and p(up->down) = min(1, (1-c)/c).
+ *   - Spin-S proposal: k' = (k + 1 + floor(u*two_S / 2^32)) mod (two_S+1),
+ *     k the state index (0 = most negative spin).
+ *   - Return codes: 0 on success, a negative LAT_E* code on error;
+ *     lattice_strerror() names it.  Argument errors are reported before any
+ *     GPU work is queued.  Handles are owned by the library and are not
+ *     thread-safe; a server handle is.
+ *   - Host buffers passed in are owned by the caller; the library never
+ *     keeps a pointer to them after the call returns.
+ *   - All GPU work of a handle runs on the stream given at creation (NULL =
+ *     the legacy default stream).  Entry points that return host data
+ *     synchronise that stream.
+ */
+#ifndef LATTICE_H
+#define LATTICE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum lattice_status {
+    LAT_OK = 0,
+    LAT_EINVAL = -1,   /* invalid argument */
+    LAT_ENOMEM = -2,   /* device or host allocation failed */
+    LAT_ECUDA = -3,    /* a CUDA call failed (see lattice_last_cuda_error) */
+    LAT_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    LAT_EBUSY = -5,    /* result not ready yet (server poll) */
+    LAT_ENOTSUP = -6,  /* valid but unsupported combination */
+    LAT_ERANGE = -7,   /* index or size out of range */
+    LAT_ENOENT = -8    /* unknown id */
+};
+
+enum lattice_model { LAT_ISING = 0, LAT_NE = 1 };
+enum lattice_init {
+    LAT_INIT_COLD = 0,        /* every spin at its top value (+1 for spin-1/2) */
+    LAT_INIT_RANDOM = 1,      /* uniform over the 2S+1 values */
+    LAT_INIT_EQUILIBRIUM = 2  /* North-East, c-mode: up with probability c (§III.B) */
+};
+enum lattice_layout {
+    LAT_INT8 = 0,      /* one int8 spin per site */
+    LAT_BITPACKED = 1  /* spin-1/2, 2D only: one bit per site, colour-separated planes */
+};
+/* Kernel selection for lattice_set_kernel (tests and the autotuner). */
+enum lattice_kernel {
+    LAT_KERNEL_AUTO = 0,    /* library choice (tuned tile shape when eligible) */
+    LAT_KERNEL_GENERIC = 1, /* two launches per sweep, one per colour; any model */
+    LAT_KERNEL_TILED = 2    /* one launch per sweep, shared-memory tiles with halo
+                               recompute; 2D spin-1/2 (Ising and North-East), L % 16 == 0 */
+};
+
+typedef struct lattice lattice_t;
+typedef struct lattice_batch lattice_batch_t;
+typedef struct lattice_server lattice_server_t;
+
+/* ------------------------------------------------------------------ */
+/* Single lattice                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Create a lattice on the current CUDA device and write its initial state
+ * on the device (§III.A step 1, §III.B step 1 -- done on the GPU here).
+ *   dims     2 or 3
+ *   L        even, >= 2, L^dims < 2^32
+ *   two_S    1..8 (2 * spin); North-East and the bit-packed layout need 1
+ *   model    LAT_ISING or LAT_NE (North-East needs dims = 2)
+ *   J, h     coupling and field of H above
+ *   T_or_c   temperature (> 0) in energy units, or, for LAT_NE with
+ *            J = h = 0, the concentration c in (0, 1)
+ *   seed     64-bit Philox key
+ *   init     enum lattice_init (EQUILIBRIUM needs LAT_NE with J = h = 0)
+ *   layout   enum lattice_layout
+ *   cuda_stream  a cudaStream_t, or NULL for the default stream
+ * On success *out owns the device memory (spins, persistence bitmap,
+ * threshold table, per-sweep counters) until lattice_destroy. */
+int lattice_create(lattice_t **out, int dims, int L, int two_S, int model,
+                   double J, double h, double T_or_c, uint64_t seed,
+                   int init, int layout, void *cuda_stream);
+
+/* Queue n >= 0 checkerboard sweeps (§III.A steps 5-8; §III.B rule) on the
+ * handle's stream; returns without waiting.  After each sweep t the four
+ * exact int64 counters of lattice_series are recorded on the device. */
+int lattice_sweep(lattice_t *lat, int64_t n);
+
+/* Per-site observables of the current configuration (waits for the
+ * stream): E/N = (-J*bond - h*mag)/N, M/N, up density, and persistence =
+ * fraction of sites that never changed since creation or the last
+ * lattice_set_state (North-East only; NaN for Ising).  NULL outputs are
+ * skipped.  For North-East in c-mode E uses J = 0, h = -1. */
+int lattice_observables(lattice_t *lat, double *E, double *M, double *density,
+                        double *persistence);
+
+/* Copy the exact per-sweep counters of sweeps [first, first+count) (0-based
+ * global sweep index, counted since creation or the last set_state) to the
+ * caller's host arrays (NULL arrays are skipped):
+ *   bond[k]      sum over sites and directions of s_i * s_{i+e_d}
+ *   mag[k]       sum of s_i
+ *   up[k]        number of sites with s_i > 0
+ *   unflipped[k] number of sites never changed (North-East; 0 for Ising)
+ * LAT_ERANGE if the range is not recorded. */
+int lattice_series(lattice_t *lat, int64_t first, int64_t count, int64_t *bond,
+                   int64_t *mag, int64_t *up, int64_t *unflipped);
+
+/* Copy the N = L^dims spins (int8, x fastest, spin values) to host_out,
+ * whatever the layout (waits for the stream). */
+int lattice_get_spins(lattice_t *lat, int8_t *host_out);
+
+/* Replace the spins from a caller host array of N int8 spin values (each
+ * must be an allowed value; LAT_EINVAL otherwise).  The persistence flags
+ * and the sweep counter are left unchanged. */
+int lattice_set_spins(lattice_t *lat, const int8_t *host_in);
+
+/* Checkpoint: spins (N int8), persistence flags (N uint8, 0/1; may be NULL)
+ * and the number of sweeps done.  lattice_set_state restores them; the
+ * counter-based random numbers make a resumed run bit-exact with an
+ * uninterrupted one.  set_state clears the recorded series. */
+int lattice_get_state(lattice_t *lat, int8_t *spins, uint8_t *flags, int64_t *sweeps);
+int lattice_set_state(lattice_t *lat, const int8_t *spins, const uint8_t *flags,
+                      int64_t sweeps);
+
+/* Number of sweeps done, N, and device bytes held by the handle. */
+int lattice_info(lattice_t *lat, int64_t *sweeps, int64_t *n_sites, int64_t *device_bytes);
+
+/* Device address and size of the spin storage (for zero-copy device use;
+ * the layout is the one given at creation: N int8 spins, or for the
+ * bit-packed layout 2 colour planes of L rows x ceil(L/64) uint32 pairs). */
+int lattice_device_spins(lattice_t *lat, void **dev_ptr, size_t *bytes);
+
+/* Pick the kernel (enum lattice_kernel), the tile shape (tile_w columns x
+ * tile_h rows; 0 = default) and the sweeps per CUDA-graph replay
+ * (0 = default).  LAT_ENOTSUP if the kernel does not cover the lattice. */
+int lattice_set_kernel(lattice_t *lat, int kernel, int tile_w, int tile_h,
+                       int sweeps_per_graph);
+
+/* The acceptance table the library builds on the host (no GPU needed) for
+ * the given model parameters (same meaning and checks as lattice_create):
+ * for ds = s' - s in [-dsmax, dsmax] and neighbour sum n in [-nmax, nmax],
+ * entry (ds + dsmax) * (2 nmax + 1) + (n + nmax) holds always (1 = accept
+ * without a draw) and thr (accept iff u < thr).  Writes at most cap
+ * entries (thr / always may be NULL); *count, *dsmax, *nmax receive the
+ * table size and ranges. */
+int lattice_threshold_table(int dims, int two_S, int model, double J, double h, double T_or_c,
+                            uint32_t *thr, uint8_t *always, int cap, int *count, int *dsmax,
+                            int *nmax);
+
+/* Wait for all queued work of the handle. */
+int lattice_synchronize(lattice_t *lat);
+
+void lattice_destroy(lattice_t *lat);
+
+/* ------------------------------------------------------------------ */
+/* Batch: many lattices (any sizes and models) advanced by one          */
+/* persistent-kernel launch per sweep step, replayed from a CUDA graph. */
+/* Results are bit-exact with running each lattice alone.               */
+/* ------------------------------------------------------------------ */
+
+/* A batch runs on its own stream (NULL = default stream); lattices added
+ * to it must not have other work in flight. */
+int lattice_batch_create(lattice_batch_t **out, void *cuda_stream);
+/* Schedule n more sweeps of lat in the next lattice_batch_run. */
+int lattice_batch_add(lattice_batch_t *b, lattice_t *lat, int64_t n);
+/* Run every scheduled sweep; returns after queueing (lattice_synchronize
+ * or lattice_batch_synchronize waits).  Lattices with fewer remaining
+ * sweeps drop out of later launches. */
+int lattice_batch_run(lattice_batch_t *b);
+int lattice_batch_synchronize(lattice_batch_t *b);
+void lattice_batch_destroy(lattice_batch_t *b);
+
+/* ------------------------------------------------------------------ */
+/* Server: continuous batching of independent simulation requests.     */
+/* ------------------------------------------------------------------ */
+typedef struct lattice_request {
+    int dims, L, two_S, model;
+    double J, h, T_or_c;
+    uint64_t seed;
+    int init;
+    int64_t sweeps;
+} lattice_request_t;
+
+typedef struct lattice_result {
+    int status;             /* LAT_OK, or the error that ended the request */
+    int64_t sweeps_done;
+    int64_t bond, mag, up, unflipped;  /* counters after the last sweep */
+    double E, M, density, persistence; /* per site, as lattice_observables */
+    double t_submit, t_admit, t_done;  /* seconds on the server's clock */
+} lattice_result_t;
+
+/* A server owns one CUDA stream and one scheduler thread.  Requests are
+ * admitted while their device footprint fits in hbm_budget_bytes and
+ * fewer than max_slots are resident; each scheduling round advances every
+ * resident lattice by up to chunk_sweeps sweeps in one batched launch
+ * sequence, retiring finished lattices and admitting waiting ones. */
+int lattice_server_create(lattice_server_t **out, size_t hbm_budget_bytes, int max_slots,
+                          int chunk_sweeps);
+/* Non-blocking; *id identifies the request. LAT_EINVAL for a bad request,
+ * LAT_ENOMEM if it can never fit the budget. */
+int lattice_server_submit(lattice_server_t *s, const lattice_request_t *req, uint64_t *id);
+/* LAT_EBUSY until done; then fills *res and, if spins_out is not NULL,
+ * copies the final N spins there.  A finished result can be polled once
+ * more after which it is released (LAT_ENOENT). */
+int lattice_server_poll(lattice_server_t *s, uint64_t id, lattice_result_t *res,
+                        int8_t *spins_out);
+/* Block until every submitted request is finished (or timeout_s seconds,
+ * LAT_ETIMEOUT; timeout_s <= 0 waits without limit). */
+int lattice_server_drain(lattice_server_t *s, double timeout_s);
+/* Seconds on the server's clock (same clock as lattice_result times). */
+double lattice_server_clock(lattice_server_t *s);
+void lattice_server_destroy(lattice_server_t *s);
+
+/* ------------------------------------------------------------------ */
+const char *lattice_strerror(int code);
+/* The last CUDA error string seen by the calling thread (or ""). */
+const char *lattice_last_cuda_error(void);
+/* Library version string. */
+const char *lattice_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LATTICE_H */

@@ -1,0 +1,664 @@
+// capi.cu -- the C ABI of include/lattice.h for single lattices: argument
+// checks, device memory, the host-built acceptance table, the sweep loop
+// (direct launches or CUDA-graph replays), counters, checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lattice_capi_internal.h"
+
+namespace lat {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    g_last_cuda_error = buf;
+    return LAT_ECUDA;
+}
+
+// Test hook: make the n-th next device allocation fail (0 = off).
+static std::atomic<int> g_fail_alloc_countdown{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    int c = g_fail_alloc_countdown.load();
+    if (c > 0) {
+        if (g_fail_alloc_countdown.fetch_sub(1) == 1) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+void dev_free(void *p, cudaStream_t st)
+{
+    if (p != nullptr) cudaFreeAsync(p, st);
+}
+
+// ---------------------------------------------------------------------------
+// Acceptance table (§III.A: P_acc = min[1, exp(-dH/T)]; §III.B: rates at
+// concentration c).  Built on the host in double precision:
+//   dE = -(J * (ds*n)) - h * ds
+//   dE <= 0           -> always
+//   otherwise         -> thr = floor(exp(-dE/T) * 2^32)
+// North-East c-mode: p = c/(1-c) for ds > 0 (down->up), (1-c)/c for ds < 0;
+// p >= 1 -> always, else thr = floor(p * 2^32).
+// ---------------------------------------------------------------------------
+void build_table(const Params &P, std::vector<TabEntry> &tab, int &dsmax, int &nmax, int &nn)
+{
+    const int smax = max_spin(P.two_S);
+    dsmax = 2 * smax;
+    nmax = 2 * P.dims * smax;
+    nn = 2 * nmax + 1;
+    const int nds = 2 * dsmax + 1;
+    tab.assign((size_t)nds * nn, TabEntry{0u, 0u});
+    for (int ds = -dsmax; ds <= dsmax; ++ds) {
+        for (int n = -nmax; n <= nmax; ++n) {
+            TabEntry e{0u, 0u};
+            double p;
+            bool always;
+            if (P.cmode) {
+                p = ds > 0 ? P.c / (1.0 - P.c) : (1.0 - P.c) / P.c;
+                always = (p >= 1.0);
+            } else {
+                const double dE = -(P.J * (double)(ds * n)) - P.h * (double)ds;
+                always = (dE <= 0.0);
+                p = always ? 1.0 : std::exp(-dE / P.T);
+            }
+            if (always) {
+                e.always = 1u;
+            } else {
+                e.thr = (uint32_t)std::floor(std::ldexp(p, 32));
+            }
+            tab[(size_t)(ds + dsmax) * nn + (n + nmax)] = e;
+        }
+    }
+}
+
+int validate(int dims, int L, int two_S, int model, double J, double h, double T_or_c,
+             int init, int layout, Params &P)
+{
+    if (dims != 2 && dims != 3) return LAT_EINVAL;
+    if (L < 2 || (L & 1)) return LAT_EINVAL;
+    if (two_S < 1 || two_S > 8) return LAT_EINVAL;
+    if (model != LAT_ISING && model != LAT_NE) return LAT_EINVAL;
+    if (model == LAT_NE && (dims != 2 || two_S != 1)) return LAT_EINVAL;
+    if (!std::isfinite(J) || !std::isfinite(h) || !std::isfinite(T_or_c)) return LAT_EINVAL;
+    const double N = std::pow((double)L, (double)dims);
+    if (N >= 4294967296.0) return LAT_EINVAL;
+    const bool cmode = (model == LAT_NE && J == 0.0 && h == 0.0);
+    if (cmode) {
+        if (!(T_or_c > 0.0 && T_or_c < 1.0)) return LAT_EINVAL;
+    } else if (!(T_or_c > 0.0)) {
+        return LAT_EINVAL;
+    }
+    if (init != LAT_INIT_COLD && init != LAT_INIT_RANDOM && init != LAT_INIT_EQUILIBRIUM)
+        return LAT_EINVAL;
+    if (init == LAT_INIT_EQUILIBRIUM && !cmode) return LAT_EINVAL;
+    if (layout != LAT_INT8 && layout != LAT_BITPACKED) return LAT_EINVAL;
+    if (layout == LAT_BITPACKED && (dims != 2 || two_S != 1)) return LAT_ENOTSUP;
+    P.dims = dims;
+    P.L = L;
+    P.two_S = two_S;
+    P.model = model;
+    P.J = J;
+    P.h = h;
+    P.cmode = cmode ? 1 : 0;
+    P.T = cmode ? 0.0 : T_or_c;
+    P.c = cmode ? T_or_c : 0.0;
+    P.init = init;
+    P.layout = layout;
+    P.N = (uint64_t)N;
+    return LAT_OK;
+}
+
+size_t footprint_bytes(const Params &P)
+{
+    size_t b = (size_t)P.N;                                 // int8 spins
+    if (P.model == LAT_NE) b += ((P.N + 31) / 32) * 4;      // persistence bitmap
+    if (P.layout == LAT_BITPACKED) b += (size_t)2 * P.L * (((size_t)P.L / 2 + 31) / 32) * 4;
+    const int smax = max_spin(P.two_S);
+    b += (size_t)(4 * smax + 1) * (4 * P.dims * smax + 1) * sizeof(TabEntry);
+    b += sizeof(Ctrl) + 4096;                               // control + first series block
+    return b;
+}
+
+// Make the per-sweep counter buffer hold global sweeps [series_first, need).
+static int ensure_series(lattice *lt, unsigned long long need)
+{
+    const unsigned long long base = (unsigned long long)lt->series_first;
+    const unsigned long long slots = need > base ? need - base : 0;
+    if (slots <= lt->series_cap && lt->series != nullptr) return LAT_OK;
+    unsigned long long cap = lt->series_cap ? lt->series_cap : 64;
+    while (cap < slots) cap *= 2;
+    const size_t bytes = (size_t)cap * 4 * sizeof(unsigned long long);
+    void *p = nullptr;
+    cudaError_t e = dev_alloc(&p, bytes, lt->stream);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "series alloc");
+    e = cudaMemsetAsync(p, 0, bytes, lt->stream);
+    if (e == cudaSuccess && lt->series != nullptr)
+        e = cudaMemcpyAsync(p, lt->series, (size_t)lt->series_cap * 4 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, lt->stream);
+    if (e == cudaSuccess)
+        e = launch_set_ctrl(lt->ctrl, (unsigned long long)lt->sweeps, (unsigned long long *)p, base,
+                            cap, lt->stream);
+    if (e != cudaSuccess) {
+        dev_free(p, lt->stream);
+        return cuda_fail(e, "series grow");
+    }
+    dev_free(lt->series, lt->stream);
+    lt->series = (unsigned long long *)p;
+    lt->series_cap = cap;
+    return LAT_OK;
+}
+
+// Compact 16-entry table for spin-1/2 in 2D: index (sd << 3) | nd with sd = 1
+// for a down spin (s = -1) and nd the number of down neighbours; then
+// ds = s' - s = +2 (down->up) or -2, and n = 4 - 2*nd.
+void compact_table(Geom &g, const TabEntry *host_tab)
+{
+    g.always16 = 0;
+    for (int k = 0; k < 16; ++k) g.thr16[k] = 0;
+    if (g.dims != 2 || g.two_S != 1) return;
+    for (int k = 0; k < 16; ++k) {
+        const int sd = k >> 3, nd = k & 7;
+        if (nd > 4) continue;
+        const int ds = sd ? 2 : -2;
+        const int n = 4 - 2 * nd;
+        const TabEntry e = host_tab[(ds + g.dsmax) * g.nn + (n + g.nmax)];
+        g.thr16[k] = e.thr;
+        if (e.always) g.always16 |= 1u << k;
+    }
+}
+
+int choose_kernel(const lattice *lt)
+{
+    if (lt->P.layout == LAT_BITPACKED) return LAT_KERNEL_AUTO;  // bit-packed path
+    if (lt->kernel == LAT_KERNEL_GENERIC) return LAT_KERNEL_GENERIC;
+    if (tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
+    return LAT_KERNEL_GENERIC;
+}
+
+// Queue k sweeps with sweep offsets 0..k-1 relative to ctrl->sweep, then
+// advance ctrl->sweep by k.  Used directly and under stream capture.
+int enqueue_sweeps(lattice *lt, int k, cudaStream_t st)
+{
+    const int kern = choose_kernel(lt);
+    for (int off = 0; off < k; ++off) {
+        cudaError_t e;
+        if (lt->P.layout == LAT_BITPACKED) {
+            e = launch_sweep_bitpacked(lt->geom, off, st);
+        } else if (kern == LAT_KERNEL_TILED) {
+            e = launch_sweep_tiled(lt->geom, lt->tile_w, lt->tile_h, off, st);
+        } else {
+            e = launch_half_sweep_generic(lt->geom, 0, off, st);
+            if (e == cudaSuccess) e = launch_half_sweep_generic(lt->geom, 1, off, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    }
+    cudaError_t e = launch_advance(lt->ctrl, (unsigned long long)k, st);
+    if (e != cudaSuccess) return cuda_fail(e, "advance launch");
+    return LAT_OK;
+}
+
+static int ensure_graph(lattice *lt)
+{
+    if (lt->graph_valid) return LAT_OK;
+    if (lt->graph_exec != nullptr) {
+        cudaGraphExecDestroy(lt->graph_exec);
+        lt->graph_exec = nullptr;
+    }
+    if (lt->cap_stream == nullptr) {
+        cudaError_t e = cudaStreamCreateWithFlags(&lt->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(lt->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    int rc = enqueue_sweeps(lt, lt->graph_sweeps, lt->cap_stream);
+    e = cudaStreamEndCapture(lt->cap_stream, &graph);
+    if (rc != LAT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&lt->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    lt->graph_valid = true;
+    return LAT_OK;
+}
+
+int sweep_impl(lattice *lt, int64_t n)
+{
+    if (n < 0) return LAT_EINVAL;
+    if (n == 0) return LAT_OK;
+    int rc = ensure_series(lt, (unsigned long long)(lt->sweeps + n));
+    if (rc != LAT_OK) return rc;
+    int64_t left = n;
+    const int gk = lt->graph_sweeps;
+    if (gk > 0 && left >= gk) {
+        rc = ensure_graph(lt);
+        if (rc != LAT_OK) return rc;
+        while (left >= gk) {
+            cudaError_t e = cudaGraphLaunch(lt->graph_exec, lt->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+            left -= gk;
+        }
+    }
+    if (left > 0) {
+        rc = enqueue_sweeps(lt, (int)left, lt->stream);
+        if (rc != LAT_OK) return rc;
+    }
+    lt->sweeps += n;
+    return LAT_OK;
+}
+
+static void release(lattice *lt)
+{
+    if (lt == nullptr) return;
+    if (lt->graph_exec) cudaGraphExecDestroy(lt->graph_exec);
+    if (lt->cap_stream) cudaStreamDestroy(lt->cap_stream);
+    cudaStream_t st = lt->stream;
+    dev_free(lt->spins[0], st);
+    dev_free(lt->spins[1], st);
+    dev_free(lt->bits[0], st);
+    dev_free(lt->bits[1], st);
+    dev_free(lt->flags, st);
+    dev_free(lt->tab, st);
+    dev_free(lt->ctrl, st);
+    dev_free(lt->series, st);
+    dev_free(lt->scratch4, st);
+    delete lt;
+}
+
+int create_impl(lattice_t **out, int dims, int L, int two_S, int model, double J, double h,
+                double T_or_c, uint64_t seed, int init, int layout, void *cuda_stream)
+{
+    if (out == nullptr) return LAT_EINVAL;
+    *out = nullptr;
+    Params P{};
+    int rc = validate(dims, L, two_S, model, J, h, T_or_c, init, layout, P);
+    if (rc != LAT_OK) return rc;
+    P.seed = seed;
+    lattice *lt = new (std::nothrow) lattice();
+    if (lt == nullptr) return LAT_ENOMEM;
+    lt->P = P;
+    lt->stream = (cudaStream_t)cuda_stream;
+    cudaStream_t st = lt->stream;
+
+    std::vector<TabEntry> tab;
+    int dsmax, nmax, nn;
+    build_table(P, tab, dsmax, nmax, nn);
+    lt->host_tab = tab;
+
+    Geom &g = lt->geom;
+    g.dims = dims;
+    g.L = L;
+    g.two_S = two_S;
+    g.model = model;
+    g.cmode = P.cmode;
+    g.sh = (two_S == 1) ? 2 : 1;
+    g.G = (uint32_t)(((uint32_t)(L / 2) + (1u << g.sh) - 1) >> g.sh);
+    g.rows = (uint32_t)(dims == 3 ? (uint64_t)L * L : (uint64_t)L);
+    g.N = P.N;
+    g.key0 = (uint32_t)(seed & 0xffffffffu);
+    g.key1 = (uint32_t)(seed >> 32);
+    g.dsmax = dsmax;
+    g.nmax = nmax;
+    g.nn = nn;
+    g.tab_n = (int)tab.size();
+    g.bw = (uint32_t)(((uint32_t)(L / 2) + 31) / 32);
+
+    cudaError_t e = dev_alloc((void **)&lt->spins[0], (size_t)P.N, st);
+    if (e == cudaSuccess && layout == LAT_INT8) e = dev_alloc((void **)&lt->spins[1], (size_t)P.N, st);
+    if (e == cudaSuccess && model == LAT_NE)
+        e = dev_alloc((void **)&lt->flags, ((P.N + 31) / 32) * 4, st);
+    if (e == cudaSuccess && layout == LAT_BITPACKED) {
+        e = dev_alloc((void **)&lt->bits[0], (size_t)2 * L * g.bw * 4, st);
+        if (e == cudaSuccess) e = dev_alloc((void **)&lt->bits[1], (size_t)2 * L * g.bw * 4, st);
+    }
+    if (e == cudaSuccess) e = dev_alloc((void **)&lt->tab, tab.size() * sizeof(TabEntry), st);
+    if (e == cudaSuccess) e = dev_alloc((void **)&lt->ctrl, sizeof(Ctrl), st);
+    if (e == cudaSuccess) e = dev_alloc((void **)&lt->scratch4, 4 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+        rc = (e == cudaErrorMemoryAllocation) ? LAT_ENOMEM : cuda_fail(e, "alloc");
+        release(lt);
+        return rc;
+    }
+    g.s[0] = lt->spins[0];
+    g.s[1] = lt->spins[1];
+    g.bits[0] = lt->bits[0];
+    g.bits[1] = lt->bits[1];
+    g.flags = lt->flags;
+    compact_table(g, tab.data());
+    g.tab = lt->tab;
+    g.ctrl = lt->ctrl;
+
+    e = cudaMemcpyAsync(lt->tab, tab.data(), tab.size() * sizeof(TabEntry), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lt->ctrl, 0, sizeof(Ctrl), st);
+    if (e == cudaSuccess && lt->flags) e = cudaMemsetAsync(lt->flags, 0, ((P.N + 31) / 32) * 4, st);
+    if (e == cudaSuccess) e = launch_init(g, init, P.c, st);
+    if (e == cudaSuccess && layout == LAT_BITPACKED) e = launch_pack_bits(g, lt->spins[0], lt->bits[0], st);
+    // The host table must outlive the async copy: wait once at creation.
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "create");
+        release(lt);
+        return rc;
+    }
+    lt->kernel = LAT_KERNEL_AUTO;
+    lt->tile_w = 0;
+    lt->tile_h = 0;
+    lt->graph_sweeps = default_graph_sweeps(P);
+    rc = ensure_series(lt, 64);
+    if (rc != LAT_OK) {
+        release(lt);
+        return rc;
+    }
+    *out = lt;
+    return LAT_OK;
+}
+
+}  // namespace lat
+
+using namespace lat;
+
+extern "C" {
+
+int lattice_create(lattice_t **out, int dims, int L, int two_S, int model, double J, double h,
+                   double T_or_c, uint64_t seed, int init, int layout, void *cuda_stream)
+{
+    return create_impl(out, dims, L, two_S, model, J, h, T_or_c, seed, init, layout, cuda_stream);
+}
+
+int lattice_sweep(lattice_t *lt, int64_t n)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    return sweep_impl(lt, n);
+}
+
+// The int8 spins of the current state (for the bit-packed layout, unpacked
+// into the int8 staging buffer first).
+static int current_int8(lattice *lt, int8_t **out)
+{
+    const int par = (int)(lt->sweeps & 1);
+    if (lt->P.layout == LAT_BITPACKED) {
+        cudaError_t e = launch_unpack_bits(lt->geom, lt->bits[par], lt->spins[0], lt->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "unpack");
+        *out = lt->spins[0];
+    } else {
+        *out = lt->spins[par];
+    }
+    return LAT_OK;
+}
+
+static int current_counters(lattice *lt, long long c[4])
+{
+    cudaError_t e;
+    if (lt->sweeps > lt->series_first) {
+        e = cudaMemcpyAsync(c, lt->series + 4ull * (unsigned long long)(lt->sweeps - 1 - lt->series_first),
+                            4 * sizeof(long long), cudaMemcpyDeviceToHost, lt->stream);
+    } else {
+        int8_t *cur = nullptr;
+        int rc = current_int8(lt, &cur);
+        if (rc != LAT_OK) return rc;
+        e = cudaMemsetAsync(lt->scratch4, 0, 4 * sizeof(long long), lt->stream);
+        if (e == cudaSuccess) e = launch_measure(lt->geom, cur, lt->scratch4, lt->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c, lt->scratch4, 4 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                lt->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "counters");
+    return LAT_OK;
+}
+
+int lattice_observables(lattice_t *lt, double *E, double *M, double *density, double *persistence)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    long long c[4];
+    int rc = current_counters(lt, c);
+    if (rc != LAT_OK) return rc;
+    const double N = (double)lt->P.N;
+    double J = lt->P.J, h = lt->P.h;
+    if (lt->P.cmode) {
+        J = 0.0;
+        h = -1.0;
+    }
+    if (E) *E = (-J * (double)c[0] - h * (double)c[1]) / N;
+    if (M) *M = (double)c[1] / N;
+    if (density) *density = (double)c[2] / N;
+    if (persistence) *persistence = (lt->P.model == LAT_NE) ? (double)c[3] / N : NAN;
+    return LAT_OK;
+}
+
+int lattice_series(lattice_t *lt, int64_t first, int64_t count, int64_t *bond, int64_t *mag,
+                   int64_t *up, int64_t *unflipped)
+{
+    if (lt == nullptr || first < 0 || count < 0) return LAT_EINVAL;
+    if (first < lt->series_first || first + count > lt->sweeps) return LAT_ERANGE;
+    if (count == 0) return LAT_OK;
+    std::vector<long long> buf((size_t)count * 4);
+    cudaError_t e = cudaMemcpyAsync(buf.data(),
+                                    lt->series + 4ull * (unsigned long long)(first - lt->series_first),
+                                    (size_t)count * 4 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                    lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "series copy");
+    for (int64_t k = 0; k < count; ++k) {
+        if (bond) bond[k] = buf[4 * k + 0];
+        if (mag) mag[k] = buf[4 * k + 1];
+        if (up) up[k] = buf[4 * k + 2];
+        if (unflipped) unflipped[k] = buf[4 * k + 3];
+    }
+    return LAT_OK;
+}
+
+int lattice_get_spins(lattice_t *lt, int8_t *host_out)
+{
+    if (lt == nullptr || host_out == nullptr) return LAT_EINVAL;
+    int8_t *cur = nullptr;
+    int rc = current_int8(lt, &cur);
+    if (rc != LAT_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(host_out, cur, (size_t)lt->P.N, cudaMemcpyDeviceToHost, lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get spins");
+    return LAT_OK;
+}
+
+static bool spins_allowed(const Params &P, const int8_t *s)
+{
+    const int smax = max_spin(P.two_S);
+    for (uint64_t i = 0; i < P.N; ++i) {
+        const int v = s[i];
+        if (v < -smax || v > smax) return false;
+        if ((P.two_S & 1) && ((v + P.two_S) & 1)) return false;
+    }
+    return true;
+}
+
+// Copy host spins into the current-state buffer (packing for bit-packed).
+static cudaError_t put_spins(lattice *lt, const int8_t *host_in)
+{
+    const int par = (int)(lt->sweeps & 1);
+    if (lt->P.layout == LAT_BITPACKED) {
+        cudaError_t e = cudaMemcpyAsync(lt->spins[0], host_in, (size_t)lt->P.N, cudaMemcpyHostToDevice,
+                                        lt->stream);
+        if (e == cudaSuccess) e = launch_pack_bits(lt->geom, lt->spins[0], lt->bits[par], lt->stream);
+        return e;
+    }
+    return cudaMemcpyAsync(lt->spins[par], host_in, (size_t)lt->P.N, cudaMemcpyHostToDevice, lt->stream);
+}
+
+int lattice_set_spins(lattice_t *lt, const int8_t *host_in)
+{
+    if (lt == nullptr || host_in == nullptr) return LAT_EINVAL;
+    if (!spins_allowed(lt->P, host_in)) return LAT_EINVAL;
+    cudaError_t e = put_spins(lt, host_in);
+    // The caller's buffer may be reused as soon as we return.
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set spins");
+    return LAT_OK;
+}
+
+int lattice_get_state(lattice_t *lt, int8_t *spins, uint8_t *flags, int64_t *sweeps)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    if (spins) {
+        int rc = lattice_get_spins(lt, spins);
+        if (rc != LAT_OK) return rc;
+    }
+    if (flags) {
+        const uint64_t N = lt->P.N;
+        std::vector<uint32_t> bm((N + 31) / 32, 0u);
+        if (lt->flags) {
+            cudaError_t e = cudaMemcpyAsync(bm.data(), lt->flags, bm.size() * 4, cudaMemcpyDeviceToHost,
+                                            lt->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "get flags");
+        }
+        for (uint64_t i = 0; i < N; ++i) flags[i] = (uint8_t)((bm[i >> 5] >> (i & 31)) & 1u);
+    }
+    if (sweeps) *sweeps = lt->sweeps;
+    return LAT_OK;
+}
+
+int lattice_set_state(lattice_t *lt, const int8_t *spins, const uint8_t *flags, int64_t sweeps)
+{
+    if (lt == nullptr || spins == nullptr || sweeps < 0) return LAT_EINVAL;
+    if (!spins_allowed(lt->P, spins)) return LAT_EINVAL;
+    const uint64_t N = lt->P.N;
+    std::vector<uint32_t> bm((N + 31) / 32, 0u);
+    if (flags)
+        for (uint64_t i = 0; i < N; ++i)
+            if (flags[i]) bm[i >> 5] |= 1u << (i & 31);
+    cudaError_t e = cudaStreamSynchronize(lt->stream);
+    const int64_t old_sweeps = lt->sweeps;
+    lt->sweeps = sweeps;  // selects the buffer parity put_spins writes
+    if (e == cudaSuccess) e = put_spins(lt, spins);
+    if (e == cudaSuccess && lt->flags)
+        e = cudaMemcpyAsync(lt->flags, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) lt->sweeps = old_sweeps;
+    if (e != cudaSuccess) return cuda_fail(e, "set state");
+    // The recorded series restarts at the restored sweep index.
+    dev_free(lt->series, lt->stream);
+    lt->series = nullptr;
+    lt->series_cap = 0;
+    lt->sweeps = sweeps;
+    lt->series_first = sweeps;
+    return ensure_series(lt, (unsigned long long)sweeps + 64);
+}
+
+int lattice_info(lattice_t *lt, int64_t *sweeps, int64_t *n_sites, int64_t *device_bytes)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    if (sweeps) *sweeps = lt->sweeps;
+    if (n_sites) *n_sites = (int64_t)lt->P.N;
+    if (device_bytes)
+        *device_bytes = (int64_t)(footprint_bytes(lt->P) +
+                                  (size_t)lt->series_cap * 4 * sizeof(long long));
+    return LAT_OK;
+}
+
+int lattice_device_spins(lattice_t *lt, void **dev_ptr, size_t *bytes)
+{
+    if (lt == nullptr || dev_ptr == nullptr) return LAT_EINVAL;
+    const int par = (int)(lt->sweeps & 1);
+    if (lt->P.layout == LAT_BITPACKED) {
+        *dev_ptr = lt->bits[par];
+        if (bytes) *bytes = (size_t)2 * lt->P.L * lt->geom.bw * 4;
+    } else {
+        *dev_ptr = lt->spins[par];
+        if (bytes) *bytes = (size_t)lt->P.N;
+    }
+    return LAT_OK;
+}
+
+int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sweeps_per_graph)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_TILED) return LAT_EINVAL;
+    if (tile_w < 0 || tile_h < 0 || sweeps_per_graph < 0) return LAT_EINVAL;
+    if (kernel == LAT_KERNEL_TILED && !tiled_supported(lt->geom)) return LAT_ENOTSUP;
+    if (!tile_shape_ok(tile_w, tile_h)) return LAT_EINVAL;
+    lt->kernel = kernel;
+    lt->tile_w = tile_w;
+    lt->tile_h = tile_h;
+    lt->graph_sweeps = sweeps_per_graph ? sweeps_per_graph : default_graph_sweeps(lt->P);
+    lt->graph_valid = false;
+    return LAT_OK;
+}
+
+int lattice_threshold_table(int dims, int two_S, int model, double J, double h, double T_or_c,
+                            uint32_t *thr, uint8_t *always, int cap, int *count, int *dsmax,
+                            int *nmax)
+{
+    Params P{};
+    const int init = (model == LAT_NE && J == 0.0 && h == 0.0) ? LAT_INIT_EQUILIBRIUM : LAT_INIT_COLD;
+    int rc = validate(dims, 2, two_S, model, J, h, T_or_c, init, LAT_INT8, P);
+    if (rc != LAT_OK) return rc;
+    std::vector<TabEntry> tab;
+    int dm, nm, nn;
+    build_table(P, tab, dm, nm, nn);
+    const int n = (int)tab.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (thr) thr[i] = tab[i].thr;
+        if (always) always[i] = (uint8_t)tab[i].always;
+    }
+    if (count) *count = n;
+    if (dsmax) *dsmax = dm;
+    if (nmax) *nmax = nm;
+    return LAT_OK;
+}
+
+int lattice_synchronize(lattice_t *lt)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    return LAT_OK;
+}
+
+void lattice_destroy(lattice_t *lt) { release(lt); }
+
+const char *lattice_strerror(int code)
+{
+    switch (code) {
+    case LAT_OK: return "success";
+    case LAT_EINVAL: return "invalid argument";
+    case LAT_ENOMEM: return "out of memory";
+    case LAT_ECUDA: return "CUDA error";
+    case LAT_ETIMEOUT: return "device-side wait timed out";
+    case LAT_EBUSY: return "not ready";
+    case LAT_ENOTSUP: return "not supported";
+    case LAT_ERANGE: return "out of range";
+    case LAT_ENOENT: return "no such id";
+    default: return "unknown error";
+    }
+}
+
+const char *lattice_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+const char *lattice_version(void) { return "lattice-gb300 1.0 (sm_103a)"; }
+
+// Test hook (not part of the documented API surface): the countdown-th next
+// device allocation fails with out-of-memory.
+int lattice_test_fail_alloc(int countdown)
+{
+    g_fail_alloc_countdown.store(countdown < 0 ? 0 : countdown);
+    return LAT_OK;
+}
+
+}  // extern "C"

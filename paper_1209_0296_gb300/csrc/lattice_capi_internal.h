@@ -1,0 +1,64 @@
+// lattice_capi_internal.h -- host-side handle of one lattice and helpers
+// shared by the C-ABI, batch and server translation units.
+#pragma once
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "lattice_internal.cuh"
+
+namespace lat {
+
+struct Params {
+    int dims, L, two_S, model, cmode, init, layout;
+    double J, h, T, c;
+    uint64_t seed;
+    uint64_t N;
+};
+
+int cuda_fail(cudaError_t e, const char *what);
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+int validate(int dims, int L, int two_S, int model, double J, double h, double T_or_c, int init,
+             int layout, Params &P);
+void build_table(const Params &P, std::vector<TabEntry> &tab, int &dsmax, int &nmax, int &nn);
+size_t footprint_bytes(const Params &P);
+int create_impl(struct ::lattice **out, int dims, int L, int two_S, int model, double J, double h,
+                double T_or_c, uint64_t seed, int init, int layout, void *cuda_stream);
+int sweep_impl(struct ::lattice *lt, int64_t n);
+int choose_kernel(const struct ::lattice *lt);
+bool tile_shape_ok(int tile_w, int tile_h);
+void compact_table(Geom &g, const TabEntry *host_tab);
+
+// Sweeps per captured CUDA graph: small lattices are launch-bound, so they
+// replay long graphs; large ones need only a few sweeps per graph.
+inline int default_graph_sweeps(const Params &P)
+{
+    if (P.N <= (1u << 16)) return 64;
+    if (P.N <= (1u << 22)) return 16;
+    return 8;
+}
+
+}  // namespace lat
+
+struct lattice {
+    lat::Params P;
+    lat::Geom geom;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int8_t *spins[2] = {nullptr, nullptr};   // int8 layout: double buffer; bit-packed: [0] = staging
+    uint32_t *flags = nullptr;
+    uint32_t *bits[2] = {nullptr, nullptr};
+    lat::TabEntry *tab = nullptr;
+    lat::Ctrl *ctrl = nullptr;
+    unsigned long long *series = nullptr;
+    unsigned long long series_cap = 0;   // sweeps the buffer can hold (from series_first)
+    unsigned long long *scratch4 = nullptr;
+    std::vector<lat::TabEntry> host_tab;
+    int64_t sweeps = 0;        // sweeps done (global index of the next sweep)
+    int64_t series_first = 0;  // first sweep index recorded in the series buffer
+    int kernel = 0, tile_w = 0, tile_h = 0, graph_sweeps = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool graph_valid = false;
+};

@@ -1,0 +1,171 @@
+// lattice_internal.cuh -- device-side definitions shared by the library's
+// kernels: Philox4x32-10, the per-lattice parameter block, the threshold
+// table entry and warp/block reductions.  Library code only; the CPU
+// oracle has its own independent copy of every rule.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice.h"
+
+#if defined(__CUDACC__)
+#define LAT_HD __host__ __device__ __forceinline__
+#define LAT_D __device__ __forceinline__
+#else
+#define LAT_HD inline
+#define LAT_D inline
+#endif
+
+namespace lat {
+
+// Philox4x32-10 of Salmon, Moraes, Dror & Shaw (SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplications by fixed odd constants, with the two key
+// words advanced by the Weyl increments (golden ratio, sqrt(3)-1) between
+// rounds.  Replaces the paper's per-thread LCG of §IV (Eqs. 5-7) so that a
+// draw depends only on (seed, site group, sweep, colour).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+LAT_HD void mul_hi_lo(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo)
+{
+#if defined(__CUDA_ARCH__)
+    lo = a * b;
+    hi = __umulhi(a, b);
+#else
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+#endif
+}
+
+LAT_HD U4 philox(U4 c, uint32_t k0, uint32_t k1)
+{
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int r = 0; r < 10; ++r) {
+        uint32_t h0, l0, h1, l1;
+        mul_hi_lo(kPhiloxM0, c.x, h0, l0);
+        mul_hi_lo(kPhiloxM1, c.z, h1, l1);
+        U4 n;
+        n.x = h1 ^ c.y ^ k0;
+        n.y = l1;
+        n.z = h0 ^ c.w ^ k1;
+        n.w = l0;
+        c = n;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+LAT_HD uint32_t word_of(const U4 &v, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// One acceptance-table entry: accept without a draw (always = 1), or
+// accept iff the 32-bit draw u < thr.
+struct TabEntry {
+    uint32_t thr;
+    uint32_t always;
+};
+
+// Dynamic, device-resident state of one lattice: read by every sweep
+// kernel so that a captured CUDA graph can be replayed unchanged.
+struct Ctrl {
+    unsigned long long sweep;        // global index of the next sweep
+    unsigned long long *series;      // [series_cap][4] exact counters
+    unsigned long long series_base;  // global sweep index of series[0]
+    unsigned long long series_cap;   // sweeps the series buffer can hold
+    unsigned int error;              // device error word (0 = none)
+    unsigned int pad;
+};
+
+#if defined(__CUDACC__)
+// Counter slot of global sweep `sweep` (4 x int64: bond, mag, up, unflipped).
+LAT_D unsigned long long *series_slot(const Ctrl *c, unsigned long long sweep)
+{
+    return c->series + 4ull * (sweep - c->series_base);
+}
+#endif
+
+// Static description of one lattice, passed by value to its kernels and
+// stored in device memory for the batched engine.
+struct Geom {
+    int dims, L, two_S, model, cmode;
+    int sh;               // log2(sites per Philox call)
+    uint32_t G;           // Philox groups per row = ceil((L/2) >> sh)
+    uint32_t rows;        // L^(dims-1)
+    uint64_t N;           // sites
+    uint32_t key0, key1;  // Philox key = seed
+    int dsmax, nmax, nn, tab_n;
+    const TabEntry *tab;  // [nds * nn], nds = 2*dsmax+1
+    // Spins are double-buffered: after t sweeps the state is in s[t & 1]
+    // (int8 layout: N spins, x fastest) or bits[t & 1] (bit-packed layout:
+    // [2 colours][L rows][bw] words).  A sweep reads one buffer and writes
+    // the other, so no CTA can see a neighbour's half-finished sweep.
+    int8_t *s[2];
+    uint32_t *bits[2];
+    uint32_t bw;          // bit-packed words per row
+    uint32_t *flags;      // persistence bitmap, bit i = site i (North-East), or null
+    Ctrl *ctrl;
+    // Compact acceptance table for 2D spin-1/2 (tiled and bit-packed
+    // kernels): index (self down) << 3 | (# down neighbours).
+    uint32_t thr16[16];
+    uint32_t always16;
+};
+
+// Spin value <-> state index (state 0 = most negative value).
+LAT_HD int spin_of_state(int two_S, int k) { return (two_S & 1) ? 2 * k - two_S : k - (two_S >> 1); }
+LAT_HD int state_of_spin(int two_S, int s) { return (two_S & 1) ? (s + two_S) >> 1 : s + (two_S >> 1); }
+LAT_HD int max_spin(int two_S) { return (two_S & 1) ? two_S : (two_S >> 1); }
+
+#if defined(__CUDACC__)
+// Sum of an int over the block; result valid in thread 0.  `red` must hold
+// one int per warp.  Every thread of the block must call it.
+LAT_D long long block_sum_ll(long long v, long long *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    long long t = 0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) t += red[w];
+    }
+    return t;
+}
+
+LAT_D void add_counter(unsigned long long *slot, long long v)
+{
+    if (v != 0) atomicAdd(slot, (unsigned long long)v);
+}
+#endif
+
+}  // namespace lat
+
+// Host-side launchers implemented in the .cu files.
+namespace lat {
+cudaError_t launch_init(const Geom &g, int init, double c, cudaStream_t st);
+cudaError_t launch_half_sweep_generic(const Geom &g, int colour, int off, cudaStream_t st);
+cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out4, cudaStream_t st);
+cudaError_t launch_advance(Ctrl *ctrl, unsigned long long k, cudaStream_t st);
+cudaError_t launch_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
+                            unsigned long long base, unsigned long long cap, cudaStream_t st);
+bool tiled_supported(const Geom &g);
+cudaError_t launch_sweep_tiled(const Geom &g, int tile_w, int tile_h, int off, cudaStream_t st);
+cudaError_t launch_pack_bits(const Geom &g, const int8_t *spins, uint32_t *bits, cudaStream_t st);
+cudaError_t launch_unpack_bits(const Geom &g, const uint32_t *bits, int8_t *spins, cudaStream_t st);
+cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
+}  // namespace lat

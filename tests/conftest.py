@@ -16,3 +16,22 @@ def pytest_configure(config):
 def pytest_collection_modifyitems(config, items):
     # A file named test_zz_* is collected last by name; keep that order stable.
     items.sort(key=lambda it: (os.path.basename(str(it.fspath)).startswith("test_zz_"),))
+
+
+_GPU = None
+
+
+def _have_gpu():
+    global _GPU
+    if _GPU is None:
+        try:
+            import torch
+            _GPU = bool(torch.cuda.is_available())
+        except Exception:
+            _GPU = False
+    return _GPU
+
+
+def pytest_runtest_setup(item):
+    if item.get_closest_marker("gpu") is not None and not _have_gpu():
+        pytest.skip("no CUDA device visible")

@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA library against the CPU oracle, bit for bit.
+
+Every case creates the same lattice on both sides from the same seed, runs
+the same number of checkerboard sweeps (§III.A steps 5-8; §III.B rule) and
+requires identical int8 spins, identical persistence flags (North-East) and
+identical per-sweep int64 counters.  Integer work, so the tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1209_0296_gb300 as lt
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pair(dims, L, two_S, model, J, h, Tc, seed, init, nsweeps, kernel=lt.KERNEL_AUTO,
+             tile=(0, 0), graph=0, chunks=None):
+    o = oracle.Lattice(dims, L, two_S, model, J, h, Tc, seed=seed, init=init)
+    g = lt.Lattice(dims, L, two_S, model, J, h, Tc, seed=seed, init=init)
+    try:
+        assert np.array_equal(g.get_spins(), o.spins), "initial state differs"
+        g.set_kernel(kernel, tile[0], tile[1], graph)
+        ser_o = o.sweep(nsweeps)
+        for c in (chunks or [nsweeps]):
+            g.sweep(c)
+        ser_g = g.series(0, nsweeps)
+        spins, flags, n = g.get_state()
+        assert n == nsweeps
+        bad = np.flatnonzero(spins != o.spins)
+        assert bad.size == 0, "spins differ at %d sites, first %s" % (bad.size, bad[:8])
+        if model == lt.NE:
+            assert np.array_equal(flags, o.flags), "persistence flags differ"
+        keys = ("bond", "mag", "up", "unflipped") if model == lt.NE else ("bond", "mag", "up")
+        for k in keys:
+            assert np.array_equal(ser_g[k], ser_o[k]), k
+        return g, o, ser_g
+    finally:
+        g.close()
+
+
+def test_config_L64_cold_1000_sweeps_tiled():
+    # 2D Ising spin-1/2, L=64, J=1, h=0, T=2.269185, cold start, seed 1234,
+    # 1000 sweeps with per-sweep E and M (every counter compared).
+    run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 1000)
+
+
+def test_config_L64_cold_1000_sweeps_generic():
+    run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 1000,
+             kernel=lt.KERNEL_GENERIC)
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 16, 32, 48])
+@pytest.mark.parametrize("T,J,h", [(1.5, 1.0, 0.0), (2.269185, 1.0, 0.2), (3.5, -0.8, -0.3)])
+def test_2d_spin_half_small(L, T, J, h):
+    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
+        run_pair(2, L, 1, lt.ISING, J, h, T, 100 + L, lt.INIT_RANDOM, 25, kernel=kernel)
+
+
+@pytest.mark.parametrize("L,tile", [(272, (256, 32)), (528, (256, 32)), (528, (128, 8)),
+                                    (528, (512, 64)), (96, (16, 2)), (4112, (512, 64))])
+def test_tiled_ragged_tiles(L, tile):
+    n = 12 if L < 4000 else 3
+    run_pair(2, L, 1, lt.ISING, 1.0, 0.1, 2.4, 7 + L, lt.INIT_RANDOM, n, kernel=lt.KERNEL_TILED,
+             tile=tile)
+
+
+@pytest.mark.parametrize("two_S", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("L", [2, 4, 6, 10])
+def test_3d_spin_S(two_S, L):
+    T = 2.0 * max(1, two_S) ** 1.2
+    run_pair(3, L, two_S, lt.ISING, 1.0, 0.15, T, 11 + L, lt.INIT_RANDOM, 20)
+
+
+@pytest.mark.parametrize("two_S", [2, 3, 5])
+def test_2d_spin_S(two_S):
+    run_pair(2, 12, two_S, lt.ISING, 0.9, -0.1, 1.7 * two_S, 5, lt.INIT_RANDOM, 30)
+
+
+@pytest.mark.parametrize("L", [4, 16, 48, 64, 272])
+@pytest.mark.parametrize("c", [0.05, 0.3, 0.45, 0.7])
+def test_north_east_c_mode(L, c):
+    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
+        run_pair(2, L, 1, lt.NE, 0.0, 0.0, c, 21 + L, lt.INIT_EQUILIBRIUM, 30, kernel=kernel)
+
+
+@pytest.mark.parametrize("L", [8, 32, 64])
+def test_north_east_temperature_mode(L):
+    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
+        run_pair(2, L, 1, lt.NE, 0.5, -1.0, 1.5, 3, lt.INIT_RANDOM, 30, kernel=kernel)
+
+
+def test_graph_replay_and_direct_launch_paths_agree():
+    # Graph replays (64 sweeps each for this size) and direct launches mixed.
+    run_pair(2, 32, 1, lt.ISING, 1.0, 0.0, 2.2, 9, lt.INIT_RANDOM, 333,
+             chunks=[1, 63, 64, 200, 5])
+    run_pair(3, 8, 2, lt.ISING, 1.0, 0.0, 2.5, 9, lt.INIT_RANDOM, 150, graph=16,
+             chunks=[7, 16, 100, 27])
+
+
+def test_checkpoint_resume_is_bit_exact():
+    args = (2, 48, 1, lt.NE, 0.0, 0.0, 0.35, 77, lt.INIT_EQUILIBRIUM)
+    a = lt.Lattice(*args[:7], seed=args[7], init=args[8])
+    a.sweep(40)
+    full = a.get_state()
+    b = lt.Lattice(*args[:7], seed=args[7], init=args[8])
+    b.sweep(17)
+    s, f, n = b.get_state()
+    c = lt.Lattice(*args[:7], seed=args[7], init=args[8])
+    c.set_state(s, f, n)
+    c.sweep(23)
+    resumed = c.get_state()
+    assert resumed[2] == 40
+    assert np.array_equal(resumed[0], full[0]) and np.array_equal(resumed[1], full[1])
+    assert np.array_equal(c.series(17, 23)["unflipped"], a.series(17, 23)["unflipped"])
+    with pytest.raises(lt.LatticeError):
+        c.series(0, 5)   # sweeps before the restore point are not recorded here
+
+
+def test_observables_follow_series():
+    g = lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.3, 2.1, seed=4, init=lt.INIT_RANDOM)
+    o0 = g.observables()
+    s = g.get_spins().astype(np.int64).reshape(64, 64)
+    bond = int((s * np.roll(s, -1, 1)).sum() + (s * np.roll(s, -1, 0)).sum())
+    assert o0["E"] == pytest.approx((-bond - 0.3 * s.sum()) / 4096)
+    assert o0["M"] == pytest.approx(s.sum() / 4096)
+    g.sweep(10)
+    ser = g.series(9, 1)
+    o = g.observables()
+    assert o["E"] == pytest.approx((-ser["bond"][0] - 0.3 * ser["mag"][0]) / 4096)
+    assert o["density"] == pytest.approx(ser["up"][0] / 4096)
+    assert np.isnan(o["persistence"])
+
+
+def test_set_spins_roundtrip_and_validation():
+    g = lt.Lattice(3, 6, 2, lt.ISING, 1.0, 0.0, 2.0, seed=1, init=lt.INIT_RANDOM)
+    rng = np.random.default_rng(0)
+    s = rng.integers(-1, 2, 216).astype(np.int8)
+    g.set_spins(s)
+    assert np.array_equal(g.get_spins(), s)
+    with pytest.raises(lt.LatticeError):
+        g.set_spins(np.full(216, 2, dtype=np.int8))
+
+
+def test_allocation_failure_is_reported():
+    lib = lt.load()
+    lib.lattice_test_fail_alloc(2)  # second allocation of the next create fails
+    with pytest.raises(lt.LatticeError) as e:
+        lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.0, seed=1)
+    assert e.value.code == -2
+    lib.lattice_test_fail_alloc(0)
+    lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.0, seed=1).sweep(3)   # still usable
+
+
+# ---- full sizes, in the launch configuration the benchmark times ----------
+
+def test_full_size_2d_L4096_random_tiled():
+    # 2D Ising spin-1/2, L=4096, T=2.0, random +-1 start (seed 7).
+    run_pair(2, 4096, 1, lt.ISING, 1.0, 0.0, 2.0, 7, lt.INIT_RANDOM, 4)
+
+
+def test_full_size_3d_L256_spin_one():
+    # 3D spin-1, L=256, T=2.0 + 7*(2/15), uniform random start (seed 11).
+    run_pair(3, 256, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, 11, lt.INIT_RANDOM, 1)
+
+
+def test_full_size_north_east_L8192():
+    run_pair(2, 8192, 1, lt.NE, 0.0, 0.0, 0.3, 21, lt.INIT_EQUILIBRIUM, 1)
+
+
+def test_full_size_properties_after_many_sweeps():
+    # Beyond what the oracle can follow: every counter must match a direct
+    # recount of the final lattice, and spins stay in {-1, +1}.
+    L = 4096
+    g = lt.Lattice(2, L, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=7, init=lt.INIT_RANDOM)
+    g.sweep(300)
+    s = g.get_spins()
+    assert set(np.unique(s).tolist()) <= {-1, 1}
+    s = s.astype(np.int64).reshape(L, L)
+    ser = g.series(299, 1)
+    assert ser["bond"][0] == (s * np.roll(s, -1, 1)).sum() + (s * np.roll(s, -1, 0)).sum()
+    assert ser["mag"][0] == s.sum()
+    assert ser["up"][0] == (s > 0).sum()
