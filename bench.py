@@ -1,0 +1,379 @@
+"""Benchmark: checkerboard Metropolis sweeps of the 2D Ising model on GB300.
+
+Workload (one step): `--sweeps` checkerboard sweeps of each of three 2D
+Ising spin-1/2 lattices, L = 4096 periodic, J = 1, h = 0, T in
+{2.0, 2.269185, 3.0}, random +-1 start (seed 7), int8 spins, advanced
+through the C ABI of liblattice.so.  One spin update = one site visited in
+one sweep.
+
+Prints ONE JSON line (rank 0):
+  value      spin updates per ns over all GPUs, inputs resident in HBM
+  roofline   the dominant kernel (one-launch tiled sweep) against measured
+             HBM bandwidth, with algorithmic bytes = 2 B per site per sweep
+             (one int8 read + one int8 write), plus its issue-rate roofline
+  e2e        same metric through the C ABI with pinned host buffers: upload
+             of the three lattices, the sweeps, and the read-back of the
+             per-sweep E/M counters inside the timed region
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample
+`--impl reference` times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L = 4096
+TEMPS = (2.0, 2.269185, 3.0)
+SEED = 7
+WORKLOAD = ("2D Ising spin-1/2, L=4096 periodic, J=1, h=0, T in {2.0, 2.269185, 3.0}, "
+            "random +-1 start (seed 7), int8 spins")
+METRIC = "spin updates/ns"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons in the background."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "out", "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(seconds_target=12.0, max_sweeps_per_T=3):
+    """Time the CPU oracle (as it stands, single thread) on L=4096 sweeps."""
+    import oracle
+    done = 0
+    t_total = 0.0
+    n_T = 0
+    for T in TEMPS:
+        lat = oracle.Lattice(2, L, 1, oracle.ISING, 1.0, 0.0, T, seed=SEED, init=oracle.INIT_RANDOM)
+        n_T += 1
+        for _ in range(max_sweeps_per_T):
+            t0 = time.perf_counter()
+            lat.sweep(1)
+            t_total += time.perf_counter() - t0
+            done += 1
+            if t_total > seconds_target:
+                break
+        if t_total > seconds_target:
+            break
+    ups = done * L * L / t_total / 1e9
+    return {"value": ups, "unit": "updates/ns", "cores": 1, "kind": "oracle",
+            "sample": "%d single-threaded oracle sweeps of L=4096 lattices over %d temperature(s), "
+                      "%.1f s (init excluded)" % (done, n_T, t_total)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    # each step: one oracle sweep of each of the three lattices (a bounded
+    # sample of the same workload; the full sweep count would take hours).
+    lats = [oracle.Lattice(2, L, 1, oracle.ISING, 1.0, 0.0, T, seed=SEED, init=oracle.INIT_RANDOM)
+            for T in TEMPS]
+    for _ in range(args.warmup):
+        for lat in lats:
+            lat.sweep(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for lat in lats:
+            lat.sweep(1)
+    dt = time.perf_counter() - t0
+    ups = args.steps * len(TEMPS) * L * L / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": "updates/ns",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sweeps_per_step": 1, "lattices": len(TEMPS)},
+            "cpu_baseline": {"value": ups, "unit": "updates/ns", "cores": 1, "kind": "oracle",
+                             "sample": "%d steps x 3 lattices x 1 sweep, single-threaded CPU oracle"
+                                       % args.steps},
+            "e2e": {"value": ups, "unit": "updates/ns", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import paper_1209_0296_gb300 as lt
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    S = args.sweeps
+
+    lats = [lt.Lattice(2, L, 1, lt.ISING, 1.0, 0.0, T, seed=SEED, init=lt.INIT_RANDOM, stream=stream)
+            for T in TEMPS]
+    for g in lats:
+        g.set_kernel(lt.KERNEL_AUTO, 0, args.tile_h, args.graph)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
+
+    def step():
+        for g in lats:
+            g.sweep(S)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        stream.synchronize()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with Clocks(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(k & 255)          # evict the lattices from L2 (outside the timed pair)
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+            stream.synchronize()
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = world * args.steps * len(TEMPS) * S * L * L
+    value = updates / (total_ms * 1e6)
+
+    # Kernel launches per step: per lattice, S sweep kernels plus one
+    # counter-advance kernel per graph replay and per direct remainder.
+    gk = lats[0].sweeps_per_graph()
+    per_lat = S + S // gk + (1 if S % gk else 0)
+    launches = args.steps * len(TEMPS) * per_lat
+    sweep_launches = args.steps * len(TEMPS) * S
+    avg_kernel_us = total_ms * 1e3 / (args.steps * len(TEMPS) * S)  # includes the tiny advance kernels
+
+    hbm, _, peak_kind = peaks()
+    alg_bytes = 2.0 * L * L  # one int8 read + one int8 write per site per sweep
+    achieved = alg_bytes / (avg_kernel_us * 1e-6) / 1e9
+    prof = load_profile_numbers()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": prof.get("traffic_bytes_per_launch"),
+                "kernel": "k_sweep_tiled<Ising>", "peak_kind": peak_kind + " (copy bandwidth)",
+                "bytes_per_launch": alg_bytes,
+                "avg_launch_us": avg_kernel_us}
+    if prof.get("warp_inst_per_launch"):
+        sm_clk = (clk.summary().get("sm_mhz") or 2070.0) * 1e6
+        inst_rate = prof["warp_inst_per_launch"] / (avg_kernel_us * 1e-6)
+        issue_peak = 152 * 4 * sm_clk
+        roofline["issue"] = {"bound": "alu", "achieved": inst_rate / 1e12, "peak": issue_peak / 1e12,
+                             "unit": "Twarp-inst/s", "frac": inst_rate / issue_peak,
+                             "inst_per_site": prof["warp_inst_per_launch"] * 32 / (L * L)}
+
+    # ---- end to end through the C ABI with pinned host buffers ----------
+    e2e = None
+    if not args.no_e2e:
+        host_in = [torch.empty(L * L, dtype=torch.int8, pin_memory=True) for _ in TEMPS]
+        rng = np.random.default_rng(1000 + rank)
+        for h in host_in:
+            h.numpy()[:] = np.where(rng.random(L * L) < 0.5, 1, -1).astype(np.int8)
+        series = {k: np.zeros(S, dtype=np.int64) for k in ("bond", "mag")}
+
+        def e2e_step():
+            for g, h in zip(lats, host_in):
+                g.set_spins_ptr(h.data_ptr())
+                g.sweep(S)
+                first = g.sweeps() - S
+                g.series_into(first, S, series["bond"], series["mag"])
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": updates / (dt * 1e9), "unit": "updates/ns",
+               "h2d_bytes_per_step": len(TEMPS) * L * L,
+               "d2h_bytes_per_step": len(TEMPS) * S * 4 * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "updates/ns", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "lattices": len(TEMPS), "sweeps_per_step": S,
+                           "layout": "int8", "kernel": "tiled one-launch sweep",
+                           "tile": [256, lats[0].tile_h()], "sweeps_per_graph": gk,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "flushed between steps (256 MiB write outside the timed events)"},
+                "hbm_roofline_pct": 100.0 * roofline["frac"],
+                "roofline": roofline, "gpu_launches": launches, "sweep_launches": sweep_launches,
+                "clocks": clk.summary()}
+        if e2e is not None:
+            line["e2e"] = e2e
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    for g in lats:
+        g.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_profile(args):
+    """A short, untimed run of the dominant kernel for ncu captures."""
+    import torch
+    import paper_1209_0296_gb300 as lt
+    torch.cuda.set_device(0)
+    if args.profile_model == "ne":
+        g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, 0.3, seed=21, init=lt.INIT_EQUILIBRIUM)
+    else:
+        g = lt.Lattice(2, args.profile_L, 1, lt.ISING, 1.0, 0.0, TEMPS[0], seed=SEED,
+                       init=lt.INIT_RANDOM)
+    g.set_kernel(lt.KERNEL_AUTO, 0, args.tile_h, 1 << 30)  # direct launches, one per sweep
+    g.sweep(args.profile)
+    g.synchronize()
+    print("profile run: %d sweeps of L=%d (%s), kernel %s" % (args.profile, args.profile_L,
+                                                           args.profile_model, g.get_kernel()))
+
+
+def load_profile_numbers():
+    """Per-launch DRAM traffic and instruction count of the dominant kernel,
+    from the committed ncu summary (null when absent)."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_tiled_L4096.txt")
+    out = {}
+    try:
+        with open(path) as f:
+            for line in f:
+                line = line.strip()
+                if not line or line.startswith("#") or ":" not in line:
+                    continue
+                k, v = line.split(":", 1)
+                try:
+                    out[k.strip()] = float(v)
+                except ValueError:
+                    out[k.strip()] = v.strip()
+    except OSError:
+        pass
+    if out.get("kernel_matches_build") == "no":
+        out["traffic_bytes_per_launch"] = None
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=1000, help="sweeps per lattice per step")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tile-h", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=0, help="sweeps per CUDA graph (0 = default)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", type=int, default=0, metavar="N",
+                    help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
+    ap.add_argument("--profile-L", type=int, default=L)
+    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne"])
+    args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

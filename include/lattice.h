@@ -173,6 +173,12 @@ int lattice_device_spins(lattice_t *lat, void **dev_ptr, size_t *bytes);
 int lattice_set_kernel(lattice_t *lat, int kernel, int tile_w, int tile_h,
                        int sweeps_per_graph);
 
+/* The kernel actually used for this lattice (enum lattice_kernel, never
+ * AUTO), its tile shape (0 when the kernel has none) and the sweeps per
+ * CUDA-graph replay.  NULL outputs are skipped. */
+int lattice_get_kernel(lattice_t *lat, int *kernel, int *tile_w, int *tile_h,
+                       int *sweeps_per_graph);
+
 /* The acceptance table the library builds on the host (no GPU needed) for
  * the given model parameters (same meaning and checks as lattice_create):
  * for ds = s' - s in [-dsmax, dsmax] and neighbour sum n in [-nmax, nmax],

@@ -117,6 +117,28 @@ class Lattice:
         check(self._lib.lattice_set_kernel(self._h, kernel, tile_w, tile_h, sweeps_per_graph),
               "lattice_set_kernel")
 
+    def get_kernel(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        check(self._lib.lattice_get_kernel(self._h, *[ctypes.byref(x) for x in v]),
+              "lattice_get_kernel")
+        return dict(kernel=v[0].value, tile_w=v[1].value, tile_h=v[2].value,
+                    sweeps_per_graph=v[3].value)
+
+    def sweeps_per_graph(self) -> int:
+        return self.get_kernel()["sweeps_per_graph"]
+
+    def tile_h(self) -> int:
+        return self.get_kernel()["tile_h"]
+
+    def set_spins_ptr(self, host_ptr: int):
+        """lattice_set_spins from a raw host address holding N int8 spins (e.g. pinned memory)."""
+        check(self._lib.lattice_set_spins(self._h, ctypes.c_void_p(host_ptr)), "lattice_set_spins")
+
+    def series_into(self, first, count, bond=None, mag=None, up=None, unflipped=None):
+        """lattice_series into caller-provided int64 arrays (no allocation)."""
+        check(self._lib.lattice_series(self._h, int(first), int(count), _ptr(bond), _ptr(mag),
+                                       _ptr(up), _ptr(unflipped)), "lattice_series")
+
     def threshold_table(self):
         return threshold_table(self.dims, self.two_S, self.model, self.J, self.h, self.T_or_c)
 

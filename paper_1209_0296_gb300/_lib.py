@@ -46,6 +46,7 @@ SIGNATURES = {
     "lattice_info": (c_int, [c_void_p] + [ctypes.POINTER(c_int64)] * 3),
     "lattice_device_spins": (c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_size_t)]),
     "lattice_set_kernel": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
+    "lattice_get_kernel": (c_int, [c_void_p] + [ctypes.POINTER(c_int)] * 4),
     "lattice_threshold_table": (c_int, [c_int, c_int, c_int, c_double, c_double, c_double,
                                         c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
                                         ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),

@@ -479,13 +479,15 @@ int lattice_get_spins(lattice_t *lt, int8_t *host_out)
 
 static bool spins_allowed(const Params &P, const int8_t *s)
 {
+    // Branch-free scan (vectorises): count values outside the allowed set.
     const int smax = max_spin(P.two_S);
+    const int odd = P.two_S & 1;
+    uint64_t bad = 0;
     for (uint64_t i = 0; i < P.N; ++i) {
         const int v = s[i];
-        if (v < -smax || v > smax) return false;
-        if ((P.two_S & 1) && ((v + P.two_S) & 1)) return false;
+        bad += (uint64_t)((v < -smax) | (v > smax) | (odd & ((v + P.two_S) & 1)));
     }
-    return true;
+    return bad == 0;
 }
 
 // Copy host spins into the current-state buffer (packing for bit-packed).
@@ -598,6 +600,17 @@ int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sw
     lt->tile_h = tile_h;
     lt->graph_sweeps = sweeps_per_graph ? sweeps_per_graph : default_graph_sweeps(lt->P);
     lt->graph_valid = false;
+    return LAT_OK;
+}
+
+int lattice_get_kernel(lattice_t *lt, int *kernel, int *tile_w, int *tile_h, int *sweeps_per_graph)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    const int k = choose_kernel(lt);
+    if (kernel) *kernel = (k == LAT_KERNEL_AUTO) ? LAT_KERNEL_GENERIC : k;
+    if (tile_w) *tile_w = (k == LAT_KERNEL_TILED) ? 256 : 0;
+    if (tile_h) *tile_h = (k == LAT_KERNEL_TILED) ? (lt->tile_h ? lt->tile_h : default_tile_h()) : 0;
+    if (sweeps_per_graph) *sweeps_per_graph = lt->graph_sweeps;
     return LAT_OK;
 }
 

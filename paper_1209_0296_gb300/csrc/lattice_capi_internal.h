@@ -29,6 +29,7 @@ int create_impl(struct ::lattice **out, int dims, int L, int two_S, int model, d
 int sweep_impl(struct ::lattice *lt, int64_t n);
 int choose_kernel(const struct ::lattice *lt);
 bool tile_shape_ok(int tile_w, int tile_h);
+int default_tile_h();
 void compact_table(Geom &g, const TabEntry *host_tab);
 
 // Sweeps per captured CUDA graph: small lattices are launch-bound, so they

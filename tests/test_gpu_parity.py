@@ -57,8 +57,8 @@ def test_2d_spin_half_small(L, T, J, h):
         run_pair(2, L, 1, lt.ISING, J, h, T, 100 + L, lt.INIT_RANDOM, 25, kernel=kernel)
 
 
-@pytest.mark.parametrize("L,tile", [(272, (256, 32)), (528, (256, 32)), (528, (128, 8)),
-                                    (528, (512, 64)), (96, (16, 2)), (4112, (512, 64))])
+@pytest.mark.parametrize("L,tile", [(272, (256, 32)), (528, (256, 32)), (528, (256, 8)),
+                                    (528, (256, 64)), (96, (256, 2)), (4112, (256, 48)), (48, (256, 7))])
 def test_tiled_ragged_tiles(L, tile):
     n = 12 if L < 4000 else 3
     run_pair(2, L, 1, lt.ISING, 1.0, 0.1, 2.4, 7 + L, lt.INIT_RANDOM, n, kernel=lt.KERNEL_TILED,
@@ -181,3 +181,14 @@ def test_full_size_properties_after_many_sweeps():
     assert ser["bond"][0] == (s * np.roll(s, -1, 1)).sum() + (s * np.roll(s, -1, 0)).sum()
     assert ser["mag"][0] == s.sum()
     assert ser["up"][0] == (s > 0).sum()
+
+
+def test_never_accept_table_falls_back_to_generic():
+    # At T = 0.3 a dE = 8 move has p < 2^-32 (thr = 0): the tiled kernel's
+    # t' = thr - 1 encoding cannot hold it, so the library must refuse the
+    # tiled kernel and the automatic choice must still be bit-exact.
+    g = lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 0.3, seed=3, init=lt.INIT_RANDOM)
+    with pytest.raises(lt.LatticeError) as e:
+        g.set_kernel(lt.KERNEL_TILED)
+    assert e.value.code == -6
+    run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 0.3, 3, lt.INIT_RANDOM, 20)
