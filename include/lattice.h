@@ -88,7 +88,7 @@ enum lattice_kernel {
     LAT_KERNEL_AUTO = 0,    /* library choice (tuned tile shape when eligible) */
     LAT_KERNEL_GENERIC = 1, /* two launches per sweep, one per colour; any model */
     LAT_KERNEL_TILED = 2    /* one launch per sweep, shared-memory tiles with halo
-                               recompute; 2D spin-1/2 (Ising and North-East), L % 16 == 0 */
+                               recompute; 2D spin-1/2 (Ising and North-East), L % 32 == 0 */
 };
 
 typedef struct lattice lattice_t;
@@ -162,9 +162,12 @@ int lattice_set_state(lattice_t *lat, const int8_t *spins, const uint8_t *flags,
 /* Number of sweeps done, N, and device bytes held by the handle. */
 int lattice_info(lattice_t *lat, int64_t *sweeps, int64_t *n_sites, int64_t *device_bytes);
 
-/* Device address and size of the spin storage (for zero-copy device use;
- * the layout is the one given at creation: N int8 spins, or for the
- * bit-packed layout 2 colour planes of L rows x ceil(L/64) uint32 pairs). */
+/* Device address and size of the current spin storage, valid until the
+ * next sweep (the buffers alternate).  int8 layout: checkerboard-planar,
+ * N int8 spins where plane c = (x+y+z) mod 2, row r = y + L*z and
+ * j = x >> 1 sit at c*(N/2) + r*(L/2) + j.  Bit-packed layout: 2 colour
+ * planes x L rows x ceil(L/64) uint32 words, bit j of a row = site j of
+ * that plane row, set = up. */
 int lattice_device_spins(lattice_t *lat, void **dev_ptr, size_t *bytes);
 
 /* Pick the kernel (enum lattice_kernel), the tile shape (tile_w columns x

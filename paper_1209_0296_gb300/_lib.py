@@ -76,7 +76,8 @@ TEST_SIGNATURES = {
 
 
 def library_path() -> str:
-    return _build.SO
+    """liblattice.so in the package's build folder, or LATTICE_LIB if set."""
+    return os.environ.get("LATTICE_LIB", _build.SO)
 
 
 def load(build_if_missing: bool = True):
@@ -86,7 +87,7 @@ def load(build_if_missing: bool = True):
         if _lib is not None:
             return _lib
         path = library_path()
-        if not os.path.exists(path) or not _build.up_to_date():
+        if path == _build.SO and (not os.path.exists(path) or not _build.up_to_date()):
             if not build_if_missing:
                 raise RuntimeError("liblattice.so is not built: run __graft_entry__.build()")
             _build.build()

@@ -1,0 +1,227 @@
+// batch.cu -- the batched engine behind lattice_batch_*: many lattices of
+// any sizes and models advanced together.  Each sweep step is one
+// persistent-grid launch over the (lattice, tile) items of every 2D
+// spin-1/2 lattice (one fused sweep per tile) plus, for the other lattices,
+// two persistent launches over (lattice, chunk) items (colour 0, colour 1),
+// then one small kernel that advances every lattice's sweep counter.  Steps
+// with the same set of lattices are captured once in a CUDA graph and
+// replayed.  Every lattice keeps its own seed, table and sweep counter, so
+// its result is bit-identical to running it alone.
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "lattice_capi_internal.h"
+
+using namespace lat;
+
+struct lattice_batch {
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<std::pair<lattice *, int64_t>> pending;
+    Geom *d_geoms = nullptr;
+    int geoms_cap = 0;
+    uint2 *d_items = nullptr;  // tiled items, then generic items
+    int items_cap = 0;
+    Ctrl **d_ctrls = nullptr;
+    int ctrls_cap = 0;
+    unsigned *d_counters = nullptr;  // [3]: next tiled item, next colour-0 item, next colour-1 item
+    int grid_tiled = 0, grid_generic = 0;
+};
+
+namespace {
+
+constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
+constexpr int kGraphSteps = 32;   // steps per captured graph
+
+template <typename T>
+int grow(T **p, int &cap, int need, cudaStream_t st)
+{
+    if (need <= cap) return LAT_OK;
+    int c = cap ? cap : 64;
+    while (c < need) c *= 2;
+    void *q = nullptr;
+    cudaError_t e = dev_alloc(&q, (size_t)c * sizeof(T), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "batch alloc");
+    dev_free(*p, st);
+    *p = (T *)q;
+    cap = c;
+    return LAT_OK;
+}
+
+// Queue `steps` sweep steps of the current active set.
+int enqueue_steps(lattice_batch *b, int n_lat, int n_tiled, int n_gen, int steps, cudaStream_t st)
+{
+    for (int s = 0; s < steps; ++s) {
+        cudaError_t e = cudaSuccess;
+        if (n_tiled > 0)
+            e = launch_batch_tiled(b->d_geoms, b->d_items, n_tiled, b->d_counters + 0, 0, 0,
+                                   std::min(b->grid_tiled, n_tiled), st);
+        if (e == cudaSuccess && n_gen > 0)
+            e = launch_batch_generic(b->d_geoms, b->d_items + n_tiled, n_gen, b->d_counters + 1, 0, 0,
+                                     std::min(b->grid_generic, n_gen), st);
+        if (e == cudaSuccess && n_gen > 0)
+            e = launch_batch_generic(b->d_geoms, b->d_items + n_tiled, n_gen, b->d_counters + 2, 1, 0,
+                                     std::min(b->grid_generic, n_gen), st);
+        if (e == cudaSuccess) e = launch_batch_advance(b->d_ctrls, n_lat, b->d_counters, 3, 1ull, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    }
+    return LAT_OK;
+}
+
+int run_steps(lattice_batch *b, int n_lat, int n_tiled, int n_gen, int64_t steps)
+{
+    int64_t left = steps;
+    if (left >= kGraphSteps) {
+        if (b->cap_stream == nullptr) {
+            cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "batch capture stream");
+        }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "batch begin capture");
+        int rc = enqueue_steps(b, n_lat, n_tiled, n_gen, kGraphSteps, b->cap_stream);
+        e = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (rc != LAT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+        while (left >= kGraphSteps && e == cudaSuccess) {
+            e = cudaGraphLaunch(exec, b->stream);
+            left -= kGraphSteps;
+        }
+        cudaGraphExecDestroy(exec);  // safe: destruction waits for no launch; launches stay valid
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    }
+    if (left > 0) return enqueue_steps(b, n_lat, n_tiled, n_gen, (int)left, b->stream);
+    return LAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
+{
+    if (out == nullptr) return LAT_EINVAL;
+    *out = nullptr;
+    lattice_batch *b = new (std::nothrow) lattice_batch();
+    if (b == nullptr) return LAT_ENOMEM;
+    b->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = dev_alloc((void **)&b->d_counters, 3 * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, 3 * sizeof(unsigned), b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "batch create");
+    }
+    b->grid_tiled = batch_tiled_grid();
+    b->grid_generic = batch_generic_grid();
+    *out = b;
+    return LAT_OK;
+}
+
+int lattice_batch_add(lattice_batch_t *b, lattice_t *lt, int64_t n)
+{
+    if (b == nullptr || lt == nullptr || n < 0) return LAT_EINVAL;
+    if (lt->P.layout == LAT_BITPACKED) return LAT_ENOTSUP;
+    if (n == 0) return LAT_OK;
+    for (auto &pr : b->pending)
+        if (pr.first == lt) {
+            pr.second += n;
+            return LAT_OK;
+        }
+    b->pending.emplace_back(lt, n);
+    return LAT_OK;
+}
+
+int lattice_batch_run(lattice_batch_t *b)
+{
+    if (b == nullptr) return LAT_EINVAL;
+    std::vector<std::pair<lattice *, int64_t>> work;
+    work.swap(b->pending);
+    if (work.empty()) return LAT_OK;
+    // Lattices must have no work in flight on their own streams.
+    for (auto &pr : work) {
+        cudaError_t e = cudaStreamSynchronize(pr.first->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+        int rc = ensure_series(pr.first, (unsigned long long)(pr.first->sweeps + pr.second));
+        if (rc != LAT_OK) return rc;
+    }
+    // Run in phases: all lattices until the smallest remaining count is
+    // done, then drop it, and so on.
+    std::sort(work.begin(), work.end(), [](const auto &a, const auto &c) { return a.second > c.second; });
+    int64_t done = 0;
+    size_t n_active = work.size();
+    while (n_active > 0) {
+        const int64_t steps = work[n_active - 1].second - done;
+        if (steps > 0) {
+            std::vector<Geom> geoms(n_active);
+            std::vector<Ctrl *> ctrls(n_active);
+            std::vector<uint2> tiled, gen;
+            for (size_t i = 0; i < n_active; ++i) {
+                lattice *lt = work[i].first;
+                geoms[i] = tiled_geom(lt->geom);
+                ctrls[i] = lt->ctrl;
+                if (choose_kernel(lt) == LAT_KERNEL_TILED) {
+                    const int nt = tiles_of(lt->geom, 0);
+                    for (int k = 0; k < nt; ++k) tiled.push_back(make_uint2((unsigned)i, (unsigned)k));
+                } else {
+                    const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
+                    const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
+                    for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
+                }
+            }
+            const int n_tiled = (int)tiled.size(), n_gen = (int)gen.size();
+            std::vector<uint2> items(tiled);
+            items.insert(items.end(), gen.begin(), gen.end());
+            int rc = grow(&b->d_geoms, b->geoms_cap, (int)n_active, b->stream);
+            if (rc == LAT_OK) rc = grow(&b->d_items, b->items_cap, (int)items.size(), b->stream);
+            if (rc == LAT_OK) rc = grow(&b->d_ctrls, b->ctrls_cap, (int)n_active, b->stream);
+            if (rc != LAT_OK) return rc;
+            cudaError_t e = cudaMemcpyAsync(b->d_geoms, geoms.data(), n_active * sizeof(Geom),
+                                            cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(uint2),
+                                    cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->d_ctrls, ctrls.data(), n_active * sizeof(Ctrl *),
+                                    cudaMemcpyHostToDevice, b->stream);
+            // The host vectors go out of scope: make the copies complete first.
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+            rc = run_steps(b, (int)n_active, n_tiled, n_gen, steps);
+            if (rc != LAT_OK) return rc;
+            done += steps;
+        }
+        --n_active;
+    }
+    for (auto &pr : work) pr.first->sweeps += pr.second;
+    return LAT_OK;
+}
+
+int lattice_batch_synchronize(lattice_batch_t *b)
+{
+    if (b == nullptr) return LAT_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch synchronize");
+    return LAT_OK;
+}
+
+void lattice_batch_destroy(lattice_batch_t *b)
+{
+    if (b == nullptr) return;
+    cudaStreamSynchronize(b->stream);
+    dev_free(b->d_geoms, b->stream);
+    dev_free(b->d_items, b->stream);
+    dev_free(b->d_ctrls, b->stream);
+    dev_free(b->d_counters, b->stream);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,11 +1,6 @@
 // Temporary: batch and server entry points.
 #include "lattice_capi_internal.h"
 extern "C" {
-int lattice_batch_create(lattice_batch_t **, void *) { return LAT_ENOTSUP; }
-int lattice_batch_add(lattice_batch_t *, lattice_t *, int64_t) { return LAT_ENOTSUP; }
-int lattice_batch_run(lattice_batch_t *) { return LAT_ENOTSUP; }
-int lattice_batch_synchronize(lattice_batch_t *) { return LAT_ENOTSUP; }
-void lattice_batch_destroy(lattice_batch_t *) {}
 int lattice_server_create(lattice_server_t **, size_t, int, int) { return LAT_ENOTSUP; }
 int lattice_server_submit(lattice_server_t *, const lattice_request_t *, uint64_t *) { return LAT_ENOTSUP; }
 int lattice_server_poll(lattice_server_t *, uint64_t, lattice_result_t *, int8_t *) { return LAT_ENOTSUP; }

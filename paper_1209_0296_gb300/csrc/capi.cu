@@ -122,10 +122,19 @@ int validate(int dims, int L, int two_S, int model, double J, double h, double T
     return LAT_OK;
 }
 
+// Persistence flags: one byte per Philox group of same-colour sites.
+static size_t flag_bytes(const Params &P)
+{
+    const size_t rows = (size_t)(P.dims == 3 ? (size_t)P.L * P.L : (size_t)P.L);
+    const int sh = (P.two_S == 1) ? 2 : 1;
+    const size_t G = ((size_t)(P.L / 2) + (1u << sh) - 1) >> sh;
+    return 2 * rows * G;
+}
+
 size_t footprint_bytes(const Params &P)
 {
-    size_t b = (size_t)P.N;                                 // int8 spins
-    if (P.model == LAT_NE) b += ((P.N + 31) / 32) * 4;      // persistence bitmap
+    size_t b = 2 * (size_t)P.N;                             // int8 spins, double-buffered
+    if (P.model == LAT_NE) b += flag_bytes(P);              // persistence bytes
     if (P.layout == LAT_BITPACKED) b += (size_t)2 * P.L * (((size_t)P.L / 2 + 31) / 32) * 4;
     const int smax = max_spin(P.two_S);
     b += (size_t)(4 * smax + 1) * (4 * P.dims * smax + 1) * sizeof(TabEntry);
@@ -134,7 +143,7 @@ size_t footprint_bytes(const Params &P)
 }
 
 // Make the per-sweep counter buffer hold global sweeps [series_first, need).
-static int ensure_series(lattice *lt, unsigned long long need)
+int ensure_series(lattice *lt, unsigned long long need)
 {
     const unsigned long long base = (unsigned long long)lt->series_first;
     const unsigned long long slots = need > base ? need - base : 0;
@@ -319,11 +328,12 @@ int create_impl(lattice_t **out, int dims, int L, int two_S, int model, double J
     g.nn = nn;
     g.tab_n = (int)tab.size();
     g.bw = (uint32_t)(((uint32_t)(L / 2) + 31) / 32);
+    g.half = (uint32_t)(L / 2);
+    g.plane = P.N / 2;
 
     cudaError_t e = dev_alloc((void **)&lt->spins[0], (size_t)P.N, st);
-    if (e == cudaSuccess && layout == LAT_INT8) e = dev_alloc((void **)&lt->spins[1], (size_t)P.N, st);
-    if (e == cudaSuccess && model == LAT_NE)
-        e = dev_alloc((void **)&lt->flags, ((P.N + 31) / 32) * 4, st);
+    if (e == cudaSuccess) e = dev_alloc((void **)&lt->spins[1], (size_t)P.N, st);
+    if (e == cudaSuccess && model == LAT_NE) e = dev_alloc((void **)&lt->flags, flag_bytes(P), st);
     if (e == cudaSuccess && layout == LAT_BITPACKED) {
         e = dev_alloc((void **)&lt->bits[0], (size_t)2 * L * g.bw * 4, st);
         if (e == cudaSuccess) e = dev_alloc((void **)&lt->bits[1], (size_t)2 * L * g.bw * 4, st);
@@ -347,7 +357,7 @@ int create_impl(lattice_t **out, int dims, int L, int two_S, int model, double J
 
     e = cudaMemcpyAsync(lt->tab, tab.data(), tab.size() * sizeof(TabEntry), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(lt->ctrl, 0, sizeof(Ctrl), st);
-    if (e == cudaSuccess && lt->flags) e = cudaMemsetAsync(lt->flags, 0, ((P.N + 31) / 32) * 4, st);
+    if (e == cudaSuccess && lt->flags) e = cudaMemsetAsync(lt->flags, 0, flag_bytes(P), st);
     if (e == cudaSuccess) e = launch_init(g, init, P.c, st);
     if (e == cudaSuccess && layout == LAT_BITPACKED) e = launch_pack_bits(g, lt->spins[0], lt->bits[0], st);
     // The host table must outlive the async copy: wait once at creation.
@@ -388,17 +398,20 @@ int lattice_sweep(lattice_t *lt, int64_t n)
     return sweep_impl(lt, n);
 }
 
-// The int8 spins of the current state (for the bit-packed layout, unpacked
-// into the int8 staging buffer first).
-static int current_int8(lattice *lt, int8_t **out)
+// The planar int8 spins of the current state and a scratch buffer of N
+// bytes that is free until the next sweep (the idle half of the double
+// buffer; for the bit-packed layout both int8 buffers are staging).
+static int current_planar(lattice *lt, int8_t **cur, int8_t **scratch)
 {
     const int par = (int)(lt->sweeps & 1);
     if (lt->P.layout == LAT_BITPACKED) {
         cudaError_t e = launch_unpack_bits(lt->geom, lt->bits[par], lt->spins[0], lt->stream);
         if (e != cudaSuccess) return cuda_fail(e, "unpack");
-        *out = lt->spins[0];
+        *cur = lt->spins[0];
+        if (scratch) *scratch = lt->spins[1];
     } else {
-        *out = lt->spins[par];
+        *cur = lt->spins[par];
+        if (scratch) *scratch = lt->spins[par ^ 1];
     }
     return LAT_OK;
 }
@@ -411,7 +424,7 @@ static int current_counters(lattice *lt, long long c[4])
                             4 * sizeof(long long), cudaMemcpyDeviceToHost, lt->stream);
     } else {
         int8_t *cur = nullptr;
-        int rc = current_int8(lt, &cur);
+        int rc = current_planar(lt, &cur, nullptr);
         if (rc != LAT_OK) return rc;
         e = cudaMemsetAsync(lt->scratch4, 0, 4 * sizeof(long long), lt->stream);
         if (e == cudaSuccess) e = launch_measure(lt->geom, cur, lt->scratch4, lt->stream);
@@ -468,10 +481,12 @@ int lattice_series(lattice_t *lt, int64_t first, int64_t count, int64_t *bond, i
 int lattice_get_spins(lattice_t *lt, int8_t *host_out)
 {
     if (lt == nullptr || host_out == nullptr) return LAT_EINVAL;
-    int8_t *cur = nullptr;
-    int rc = current_int8(lt, &cur);
+    int8_t *cur = nullptr, *lin = nullptr;
+    int rc = current_planar(lt, &cur, &lin);
     if (rc != LAT_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(host_out, cur, (size_t)lt->P.N, cudaMemcpyDeviceToHost, lt->stream);
+    cudaError_t e = launch_to_linear(lt->geom, cur, lin, lt->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, lin, (size_t)lt->P.N, cudaMemcpyDeviceToHost, lt->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
     if (e != cudaSuccess) return cuda_fail(e, "get spins");
     return LAT_OK;
@@ -490,17 +505,52 @@ static bool spins_allowed(const Params &P, const int8_t *s)
     return bad == 0;
 }
 
-// Copy host spins into the current-state buffer (packing for bit-packed).
+// Copy host spins (x fastest) into the current-state buffer: upload to the
+// idle buffer, convert to planar (and pack for the bit-packed layout).
 static cudaError_t put_spins(lattice *lt, const int8_t *host_in)
 {
     const int par = (int)(lt->sweeps & 1);
-    if (lt->P.layout == LAT_BITPACKED) {
-        cudaError_t e = cudaMemcpyAsync(lt->spins[0], host_in, (size_t)lt->P.N, cudaMemcpyHostToDevice,
-                                        lt->stream);
-        if (e == cudaSuccess) e = launch_pack_bits(lt->geom, lt->spins[0], lt->bits[par], lt->stream);
-        return e;
+    int8_t *lin = (lt->P.layout == LAT_BITPACKED) ? lt->spins[1] : lt->spins[par ^ 1];
+    int8_t *dst = (lt->P.layout == LAT_BITPACKED) ? lt->spins[0] : lt->spins[par];
+    cudaError_t e = cudaMemcpyAsync(lin, host_in, (size_t)lt->P.N, cudaMemcpyHostToDevice, lt->stream);
+    if (e == cudaSuccess) e = launch_to_planar(lt->geom, lin, dst, lt->stream);
+    if (e == cudaSuccess && lt->P.layout == LAT_BITPACKED)
+        e = launch_pack_bits(lt->geom, dst, lt->bits[par], lt->stream);
+    return e;
+}
+
+// Persistence flags: device bytes (one per Philox group of each colour
+// plane row, bit q = site 4m+q) <-> one host byte per site, x fastest.
+static void flags_to_host(const lattice *lt, const std::vector<uint8_t> &dev, uint8_t *out)
+{
+    const Geom &g = lt->geom;
+    const int L = g.L;
+    for (uint64_t i = 0; i < g.N; ++i) {
+        const int x = (int)(i % (uint64_t)L);
+        const int y = (int)((i / (uint64_t)L) % (uint64_t)L);
+        const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
+        const int c = (x + y + z) & 1;
+        const uint64_t r = (uint64_t)y + (uint64_t)L * (uint64_t)z;
+        const uint32_t j = (uint32_t)x >> 1;
+        const uint8_t f = dev[((uint64_t)c * g.rows + r) * g.G + (j >> g.sh)];
+        out[i] = (uint8_t)((f >> (j & ((1u << g.sh) - 1u))) & 1u);
     }
-    return cudaMemcpyAsync(lt->spins[par], host_in, (size_t)lt->P.N, cudaMemcpyHostToDevice, lt->stream);
+}
+
+static void flags_from_host(const lattice *lt, const uint8_t *in, std::vector<uint8_t> &dev)
+{
+    const Geom &g = lt->geom;
+    const int L = g.L;
+    for (uint64_t i = 0; i < g.N; ++i) {
+        if (!in[i]) continue;
+        const int x = (int)(i % (uint64_t)L);
+        const int y = (int)((i / (uint64_t)L) % (uint64_t)L);
+        const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
+        const int c = (x + y + z) & 1;
+        const uint64_t r = (uint64_t)y + (uint64_t)L * (uint64_t)z;
+        const uint32_t j = (uint32_t)x >> 1;
+        dev[((uint64_t)c * g.rows + r) * g.G + (j >> g.sh)] |= (uint8_t)(1u << (j & ((1u << g.sh) - 1u)));
+    }
 }
 
 int lattice_set_spins(lattice_t *lt, const int8_t *host_in)
@@ -522,15 +572,16 @@ int lattice_get_state(lattice_t *lt, int8_t *spins, uint8_t *flags, int64_t *swe
         if (rc != LAT_OK) return rc;
     }
     if (flags) {
-        const uint64_t N = lt->P.N;
-        std::vector<uint32_t> bm((N + 31) / 32, 0u);
         if (lt->flags) {
-            cudaError_t e = cudaMemcpyAsync(bm.data(), lt->flags, bm.size() * 4, cudaMemcpyDeviceToHost,
+            std::vector<uint8_t> dev(flag_bytes(lt->P));
+            cudaError_t e = cudaMemcpyAsync(dev.data(), lt->flags, dev.size(), cudaMemcpyDeviceToHost,
                                             lt->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
             if (e != cudaSuccess) return cuda_fail(e, "get flags");
+            flags_to_host(lt, dev, flags);
+        } else {
+            memset(flags, 0, (size_t)lt->P.N);
         }
-        for (uint64_t i = 0; i < N; ++i) flags[i] = (uint8_t)((bm[i >> 5] >> (i & 31)) & 1u);
     }
     if (sweeps) *sweeps = lt->sweeps;
     return LAT_OK;
@@ -540,20 +591,22 @@ int lattice_set_state(lattice_t *lt, const int8_t *spins, const uint8_t *flags, 
 {
     if (lt == nullptr || spins == nullptr || sweeps < 0) return LAT_EINVAL;
     if (!spins_allowed(lt->P, spins)) return LAT_EINVAL;
-    const uint64_t N = lt->P.N;
-    std::vector<uint32_t> bm((N + 31) / 32, 0u);
-    if (flags)
-        for (uint64_t i = 0; i < N; ++i)
-            if (flags[i]) bm[i >> 5] |= 1u << (i & 31);
+    std::vector<uint8_t> dev;
+    if (lt->flags) {
+        dev.assign(flag_bytes(lt->P), 0u);
+        if (flags) flags_from_host(lt, flags, dev);
+    }
     cudaError_t e = cudaStreamSynchronize(lt->stream);
     const int64_t old_sweeps = lt->sweeps;
     lt->sweeps = sweeps;  // selects the buffer parity put_spins writes
     if (e == cudaSuccess) e = put_spins(lt, spins);
     if (e == cudaSuccess && lt->flags)
-        e = cudaMemcpyAsync(lt->flags, bm.data(), bm.size() * 4, cudaMemcpyHostToDevice, lt->stream);
+        e = cudaMemcpyAsync(lt->flags, dev.data(), dev.size(), cudaMemcpyHostToDevice, lt->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
-    if (e != cudaSuccess) lt->sweeps = old_sweeps;
-    if (e != cudaSuccess) return cuda_fail(e, "set state");
+    if (e != cudaSuccess) {
+        lt->sweeps = old_sweeps;
+        return cuda_fail(e, "set state");
+    }
     // The recorded series restarts at the restored sweep index.
     dev_free(lt->series, lt->stream);
     lt->series = nullptr;

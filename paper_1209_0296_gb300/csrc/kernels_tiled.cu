@@ -1,38 +1,41 @@
 // kernels_tiled.cu -- one launch per sweep for 2D spin-1/2 lattices (Ising
-// and North-East), int8 spins of +-1, L a multiple of 16.
+// and North-East), int8 spins of +-1 in the checkerboard-planar layout,
+// L a multiple of 32.
 //
 // The paper's GPU sweep (§III.A steps 5-8, Fig. 2) copies each sub-lattice
 // with its boundary into shared memory, updates the red+blue sites, ends the
 // kernel as a device-wide barrier, and relaunches for green+white: two
 // launches and two passes over memory per sweep.  Here one launch does the
-// whole sweep: each CTA stages a tile of 256 columns x tile_h rows plus a
-// two-row / one-word halo in shared memory, updates colour 0 on the tile
-// AND on the one-site ring around it (recomputing the ring is legal because
-// every draw is keyed by site group and sweep, so the ring holds bit for
-// bit what the neighbouring tile computes), then updates colour 1 on the
-// tile and writes it to the other spin buffer.  Memory traffic is one read
-// and one write per site per sweep (plus the halo).
+// whole sweep: each CTA stages a tile of 256 columns x tile_h rows of both
+// colour planes plus a two-row / one-word halo in shared memory, updates
+// colour 0 on the tile AND on the one-site ring around it (recomputing the
+// ring is legal because every draw is keyed by site group and sweep, so the
+// ring holds bit for bit what the neighbouring tile computes), then updates
+// colour 1 on the tile.  Results go to the other spin buffer: one read and
+// one write per site per sweep (plus the halo).
 //
-// Work item = one 8-byte word of a row: the four sites of the active colour
-// (bytes p, p+2, p+4, p+6, p = (colour + y) & 1) = one Philox call.  A warp
-// owns one tile row (32 words), so p is warp-uniform and the neighbour bytes
-// are gathered with byte permutes.  Bytes are 0x01 (+1) or 0xFF (-1), so
-// bits 1..7 of a byte all equal "spin down"; the number of down neighbours
-// is formed for four sites at once with a bit-sliced adder, and a scaled
-// table index is assembled with masks only.  The acceptance table is held
-// as t' = thr - 1 (all ones = accept without a draw), so a move is accepted
-// iff u <= t'; lattices whose table has a never-accept entry (thr = 0,
-// possible only for dE/T > 22) use the generic kernel instead.  The Philox
-// call is skipped when none of the four sites needs a draw.
+// Work item = one 4-byte word of a colour plane row = four same-colour
+// sites = one Philox call.  A warp owns one tile row (32 words), so the row
+// parity p is warp-uniform.  In the planar layout the north/south and
+// same-column neighbours of the four sites are the other plane's words at
+// the same index, and the row-shifted neighbours are that word funnel-
+// shifted by one byte.  Bytes are 0x01 (+1) or 0xFF (-1), so bits 1..7 of a
+// byte all equal "spin down": the number of down neighbours of four sites
+// at once comes from a bit-sliced adder, and a scaled table index is
+// assembled with masks only.  The acceptance table is held as t' = thr - 1
+// (all ones = accept without a draw), so a move is accepted iff u <= t';
+// lattices whose table has a never-accept entry (thr = 0, possible only for
+// dE/T > 22) use the generic kernel.  The Philox call is skipped when none
+// of the four sites needs a draw.
 #include "lattice_internal.cuh"
 
 namespace lat {
 
 namespace {
 
-constexpr int kTileW = 256;         // columns (bytes) per tile = 32 words
-constexpr int kWords = kTileW / 8;  // words per tile row (one per lane)
-constexpr int kPitch = kWords + 4;  // smem words per row: pad, halo, 32 words, halo, pad
+constexpr int kTileCols = 256;      // lattice columns per tile
+constexpr int kWords = 32;          // 4-byte words per plane row per tile
+constexpr int kPitch = kWords + 8;  // smem words per plane row: 3 pad, halo, 32, halo, 3 pad
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxTileH = 64;
@@ -44,11 +47,8 @@ struct TiledArgs {
     int off;  // sweep offset relative to ctrl->sweep
 };
 
-LAT_D uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) { return __byte_perm(a, b, sel); }
-
 // Byte permute in PTX's generic mode, where bit 3 of a selector nibble
-// replicates the sign bit of the selected byte over the output byte
-// (__byte_perm uses only the low three bits of each nibble).
+// replicates the sign bit of the selected byte over the output byte.
 LAT_D uint32_t prmt_sign(uint32_t a, uint32_t sel)
 {
     uint32_t r;
@@ -57,61 +57,90 @@ LAT_D uint32_t prmt_sign(uint32_t a, uint32_t sel)
 }
 
 struct Tile {
-    uint2 *w;  // [(tile_h + 4) * kPitch]; word (ry, wx) at (ry+2)*kPitch + wx + 2
-    LAT_D uint2 &at(int ry, int wx) const { return w[(ry + 2) * kPitch + wx + 2]; }
-};
-
-struct Counters {
-    int bond = 0, mag = 0, up = 0, unfl = 0;
-};
-
-// Gather the four sites of parity P of word (ry, wx) and their four
-// neighbours into 4-byte words (byte q <-> site q at byte P + 2q).
-template <int P>
-LAT_D void gather(const Tile &t, int ry, int wx, uint2 &W, uint32_t &S, uint32_t &U, uint32_t &D,
-                  uint32_t &Lf, uint32_t &R)
-{
-    W = t.at(ry, wx);
-    const uint2 Wu = t.at(ry - 1, wx);
-    const uint2 Wd = t.at(ry + 1, wx);
-    if (P == 0) {
-        // sites at bytes 0,2,4,6; left = byte 7 of the previous word, 1, 3, 5; right = 1,3,5,7
-        const uint32_t wl = t.at(ry, wx - 1).y;
-        S = prmt(W.x, W.y, 0x6420u);
-        U = prmt(Wu.x, Wu.y, 0x6420u);
-        D = prmt(Wd.x, Wd.y, 0x6420u);
-        R = prmt(W.x, W.y, 0x7531u);
-        Lf = prmt(wl, prmt(W.x, W.y, 0x0531u), 0x6543u);
-    } else {
-        // sites at bytes 1,3,5,7; left = 0,2,4,6; right = 2,4,6, byte 0 of the next word
-        const uint32_t wr = t.at(ry, wx + 1).x;
-        S = prmt(W.x, W.y, 0x7531u);
-        U = prmt(Wu.x, Wu.y, 0x7531u);
-        D = prmt(Wd.x, Wd.y, 0x7531u);
-        Lf = prmt(W.x, W.y, 0x6420u);
-        R = prmt(Lf, wr, 0x4321u);
+    uint32_t *w;  // [2 planes][tile_h + 4 rows][kPitch]
+    int plane_words;
+    LAT_D uint32_t &at(int c, int ry, int wx) const
+    {
+        return w[c * plane_words + (ry + 2) * kPitch + wx + 4];
     }
+};
+
+// Philox4x32-10 for the counters (g, sweep lo, sweep hi, colour) of one
+// launch.  Words 1..3 of the counter and the key are the same for every
+// item, so round 1's second product and round 2's first product are computed
+// once per thread; an item then costs 2 + 8x2 wide multiplies and 19 XORs.
+struct PhiloxPre {
+    uint32_t A, B;    // round-1 outputs 0 and 1 (independent of g)
+    uint32_t H2, L2;  // round-2 product of A: hi, lo
+    uint32_t k0[10], k1[10];
+};
+
+LAT_D void philox_prepare(PhiloxPre &pp, uint32_t ctr1, uint32_t ctr2, uint32_t key0, uint32_t key1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        pp.k0[r] = key0 + (uint32_t)r * kPhiloxW0;
+        pp.k1[r] = key1 + (uint32_t)r * kPhiloxW1;
+    }
+    uint32_t h1, l1;
+    mul_hi_lo(kPhiloxM1, ctr2, h1, l1);
+    pp.A = h1 ^ ctr1 ^ pp.k0[0];
+    pp.B = l1;
+    mul_hi_lo(kPhiloxM0, pp.A, pp.H2, pp.L2);
 }
 
-// Spread a 4-bit per-site mask to the 8 flag bits of a word (site q of
-// parity P sits at byte P + 2q).
-template <int P>
-LAT_D uint32_t spread_flags(uint32_t a4)
+LAT_D U4 philox_item(const PhiloxPre &pp, uint32_t g, uint32_t colour)
 {
-    const uint32_t s = (a4 & 1u) | ((a4 & 2u) << 1) | ((a4 & 4u) << 2) | ((a4 & 8u) << 3);
-    return s << P;
+    uint32_t h0, l0, h1, l1;
+    // round 1: (g, c1, c2, colour) -> (A, B, hi(M0 g) ^ colour ^ k1, lo(M0 g))
+    mul_hi_lo(kPhiloxM0, g, h0, l0);
+    const uint32_t z1 = h0 ^ colour ^ pp.k1[0];
+    // round 2: (A, B, z1, l0) -> (hi(M1 z1) ^ B ^ k0, lo(M1 z1), H2 ^ l0 ^ k1, L2)
+    mul_hi_lo(kPhiloxM1, z1, h1, l1);
+    U4 c;
+    c.x = h1 ^ pp.B ^ pp.k0[1];
+    c.y = l1;
+    c.z = pp.H2 ^ l0 ^ pp.k1[1];
+    c.w = pp.L2;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        mul_hi_lo(kPhiloxM0, c.x, h0, l0);
+        mul_hi_lo(kPhiloxM1, c.z, h1, l1);
+        U4 n;
+        n.x = h1 ^ c.y ^ pp.k0[r];
+        n.y = l1;
+        n.z = h0 ^ c.w ^ pp.k1[r];
+        n.w = l0;
+        c = n;
+    }
+    return c;
 }
 
-// Update one work item and return the new word.  flags: in, the word's
-// persistence byte; out, with this pass's flips added (North-East).
-// kMeasure (colour-1 pass): accumulate the counters of the final word.
-template <bool kNE, int P, bool kMeasure>
-LAT_D uint2 update(const Tile &t, const uint32_t *sthr, const Geom &g, int ry, int wx, uint32_t grp,
-                   uint32_t ctr1, uint32_t ctr2, uint32_t colour, uint32_t &flags, Counters &cnt)
+// Everything about one work item that does not need its random numbers.
+struct Item {
+    uint32_t S, U, D, Lf, R;  // site bytes and their north, south, west, east neighbours
+    uint32_t t0, t1, t2, t3;  // acceptance thresholds t' (all ones = no draw needed)
+    uint32_t locked;          // North-East: 0xFF bytes at locked sites
+    bool need;
+};
+
+// Gather the four colour-C sites of plane word (ry, wx) whose row has parity
+// P, count their down neighbours and look up their thresholds.
+template <bool kNE, int C, int P>
+LAT_D void prepare(const Tile &t, const uint32_t *sthr, int ry, int wx, Item &it)
 {
-    uint2 W;
-    uint32_t S, U, D, Lf, R;
-    gather<P>(t, ry, wx, W, S, U, D, Lf, R);
+    it.S = t.at(C, ry, wx);
+    const uint32_t O = t.at(1 - C, ry, wx);
+    it.U = t.at(1 - C, ry - 1, wx);  // north, row y-1
+    it.D = t.at(1 - C, ry + 1, wx);  // south, row y+1
+    if (P == 0) {  // x = 2j: left neighbour is j-1 of the other plane, right is j
+        it.Lf = __funnelshift_l(t.at(1 - C, ry, wx - 1), O, 8);
+        it.R = O;
+    } else {       // x = 2j+1: left is j, right is j+1
+        it.Lf = O;
+        it.R = __funnelshift_r(O, t.at(1 - C, ry, wx + 1), 8);
+    }
+    const uint32_t U = it.U, D = it.D, Lf = it.Lf, R = it.R;
     // Bit-sliced count (b2 b1 b0) of down neighbours, valid in bits 1..7 of each byte.
     const uint32_t s1 = U ^ D ^ Lf;
     const uint32_t c1 = (U & D) | (U & Lf) | (D & Lf);
@@ -122,58 +151,39 @@ LAT_D uint2 update(const Tile &t, const uint32_t *sthr, const Geom &g, int ry, i
     // bit 2 = b0, bit 3 = b1, bit 4 = b2, bit 5 = sd.  Every bit 1..7 of a
     // byte carries the same flag, so masks alone place them.
     const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
-                         (S & 0x20202020u);
+                         (it.S & 0x20202020u);
     const char *tb = reinterpret_cast<const char *>(sthr);
-    uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
-    uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
-    uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
-    uint32_t t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
-    uint32_t locked = 0;
+    it.t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
+    it.t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
+    it.t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
+    it.t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
+    it.locked = 0;
     if (kNE) {
         // §III.B: a site may change only if north (U) and east (R) are up.
         // Sign-replicating each byte of (U | R) gives an all-ones mask for a
         // locked site: it then needs no draw, and its flip is masked off.
-        locked = U | R;
-        t0 |= prmt_sign(locked, 0x8888u);
-        t1 |= prmt_sign(locked, 0x9999u);
-        t2 |= prmt_sign(locked, 0xAAAAu);
-        t3 |= prmt_sign(locked, 0xBBBBu);
+        it.locked = U | R;
+        it.t0 |= prmt_sign(it.locked, 0x8888u);
+        it.t1 |= prmt_sign(it.locked, 0x9999u);
+        it.t2 |= prmt_sign(it.locked, 0xAAAAu);
+        it.t3 |= prmt_sign(it.locked, 0xBBBBu);
     }
-    uint32_t acc = 0xFu;
-    if (min(min(t0, t1), min(t2, t3)) != 0xFFFFFFFFu) {
-        const U4 u = philox(U4{grp, ctr1, ctr2, colour}, g.key0, g.key1);
-        acc = (u.x <= t0 ? 1u : 0u) | (u.y <= t1 ? 2u : 0u) | (u.z <= t2 ? 4u : 0u) |
-              (u.w <= t3 ? 8u : 0u);
-    }
+    it.need = (it.t0 & it.t1 & it.t2 & it.t3) != 0xFFFFFFFFu;
+}
+
+// Accept/reject the four sites with their draws u; return the new word.
+template <bool kNE>
+LAT_D uint32_t finish(const Item &it, const U4 &u, uint32_t &changed)
+{
+    const uint32_t acc = (u.x <= it.t0 ? 1u : 0u) | (u.y <= it.t1 ? 2u : 0u) |
+                         (u.z <= it.t2 ? 4u : 0u) | (u.w <= it.t3 ? 8u : 0u);
     // Byte mask 0xFE at each flipped site: +1 (0x01) <-> -1 (0xFF).
     uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu;
     if (kNE) {
-        F &= ~locked;
-        const uint32_t a4 = ((((F >> 1) & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
-        flags |= spread_flags<P>(a4);
+        F &= ~it.locked;
+        changed = ((((F >> 1) & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
     }
-    uint2 Wn;
-    if (P == 0) {
-        Wn.x = W.x ^ prmt(F, 0u, 0x4140u);
-        Wn.y = W.y ^ prmt(F, 0u, 0x4342u);
-    } else {
-        Wn.x = W.x ^ prmt(F, 0u, 0x1404u);
-        Wn.y = W.y ^ prmt(F, 0u, 0x3424u);
-    }
-    if (kMeasure) {
-        // Bond sum over this word's colour-1 sites: s' * (sum of its four
-        // colour-0 neighbours) = 2 * (# equal neighbours) - 4 per site.
-        const uint32_t Sn = S ^ F;
-        const uint32_t M1 = 0x02020202u;
-        const int eq = __popc(~(Sn ^ U) & M1) + __popc(~(Sn ^ D) & M1) +
-                       __popc(~(Sn ^ Lf) & M1) + __popc(~(Sn ^ R) & M1);
-        cnt.bond += 2 * eq - 16;
-        const int downs = __popc(Wn.x & M1) + __popc(Wn.y & M1);
-        cnt.mag += 8 - 2 * downs;
-        cnt.up += 8 - downs;
-        if (kNE) cnt.unfl += 8 - __popc(flags);
-    }
-    return Wn;
+    return it.S ^ F;
 }
 
 LAT_D int wrap(int v, int n)
@@ -183,75 +193,129 @@ LAT_D int wrap(int v, int n)
     return v;
 }
 
-template <bool kNE>
-__global__ void __launch_bounds__(kThreads) k_sweep_tiled(TiledArgs a)
+// Sum of the four bytes of x (each sum fits 16 bits).
+LAT_D int byte_sum(uint32_t x)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t sthr[16];
-    __shared__ int red[kWarps][4];
+    const uint32_t s = (x & 0x00FF00FFu) + ((x >> 8) & 0x00FF00FFu);
+    return (int)((s & 0xFFFFu) + (s >> 16));
+}
 
-    const Geom &g = a.g;
+// Process the colour-C items of rows ry and ry + kWarps (the second only if
+// `two`) at word `lane`: both rows have the same parity, so one warp-uniform
+// branch serves both and their Philox chains interleave.
+template <bool kNE, int C, int P>
+LAT_D void do_pair(const Tile &t, const uint32_t *sthr, const PhiloxPre &pp, int ry, bool two,
+                   bool active, int lane, uint32_t grp_a, uint32_t grp_b, uint32_t &nva,
+                   uint32_t &nvb, Item &a, Item &b, uint32_t &cha, uint32_t &chb)
+{
+    prepare<kNE, C, P>(t, sthr, ry, lane, a);
+    if (two) prepare<kNE, C, P>(t, sthr, ry + kWarps, lane, b);
+    else b.need = false;
+    const bool need = active && (a.need || b.need);
+    // An item that needs no draw has t' = all ones at every site, so any u
+    // accepts exactly as "no draw" would: the warp skips Philox only when no
+    // lane needs it, and otherwise every lane takes the (unused) draws.
+    U4 ua = U4{0u, 0u, 0u, 0u}, ub = ua;
+    if (__any_sync(0xffffffffu, need)) {
+        ua = philox_item(pp, grp_a, (uint32_t)C);
+        if (two) ub = philox_item(pp, grp_b, (uint32_t)C);
+    }
+    nva = finish<kNE>(a, ua, cha);
+    if (two) nvb = finish<kNE>(b, ub, chb);
+}
+
+// One sweep of the tile (bx, by) of lattice g (by the whole CTA).  sthr: the
+// lattice's 16-entry t' table in shared memory.  smem_raw: the tile buffer,
+// sized for tile_h; red: [kWarps][4] ints.  Called by every thread.
+template <bool kNE>
+LAT_D void sweep_tile(const Geom &g, const uint32_t *sthr, int bx, int by, int tile_h, int off,
+                      unsigned char *smem_raw, int (*red)[4])
+{
     const int L = g.L;
-    const int wpr = L >> 3;  // words per lattice row (= Philox groups per row)
-    const int x0 = blockIdx.x * kTileW;
-    const int y0 = blockIdx.y * a.tile_h;
+    const int half = L >> 1;            // sites per plane row
+    const int wpr = L >> 3;             // words per plane row (= Philox groups per row)
+    const int x0 = bx * kTileCols;
+    const int y0 = by * tile_h;
     const int nw = min(kWords, (L - x0) >> 3);
-    const int th = min(a.tile_h, L - y0);
+    const int th = min(tile_h, L - y0);
     const int w0 = x0 >> 3;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool active = lane < nw;
 
     Tile t;
-    t.w = reinterpret_cast<uint2 *>(smem_raw);
-    uint8_t *sflag = smem_raw + (size_t)(a.tile_h + 4) * kPitch * sizeof(uint2);  // [tile_h][32]
+    t.w = reinterpret_cast<uint32_t *>(smem_raw);
+    t.plane_words = (tile_h + 4) * kPitch;
+    uint8_t *sflag0 = smem_raw + (size_t)2 * t.plane_words * 4;  // [tile_h][32], colour-0 flags
 
-    if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
-    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)a.off;
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const int8_t *src = g.s[sweep & 1];
     int8_t *dst = g.s[(sweep + 1) & 1];
-    const uint32_t ctr1 = (uint32_t)sweep, ctr2 = (uint32_t)(sweep >> 32);
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
 
-    // ---- stage rows y0-2 .. y0+th+1: 16-byte interior loads, 8-byte halo words
+    // ---- stage both planes, rows y0-2 .. y0+th+1: 16-byte interior loads + halo words
     const int rows = th + 4;
-    const int n16 = nw >> 1;  // 16-byte chunks per row
-    for (int i = threadIdx.x; i < rows * 16; i += kThreads) {
-        const int r = i >> 4, c = i & 15;
-        if (c >= n16) continue;
+    const int n16 = nw >> 2;  // 16-byte chunks per plane row
+    for (int i = threadIdx.x; i < 2 * rows * 8; i += kThreads) {
+        const int c = i / (rows * 8);
+        const int rem = i - c * rows * 8;
+        const int r = rem >> 3, k = rem & 7;
+        if (k >= n16) continue;
         const int gy = wrap(y0 + r - 2, L);
-        const uint4 v = *reinterpret_cast<const uint4 *>(src + (size_t)gy * L + x0 + 16 * c);
-        *reinterpret_cast<uint4 *>(&t.at(r - 2, 2 * c)) = v;
+        const uint4 v = *reinterpret_cast<const uint4 *>(src + (size_t)c * g.plane +
+                                                         (size_t)gy * half + 4 * (w0 + 4 * k));
+        *reinterpret_cast<uint4 *>(&t.at(c, r - 2, 4 * k)) = v;
     }
-    for (int i = threadIdx.x; i < rows * 2; i += kThreads) {
-        const int r = i >> 1, side = i & 1;
+    for (int i = threadIdx.x; i < 2 * rows * 2; i += kThreads) {
+        const int c = i / (rows * 2);
+        const int rem = i - c * rows * 2;
+        const int r = rem >> 1, side = rem & 1;
         const int gy = wrap(y0 + r - 2, L);
         const int gw = wrap(side ? w0 + nw : w0 - 1, wpr);
-        t.at(r - 2, side ? nw : -1) =
-            *reinterpret_cast<const uint2 *>(src + (size_t)gy * L + 8 * (size_t)gw);
-    }
-    if (kNE) {
-        const uint8_t *fl = reinterpret_cast<const uint8_t *>(g.flags);
-        for (int i = threadIdx.x; i < th * kWords; i += kThreads) {
-            const int r = i >> 5, c = i & 31;
-            if (c < nw) sflag[i] = fl[(((size_t)(y0 + r) * L + x0) >> 3) + c];
-        }
+        t.at(c, r - 2, side ? nw : -1) = *reinterpret_cast<const uint32_t *>(
+            src + (size_t)c * g.plane + (size_t)gy * half + 4 * (size_t)gw);
     }
     __syncthreads();
 
-    Counters cnt;
+    const size_t row_bytes = (size_t)half;
+    Item ia, ib;
+    uint32_t cha = 0, chb = 0, nva = 0, nvb = 0;
 
-    // ---- colour 0 on rows -1..th (the tile and its ring rows), one warp per row
-    for (int ry = warp - 1; ry <= th; ry += kWarps) {
-        if (lane >= nw) continue;
+    // ---- colour 0 on rows -1..th (the tile and its ring rows); warp w takes
+    // rows w-1 and w-1+8, then w-1+16 and w-1+24, ...
+    for (int ry = warp - 1; ry <= th; ry += 2 * kWarps) {
+        const bool two = ry + kWarps <= th;
         const int gy = wrap(y0 + ry, L);
-        const uint32_t grp = (uint32_t)gy * (uint32_t)wpr + (uint32_t)(w0 + lane);
-        const bool inside = ry >= 0 && ry < th;
-        uint32_t fl = (kNE && inside) ? sflag[ry * kWords + lane] : 0u;
-        uint2 nv;
+        const int gyb = wrap(y0 + ry + kWarps, L);
+        const uint32_t ga = (uint32_t)gy * (uint32_t)wpr + (uint32_t)(w0 + lane);
+        const uint32_t gb = (uint32_t)gyb * (uint32_t)wpr + (uint32_t)(w0 + lane);
         if ((gy & 1) == 0)
-            nv = update<kNE, 0, false>(t, sthr, g, ry, lane, grp, ctr1, ctr2, 0u, fl, cnt);
+            do_pair<kNE, 0, 0>(t, sthr, pp, ry, two, active, lane, ga, gb, nva, nvb, ia, ib, cha, chb);
         else
-            nv = update<kNE, 1, false>(t, sthr, g, ry, lane, grp, ctr1, ctr2, 0u, fl, cnt);
-        if (kNE && inside) sflag[ry * kWords + lane] = (uint8_t)fl;
-        t.at(ry, lane) = nv;
+            do_pair<kNE, 0, 1>(t, sthr, pp, ry, two, active, lane, ga, gb, nva, nvb, ia, ib, cha, chb);
+        if (active) {
+            t.at(0, ry, lane) = nva;
+            if (two) t.at(0, ry + kWarps, lane) = nvb;
+            if (ry >= 0 && ry < th) {
+                *reinterpret_cast<uint32_t *>(dst + (size_t)gy * row_bytes + 4 * (size_t)(w0 + lane)) = nva;
+                if (kNE) {
+                    uint8_t *fp = g.flags + (size_t)gy * wpr + w0 + lane;
+                    const uint8_t f = (uint8_t)(*fp | cha);
+                    *fp = f;
+                    sflag0[ry * kWords + lane] = f;
+                }
+            }
+            const int ryb = ry + kWarps;
+            if (two && ryb < th) {
+                *reinterpret_cast<uint32_t *>(dst + (size_t)gyb * row_bytes + 4 * (size_t)(w0 + lane)) = nvb;
+                if (kNE) {
+                    uint8_t *fp = g.flags + (size_t)gyb * wpr + w0 + lane;
+                    const uint8_t f = (uint8_t)(*fp | chb);
+                    *fp = f;
+                    sflag0[ryb * kWords + lane] = f;
+                }
+            }
+        }
     }
     // ---- colour 0 on the edge words: the site at column x0-1 is colour 0 on
     // odd rows (a parity-1 word at wx = -1), the one at x0+8*nw on even rows
@@ -264,37 +328,66 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(TiledArgs a)
             const int gw = wrap(want ? w0 - 1 : w0 + nw, wpr);
             const uint32_t grp = (uint32_t)gy * (uint32_t)wpr + (uint32_t)gw;
             const int wx = want ? -1 : nw;
-            uint32_t fl = 0;
-            uint2 nv;
-            if (want)
-                nv = update<kNE, 1, false>(t, sthr, g, ry, wx, grp, ctr1, ctr2, 0u, fl, cnt);
-            else
-                nv = update<kNE, 0, false>(t, sthr, g, ry, wx, grp, ctr1, ctr2, 0u, fl, cnt);
-            t.at(ry, wx) = nv;
+            if (want) prepare<kNE, 0, 1>(t, sthr, ry, wx, ia);
+            else prepare<kNE, 0, 0>(t, sthr, ry, wx, ia);
+            const U4 u = ia.need ? philox_item(pp, grp, 0u) : U4{0u, 0u, 0u, 0u};
+            t.at(0, ry, wx) = finish<kNE>(ia, u, cha);
         }
     }
     __syncthreads();
 
-    // ---- colour 1 on the tile rows; results go to the other spin buffer
-    for (int ry = warp; ry < th; ry += kWarps) {
-        if (lane >= nw) continue;
-        const int gy = y0 + ry;
-        const uint32_t grp = (uint32_t)gy * (uint32_t)wpr + (uint32_t)(w0 + lane);
-        uint32_t fl = kNE ? (uint32_t)sflag[ry * kWords + lane] : 0u;
-        uint2 nv;
-        if ((gy & 1) == 0)  // colour 1 on an even row sits at odd bytes
-            nv = update<kNE, 1, true>(t, sthr, g, ry, lane, grp, ctr1, ctr2, 1u, fl, cnt);
+    // ---- colour 1 on the tile rows, with the sweep's counters.  Byte-wise
+    // accumulators: ue counts 2 per unequal bond around a colour-1 site, dn
+    // counts 2 per down spin; they are summed once at the end.
+    const uint32_t M1 = 0x02020202u;
+    uint32_t ue = 0, dn = 0;
+    int items = 0, unfl = 0;
+    for (int ry = warp; ry < th; ry += 2 * kWarps) {
+        const bool two = ry + kWarps < th;
+        const int gy = y0 + ry, gyb = y0 + ry + kWarps;
+        const uint32_t ga = (uint32_t)gy * (uint32_t)wpr + (uint32_t)(w0 + lane);
+        const uint32_t gb = (uint32_t)gyb * (uint32_t)wpr + (uint32_t)(w0 + lane);
+        if ((gy & 1) == 0)  // colour 1 on an even row sits at odd columns
+            do_pair<kNE, 1, 1>(t, sthr, pp, ry, two, active, lane, ga, gb, nva, nvb, ia, ib, cha, chb);
         else
-            nv = update<kNE, 0, true>(t, sthr, g, ry, lane, grp, ctr1, ctr2, 1u, fl, cnt);
-        *reinterpret_cast<uint2 *>(dst + (size_t)gy * L + x0 + 8 * lane) = nv;
-        if (kNE) reinterpret_cast<uint8_t *>(g.flags)[(((size_t)gy * L + x0) >> 3) + lane] = (uint8_t)fl;
+            do_pair<kNE, 1, 0>(t, sthr, pp, ry, two, active, lane, ga, gb, nva, nvb, ia, ib, cha, chb);
+        if (active) {
+            *reinterpret_cast<uint32_t *>(dst + g.plane + (size_t)gy * row_bytes + 4 * (size_t)(w0 + lane)) = nva;
+            ue += ((ia.U ^ nva) & M1) + ((ia.D ^ nva) & M1) + ((ia.Lf ^ nva) & M1) + ((ia.R ^ nva) & M1);
+            dn += (nva & M1) + (t.at(0, ry, lane) & M1);
+            ++items;
+            if (kNE) {
+                uint8_t *fp = g.flags + (size_t)g.rows * wpr + (size_t)gy * wpr + w0 + lane;
+                const uint32_t f1 = *fp | cha;
+                *fp = (uint8_t)f1;
+                unfl += 8 - __popc(f1) - __popc((uint32_t)sflag0[ry * kWords + lane]);
+            }
+            if (two) {
+                *reinterpret_cast<uint32_t *>(dst + g.plane + (size_t)gyb * row_bytes + 4 * (size_t)(w0 + lane)) = nvb;
+                ue += ((ib.U ^ nvb) & M1) + ((ib.D ^ nvb) & M1) + ((ib.Lf ^ nvb) & M1) + ((ib.R ^ nvb) & M1);
+                dn += (nvb & M1) + (t.at(0, ry + kWarps, lane) & M1);
+                ++items;
+                if (kNE) {
+                    uint8_t *fp = g.flags + (size_t)g.rows * wpr + (size_t)gyb * wpr + w0 + lane;
+                    const uint32_t f1 = *fp | chb;
+                    *fp = (uint8_t)f1;
+                    unfl += 8 - __popc(f1) - __popc((uint32_t)sflag0[(ry + kWarps) * kWords + lane]);
+                }
+            }
+        }
     }
+    // bond over 4 colour-1 sites = 16 - 2 * (# unequal bonds); mag and up
+    // over the 8 sites of the two plane words.
+    const int d2 = byte_sum(dn);
+    const int bond = 16 * items - byte_sum(ue);
+    const int mag = 8 * items - d2;
+    const int up = 8 * items - (d2 >> 1);
 
     // ---- per-sweep counters: warp reduce, then one atomic per CTA and counter
-    const int rb = __reduce_add_sync(0xffffffffu, cnt.bond);
-    const int rm = __reduce_add_sync(0xffffffffu, cnt.mag);
-    const int ru = __reduce_add_sync(0xffffffffu, cnt.up);
-    const int rf = kNE ? __reduce_add_sync(0xffffffffu, cnt.unfl) : 0;
+    const int rb = __reduce_add_sync(0xffffffffu, bond);
+    const int rm = __reduce_add_sync(0xffffffffu, mag);
+    const int ru = __reduce_add_sync(0xffffffffu, up);
+    const int rf = kNE ? __reduce_add_sync(0xffffffffu, unfl) : 0;
     if (lane == 0) {
         red[warp][0] = rb;
         red[warp][1] = rm;
@@ -310,20 +403,69 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(TiledArgs a)
     }
 }
 
+size_t tile_smem_bytes(int tile_h) { return (size_t)2 * (tile_h + 4) * kPitch * 4 + (size_t)tile_h * kWords; }
+
+template <bool kNE>
+__global__ void __launch_bounds__(kThreads) k_sweep_tiled(TiledArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kWarps][4];
+    if (threadIdx.x < 16) sthr[threadIdx.x] = a.g.thr16[threadIdx.x];
+    sweep_tile<kNE>(a.g, sthr, blockIdx.x, blockIdx.y, a.tile_h, a.off, smem_raw, red);
+}
+
+// Batched sweep: a persistent grid works through a list of (lattice, tile)
+// items of many lattices, one sweep each, taking items from a shared
+// counter.  Each lattice keeps its own parameters, table, seed and sweep
+// counter (its Geom in device memory), so every tile computes exactly what
+// its lattice's own launch would.  Tiles of one lattice are independent
+// within a sweep (they read one buffer and write the other).
+__global__ void __launch_bounds__(kThreads) k_batch_tiled(const Geom *geoms, const uint2 *items,
+                                                         int n_items, unsigned *next_item, int tile_h,
+                                                         int off)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Geom sg;
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kWarps][4];
+    __shared__ int cur;
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = cur;
+        if (it >= n_items) break;
+        const uint2 w = items[it];
+        if (threadIdx.x < sizeof(Geom) / 4)
+            reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
+                reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
+        __syncthreads();
+        const int tiles_x = (sg.L + kTileCols - 1) / kTileCols;
+        const int bx = (int)(w.y % (unsigned)tiles_x), by = (int)(w.y / (unsigned)tiles_x);
+        if (sg.model == LAT_NE)
+            sweep_tile<true>(sg, sthr, bx, by, tile_h, off, smem_raw, red);
+        else
+            sweep_tile<false>(sg, sthr, bx, by, tile_h, off, smem_raw, red);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int default_tile_h() { return kDefTileH; }
 
 bool tile_shape_ok(int tile_w, int tile_h)
 {
-    if (tile_w != 0 && tile_w != kTileW) return false;
+    if (tile_w != 0 && tile_w != kTileCols) return false;
     if (tile_h != 0 && (tile_h < 2 || tile_h > kMaxTileH)) return false;
     return true;
 }
 
 bool tiled_supported(const Geom &g)
 {
-    if (!(g.dims == 2 && g.two_S == 1 && g.bits[0] == nullptr && (g.L % 16) == 0)) return false;
+    if (!(g.dims == 2 && g.two_S == 1 && g.bits[0] == nullptr && (g.L % 32) == 0)) return false;
     // Every non-always entry must have thr >= 1 (t' = thr - 1 >= 0).
     for (int k = 0; k < 16; ++k) {
         if ((k & 7) > 4) continue;
@@ -342,8 +484,8 @@ cudaError_t launch_sweep_tiled(const Geom &g, int tile_w, int tile_h, int off, c
     // Kernel-side table: t' = thr - 1, all ones = accept without a draw.
     for (int k = 0; k < 16; ++k)
         a.g.thr16[k] = ((g.always16 >> k) & 1u) ? 0xFFFFFFFFu : g.thr16[k] - 1u;
-    const size_t smem = (size_t)(a.tile_h + 4) * kPitch * sizeof(uint2) + (size_t)a.tile_h * kWords;
-    dim3 grid((unsigned)((g.L + kTileW - 1) / kTileW), (unsigned)((g.L + a.tile_h - 1) / a.tile_h));
+    const size_t smem = tile_smem_bytes(a.tile_h);
+    dim3 grid((unsigned)((g.L + kTileCols - 1) / kTileCols), (unsigned)((g.L + a.tile_h - 1) / a.tile_h));
     if (g.model == LAT_NE) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_sweep_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -354,6 +496,43 @@ cudaError_t launch_sweep_tiled(const Geom &g, int tile_w, int tile_h, int off, c
         k_sweep_tiled<false><<<grid, kThreads, smem, st>>>(a);
     }
     return cudaGetLastError();
+}
+
+// Kernel-side copy of a lattice's description for the batched kernel: the
+// compact table in t' = thr - 1 form.
+Geom tiled_geom(const Geom &g)
+{
+    Geom k = g;
+    for (int i = 0; i < 16; ++i)
+        k.thr16[i] = ((g.always16 >> i) & 1u) ? 0xFFFFFFFFu : g.thr16[i] - 1u;
+    return k;
+}
+
+int tiles_of(const Geom &g, int tile_h)
+{
+    const int th = tile_h ? tile_h : kDefTileH;
+    return ((g.L + kTileCols - 1) / kTileCols) * ((g.L + th - 1) / th);
+}
+
+cudaError_t launch_batch_tiled(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                               int tile_h, int off, int grid, cudaStream_t st)
+{
+    const int th = tile_h ? tile_h : kDefTileH;
+    const size_t smem = tile_smem_bytes(th);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_batch_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch_tiled<<<grid, kThreads, smem, st>>>(geoms, items, n_items, next_item, th, off);
+    return cudaGetLastError();
+}
+
+int batch_tiled_grid()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_tiled, kThreads, tile_smem_bytes(kDefTileH));
+    if (per < 1) per = 1;
+    return sms * per;
 }
 
 }  // namespace lat

@@ -28,6 +28,7 @@ int create_impl(struct ::lattice **out, int dims, int L, int two_S, int model, d
                 double T_or_c, uint64_t seed, int init, int layout, void *cuda_stream);
 int sweep_impl(struct ::lattice *lt, int64_t n);
 int choose_kernel(const struct ::lattice *lt);
+int ensure_series(struct ::lattice *lt, unsigned long long need);
 bool tile_shape_ok(int tile_w, int tile_h);
 int default_tile_h();
 void compact_table(Geom &g, const TabEntry *host_tab);
@@ -49,7 +50,7 @@ struct lattice {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int8_t *spins[2] = {nullptr, nullptr};   // int8 layout: double buffer; bit-packed: [0] = staging
-    uint32_t *flags = nullptr;
+    uint8_t *flags = nullptr;      // North-East persistence bytes (see Geom)
     uint32_t *bits[2] = {nullptr, nullptr};
     lat::TabEntry *tab = nullptr;
     lat::Ctrl *ctrl = nullptr;

@@ -33,16 +33,13 @@ struct U4 {
     uint32_t x, y, z, w;
 };
 
+// 32 x 32 -> 64-bit product as one wide multiply (a single IMAD.WIDE on
+// the GPU rather than a low and a high multiply).
 LAT_HD void mul_hi_lo(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo)
 {
-#if defined(__CUDA_ARCH__)
-    lo = a * b;
-    hi = __umulhi(a, b);
-#else
-    uint64_t p = (uint64_t)a * (uint64_t)b;
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
     lo = (uint32_t)p;
     hi = (uint32_t)(p >> 32);
-#endif
 }
 
 LAT_HD U4 philox(U4 c, uint32_t k0, uint32_t k1)
@@ -109,19 +106,36 @@ struct Geom {
     int dsmax, nmax, nn, tab_n;
     const TabEntry *tab;  // [nds * nn], nds = 2*dsmax+1
     // Spins are double-buffered: after t sweeps the state is in s[t & 1]
-    // (int8 layout: N spins, x fastest) or bits[t & 1] (bit-packed layout:
-    // [2 colours][L rows][bw] words).  A sweep reads one buffer and writes
-    // the other, so no CTA can see a neighbour's half-finished sweep.
+    // (int8 layout) or bits[t & 1] (bit-packed layout).  A sweep reads one
+    // buffer and writes the other, so no CTA can see a neighbour's
+    // half-finished sweep.
+    //
+    // int8 layout is checkerboard-planar: plane c (colour c), row
+    // r = y + L*z, index j = x >> 1 holds the spin at x = 2j + ((c+y+z)&1):
+    //   s[buf][c * (N/2) + r * (L/2) + j].
+    // Bit-packed layout: bits[buf][(c * L + y) * bw + (j >> 5)] bit (j & 31).
     int8_t *s[2];
     uint32_t *bits[2];
     uint32_t bw;          // bit-packed words per row
-    uint32_t *flags;      // persistence bitmap, bit i = site i (North-East), or null
+    uint32_t half;        // L/2: sites per plane row
+    uint64_t plane;       // N/2: sites per plane
+    // North-East persistence: one byte per Philox group of 4 same-colour
+    // sites, bit q = site 4m+q ever changed: flags[(c * rows + r) * G + m].
+    uint8_t *flags;
     Ctrl *ctrl;
     // Compact acceptance table for 2D spin-1/2 (tiled and bit-packed
     // kernels): index (self down) << 3 | (# down neighbours).
     uint32_t thr16[16];
     uint32_t always16;
 };
+
+// Planar address of site (x, y, z) (coordinates already wrapped).
+LAT_HD uint64_t planar_index(const Geom &g, int x, int y, int z)
+{
+    const int c = (x + y + z) & 1;
+    const uint64_t r = (uint64_t)y + (uint64_t)g.L * (uint64_t)z;
+    return (uint64_t)c * g.plane + r * g.half + (uint64_t)(x >> 1);
+}
 
 // Spin value <-> state index (state 0 = most negative value).
 LAT_HD int spin_of_state(int two_S, int k) { return (two_S & 1) ? 2 * k - two_S : k - (two_S >> 1); }
@@ -165,7 +179,21 @@ cudaError_t launch_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long 
                             unsigned long long base, unsigned long long cap, cudaStream_t st);
 bool tiled_supported(const Geom &g);
 cudaError_t launch_sweep_tiled(const Geom &g, int tile_w, int tile_h, int off, cudaStream_t st);
-cudaError_t launch_pack_bits(const Geom &g, const int8_t *spins, uint32_t *bits, cudaStream_t st);
-cudaError_t launch_unpack_bits(const Geom &g, const uint32_t *bits, int8_t *spins, cudaStream_t st);
+cudaError_t launch_pack_bits(const Geom &g, const int8_t *planar, uint32_t *bits, cudaStream_t st);
+cudaError_t launch_unpack_bits(const Geom &g, const uint32_t *bits, int8_t *planar, cudaStream_t st);
+// planar <-> x-fastest (linear) int8 spins
+cudaError_t launch_to_linear(const Geom &g, const int8_t *planar, int8_t *linear, cudaStream_t st);
+cudaError_t launch_to_planar(const Geom &g, const int8_t *linear, int8_t *planar, cudaStream_t st);
 cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
+// batched engine
+Geom tiled_geom(const Geom &g);
+int tiles_of(const Geom &g, int tile_h);
+int batch_tiled_grid();
+cudaError_t launch_batch_tiled(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                               int tile_h, int off, int grid, cudaStream_t st);
+cudaError_t launch_batch_generic(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                                 int colour, int off, int grid, cudaStream_t st);
+int batch_generic_grid();
+cudaError_t launch_batch_advance(Ctrl *const *ctrls, int n, unsigned *counters, int n_counters,
+                                 unsigned long long k, cudaStream_t st);
 }  // namespace lat

@@ -1,0 +1,103 @@
+"""Batched engine: many uneven lattices advanced together must end bit for
+bit where each would end alone, and where the oracle ends.
+
+Mixed batches cover the one-launch tiled sweep (2D spin-1/2, L % 32 == 0,
+Ising and North-East), the two-launch generic sweep (3D, spin-S, other L),
+lattices dropping out at different sweep counts, and graph replays.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1209_0296_gb300 as lt
+
+pytestmark = pytest.mark.gpu
+
+MIX = [
+    # dims, L, two_S, model, J, h, T_or_c, seed, init, sweeps
+    (2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 70),
+    (2, 96, 1, lt.ISING, 1.0, 0.1, 2.4, 5, lt.INIT_RANDOM, 37),
+    (2, 50, 1, lt.ISING, -0.8, 0.3, 1.9, 6, lt.INIT_RANDOM, 10),
+    (3, 8, 2, lt.ISING, 1.0, 0.0, 3.0, 11, lt.INIT_RANDOM, 64),
+    (3, 6, 3, lt.ISING, 0.7, 0.2, 9.0, 12, lt.INIT_RANDOM, 33),
+    (2, 64, 1, lt.NE, 0.0, 0.0, 0.3, 21, lt.INIT_EQUILIBRIUM, 100),
+    (2, 20, 1, lt.NE, 0.0, 0.0, 0.45, 22, lt.INIT_EQUILIBRIUM, 45),
+    (2, 288, 1, lt.NE, 0.5, -1.0, 1.5, 23, lt.INIT_RANDOM, 9),
+    (2, 32, 1, lt.ISING, 1.0, 0.0, 3.5, 24, lt.INIT_RANDOM, 1),
+]
+
+
+def _make(c):
+    dims, L, two_S, model, J, h, Tc, seed, init, _ = c
+    return lt.Lattice(dims, L, two_S, model, J, h, Tc, seed=seed, init=init)
+
+
+def test_mixed_batch_matches_oracle_and_solo():
+    lats = [_make(c) for c in MIX]
+    b = lt.Batch()
+    for g, c in zip(lats, MIX):
+        b.add(g, c[-1])
+    b.run()
+    b.synchronize()
+    for g, c in zip(lats, MIX):
+        dims, L, two_S, model, J, h, Tc, seed, init, n = c
+        o = oracle.Lattice(dims, L, two_S, model, J, h, Tc, seed=seed, init=init)
+        ser_o = o.sweep(n)
+        spins, flags, done = g.get_state()
+        assert done == n
+        assert np.array_equal(spins, o.spins), c
+        if model == lt.NE:
+            assert np.array_equal(flags, o.flags), c
+        ser = g.series(0, n)
+        for k in ("bond", "mag", "up") + (("unflipped",) if model == lt.NE else ()):
+            assert np.array_equal(ser[k], ser_o[k]), (c, k)
+        # and the same as a solo run of the same lattice
+        solo = _make(c)
+        solo.sweep(n)
+        assert np.array_equal(solo.get_spins(), spins)
+    b.close()
+
+
+def test_batch_then_solo_continues_the_same_chain():
+    c = MIX[0]
+    g = _make(c)
+    b = lt.Batch()
+    b.add(g, 40)
+    b.add(g, 5)          # adds up: 45 sweeps
+    b.run()
+    g.sweep(15)          # continue alone
+    ref = _make(c)
+    ref.sweep(60)
+    assert g.sweeps() == 60
+    assert np.array_equal(g.get_spins(), ref.get_spins())
+    assert np.array_equal(g.series(0, 60)["bond"], ref.series(0, 60)["bond"])
+
+
+def test_three_dimensional_spin_one_batch_full_size():
+    # 3D spin-1, L = 256, T_k = 2 + k * 2/15 (seed 11): four of the sixteen
+    # temperatures batched for one sweep; two checked against the oracle,
+    # all against their solo runs.
+    Ts = [2.0 + k * 2.0 / 15 for k in (0, 5, 10, 15)]
+    lats = [lt.Lattice(3, 256, 2, lt.ISING, 1.0, 0.0, T, seed=11, init=lt.INIT_RANDOM) for T in Ts]
+    b = lt.Batch()
+    for g in lats:
+        b.add(g, 1)
+    b.run()
+    for i, (g, T) in enumerate(zip(lats, Ts)):
+        s = g.get_spins()
+        solo = lt.Lattice(3, 256, 2, lt.ISING, 1.0, 0.0, T, seed=11, init=lt.INIT_RANDOM)
+        solo.sweep(1)
+        assert np.array_equal(s, solo.get_spins())
+        if i in (0, 3):
+            o = oracle.Lattice(3, 256, 2, oracle.ISING, 1.0, 0.0, T, seed=11, init=oracle.INIT_RANDOM)
+            o.sweep(1)
+            assert np.array_equal(s, o.spins)
+
+
+def test_batch_rejects_bitpacked_and_bad_arguments():
+    b = lt.Batch()
+    with pytest.raises(lt.LatticeError):
+        b.add(lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.0, seed=1, layout=lt.BITPACKED), 3)
+    with pytest.raises(lt.LatticeError):
+        b.add(_make(MIX[0]), -1)
+    b.run()  # empty run is a no-op

@@ -57,8 +57,9 @@ def test_2d_spin_half_small(L, T, J, h):
         run_pair(2, L, 1, lt.ISING, J, h, T, 100 + L, lt.INIT_RANDOM, 25, kernel=kernel)
 
 
-@pytest.mark.parametrize("L,tile", [(272, (256, 32)), (528, (256, 32)), (528, (256, 8)),
-                                    (528, (256, 64)), (96, (256, 2)), (4112, (256, 48)), (48, (256, 7))])
+@pytest.mark.parametrize("L,tile", [(288, (256, 32)), (544, (256, 32)), (544, (256, 8)),
+                                    (544, (256, 64)), (96, (256, 2)), (4128, (256, 48)),
+                                    (64, (256, 7)), (32, (256, 64))])
 def test_tiled_ragged_tiles(L, tile):
     n = 12 if L < 4000 else 3
     run_pair(2, L, 1, lt.ISING, 1.0, 0.1, 2.4, 7 + L, lt.INIT_RANDOM, n, kernel=lt.KERNEL_TILED,
@@ -77,7 +78,7 @@ def test_2d_spin_S(two_S):
     run_pair(2, 12, two_S, lt.ISING, 0.9, -0.1, 1.7 * two_S, 5, lt.INIT_RANDOM, 30)
 
 
-@pytest.mark.parametrize("L", [4, 16, 48, 64, 272])
+@pytest.mark.parametrize("L", [4, 16, 48, 64, 288])
 @pytest.mark.parametrize("c", [0.05, 0.3, 0.45, 0.7])
 def test_north_east_c_mode(L, c):
     for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
