@@ -220,30 +220,38 @@ def run_gpu(args):
     updates = world * args.steps * len(TEMPS) * S * L * L
     value = updates / (total_ms * 1e6)
 
-    # Kernel launches per step: per lattice, S sweep kernels plus one
-    # counter-advance kernel per graph replay and per direct remainder.
-    gk = lats[0].sweeps_per_graph()
-    per_lat = S + S // gk + (1 if S % gk else 0)
+    # Kernel launches per step: per lattice, S sweeps (one launch each for the
+    # tiled kernel, two for the wide one) plus one counter-advance kernel per
+    # graph replay and per direct remainder.
+    kinfo = lats[0].get_kernel()
+    gk = kinfo["sweeps_per_graph"]
+    per_sweep = 1 if kinfo["kernel"] == lt.KERNEL_TILED else 2
+    per_lat = per_sweep * S + S // gk + (1 if S % gk else 0)
     launches = args.steps * len(TEMPS) * per_lat
-    sweep_launches = args.steps * len(TEMPS) * S
-    avg_kernel_us = total_ms * 1e3 / (args.steps * len(TEMPS) * S)  # includes the tiny advance kernels
+    sweep_launches = args.steps * len(TEMPS) * S * per_sweep
+    # average duration of one sweep (all its launches; includes the tiny
+    # advance kernels and launch gaps, so this under-reports the kernel rate)
+    avg_kernel_us = total_ms * 1e3 / (args.steps * len(TEMPS) * S)
 
     hbm, _, peak_kind = peaks()
     alg_bytes = 2.0 * L * L  # one int8 read + one int8 write per site per sweep
     achieved = alg_bytes / (avg_kernel_us * 1e-6) / 1e9
-    prof = load_profile_numbers()
+    kname = {lt.KERNEL_TILED: "tiled", lt.KERNEL_WIDE: "wide", lt.KERNEL_GENERIC: "generic"}.get(
+        kinfo["kernel"], "?")
+    prof = load_profile_numbers(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": prof.get("traffic_bytes_per_launch"),
-                "kernel": "k_sweep_tiled<Ising>", "peak_kind": peak_kind + " (copy bandwidth)",
-                "bytes_per_launch": alg_bytes,
-                "avg_launch_us": avg_kernel_us}
-    if prof.get("warp_inst_per_launch"):
+                "frac": achieved / hbm, "traffic": prof.get("traffic_bytes_per_sweep"),
+                "kernel": "k_sweep_tiled<Ising>" if kname == "tiled" else "k_wide_half<Ising> x2",
+                "peak_kind": peak_kind + " (copy bandwidth)",
+                "bytes_per_sweep": alg_bytes,
+                "avg_sweep_us": avg_kernel_us}
+    if prof.get("warp_inst_per_sweep"):
         sm_clk = (clk.summary().get("sm_mhz") or 2070.0) * 1e6
-        inst_rate = prof["warp_inst_per_launch"] / (avg_kernel_us * 1e-6)
+        inst_rate = prof["warp_inst_per_sweep"] / (avg_kernel_us * 1e-6)
         issue_peak = 152 * 4 * sm_clk
         roofline["issue"] = {"bound": "alu", "achieved": inst_rate / 1e12, "peak": issue_peak / 1e12,
                              "unit": "Twarp-inst/s", "frac": inst_rate / issue_peak,
-                             "inst_per_site": prof["warp_inst_per_launch"] * 32 / (L * L)}
+                             "inst_per_site": prof["warp_inst_per_sweep"] * 32 / (L * L)}
 
     # ---- end to end through the C ABI with pinned host buffers ----------
     e2e = None
@@ -289,8 +297,9 @@ def run_gpu(args):
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "lattices": len(TEMPS), "sweeps_per_step": S,
-                           "layout": "int8", "kernel": "tiled one-launch sweep",
-                           "tile": [256, lats[0].tile_h()], "sweeps_per_graph": gk,
+                           "layout": "int8", "kernel": kname + " (autotuned)",
+                           "tile": [256, kinfo["tile_h"]] if kname == "tiled" else None,
+                           "sweeps_per_graph": gk,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MiB write outside the timed events)"},
                 "hbm_roofline_pct": 100.0 * roofline["frac"],
@@ -318,17 +327,19 @@ def run_profile(args):
     else:
         g = lt.Lattice(2, args.profile_L, 1, lt.ISING, 1.0, 0.0, TEMPS[0], seed=SEED,
                        init=lt.INIT_RANDOM)
-    g.set_kernel(lt.KERNEL_AUTO, 0, args.tile_h, 1 << 30)  # direct launches, one per sweep
+    kern = {"auto": lt.KERNEL_AUTO, "tiled": lt.KERNEL_TILED, "wide": lt.KERNEL_WIDE,
+            "generic": lt.KERNEL_GENERIC}[args.profile_kernel]
+    g.set_kernel(kern, 0, args.tile_h, 1 << 30)  # direct launches, no graphs
     g.sweep(args.profile)
     g.synchronize()
     print("profile run: %d sweeps of L=%d (%s), kernel %s" % (args.profile, args.profile_L,
                                                            args.profile_model, g.get_kernel()))
 
 
-def load_profile_numbers():
-    """Per-launch DRAM traffic and instruction count of the dominant kernel,
-    from the committed ncu summary (null when absent)."""
-    path = os.path.join(ROOT, "profiles", "k_sweep_tiled_L4096.txt")
+def load_profile_numbers(kname):
+    """Per-sweep DRAM traffic and instruction count of the chosen kernel,
+    from the committed ncu summary (empty when absent)."""
+    path = os.path.join(ROOT, "profiles", "%s_sweep_ising_L4096.txt" % kname)
     out = {}
     try:
         with open(path) as f:
@@ -363,6 +374,7 @@ def main():
                     help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
     ap.add_argument("--profile-L", type=int, default=L)
     ap.add_argument("--profile-model", default="ising", choices=["ising", "ne"])
+    ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic"])
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -87,8 +87,10 @@ enum lattice_layout {
 enum lattice_kernel {
     LAT_KERNEL_AUTO = 0,    /* library choice (tuned tile shape when eligible) */
     LAT_KERNEL_GENERIC = 1, /* two launches per sweep, one per colour; any model */
-    LAT_KERNEL_TILED = 2    /* one launch per sweep, shared-memory tiles with halo
+    LAT_KERNEL_TILED = 2,   /* one launch per sweep, shared-memory tiles with halo
                                recompute; 2D spin-1/2 (Ising and North-East), L % 32 == 0 */
+    LAT_KERNEL_WIDE = 3     /* two launches per sweep, 16 sites per thread; 2D spin-1/2
+                               (Ising and North-East), L % 32 == 0 */
 };
 
 typedef struct lattice lattice_t;
@@ -220,11 +222,12 @@ void lattice_batch_destroy(lattice_batch_t *b);
 /* Server: continuous batching of independent simulation requests.     */
 /* ------------------------------------------------------------------ */
 typedef struct lattice_request {
-    int dims, L, two_S, model;
+    int dims, L, two_S, model;      /* as lattice_create */
     double J, h, T_or_c;
     uint64_t seed;
     int init;
-    int64_t sweeps;
+    int64_t sweeps;                 /* sweeps to run, >= 0 */
+    int keep_spins;                 /* 1: keep the final spins for lattice_server_poll */
 } lattice_request_t;
 
 typedef struct lattice_result {
@@ -235,11 +238,16 @@ typedef struct lattice_result {
     double t_submit, t_admit, t_done;  /* seconds on the server's clock */
 } lattice_result_t;
 
-/* A server owns one CUDA stream and one scheduler thread.  Requests are
- * admitted while their device footprint fits in hbm_budget_bytes and
- * fewer than max_slots are resident; each scheduling round advances every
- * resident lattice by up to chunk_sweeps sweeps in one batched launch
- * sequence, retiring finished lattices and admitting waiting ones. */
+/* A server owns one CUDA stream (on the device current at creation) and
+ * one scheduler thread.  Requests wait in arrival order and are admitted
+ * while their device footprint fits in hbm_budget_bytes and fewer than
+ * max_slots lattices are resident.  Each scheduling round advances every
+ * resident lattice by up to chunk_sweeps sweeps through the batched engine
+ * (so work of requests that arrived at different times shares launches),
+ * then retires finished lattices (freeing their memory) and admits waiting
+ * requests.  Every result is bit-identical to running its lattice alone.
+ * This is continuous batching in the sense of the spec: admission
+ * happens between rounds, never by stopping resident work. */
 int lattice_server_create(lattice_server_t **out, size_t hbm_budget_bytes, int max_slots,
                           int chunk_sweeps);
 /* Non-blocking; *id identifies the request. LAT_EINVAL for a bad request,

@@ -15,12 +15,12 @@ from ._lib import LatticeError, LatticeRequest, LatticeResult, check, load
 
 __all__ = ["Lattice", "Batch", "Server", "LatticeError", "load", "threshold_table",
            "ISING", "NE", "INIT_COLD", "INIT_RANDOM", "INIT_EQUILIBRIUM", "INT8", "BITPACKED",
-           "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED"]
+           "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED", "KERNEL_WIDE"]
 
 ISING, NE = 0, 1
 INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
 INT8, BITPACKED = 0, 1
-KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED = 0, 1, 2
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_WIDE = 0, 1, 2, 3
 
 
 def _stream_handle(stream) -> int:
@@ -225,9 +225,9 @@ class Server:
         self._h = h
 
     def submit(self, dims=2, L=64, two_S=1, model=ISING, J=1.0, h=0.0, T_or_c=2.269185, seed=0,
-               init=INIT_RANDOM, sweeps=1000) -> int:
+               init=INIT_RANDOM, sweeps=1000, keep_spins=False) -> int:
         req = LatticeRequest(dims, L, two_S, model, float(J), float(h), float(T_or_c),
-                             int(seed) & (2**64 - 1), init, int(sweeps))
+                             int(seed) & (2**64 - 1), init, int(sweeps), 1 if keep_spins else 0)
         rid = ctypes.c_uint64()
         check(self._lib.lattice_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)),
               "lattice_server_submit")

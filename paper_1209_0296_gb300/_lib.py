@@ -22,7 +22,7 @@ c_int, c_int64, c_uint64, c_double, c_void_p, c_size_t = (
 class LatticeRequest(ctypes.Structure):
     _fields_ = [("dims", c_int), ("L", c_int), ("two_S", c_int), ("model", c_int),
                 ("J", c_double), ("h", c_double), ("T_or_c", c_double),
-                ("seed", c_uint64), ("init", c_int), ("sweeps", c_int64)]
+                ("seed", c_uint64), ("init", c_int), ("sweeps", c_int64), ("keep_spins", c_int)]
 
 
 class LatticeResult(ctypes.Structure):

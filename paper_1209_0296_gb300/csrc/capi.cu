@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -194,6 +195,10 @@ int choose_kernel(const lattice *lt)
 {
     if (lt->P.layout == LAT_BITPACKED) return LAT_KERNEL_AUTO;  // bit-packed path
     if (lt->kernel == LAT_KERNEL_GENERIC) return LAT_KERNEL_GENERIC;
+    if (lt->kernel == LAT_KERNEL_TILED && tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
+    if (lt->kernel == LAT_KERNEL_WIDE && wide_supported(lt->geom)) return LAT_KERNEL_WIDE;
+    if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel != 0) return lt->tuned_kernel;
+    if (wide_supported(lt->geom)) return LAT_KERNEL_WIDE;
     if (tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
     return LAT_KERNEL_GENERIC;
 }
@@ -209,6 +214,8 @@ int enqueue_sweeps(lattice *lt, int k, cudaStream_t st)
             e = launch_sweep_bitpacked(lt->geom, off, st);
         } else if (kern == LAT_KERNEL_TILED) {
             e = launch_sweep_tiled(lt->geom, lt->tile_w, lt->tile_h, off, st);
+        } else if (kern == LAT_KERNEL_WIDE) {
+            e = launch_sweep_wide(lt->geom, off, st);
         } else {
             e = launch_half_sweep_generic(lt->geom, 0, off, st);
             if (e == cudaSuccess) e = launch_half_sweep_generic(lt->geom, 1, off, st);
@@ -248,6 +255,80 @@ static int ensure_graph(lattice *lt)
     return LAT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner for LAT_KERNEL_AUTO on 2D spin-1/2 lattices: the first sweep call
+// with enough sweeps times a few of them with each candidate (the wide
+// two-launch kernel, the tiled one-launch kernel at two tile heights) and
+// keeps the fastest.  The timed sweeps are the caller's own sweeps: every
+// kernel produces the same bits, so tuning changes no result.  Choices are
+// cached per (model, L) for the life of the process.
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneChoice {
+    int kernel, tile_h;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, TuneChoice> g_tune;
+constexpr int kTuneSweeps = 3;
+}  // namespace
+
+static int autotune(lattice *lt, int64_t &left)
+{
+    const std::pair<int, int> key(lt->P.model, lt->P.L);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            lt->tuned_kernel = it->second.kernel;
+            if (lt->tile_h == 0) lt->tile_h = it->second.tile_h;
+            return LAT_OK;
+        }
+    }
+    const TuneChoice cands[] = {{LAT_KERNEL_WIDE, 0}, {LAT_KERNEL_TILED, 64}, {LAT_KERNEL_TILED, 32}};
+    const int n_c = (int)(sizeof cands / sizeof cands[0]);
+    if (left < (int64_t)(n_c * (kTuneSweeps + 1))) return LAT_OK;  // too short to tune now
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return LAT_OK;
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return LAT_OK;
+    }
+    float best = 1e30f;
+    TuneChoice pick = cands[0];
+    const int keep_tile = lt->tile_h;
+    for (int c = 0; c < n_c; ++c) {
+        lt->tuned_kernel = cands[c].kernel;
+        lt->tile_h = cands[c].tile_h;
+        // one untimed sweep (first launch of this kernel), then the timed ones
+        int rc = enqueue_sweeps(lt, 1, lt->stream);
+        if (rc == LAT_OK && cudaEventRecord(ev[0], lt->stream) != cudaSuccess) rc = LAT_ECUDA;
+        if (rc == LAT_OK) rc = enqueue_sweeps(lt, kTuneSweeps, lt->stream);
+        if (rc == LAT_OK && cudaEventRecord(ev[1], lt->stream) != cudaSuccess) rc = LAT_ECUDA;
+        if (rc == LAT_OK && cudaEventSynchronize(ev[1]) != cudaSuccess) rc = LAT_ECUDA;
+        float ms = 0.f;
+        if (rc == LAT_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) rc = LAT_ECUDA;
+        if (rc != LAT_OK) {
+            cudaEventDestroy(ev[0]);
+            cudaEventDestroy(ev[1]);
+            return rc;
+        }
+        lt->sweeps += kTuneSweeps + 1;
+        left -= kTuneSweeps + 1;
+        if (ms < best) {
+            best = ms;
+            pick = cands[c];
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    lt->tuned_kernel = pick.kernel;
+    lt->tile_h = keep_tile ? keep_tile : pick.tile_h;
+    lt->graph_valid = false;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = pick;
+    return LAT_OK;
+}
+
 int sweep_impl(lattice *lt, int64_t n)
 {
     if (n < 0) return LAT_EINVAL;
@@ -255,6 +336,14 @@ int sweep_impl(lattice *lt, int64_t n)
     int rc = ensure_series(lt, (unsigned long long)(lt->sweeps + n));
     if (rc != LAT_OK) return rc;
     int64_t left = n;
+    if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel == 0 && lt->P.layout == LAT_INT8 &&
+        wide_supported(lt->geom) && tiled_supported(lt->geom)) {
+        const int64_t before = lt->sweeps;
+        rc = autotune(lt, left);
+        if (rc != LAT_OK) return rc;
+        n -= lt->sweeps - before;   // sweeps already done (and counted) by the tuner
+        if (left == 0) return LAT_OK;
+    }
     const int gk = lt->graph_sweeps;
     if (gk > 0 && left >= gk) {
         rc = ensure_graph(lt);
@@ -330,6 +419,17 @@ int create_impl(lattice_t **out, int dims, int L, int two_S, int model, double J
     g.bw = (uint32_t)(((uint32_t)(L / 2) + 31) / 32);
     g.half = (uint32_t)(L / 2);
     g.plane = P.N / 2;
+    compact_table(g, tab.data());
+    // The bit-packed kernel needs whole 32-site words per plane row and a
+    // table without never-accept entries.
+    if (layout == LAT_BITPACKED) {
+        Geom probe = g;
+        probe.bits[0] = reinterpret_cast<uint32_t *>(1);
+        if (!bitpacked_supported(probe)) {
+            delete lt;
+            return LAT_ENOTSUP;
+        }
+    }
 
     cudaError_t e = dev_alloc((void **)&lt->spins[0], (size_t)P.N, st);
     if (e == cudaSuccess) e = dev_alloc((void **)&lt->spins[1], (size_t)P.N, st);
@@ -351,7 +451,6 @@ int create_impl(lattice_t **out, int dims, int L, int two_S, int model, double J
     g.bits[0] = lt->bits[0];
     g.bits[1] = lt->bits[1];
     g.flags = lt->flags;
-    compact_table(g, tab.data());
     g.tab = lt->tab;
     g.ctrl = lt->ctrl;
 
@@ -644,9 +743,10 @@ int lattice_device_spins(lattice_t *lt, void **dev_ptr, size_t *bytes)
 int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sweeps_per_graph)
 {
     if (lt == nullptr) return LAT_EINVAL;
-    if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_TILED) return LAT_EINVAL;
+    if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_WIDE) return LAT_EINVAL;
     if (tile_w < 0 || tile_h < 0 || sweeps_per_graph < 0) return LAT_EINVAL;
     if (kernel == LAT_KERNEL_TILED && !tiled_supported(lt->geom)) return LAT_ENOTSUP;
+    if (kernel == LAT_KERNEL_WIDE && !wide_supported(lt->geom)) return LAT_ENOTSUP;
     if (!tile_shape_ok(tile_w, tile_h)) return LAT_EINVAL;
     lt->kernel = kernel;
     lt->tile_w = tile_w;

@@ -65,57 +65,6 @@ struct Tile {
     }
 };
 
-// Philox4x32-10 for the counters (g, sweep lo, sweep hi, colour) of one
-// launch.  Words 1..3 of the counter and the key are the same for every
-// item, so round 1's second product and round 2's first product are computed
-// once per thread; an item then costs 2 + 8x2 wide multiplies and 19 XORs.
-struct PhiloxPre {
-    uint32_t A, B;    // round-1 outputs 0 and 1 (independent of g)
-    uint32_t H2, L2;  // round-2 product of A: hi, lo
-    uint32_t k0[10], k1[10];
-};
-
-LAT_D void philox_prepare(PhiloxPre &pp, uint32_t ctr1, uint32_t ctr2, uint32_t key0, uint32_t key1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        pp.k0[r] = key0 + (uint32_t)r * kPhiloxW0;
-        pp.k1[r] = key1 + (uint32_t)r * kPhiloxW1;
-    }
-    uint32_t h1, l1;
-    mul_hi_lo(kPhiloxM1, ctr2, h1, l1);
-    pp.A = h1 ^ ctr1 ^ pp.k0[0];
-    pp.B = l1;
-    mul_hi_lo(kPhiloxM0, pp.A, pp.H2, pp.L2);
-}
-
-LAT_D U4 philox_item(const PhiloxPre &pp, uint32_t g, uint32_t colour)
-{
-    uint32_t h0, l0, h1, l1;
-    // round 1: (g, c1, c2, colour) -> (A, B, hi(M0 g) ^ colour ^ k1, lo(M0 g))
-    mul_hi_lo(kPhiloxM0, g, h0, l0);
-    const uint32_t z1 = h0 ^ colour ^ pp.k1[0];
-    // round 2: (A, B, z1, l0) -> (hi(M1 z1) ^ B ^ k0, lo(M1 z1), H2 ^ l0 ^ k1, L2)
-    mul_hi_lo(kPhiloxM1, z1, h1, l1);
-    U4 c;
-    c.x = h1 ^ pp.B ^ pp.k0[1];
-    c.y = l1;
-    c.z = pp.H2 ^ l0 ^ pp.k1[1];
-    c.w = pp.L2;
-#pragma unroll
-    for (int r = 2; r < 10; ++r) {
-        mul_hi_lo(kPhiloxM0, c.x, h0, l0);
-        mul_hi_lo(kPhiloxM1, c.z, h1, l1);
-        U4 n;
-        n.x = h1 ^ c.y ^ pp.k0[r];
-        n.y = l1;
-        n.z = h0 ^ c.w ^ pp.k1[r];
-        n.w = l0;
-        c = n;
-    }
-    return c;
-}
-
 // Everything about one work item that does not need its random numbers.
 struct Item {
     uint32_t S, U, D, Lf, R;  // site bytes and their north, south, west, east neighbours

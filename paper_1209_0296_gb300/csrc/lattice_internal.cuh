@@ -63,6 +63,62 @@ LAT_HD U4 philox(U4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// Philox4x32-10 for counters (g, c1, c2, c3) whose words 1..3 and key are
+// fixed for a whole launch (sweep and colour): round 1's product of c2 and
+// round 2's product of the round-1 word 0 do not depend on g, so they are
+// computed once per thread; an item then costs 18 wide products and 19
+// XORs.  Same rounds, constants and key schedule as philox() above.
+struct PhiloxPre {
+    uint32_t A, B;    // round-1 outputs 0 and 1
+    uint32_t H2, L2;  // round-2 product of A: hi, lo
+    uint32_t k0[10], k1[10];
+};
+
+LAT_HD void philox_prepare(PhiloxPre &pp, uint32_t ctr1, uint32_t ctr2, uint32_t key0, uint32_t key1)
+{
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int r = 0; r < 10; ++r) {
+        pp.k0[r] = key0 + (uint32_t)r * kPhiloxW0;
+        pp.k1[r] = key1 + (uint32_t)r * kPhiloxW1;
+    }
+    uint32_t h1, l1;
+    mul_hi_lo(kPhiloxM1, ctr2, h1, l1);
+    pp.A = h1 ^ ctr1 ^ pp.k0[0];
+    pp.B = l1;
+    mul_hi_lo(kPhiloxM0, pp.A, pp.H2, pp.L2);
+}
+
+LAT_HD U4 philox_item(const PhiloxPre &pp, uint32_t g, uint32_t c3)
+{
+    uint32_t h0, l0, h1, l1;
+    // round 1: (g, c1, c2, c3) -> (A, B, hi(M0 g) ^ c3 ^ k1, lo(M0 g))
+    mul_hi_lo(kPhiloxM0, g, h0, l0);
+    const uint32_t z1 = h0 ^ c3 ^ pp.k1[0];
+    // round 2: (A, B, z1, l0) -> (hi(M1 z1) ^ B ^ k0, lo(M1 z1), H2 ^ l0 ^ k1, L2)
+    mul_hi_lo(kPhiloxM1, z1, h1, l1);
+    U4 c;
+    c.x = h1 ^ pp.B ^ pp.k0[1];
+    c.y = l1;
+    c.z = pp.H2 ^ l0 ^ pp.k1[1];
+    c.w = pp.L2;
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int r = 2; r < 10; ++r) {
+        mul_hi_lo(kPhiloxM0, c.x, h0, l0);
+        mul_hi_lo(kPhiloxM1, c.z, h1, l1);
+        U4 n;
+        n.x = h1 ^ c.y ^ pp.k0[r];
+        n.y = l1;
+        n.z = h0 ^ c.w ^ pp.k1[r];
+        n.w = l0;
+        c = n;
+    }
+    return c;
+}
+
 LAT_HD uint32_t word_of(const U4 &v, int k)
 {
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
@@ -185,6 +241,13 @@ cudaError_t launch_unpack_bits(const Geom &g, const uint32_t *bits, int8_t *plan
 cudaError_t launch_to_linear(const Geom &g, const int8_t *planar, int8_t *linear, cudaStream_t st);
 cudaError_t launch_to_planar(const Geom &g, const int8_t *linear, int8_t *planar, cudaStream_t st);
 cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
+bool bitpacked_supported(const Geom &g);
+bool wide_supported(const Geom &g);
+cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st);
+cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                              int colour, int grid, cudaStream_t st);
+int batch_wide_grid();
+int wide_chunks(const Geom &g);
 // batched engine
 Geom tiled_geom(const Geom &g);
 int tiles_of(const Geom &g, int tile_h);

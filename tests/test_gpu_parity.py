@@ -45,6 +45,11 @@ def test_config_L64_cold_1000_sweeps_tiled():
     run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 1000)
 
 
+def test_config_L64_cold_1000_sweeps_wide():
+    run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 1000,
+             kernel=lt.KERNEL_WIDE)
+
+
 def test_config_L64_cold_1000_sweeps_generic():
     run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 1000,
              kernel=lt.KERNEL_GENERIC)
@@ -53,7 +58,7 @@ def test_config_L64_cold_1000_sweeps_generic():
 @pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 16, 32, 48])
 @pytest.mark.parametrize("T,J,h", [(1.5, 1.0, 0.0), (2.269185, 1.0, 0.2), (3.5, -0.8, -0.3)])
 def test_2d_spin_half_small(L, T, J, h):
-    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
+    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO) + ((lt.KERNEL_TILED,) if L % 32 == 0 else ()):
         run_pair(2, L, 1, lt.ISING, J, h, T, 100 + L, lt.INIT_RANDOM, 25, kernel=kernel)
 
 
@@ -64,6 +69,13 @@ def test_tiled_ragged_tiles(L, tile):
     n = 12 if L < 4000 else 3
     run_pair(2, L, 1, lt.ISING, 1.0, 0.1, 2.4, 7 + L, lt.INIT_RANDOM, n, kernel=lt.KERNEL_TILED,
              tile=tile)
+
+
+@pytest.mark.parametrize("L", [32, 64, 96, 288, 4128])
+def test_wide_sizes(L):
+    n = 12 if L < 4000 else 3
+    run_pair(2, L, 1, lt.ISING, 1.0, 0.1, 2.4, 9 + L, lt.INIT_RANDOM, n, kernel=lt.KERNEL_WIDE)
+    run_pair(2, L, 1, lt.NE, 0.0, 0.0, 0.35, 9 + L, lt.INIT_EQUILIBRIUM, n, kernel=lt.KERNEL_WIDE)
 
 
 @pytest.mark.parametrize("two_S", [1, 2, 3, 4, 8])
@@ -81,13 +93,13 @@ def test_2d_spin_S(two_S):
 @pytest.mark.parametrize("L", [4, 16, 48, 64, 288])
 @pytest.mark.parametrize("c", [0.05, 0.3, 0.45, 0.7])
 def test_north_east_c_mode(L, c):
-    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
+    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO) + ((lt.KERNEL_TILED,) if L % 32 == 0 else ()):
         run_pair(2, L, 1, lt.NE, 0.0, 0.0, c, 21 + L, lt.INIT_EQUILIBRIUM, 30, kernel=kernel)
 
 
 @pytest.mark.parametrize("L", [8, 32, 64])
 def test_north_east_temperature_mode(L):
-    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO):
+    for kernel in (lt.KERNEL_GENERIC, lt.KERNEL_AUTO) + ((lt.KERNEL_TILED,) if L % 32 == 0 else ()):
         run_pair(2, L, 1, lt.NE, 0.5, -1.0, 1.5, 3, lt.INIT_RANDOM, 30, kernel=kernel)
 
 
@@ -155,9 +167,10 @@ def test_allocation_failure_is_reported():
 
 # ---- full sizes, in the launch configuration the benchmark times ----------
 
-def test_full_size_2d_L4096_random_tiled():
+@pytest.mark.parametrize("kernel", [lt.KERNEL_TILED, lt.KERNEL_WIDE])
+def test_full_size_2d_L4096_random(kernel):
     # 2D Ising spin-1/2, L=4096, T=2.0, random +-1 start (seed 7).
-    run_pair(2, 4096, 1, lt.ISING, 1.0, 0.0, 2.0, 7, lt.INIT_RANDOM, 4)
+    run_pair(2, 4096, 1, lt.ISING, 1.0, 0.0, 2.0, 7, lt.INIT_RANDOM, 3, kernel=kernel)
 
 
 def test_full_size_3d_L256_spin_one():
@@ -165,8 +178,9 @@ def test_full_size_3d_L256_spin_one():
     run_pair(3, 256, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, 11, lt.INIT_RANDOM, 1)
 
 
-def test_full_size_north_east_L8192():
-    run_pair(2, 8192, 1, lt.NE, 0.0, 0.0, 0.3, 21, lt.INIT_EQUILIBRIUM, 1)
+@pytest.mark.parametrize("kernel", [lt.KERNEL_TILED, lt.KERNEL_WIDE])
+def test_full_size_north_east_L8192(kernel):
+    run_pair(2, 8192, 1, lt.NE, 0.0, 0.0, 0.3, 21, lt.INIT_EQUILIBRIUM, 1, kernel=kernel)
 
 
 def test_full_size_properties_after_many_sweeps():

@@ -1,0 +1,109 @@
+"""Serving loop: continuous batching of independent requests.
+
+Each served result must equal its lattice run alone (bit for bit), requests
+that arrive while others run must be admitted and finish before long ones
+do, and admission must respect the HBM budget and the slot limit.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import paper_1209_0296_gb300 as lt
+
+pytestmark = pytest.mark.gpu
+
+REQS = [
+    dict(dims=2, L=64, two_S=1, model=lt.ISING, J=1.0, h=0.0, T_or_c=2.269185, seed=1234,
+         init=lt.INIT_COLD, sweeps=300),
+    dict(dims=2, L=128, two_S=1, model=lt.ISING, J=1.0, h=0.0, T_or_c=2.0, seed=5,
+         init=lt.INIT_RANDOM, sweeps=77),
+    dict(dims=2, L=96, two_S=1, model=lt.NE, J=0.0, h=0.0, T_or_c=0.2, seed=6,
+         init=lt.INIT_EQUILIBRIUM, sweeps=500),
+    dict(dims=2, L=50, two_S=1, model=lt.ISING, J=1.0, h=0.2, T_or_c=2.5, seed=7,
+         init=lt.INIT_RANDOM, sweeps=41),
+    dict(dims=3, L=8, two_S=2, model=lt.ISING, J=1.0, h=0.0, T_or_c=3.0, seed=8,
+         init=lt.INIT_RANDOM, sweeps=260),
+    dict(dims=2, L=256, two_S=1, model=lt.ISING, J=1.0, h=0.0, T_or_c=3.0, seed=9,
+         init=lt.INIT_RANDOM, sweeps=0),
+    dict(dims=2, L=320, two_S=1, model=lt.NE, J=0.0, h=0.0, T_or_c=0.05, seed=10,
+         init=lt.INIT_EQUILIBRIUM, sweeps=129),
+]
+
+
+def _solo(r):
+    g = lt.Lattice(r["dims"], r["L"], r["two_S"], r["model"], r["J"], r["h"], r["T_or_c"],
+                   seed=r["seed"], init=r["init"])
+    g.sweep(r["sweeps"])
+    return g
+
+
+def test_served_results_equal_solo_runs():
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=64, chunk_sweeps=64)
+    ids = [srv.submit(**r, keep_spins=True) for r in REQS]
+    srv.drain(120.0)
+    for rid, r in zip(ids, REQS):
+        N = r["L"] ** r["dims"]
+        spins = np.empty(N, dtype=np.int8)
+        res = srv.poll(rid, spins)
+        assert res is not None and res["status"] == 0, res
+        assert res["sweeps_done"] == r["sweeps"]
+        g = _solo(r)
+        assert np.array_equal(spins, g.get_spins()), r
+        o = g.observables()
+        assert res["E"] == pytest.approx(o["E"]) and res["M"] == pytest.approx(o["M"])
+        if r["sweeps"] > 0:
+            ser = g.series(r["sweeps"] - 1, 1)
+            assert res["bond"] == ser["bond"][0] and res["mag"] == ser["mag"][0]
+        assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
+        with pytest.raises(lt.LatticeError):
+            srv.poll(rid)  # released after the first successful poll
+    srv.close()
+
+
+def test_late_short_request_overlaps_and_finishes_first():
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=16, chunk_sweeps=32)
+    long_id = srv.submit(dims=2, L=1024, model=lt.ISING, T_or_c=2.3, seed=3, sweeps=4000)
+    time.sleep(0.05)
+    short_id = srv.submit(dims=2, L=64, model=lt.ISING, T_or_c=2.3, seed=4, sweeps=64)
+    assert srv.poll(long_id) is None          # still running (LAT_EBUSY)
+    srv.drain(300.0)
+    a, b = srv.poll(long_id), srv.poll(short_id)
+    assert b["t_admit"] < a["t_done"]         # admitted while the long one ran
+    assert b["t_done"] < a["t_done"]          # and finished first
+    srv.close()
+
+
+def test_budget_and_slots_serialise_admission():
+    # each L=256 Ising lattice is charged ~142 kB (two spin buffers, table,
+    # counters); a 200 kB budget holds one at a time
+    srv = lt.Server(hbm_budget_bytes=200_000, max_slots=8, chunk_sweeps=16)
+    ids = [srv.submit(dims=2, L=256, model=lt.ISING, T_or_c=2.5, seed=s, sweeps=40)
+           for s in range(4)]
+    srv.drain(120.0)
+    res = [srv.poll(i) for i in ids]
+    assert all(r["status"] == 0 for r in res)
+    for prev, nxt in zip(res, res[1:]):
+        assert nxt["t_admit"] >= prev["t_done"] - 1e-6
+    srv.close()
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=1, chunk_sweeps=16)
+    ids = [srv.submit(dims=2, L=64, model=lt.ISING, T_or_c=2.5, seed=s, sweeps=20) for s in range(3)]
+    srv.drain(120.0)
+    res = [srv.poll(i) for i in ids]
+    for prev, nxt in zip(res, res[1:]):
+        assert nxt["t_admit"] >= prev["t_done"] - 1e-6
+    srv.close()
+
+
+def test_invalid_and_oversized_requests():
+    srv = lt.Server(hbm_budget_bytes=100_000, max_slots=4, chunk_sweeps=16)
+    with pytest.raises(lt.LatticeError) as e:
+        srv.submit(dims=4, L=16, sweeps=1)
+    assert e.value.code == -1
+    with pytest.raises(lt.LatticeError) as e:
+        srv.submit(dims=2, L=1024, sweeps=1)      # 2 MB > budget: can never be admitted
+    assert e.value.code == -2
+    with pytest.raises(lt.LatticeError) as e:
+        srv.poll(12345)
+    assert e.value.code == -8
+    srv.close()
