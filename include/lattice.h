@@ -266,6 +266,56 @@ double lattice_server_clock(lattice_server_t *s);
 void lattice_server_destroy(lattice_server_t *s);
 
 /* ------------------------------------------------------------------ */
+/* No-allocation batched sweep (this entry point has no counterpart in  */
+/* the paper; it serves callers that cannot let a library allocate).    */
+/* ------------------------------------------------------------------ */
+
+/* One 2D spin-1/2 Ising lattice (H = -J sum s_i s_j - h sum s_i, same
+ * rules, random numbers and counters as lattice_create / lattice_sweep)
+ * held entirely in caller-owned device memory:
+ *   L         lattice side, a multiple of 32, 32 <= L <= 32768
+ *   J, h, T   coupling, field, temperature (T > 0; the acceptance table
+ *             must not contain a never-accept entry, i.e. dE/T <= 22)
+ *   seed      Philox key
+ *   sweep0    sweeps already done (global sweep index of the first sweep)
+ *   spins[2]  two device buffers of L*L int8 spins each, in the
+ *             checkerboard-planar layout of lattice_device_spins; the state
+ *             after t sweeps is in spins[t & 1] (the other is overwritten)
+ *   counters  device int64[4 * n_sweeps]: bond, mag, up, unflipped (0) of
+ *             each sweep, in order; cleared by the call before use */
+typedef struct lattice_static_desc {
+    int L;
+    double J, h, T;
+    uint64_t seed;
+    int64_t sweep0;
+    int8_t *spins[2];
+    int64_t *counters;
+} lattice_static_desc_t;
+
+/* Queue n_sweeps checkerboard sweeps of n_lattices lattices on cuda_stream
+ * (NULL = default stream) without allocating any memory: no cudaMalloc,
+ * cudaFree or allocating library call.  For callers whose device memory
+ * all comes from their own pool (a framework's caching allocator, a
+ * memory-capped service) or that must not trigger the device-wide
+ * synchronisation an allocation can cause.
+ *   - The library's scratch (descriptors, tables, sweep counters, the tile
+ *     work list) is one fixed array of about 560 kB in device memory that
+ *     every GPU loading the library holds until the process exits.  Limits:
+ *     at most 64 lattices and 65536 tiles of 256 x 64 sites per call
+ *     (LAT_ERANGE beyond either; one L = 32768 lattice is 65536 tiles).
+ *   - The first call on a device looks up the scratch's address (with that
+ *     device current); make that first call before any stream capture.
+ *   - All calls share the scratch, which keeps the last call's contents;
+ *     the call clears what must start at zero.  Calls whose work overlaps
+ *     on the GPU (for example on two streams, or from two host threads)
+ *     race on the scratch: serialise them.
+ *   - Waits for its own small host-to-device copies of the descriptors
+ *     before queueing the sweeps; returns without waiting for the sweeps.
+ * Returns LAT_EINVAL / LAT_ENOTSUP for bad or unsupported lattices. */
+int lattice_sweep_static(const lattice_static_desc_t *descs, int n_lattices, int64_t n_sweeps,
+                         void *cuda_stream);
+
+/* ------------------------------------------------------------------ */
 const char *lattice_strerror(int code);
 /* The last CUDA error string seen by the calling thread (or ""). */
 const char *lattice_last_cuda_error(void);

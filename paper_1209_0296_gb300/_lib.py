@@ -32,6 +32,12 @@ class LatticeResult(ctypes.Structure):
                 ("t_submit", c_double), ("t_admit", c_double), ("t_done", c_double)]
 
 
+class LatticeStaticDesc(ctypes.Structure):
+    _fields_ = [("L", c_int), ("J", c_double), ("h", c_double), ("T", c_double),
+                ("seed", c_uint64), ("sweep0", c_int64), ("spins", c_void_p * 2),
+                ("counters", c_void_p)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "lattice_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_double,
@@ -64,6 +70,7 @@ SIGNATURES = {
     "lattice_server_drain": (c_int, [c_void_p, c_double]),
     "lattice_server_clock": (c_double, [c_void_p]),
     "lattice_server_destroy": (None, [c_void_p]),
+    "lattice_sweep_static": (c_int, [c_void_p, c_int, c_int64, c_void_p]),
     "lattice_strerror": (ctypes.c_char_p, [c_int]),
     "lattice_last_cuda_error": (ctypes.c_char_p, []),
     "lattice_version": (ctypes.c_char_p, []),
