@@ -290,6 +290,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_sample()
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_serving:
+        extra["batched"] = batched_bench()
+        extra["served"] = served_bench()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "updates/ns", "n_gpus": world,
@@ -309,6 +313,7 @@ def run_gpu(args):
             line["e2e"] = e2e
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        line.update(extra)
         print(json.dumps(line), flush=True)
     for g in lats:
         g.close()
@@ -334,6 +339,132 @@ def run_profile(args):
     g.synchronize()
     print("profile run: %d sweeps of L=%d (%s), kernel %s" % (args.profile, args.profile_L,
                                                            args.profile_model, g.get_kernel()))
+
+
+def _lat_of(lt, r, stream=None):
+    return lt.Lattice(r["dims"], r["L"], r["two_S"], r["model"], r["J"], r["h"], r["T_or_c"],
+                      seed=r["seed"], init=r["init"], stream=stream)
+
+
+def _warm_tuner(lt, reqs):
+    """Run the kernel autotuner once per (model, L) on throw-away lattices so
+    the plain arm is timed with its tuned kernels, as in a long-running job."""
+    seen = set()
+    for r in reqs:
+        key = (r["model"], r["L"])
+        if key in seen:
+            continue
+        seen.add(key)
+        g = _lat_of(lt, r)
+        g.sweep(16)
+        g.close()
+
+
+def batched_bench(n_lat=64, sweeps=200):
+    """The same mixed lattices (served-mix sizes and models) advanced (a) by
+    the batched engine and (b) one lattice after another with its own
+    launches: updates/ns of each, and a bit-exactness check of (a) vs (b)."""
+    import torch
+    import paper_1209_0296_gb300 as lt
+    from paper_1209_0296_gb300.workloads import served_mix
+    reqs = served_mix(n=n_lat, seed=99)
+    for r in reqs:
+        r["sweeps"] = sweeps
+    upd = sum(r["L"] ** 2 for r in reqs) * sweeps
+    _warm_tuner(lt, reqs)
+    # plain
+    lats = [_lat_of(lt, r) for r in reqs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in lats:
+        g.sweep(sweeps)
+        g.synchronize()
+    t_plain = time.perf_counter() - t0
+    plain_spins = [g.get_spins() for g in lats[:4]]
+    for g in lats:
+        g.close()
+    # batched
+    lats = [_lat_of(lt, r) for r in reqs]
+    b = lt.Batch()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in lats:
+        b.add(g, sweeps)
+    b.run()
+    b.synchronize()
+    t_batch = time.perf_counter() - t0
+    exact = all(np.array_equal(g.get_spins(), ps) for g, ps in zip(lats[:4], plain_spins))
+    for g in lats:
+        g.close()
+    b.close()
+    return {"workload": "%d lattices of the served mix (2D Ising/North-East, L 32..4096), %d sweeps each"
+                        % (n_lat, sweeps),
+            "batched": upd / t_batch / 1e9, "plain": upd / t_plain / 1e9, "unit": "updates/ns",
+            "speedup": t_plain / t_batch, "bit_exact_vs_plain": exact}
+
+
+def served_bench(n_req=256, sweep_scale=0.01, load=None):
+    """Requests of the served mix arriving as a Poisson process: served by
+    the continuous-batching server, and (plain) one after another with one
+    lattice's own launches each.  Latency = completion - arrival."""
+    import torch
+    import paper_1209_0296_gb300 as lt
+    from paper_1209_0296_gb300.workloads import served_mix, offered_updates
+    base = served_mix(n=n_req, seed=99, gap_ms=2.0 * sweep_scale, sweep_scale=sweep_scale)
+    upd = offered_updates(base)
+    _warm_tuner(lt, base)
+
+    def run_served(reqs):
+        srv = lt.Server(hbm_budget_bytes=32 << 30, max_slots=1024, chunk_sweeps=64)
+        t0 = srv.clock()
+        ids = []
+        for r in reqs:
+            while srv.clock() - t0 < r["arrival"]:
+                pass
+            ids.append(srv.submit(dims=r["dims"], L=r["L"], two_S=r["two_S"], model=r["model"],
+                                  J=r["J"], h=r["h"], T_or_c=r["T_or_c"], seed=r["seed"],
+                                  init=r["init"], sweeps=r["sweeps"]))
+        srv.drain(600.0)
+        res = [srv.poll(i) for i in ids]
+        srv.close()
+        lat = np.array([q["t_done"] - q["t_submit"] for q in res])
+        span = max(q["t_done"] for q in res) - min(q["t_submit"] for q in res)
+        ok = all(q["status"] == 0 for q in res)
+        return lat, span, ok
+
+    def run_plain(reqs):
+        t0 = time.perf_counter()
+        lat = []
+        for r in reqs:
+            while time.perf_counter() - t0 < r["arrival"]:
+                pass
+            g = _lat_of(lt, r)
+            g.sweep(r["sweeps"])
+            g.synchronize()
+            lat.append(time.perf_counter() - t0 - r["arrival"])
+            g.close()
+        return np.array(lat), time.perf_counter() - t0
+
+    def pct(a):
+        return {"p50_ms": float(np.percentile(a, 50) * 1e3), "p99_ms": float(np.percentile(a, 99) * 1e3)}
+
+    out = {"workload": "first %d requests of the served mix (default_rng(99)), sweeps x%g, gaps x%g"
+                       % (n_req, sweep_scale, sweep_scale), "offered_updates": upd}
+    lat, span, ok = run_served(base)
+    out["served"] = dict(pct(lat), throughput=upd / span / 1e9, all_ok=ok)
+    plat, pspan = run_plain(base)
+    out["plain"] = dict(pct(plat), throughput=upd / pspan / 1e9)
+    arrival_span = base[-1]["arrival"]
+    out["offered_load"] = upd / arrival_span / 1e9 / out["served"]["throughput"]
+    # the same requests at an offered load of about 0.7 of the served throughput
+    scale = (upd / (0.7 * out["served"]["throughput"] * 1e9)) / arrival_span
+    slow = [dict(r, arrival=r["arrival"] * scale) for r in base]
+    lat2, span2, ok2 = run_served(slow)
+    out["served_load_0.7"] = dict(pct(lat2), throughput=upd / span2 / 1e9, all_ok=ok2)
+    plat2, pspan2 = run_plain(slow)
+    out["plain_load_0.7"] = dict(pct(plat2), throughput=upd / pspan2 / 1e9)
+    out["unit"] = "updates/ns"
+    return out
 
 
 def load_profile_numbers(kname):
@@ -370,6 +501,7 @@ def main():
     ap.add_argument("--graph", type=int, default=0, help="sweeps per CUDA graph (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
     ap.add_argument("--profile-L", type=int, default=L)

@@ -26,8 +26,8 @@ struct lattice_batch {
     int items_cap = 0;
     Ctrl **d_ctrls = nullptr;
     int ctrls_cap = 0;
-    unsigned *d_counters = nullptr;  // [3]: next tiled item, next colour-0 item, next colour-1 item
-    int grid_tiled = 0, grid_generic = 0;
+    unsigned *d_counters = nullptr;  // [4]: next Ising-tile, NE-tile, colour-0, colour-1 item
+    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0;
 };
 
 namespace {
@@ -50,27 +50,37 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
     return LAT_OK;
 }
 
+// Item counts of the current active set: tiles of Ising lattices, tiles of
+// North-East lattices, then generic chunks, in that order in d_items.
+struct Shape {
+    int n_lat, n_ising, n_ne, n_gen;
+};
+
 // Queue `steps` sweep steps of the current active set.
-int enqueue_steps(lattice_batch *b, int n_lat, int n_tiled, int n_gen, int steps, cudaStream_t st)
+int enqueue_steps(lattice_batch *b, const Shape &sh, int steps, cudaStream_t st)
 {
     for (int s = 0; s < steps; ++s) {
         cudaError_t e = cudaSuccess;
-        if (n_tiled > 0)
-            e = launch_batch_tiled(b->d_geoms, b->d_items, n_tiled, b->d_counters + 0, 0, 0,
-                                   std::min(b->grid_tiled, n_tiled), st);
-        if (e == cudaSuccess && n_gen > 0)
-            e = launch_batch_generic(b->d_geoms, b->d_items + n_tiled, n_gen, b->d_counters + 1, 0, 0,
-                                     std::min(b->grid_generic, n_gen), st);
-        if (e == cudaSuccess && n_gen > 0)
-            e = launch_batch_generic(b->d_geoms, b->d_items + n_tiled, n_gen, b->d_counters + 2, 1, 0,
-                                     std::min(b->grid_generic, n_gen), st);
-        if (e == cudaSuccess) e = launch_batch_advance(b->d_ctrls, n_lat, b->d_counters, 3, 1ull, st);
+        if (sh.n_ising > 0)
+            e = launch_batch_tiled(b->d_geoms, b->d_items, sh.n_ising, b->d_counters + 0, 0, 0,
+                                   std::min(b->grid_tiled_ising, sh.n_ising), false, st);
+        if (e == cudaSuccess && sh.n_ne > 0)
+            e = launch_batch_tiled(b->d_geoms, b->d_items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
+                                   std::min(b->grid_tiled_ne, sh.n_ne), true, st);
+        const uint2 *gen = b->d_items + sh.n_ising + sh.n_ne;
+        if (e == cudaSuccess && sh.n_gen > 0)
+            e = launch_batch_generic(b->d_geoms, gen, sh.n_gen, b->d_counters + 2, 0, 0,
+                                     std::min(b->grid_generic, sh.n_gen), st);
+        if (e == cudaSuccess && sh.n_gen > 0)
+            e = launch_batch_generic(b->d_geoms, gen, sh.n_gen, b->d_counters + 3, 1, 0,
+                                     std::min(b->grid_generic, sh.n_gen), st);
+        if (e == cudaSuccess) e = launch_batch_advance(b->d_ctrls, sh.n_lat, b->d_counters, 4, 1ull, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     }
     return LAT_OK;
 }
 
-int run_steps(lattice_batch *b, int n_lat, int n_tiled, int n_gen, int64_t steps)
+int run_steps(lattice_batch *b, const Shape &sh, int64_t steps)
 {
     int64_t left = steps;
     if (left >= kGraphSteps) {
@@ -82,7 +92,7 @@ int run_steps(lattice_batch *b, int n_lat, int n_tiled, int n_gen, int64_t steps
         cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "batch begin capture");
-        int rc = enqueue_steps(b, n_lat, n_tiled, n_gen, kGraphSteps, b->cap_stream);
+        int rc = enqueue_steps(b, sh, kGraphSteps, b->cap_stream);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (rc != LAT_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -98,7 +108,7 @@ int run_steps(lattice_batch *b, int n_lat, int n_tiled, int n_gen, int64_t steps
         cudaGraphExecDestroy(exec);  // safe: destruction waits for no launch; launches stay valid
         if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
     }
-    if (left > 0) return enqueue_steps(b, n_lat, n_tiled, n_gen, (int)left, b->stream);
+    if (left > 0) return enqueue_steps(b, sh, (int)left, b->stream);
     return LAT_OK;
 }
 
@@ -113,13 +123,14 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     lattice_batch *b = new (std::nothrow) lattice_batch();
     if (b == nullptr) return LAT_ENOMEM;
     b->stream = (cudaStream_t)cuda_stream;
-    cudaError_t e = dev_alloc((void **)&b->d_counters, 3 * sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, 3 * sizeof(unsigned), b->stream);
+    cudaError_t e = dev_alloc((void **)&b->d_counters, 4 * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) {
         delete b;
         return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "batch create");
     }
-    b->grid_tiled = batch_tiled_grid();
+    b->grid_tiled_ising = batch_tiled_grid(false);
+    b->grid_tiled_ne = batch_tiled_grid(true);
     b->grid_generic = batch_generic_grid();
     *out = b;
     return LAT_OK;
@@ -162,22 +173,25 @@ int lattice_batch_run(lattice_batch_t *b)
         if (steps > 0) {
             std::vector<Geom> geoms(n_active);
             std::vector<Ctrl *> ctrls(n_active);
-            std::vector<uint2> tiled, gen;
+            std::vector<uint2> tiled, tiled_ne, gen;
             for (size_t i = 0; i < n_active; ++i) {
                 lattice *lt = work[i].first;
                 geoms[i] = tiled_geom(lt->geom);
                 ctrls[i] = lt->ctrl;
-                if (choose_kernel(lt) == LAT_KERNEL_TILED) {
+                const int kern = choose_kernel(lt);
+                if (kern == LAT_KERNEL_TILED || kern == LAT_KERNEL_WIDE) {
                     const int nt = tiles_of(lt->geom, 0);
-                    for (int k = 0; k < nt; ++k) tiled.push_back(make_uint2((unsigned)i, (unsigned)k));
+                    auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
+                    for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
                 } else {
                     const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
                     const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
                     for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
                 }
             }
-            const int n_tiled = (int)tiled.size(), n_gen = (int)gen.size();
+            Shape sh{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), (int)gen.size()};
             std::vector<uint2> items(tiled);
+            items.insert(items.end(), tiled_ne.begin(), tiled_ne.end());
             items.insert(items.end(), gen.begin(), gen.end());
             int rc = grow(&b->d_geoms, b->geoms_cap, (int)n_active, b->stream);
             if (rc == LAT_OK) rc = grow(&b->d_items, b->items_cap, (int)items.size(), b->stream);
@@ -194,7 +208,7 @@ int lattice_batch_run(lattice_batch_t *b)
             // The host vectors go out of scope: make the copies complete first.
             if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
             if (e != cudaSuccess) return cuda_fail(e, "batch upload");
-            rc = run_steps(b, (int)n_active, n_tiled, n_gen, steps);
+            rc = run_steps(b, sh, steps);
             if (rc != LAT_OK) return rc;
             done += steps;
         }

@@ -188,12 +188,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_half_sweep(const Geom *geoms
                 reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
         __syncthreads();
         for (int i = threadIdx.x; i < sg.tab_n; i += blockDim.x) stab[i] = sg.tab[i];
+        const Geom g = sg;  // register copy: no aliasing with shared-memory stores
         __syncthreads();
-        const unsigned long long sweep = sg.ctrl->sweep + (unsigned long long)off;
+        const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
         const uint64_t t = (uint64_t)w.y * kThreads + threadIdx.x;
         Part pt;
-        if (t < (uint64_t)sg.rows * sg.G) half_sweep_group(sg, stab, colour, sweep, t, pt);
-        if (colour == 1) flush_counters(sg, sweep, pt, red);
+        if (t < (uint64_t)g.rows * g.G) half_sweep_group(g, stab, colour, sweep, t, pt);
+        if (colour == 1) flush_counters(g, sweep, pt, red);
         __syncthreads();
     }
 }

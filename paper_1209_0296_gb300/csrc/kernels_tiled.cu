@@ -177,7 +177,7 @@ LAT_D void do_pair(const Tile &t, const uint32_t *sthr, const PhiloxPre &pp, int
 // lattice's 16-entry t' table in shared memory.  smem_raw: the tile buffer,
 // sized for tile_h; red: [kWarps][4] ints.  Called by every thread.
 template <bool kNE>
-LAT_D void sweep_tile(const Geom &g, const uint32_t *sthr, int bx, int by, int tile_h, int off,
+LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, int tile_h, int off,
                       unsigned char *smem_raw, int (*red)[4])
 {
     const int L = g.L;
@@ -197,8 +197,8 @@ LAT_D void sweep_tile(const Geom &g, const uint32_t *sthr, int bx, int by, int t
     uint8_t *sflag0 = smem_raw + (size_t)2 * t.plane_words * 4;  // [tile_h][32], colour-0 flags
 
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
-    const int8_t *src = g.s[sweep & 1];
-    int8_t *dst = g.s[(sweep + 1) & 1];
+    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
+    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
 
@@ -361,15 +361,18 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(TiledArgs a)
     __shared__ uint32_t sthr[16];
     __shared__ int red[kWarps][4];
     if (threadIdx.x < 16) sthr[threadIdx.x] = a.g.thr16[threadIdx.x];
-    sweep_tile<kNE>(a.g, sthr, blockIdx.x, blockIdx.y, a.tile_h, a.off, smem_raw, red);
+    sweep_tile<kNE>(sweep_view(a.g), sthr, blockIdx.x, blockIdx.y, a.tile_h, a.off, smem_raw, red);
 }
 
 // Batched sweep: a persistent grid works through a list of (lattice, tile)
-// items of many lattices, one sweep each, taking items from a shared
-// counter.  Each lattice keeps its own parameters, table, seed and sweep
-// counter (its Geom in device memory), so every tile computes exactly what
-// its lattice's own launch would.  Tiles of one lattice are independent
-// within a sweep (they read one buffer and write the other).
+// items of many lattices of one model, one sweep each, taking items from a
+// shared counter.  Each lattice keeps its own parameters, table, seed and
+// sweep counter (its Geom in device memory), so every tile computes exactly
+// what its lattice's own launch would.  Tiles of one lattice are
+// independent within a sweep (they read one buffer and write the other).
+// The descriptor is staged through shared memory into a register copy, so
+// the tile's own shared-memory stores cannot alias it.
+template <bool kNE>
 __global__ void __launch_bounds__(kThreads) k_batch_tiled(const Geom *geoms, const uint2 *items,
                                                          int n_items, unsigned *next_item, int tile_h,
                                                          int off)
@@ -390,13 +393,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_tiled(const Geom *geoms, con
                 reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
         __syncthreads();
         if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
+        const SweepView g = sweep_view(sg);
         __syncthreads();
-        const int tiles_x = (sg.L + kTileCols - 1) / kTileCols;
+        const int tiles_x = (g.L + kTileCols - 1) / kTileCols;
         const int bx = (int)(w.y % (unsigned)tiles_x), by = (int)(w.y / (unsigned)tiles_x);
-        if (sg.model == LAT_NE)
-            sweep_tile<true>(sg, sthr, bx, by, tile_h, off, smem_raw, red);
-        else
-            sweep_tile<false>(sg, sthr, bx, by, tile_h, off, smem_raw, red);
+        sweep_tile<kNE>(g, sthr, bx, by, tile_h, off, smem_raw, red);
         __syncthreads();
     }
 }
@@ -464,22 +465,26 @@ int tiles_of(const Geom &g, int tile_h)
 }
 
 cudaError_t launch_batch_tiled(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                               int tile_h, int off, int grid, cudaStream_t st)
+                               int tile_h, int off, int grid, bool ne, cudaStream_t st)
 {
     const int th = tile_h ? tile_h : kDefTileH;
-    const size_t smem = tile_smem_bytes(th);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_batch_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_batch_tiled<<<grid, kThreads, smem, st>>>(geoms, items, n_items, next_item, th, off);
+    const size_t smem = tile_smem_bytes(th);  // <= 48 kB for tile_h <= 64
+    if (ne)
+        k_batch_tiled<true><<<grid, kThreads, smem, st>>>(geoms, items, n_items, next_item, th, off);
+    else
+        k_batch_tiled<false><<<grid, kThreads, smem, st>>>(geoms, items, n_items, next_item, th, off);
     return cudaGetLastError();
 }
 
-int batch_tiled_grid()
+int batch_tiled_grid(bool ne)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_tiled, kThreads, tile_smem_bytes(kDefTileH));
+    if (ne)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_tiled<true>, kThreads, tile_smem_bytes(kDefTileH));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_tiled<false>, kThreads, tile_smem_bytes(kDefTileH));
     if (per < 1) per = 1;
     return sms * per;
 }

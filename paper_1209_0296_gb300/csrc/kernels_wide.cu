@@ -41,11 +41,11 @@ struct Counts {
 
 // Sweep colour `colour` of the 16-site chunk k of plane row y.
 template <bool kNE>
-LAT_D void wide_chunk(const Geom &g, const uint32_t *sthr, int colour, unsigned long long sweep,
+LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsigned long long sweep,
                       const PhiloxPre &pp, int y, int k, Counts &cnt)
 {
-    const int8_t *src = g.s[sweep & 1];
-    int8_t *dst = g.s[(sweep + 1) & 1];
+    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
+    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
     if (colour == 1) src = dst;
     const int L = g.L;
     const uint32_t half = g.half;
@@ -160,7 +160,7 @@ LAT_D void wide_chunk(const Geom &g, const uint32_t *sthr, int colour, unsigned 
     }
 }
 
-LAT_D void flush(const Geom &g, unsigned long long sweep, const Counts &c, bool ne, int (*red)[4])
+LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, bool ne, int (*red)[4])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = __reduce_add_sync(0xffffffffu, c.bond);
@@ -195,45 +195,9 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     const uint32_t cpr = g.half >> 4;  // 16-site chunks per plane row
     const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     Counts cnt;
-    if (t < (uint64_t)g.L * cpr) wide_chunk<kNE>(g, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
-    if (colour == 1) flush(g, sweep, cnt, kNE, red);
-}
-
-// Batched: a persistent grid works through (lattice, block) items; a block
-// is kThreads consecutive chunks of one lattice.
-__global__ void __launch_bounds__(kThreads) k_batch_wide(const Geom *geoms, const uint2 *items, int n_items,
-                                                        unsigned *next_item, int colour)
-{
-    __shared__ Geom sg;
-    __shared__ uint32_t sthr[16];
-    __shared__ int red[kThreads / 32][4];
-    __shared__ int cur;
-    for (;;) {
-        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
-        __syncthreads();
-        const int it = cur;
-        if (it >= n_items) break;
-        const uint2 w = items[it];
-        if (threadIdx.x < sizeof(Geom) / 4)
-            reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
-                reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
-        __syncthreads();
-        const unsigned long long sweep = sg.ctrl->sweep;
-        PhiloxPre pp;
-        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
-        const uint32_t cpr = sg.half >> 4;
-        const uint64_t t = (uint64_t)w.y * kThreads + threadIdx.x;
-        Counts cnt;
-        const bool ne = sg.model == LAT_NE;
-        if (t < (uint64_t)sg.L * cpr) {
-            if (ne) wide_chunk<true>(sg, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
-            else wide_chunk<false>(sg, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
-        }
-        if (colour == 1) flush(sg, sweep, cnt, ne, red);
-        __syncthreads();
-    }
+    const SweepView v = sweep_view(g);
+    if (t < (uint64_t)g.L * cpr) wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+    if (colour == 1) flush(v, sweep, cnt, kNE, red);
 }
 
 }  // namespace
@@ -263,23 +227,6 @@ cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                              int colour, int grid, cudaStream_t st)
-{
-    k_batch_wide<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
-    return cudaGetLastError();
-}
-
-int batch_wide_grid()
-{
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide, kThreads, 0);
-    if (per < 1) per = 1;
-    return sms * per;
 }
 
 }  // namespace lat

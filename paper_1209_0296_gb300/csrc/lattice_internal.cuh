@@ -185,6 +185,36 @@ struct Geom {
     uint32_t always16;
 };
 
+// The fields of a Geom that the 2D spin-1/2 sweep kernels read, small
+// enough to live in registers (the batched kernels build it from a
+// descriptor staged in shared memory).
+struct SweepView {
+    int L;
+    uint32_t rows, half, G;
+    uint64_t plane;
+    int8_t *s0, *s1;
+    uint32_t key0, key1;
+    uint8_t *flags;
+    Ctrl *ctrl;
+};
+
+LAT_HD SweepView sweep_view(const Geom &g)
+{
+    SweepView v;
+    v.L = g.L;
+    v.rows = g.rows;
+    v.half = g.half;
+    v.G = g.G;
+    v.plane = g.plane;
+    v.s0 = g.s[0];
+    v.s1 = g.s[1];
+    v.key0 = g.key0;
+    v.key1 = g.key1;
+    v.flags = g.flags;
+    v.ctrl = g.ctrl;
+    return v;
+}
+
 // Planar address of site (x, y, z) (coordinates already wrapped).
 LAT_HD uint64_t planar_index(const Geom &g, int x, int y, int z)
 {
@@ -244,16 +274,13 @@ cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
 bool bitpacked_supported(const Geom &g);
 bool wide_supported(const Geom &g);
 cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st);
-cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                              int colour, int grid, cudaStream_t st);
-int batch_wide_grid();
 int wide_chunks(const Geom &g);
 // batched engine
 Geom tiled_geom(const Geom &g);
 int tiles_of(const Geom &g, int tile_h);
-int batch_tiled_grid();
+int batch_tiled_grid(bool ne);
 cudaError_t launch_batch_tiled(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                               int tile_h, int off, int grid, cudaStream_t st);
+                               int tile_h, int off, int grid, bool ne, cudaStream_t st);
 cudaError_t launch_batch_generic(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
                                  int colour, int off, int grid, cudaStream_t st);
 int batch_generic_grid();

@@ -162,10 +162,10 @@ extern "C" int lattice_sweep_static(const lattice_static_desc_t *descs, int n_la
     // The host vectors above are released on return: let the copies finish.
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "static sweep set-up");
-    const int grid = std::min(batch_tiled_grid(), (int)items.size());
+    const int grid = std::min(batch_tiled_grid(false), (int)items.size());
     for (int64_t s = 0; s < n_sweeps; ++s) {
         e = launch_batch_tiled(sp->geoms, sp->items, (int)items.size(), &sp->next_item[0], kStaticTileH, 0,
-                               grid, st);
+                               grid, false, st);
         if (e == cudaSuccess) e = launch_batch_advance(sp->ctrl_ptr, n_lattices, sp->next_item, 1, 1ull, st);
         if (e != cudaSuccess) return cuda_fail(e, "static sweep launch");
     }
