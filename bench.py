@@ -39,7 +39,8 @@ L = 4096
 TEMPS = (2.0, 2.269185, 3.0)
 SEED = 7
 WORKLOAD = ("2D Ising spin-1/2, L=4096 periodic, J=1, h=0, T in {2.0, 2.269185, 3.0}, "
-            "random +-1 start (seed 7), int8 spins")
+            "random +-1 start (seed 7), int8 and bit-packed spin layouts")
+LAYOUTS = ("int8", "bitpacked")
 METRIC = "spin updates/ns"
 
 
@@ -50,6 +51,22 @@ def peaks():
         return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
         return 6800.0, 2070.0, "fallback"
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(updates_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job updates per ns of `world` independent replicas (weak scaling)."""
+    return world * updates_per_rank / (max_seconds * 1e9)
 
 
 def dist_info():
@@ -179,15 +196,13 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     S = args.sweeps
 
-    lats = [lt.Lattice(2, L, 1, lt.ISING, 1.0, 0.0, T, seed=SEED, init=lt.INIT_RANDOM, stream=stream)
-            for T in TEMPS]
-    for g in lats:
+    lats = {lay: [lt.Lattice(2, L, 1, lt.ISING, 1.0, 0.0, T, seed=SEED, init=lt.INIT_RANDOM,
+                             layout=lt.INT8 if lay == "int8" else lt.BITPACKED, stream=stream)
+                  for T in TEMPS] for lay in LAYOUTS}
+    for g in lats["int8"]:
         g.set_kernel(lt.KERNEL_AUTO, 0, args.tile_h, args.graph)
+    all_lats = lats["int8"] + lats["bitpacked"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
-
-    def step():
-        for g in lats:
-            g.sweep(S)
 
     def barrier():
         if world > 1:
@@ -197,42 +212,46 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.fill_(1)
-            step()
+            for g in all_lats:
+                g.sweep(S)
         stream.synchronize()
         barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+        # events: [start, after the int8 lattices, after the bit-packed lattices] per step
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
         with Clocks(local) as clk:
             for k in range(args.steps):
                 flush.fill_(k & 255)          # evict the lattices from L2 (outside the timed pair)
                 ev[k][0].record(stream)
-                step()
+                for g in lats["int8"]:
+                    g.sweep(S)
                 ev[k][1].record(stream)
+                for g in lats["bitpacked"]:
+                    g.sweep(S)
+                ev[k][2].record(stream)
             stream.synchronize()
         barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    updates = world * args.steps * len(TEMPS) * S * L * L
-    value = updates / (total_ms * 1e6)
+    ms_int8 = sum(e[0].elapsed_time(e[1]) for e in ev)
+    ms_bits = sum(e[1].elapsed_time(e[2]) for e in ev)
+    total_ms = max_over_ranks(ms_int8 + ms_bits, dev)
+    n_lat = len(all_lats)
+    updates = world * args.steps * n_lat * S * L * L
+    value = replica_value(args.steps * n_lat * S * L * L, world, total_ms * 1e-3)
 
-    # Kernel launches per step: per lattice, S sweeps (one launch each for the
-    # tiled kernel, two for the wide one) plus one counter-advance kernel per
-    # graph replay and per direct remainder.
-    kinfo = lats[0].get_kernel()
+    # Kernel launches per step: per int8 lattice, S sweeps (one launch each
+    # for the tiled kernel, two for the wide one); per bit-packed lattice two
+    # launches per sweep; plus one counter-advance kernel per graph replay
+    # and per direct remainder.
+    kinfo = lats["int8"][0].get_kernel()
     gk = kinfo["sweeps_per_graph"]
+    gkb = lats["bitpacked"][0].get_kernel()["sweeps_per_graph"]
     per_sweep = 1 if kinfo["kernel"] == lt.KERNEL_TILED else 2
-    per_lat = per_sweep * S + S // gk + (1 if S % gk else 0)
-    launches = args.steps * len(TEMPS) * per_lat
-    sweep_launches = args.steps * len(TEMPS) * S * per_sweep
-    # average duration of one sweep (all its launches; includes the tiny
-    # advance kernels and launch gaps, so this under-reports the kernel rate)
-    avg_kernel_us = total_ms * 1e3 / (args.steps * len(TEMPS) * S)
-
+    adv = lambda g_: S // g_ + (1 if S % g_ else 0)
+    launches = args.steps * len(TEMPS) * (per_sweep * S + adv(gk) + 2 * S + adv(gkb))
+    sweep_launches = args.steps * len(TEMPS) * (per_sweep + 2) * S
+    # average duration of one sweep of one lattice (all its launches, the
+    # tiny advance kernels and launch gaps: this under-reports kernel rates)
+    avg_kernel_us = ms_int8 * 1e3 / (args.steps * len(TEMPS) * S)
+    avg_bits_us = ms_bits * 1e3 / (args.steps * len(TEMPS) * S)
     hbm, _, peak_kind = peaks()
     alg_bytes = 2.0 * L * L  # one int8 read + one int8 write per site per sweep
     achieved = alg_bytes / (avg_kernel_us * 1e-6) / 1e9
@@ -245,6 +264,13 @@ def run_gpu(args):
                 "peak_kind": peak_kind + " (copy bandwidth)",
                 "bytes_per_sweep": alg_bytes,
                 "avg_sweep_us": avg_kernel_us}
+    bprof = load_profile_numbers("bitpacked")
+    bbytes = 0.25 * L * L  # one bit read + one bit written per site per sweep
+    bach = bbytes / (avg_bits_us * 1e-6) / 1e9
+    roofline_bits = {"bound": "hbm", "achieved": bach, "peak": hbm, "unit": "GB/s", "frac": bach / hbm,
+                     "traffic": bprof.get("traffic_bytes_per_sweep"), "kernel": "k_bits_half<Ising> x2",
+                     "bytes_per_sweep": bbytes, "avg_sweep_us": avg_bits_us,
+                     "updates_per_ns": L * L / (avg_bits_us * 1e3)}
     if prof.get("warp_inst_per_sweep"):
         sm_clk = (clk.summary().get("sm_mhz") or 2070.0) * 1e6
         inst_rate = prof["warp_inst_per_sweep"] / (avg_kernel_us * 1e-6)
@@ -256,14 +282,14 @@ def run_gpu(args):
     # ---- end to end through the C ABI with pinned host buffers ----------
     e2e = None
     if not args.no_e2e:
-        host_in = [torch.empty(L * L, dtype=torch.int8, pin_memory=True) for _ in TEMPS]
+        host_in = [torch.empty(L * L, dtype=torch.int8, pin_memory=True) for _ in all_lats]
         rng = np.random.default_rng(1000 + rank)
         for h in host_in:
             h.numpy()[:] = np.where(rng.random(L * L) < 0.5, 1, -1).astype(np.int8)
         series = {k: np.zeros(S, dtype=np.int64) for k in ("bond", "mag")}
 
         def e2e_step():
-            for g, h in zip(lats, host_in):
+            for g, h in zip(all_lats, host_in):
                 g.set_spins_ptr(h.data_ptr())
                 g.sweep(S)
                 first = g.sweeps() - S
@@ -277,15 +303,10 @@ def run_gpu(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
         e2e = {"value": updates / (dt * 1e9), "unit": "updates/ns",
-               "h2d_bytes_per_step": len(TEMPS) * L * L,
-               "d2h_bytes_per_step": len(TEMPS) * S * 4 * 8}
+               "h2d_bytes_per_step": n_lat * L * L,
+               "d2h_bytes_per_step": n_lat * S * 2 * 8}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -300,14 +321,16 @@ def run_gpu(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "lattices": len(TEMPS), "sweeps_per_step": S,
-                           "layout": "int8", "kernel": kname + " (autotuned)",
+                "config": {"workload": WORKLOAD, "lattices": n_lat, "sweeps_per_step": S,
+                           "layouts": list(LAYOUTS), "int8_kernel": kname + " (autotuned)",
+                           "int8_updates_per_ns": len(TEMPS) * S * L * L * args.steps / (ms_int8 * 1e6),
                            "tile": [256, kinfo["tile_h"]] if kname == "tiled" else None,
                            "sweeps_per_graph": gk,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MiB write outside the timed events)"},
                 "hbm_roofline_pct": 100.0 * roofline["frac"],
-                "roofline": roofline, "gpu_launches": launches, "sweep_launches": sweep_launches,
+                "roofline": roofline, "roofline_bitpacked": roofline_bits,
+                "gpu_launches": launches, "sweep_launches": sweep_launches,
                 "clocks": clk.summary()}
         if e2e is not None:
             line["e2e"] = e2e
@@ -315,7 +338,7 @@ def run_gpu(args):
             line["cpu_baseline"] = cpu
         line.update(extra)
         print(json.dumps(line), flush=True)
-    for g in lats:
+    for g in all_lats:
         g.close()
     if world > 1:
         import torch.distributed as dist
@@ -331,9 +354,12 @@ def run_profile(args):
         g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, 0.3, seed=21, init=lt.INIT_EQUILIBRIUM)
     else:
         g = lt.Lattice(2, args.profile_L, 1, lt.ISING, 1.0, 0.0, TEMPS[0], seed=SEED,
-                       init=lt.INIT_RANDOM)
+                       init=lt.INIT_RANDOM,
+                       layout=lt.BITPACKED if args.profile_layout == "bitpacked" else lt.INT8)
     kern = {"auto": lt.KERNEL_AUTO, "tiled": lt.KERNEL_TILED, "wide": lt.KERNEL_WIDE,
             "generic": lt.KERNEL_GENERIC}[args.profile_kernel]
+    if args.profile_layout == "bitpacked":
+        kern = lt.KERNEL_AUTO
     g.set_kernel(kern, 0, args.tile_h, 1 << 30)  # direct launches, no graphs
     g.sweep(args.profile)
     g.synchronize()
@@ -507,6 +533,7 @@ def main():
     ap.add_argument("--profile-L", type=int, default=L)
     ap.add_argument("--profile-model", default="ising", choices=["ising", "ne"])
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic"])
+    ap.add_argument("--profile-layout", default="int8", choices=["int8", "bitpacked"])
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
