@@ -89,8 +89,9 @@ enum lattice_kernel {
     LAT_KERNEL_GENERIC = 1, /* two launches per sweep, one per colour; any model */
     LAT_KERNEL_TILED = 2,   /* one launch per sweep, shared-memory tiles with halo
                                recompute; 2D spin-1/2 (Ising and North-East), L % 32 == 0 */
-    LAT_KERNEL_WIDE = 3     /* two launches per sweep, 16 sites per thread; 2D spin-1/2
-                               (Ising and North-East), L % 32 == 0 */
+    LAT_KERNEL_WIDE = 3     /* two launches per sweep, several sites per thread: 2D
+                               spin-1/2 (Ising and North-East, L % 32 == 0), or Ising
+                               in 3D / with spin S > 1/2 (L % 16 == 0) */
 };
 
 typedef struct lattice lattice_t;

@@ -2,8 +2,10 @@
 // any sizes and models advanced together.  Each sweep step is one
 // persistent-grid launch over the (lattice, tile) items of every 2D
 // spin-1/2 lattice (one fused sweep per tile) plus, for the other lattices,
-// two persistent launches over (lattice, chunk) items (colour 0, colour 1),
-// then one small kernel that advances every lattice's sweep counter.  Steps
+// two persistent launches (colour 0, colour 1) over (lattice, item) pairs of
+// the wide 3D / spin-S kernel and two over (lattice, chunk) pairs of the
+// generic kernel, then one small kernel that advances every lattice's sweep
+// counter.  Steps
 // with the same set of lattices are captured once in a CUDA graph and
 // replayed.  Every lattice keeps its own seed, table and sweep counter, so
 // its result is bit-identical to running it alone.
@@ -22,18 +24,20 @@ struct lattice_batch {
     std::vector<std::pair<lattice *, int64_t>> pending;
     Geom *d_geoms = nullptr;
     int geoms_cap = 0;
-    uint2 *d_items = nullptr;  // tiled items, then generic items
+    uint2 *d_items = nullptr;  // tiled items, then wide items, then generic items
     int items_cap = 0;
     Ctrl **d_ctrls = nullptr;
     int ctrls_cap = 0;
-    unsigned *d_counters = nullptr;  // [4]: next Ising-tile, NE-tile, colour-0, colour-1 item
-    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0;
+    // next item of: Ising tiles, NE tiles, generic colour 0 / 1, wide colour 0 / 1
+    unsigned *d_counters = nullptr;
+    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0;
 };
 
 namespace {
 
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
+constexpr int kCounters = 6;
 
 template <typename T>
 int grow(T **p, int &cap, int need, cudaStream_t st)
@@ -51,9 +55,10 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
 }
 
 // Item counts of the current active set: tiles of Ising lattices, tiles of
-// North-East lattices, then generic chunks, in that order in d_items.
+// North-East lattices, wide items, then generic chunks, in that order in
+// d_items.
 struct Shape {
-    int n_lat, n_ising, n_ne, n_gen;
+    int n_lat, n_ising, n_ne, n_wide, n_gen;
 };
 
 // Queue `steps` sweep steps of the current active set.
@@ -67,14 +72,18 @@ int enqueue_steps(lattice_batch *b, const Shape &sh, int steps, cudaStream_t st)
         if (e == cudaSuccess && sh.n_ne > 0)
             e = launch_batch_tiled(b->d_geoms, b->d_items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
                                    std::min(b->grid_tiled_ne, sh.n_ne), true, st);
-        const uint2 *gen = b->d_items + sh.n_ising + sh.n_ne;
+        const uint2 *wide = b->d_items + sh.n_ising + sh.n_ne;
+        for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide > 0; ++colour)
+            e = launch_batch_wide3(b->d_geoms, wide, sh.n_wide, b->d_counters + 4 + colour, colour,
+                                   std::min(b->grid_wide, sh.n_wide), st);
+        const uint2 *gen = wide + sh.n_wide;
         if (e == cudaSuccess && sh.n_gen > 0)
             e = launch_batch_generic(b->d_geoms, gen, sh.n_gen, b->d_counters + 2, 0, 0,
                                      std::min(b->grid_generic, sh.n_gen), st);
         if (e == cudaSuccess && sh.n_gen > 0)
             e = launch_batch_generic(b->d_geoms, gen, sh.n_gen, b->d_counters + 3, 1, 0,
                                      std::min(b->grid_generic, sh.n_gen), st);
-        if (e == cudaSuccess) e = launch_batch_advance(b->d_ctrls, sh.n_lat, b->d_counters, 4, 1ull, st);
+        if (e == cudaSuccess) e = launch_batch_advance(b->d_ctrls, sh.n_lat, b->d_counters, kCounters, 1ull, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     }
     return LAT_OK;
@@ -123,8 +132,8 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     lattice_batch *b = new (std::nothrow) lattice_batch();
     if (b == nullptr) return LAT_ENOMEM;
     b->stream = (cudaStream_t)cuda_stream;
-    cudaError_t e = dev_alloc((void **)&b->d_counters, 4 * sizeof(unsigned), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned), b->stream);
+    cudaError_t e = dev_alloc((void **)&b->d_counters, kCounters * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, kCounters * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) {
         delete b;
         return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "batch create");
@@ -132,6 +141,7 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     b->grid_tiled_ising = batch_tiled_grid(false);
     b->grid_tiled_ne = batch_tiled_grid(true);
     b->grid_generic = batch_generic_grid();
+    b->grid_wide = batch_wide3_grid();
     *out = b;
     return LAT_OK;
 }
@@ -173,25 +183,33 @@ int lattice_batch_run(lattice_batch_t *b)
         if (steps > 0) {
             std::vector<Geom> geoms(n_active);
             std::vector<Ctrl *> ctrls(n_active);
-            std::vector<uint2> tiled, tiled_ne, gen;
+            std::vector<uint2> tiled, tiled_ne, wide, gen;
             for (size_t i = 0; i < n_active; ++i) {
                 lattice *lt = work[i].first;
                 geoms[i] = tiled_geom(lt->geom);
                 ctrls[i] = lt->ctrl;
-                const int kern = choose_kernel(lt);
-                if (kern == LAT_KERNEL_TILED || kern == LAT_KERNEL_WIDE) {
+                // 2D spin-1/2 lattices whose own sweep is tiled or wide share the
+                // tiled item list; 3D and spin-S Ising lattices with L % 16 == 0
+                // take the wide items; the rest (odd sizes, an explicit generic
+                // choice) go to the generic chunks.
+                const bool generic = choose_kernel(lt) == LAT_KERNEL_GENERIC;
+                if (!generic && tiled_supported(lt->geom)) {
                     const int nt = tiles_of(lt->geom, 0);
                     auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
                     for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+                } else if (!generic && wide3_supported(lt->geom)) {
+                    const int nw = wide3_items(lt->geom);
+                    for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
                 } else {
                     const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
                     const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
                     for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
                 }
             }
-            Shape sh{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), (int)gen.size()};
+            Shape sh{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), (int)wide.size(), (int)gen.size()};
             std::vector<uint2> items(tiled);
             items.insert(items.end(), tiled_ne.begin(), tiled_ne.end());
+            items.insert(items.end(), wide.begin(), wide.end());
             items.insert(items.end(), gen.begin(), gen.end());
             int rc = grow(&b->d_geoms, b->geoms_cap, (int)n_active, b->stream);
             if (rc == LAT_OK) rc = grow(&b->d_items, b->items_cap, (int)items.size(), b->stream);

@@ -191,14 +191,18 @@ void compact_table(Geom &g, const TabEntry *host_tab)
     }
 }
 
+// LAT_KERNEL_WIDE covers two kernels: the 2D spin-1/2 one (kernels_wide.cu)
+// and the 3D / spin-S one (kernels_wide3.cu).
+static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supported(g); }
+
 int choose_kernel(const lattice *lt)
 {
     if (lt->P.layout == LAT_BITPACKED) return LAT_KERNEL_AUTO;  // bit-packed path
     if (lt->kernel == LAT_KERNEL_GENERIC) return LAT_KERNEL_GENERIC;
     if (lt->kernel == LAT_KERNEL_TILED && tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
-    if (lt->kernel == LAT_KERNEL_WIDE && wide_supported(lt->geom)) return LAT_KERNEL_WIDE;
+    if (lt->kernel == LAT_KERNEL_WIDE && any_wide(lt->geom)) return LAT_KERNEL_WIDE;
     if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel != 0) return lt->tuned_kernel;
-    if (wide_supported(lt->geom)) return LAT_KERNEL_WIDE;
+    if (any_wide(lt->geom)) return LAT_KERNEL_WIDE;
     if (tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
     return LAT_KERNEL_GENERIC;
 }
@@ -215,7 +219,8 @@ int enqueue_sweeps(lattice *lt, int k, cudaStream_t st)
         } else if (kern == LAT_KERNEL_TILED) {
             e = launch_sweep_tiled(lt->geom, lt->tile_w, lt->tile_h, off, st);
         } else if (kern == LAT_KERNEL_WIDE) {
-            e = launch_sweep_wide(lt->geom, off, st);
+            e = wide_supported(lt->geom) ? launch_sweep_wide(lt->geom, off, st)
+                                         : launch_sweep_wide3(lt->geom, off, st);
         } else {
             e = launch_half_sweep_generic(lt->geom, 0, off, st);
             if (e == cudaSuccess) e = launch_half_sweep_generic(lt->geom, 1, off, st);
@@ -746,7 +751,7 @@ int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sw
     if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_WIDE) return LAT_EINVAL;
     if (tile_w < 0 || tile_h < 0 || sweeps_per_graph < 0) return LAT_EINVAL;
     if (kernel == LAT_KERNEL_TILED && !tiled_supported(lt->geom)) return LAT_ENOTSUP;
-    if (kernel == LAT_KERNEL_WIDE && !wide_supported(lt->geom)) return LAT_ENOTSUP;
+    if (kernel == LAT_KERNEL_WIDE && !any_wide(lt->geom)) return LAT_ENOTSUP;
     if (!tile_shape_ok(tile_w, tile_h)) return LAT_EINVAL;
     lt->kernel = kernel;
     lt->tile_w = tile_w;

@@ -12,6 +12,8 @@
 // then updates s[(sweep+1) & 1] in place and reduces the sweep's counters.
 // Neighbour counts, thresholds and acceptance are those of the tiled kernel
 // (bytes 0x01 / 0xFF, bit-sliced adder, t' = thr - 1 table).
+#include <algorithm>
+
 #include "lattice_internal.cuh"
 
 namespace lat {
@@ -193,10 +195,14 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
     const uint32_t cpr = g.half >> 4;  // 16-site chunks per plane row
-    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     Counts cnt;
     const SweepView v = sweep_view(g);
-    if (t < (uint64_t)g.L * cpr) wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+    // Grid-stride over chunks with one resident wave of CTAs: the counter
+    // reduction (and its barrier) happens once per CTA, not once per chunk.
+    const uint64_t total = (uint64_t)g.L * cpr;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
     if (colour == 1) flush(v, sweep, cnt, kNE, red);
 }
 
@@ -217,7 +223,18 @@ int wide_chunks(const Geom &g) { return (int)(((uint64_t)g.L * (g.half >> 4) + k
 cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st)
 {
     const Geom k = tiled_geom(g);  // compact table in t' = thr - 1 form
-    const unsigned blocks = (unsigned)wide_chunks(g);
+    // one wave: SMs x resident CTAs per SM (queried once per model)
+    static int resident[2] = {0, 0};
+    const int m = g.model == LAT_NE ? 1 : 0;
+    if (resident[m] == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (m) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide_half<true>, kThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide_half<false>, kThreads, 0);
+        resident[m] = sms * (per > 0 ? per : 1);
+    }
+    const unsigned blocks = (unsigned)std::min<long long>(wide_chunks(g), resident[m]);
     for (int colour = 0; colour < 2; ++colour) {
         if (g.model == LAT_NE)
             k_wide_half<true><<<blocks, kThreads, 0, st>>>(k, colour, off);

@@ -1,0 +1,307 @@
+// kernels_wide3.cu -- two launches per sweep (one per colour, the kernel
+// boundary being the device-wide barrier of §III.A steps 6-7) for Ising
+// lattices that are 3D or have spin S > 1/2 (the extension of §III: "any
+// spin value"), int8 spins in the checkerboard-planar layout, L a multiple
+// of 16.
+//
+// A thread owns 8 consecutive same-colour sites of one plane row (one 8-byte
+// load).  Neighbour sums of the 8 sites come from byte-wise additions: each
+// neighbour byte is first offset by smax (so every byte is in [0, 2 smax])
+// with a carry-free SWAR add, then the 2*dims neighbour words are summed
+// with plain adds (at most 6 * 2 * 8 = 96 per byte, no carries).  The
+// proposal, dE index, table lookup and acceptance follow the generic
+// kernel site by site; draws come from the same Philox groups (4 sites per
+// call for spin-1/2, 2 for spin-S).  Colour 0 reads s[sweep & 1] and writes
+// the new colour-0 sites and a copy of the colour-1 sites into
+// s[(sweep+1) & 1]; colour 1 then updates that buffer in place and reduces
+// the sweep's counters.
+#include <algorithm>
+
+#include "lattice_internal.cuh"
+
+namespace lat {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxTab = 2465;  // largest table: two_S = 7, 3D
+
+// Byte-wise a + b for bytes whose true sums stay in [0, 255] (no carry
+// between bytes).
+LAT_D uint32_t add_bytes(uint32_t a, uint32_t b)
+{
+    return ((a & 0x7F7F7F7Fu) + (b & 0x7F7F7F7Fu)) ^ ((a ^ b) & 0x80808080u);
+}
+
+struct Acc3 {
+    long long bond = 0, mag = 0, up = 0;
+};
+
+// The fields of a Geom that this kernel reads, small enough for registers.
+struct View3 {
+    int dims, L, two_S, dsmax, nmax, nn;
+    uint32_t G, rows, half;
+    uint64_t plane;
+    int8_t *s0, *s1;
+};
+
+LAT_D View3 view3(const Geom &g)
+{
+    View3 v;
+    v.dims = g.dims;
+    v.L = g.L;
+    v.two_S = g.two_S;
+    v.dsmax = g.dsmax;
+    v.nmax = g.nmax;
+    v.nn = g.nn;
+    v.G = g.G;
+    v.rows = g.rows;
+    v.half = g.half;
+    v.plane = g.plane;
+    v.s0 = g.s[0];
+    v.s1 = g.s[1];
+    return v;
+}
+
+// Colour `colour` of the 8-site chunk k of plane row r = y + L*z.
+template <int SH>
+LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigned long long sweep,
+                       const PhiloxPre &pp, uint32_t r, uint32_t k, Acc3 &acc)
+{
+    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
+    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
+    if (colour == 1) src = dst;
+    const int L = g.L;
+    const uint32_t half = g.half;
+    const int oc = 1 - colour;
+    const int y = (int)(r % (uint32_t)L), z = (int)(r / (uint32_t)L);
+    auto row = [&](int c, uint32_t rr) { return src + (uint64_t)c * g.plane + (uint64_t)rr * half; };
+    const uint32_t ym = (uint32_t)((y == 0 ? L - 1 : y - 1) + L * z);
+    const uint32_t yp = (uint32_t)((y == L - 1 ? 0 : y + 1) + L * z);
+    const uint2 S = *reinterpret_cast<const uint2 *>(row(colour, r) + 8 * k);
+    const uint2 O = *reinterpret_cast<const uint2 *>(row(oc, r) + 8 * k);
+    const uint2 Yn = *reinterpret_cast<const uint2 *>(row(oc, ym) + 8 * k);
+    const uint2 Ys = *reinterpret_cast<const uint2 *>(row(oc, yp) + 8 * k);
+    uint2 Zd = make_uint2(0u, 0u), Zu = make_uint2(0u, 0u);
+    if (g.dims == 3) {
+        const uint32_t zm = (uint32_t)(y + L * (z == 0 ? L - 1 : z - 1));
+        const uint32_t zp = (uint32_t)(y + L * (z == L - 1 ? 0 : z + 1));
+        Zd = *reinterpret_cast<const uint2 *>(row(oc, zm) + 8 * k);
+        Zu = *reinterpret_cast<const uint2 *>(row(oc, zp) + 8 * k);
+    }
+    // row-shifted neighbours: x = 2j + p with p = (colour + y + z) & 1
+    const bool p1 = ((colour + y + z) & 1) != 0;
+    const uint32_t nwr = half >> 2;
+    uint2 Lf, R;
+    if (!p1) {  // west is j-1 of the other plane, east is j
+        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k - 1 + nwr) % nwr];
+        Lf.x = __funnelshift_l(prev, O.x, 8);
+        Lf.y = __funnelshift_l(O.x, O.y, 8);
+        R = O;
+    } else {    // west is j, east is j+1
+        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k + 2) % nwr];
+        Lf = O;
+        R.x = __funnelshift_r(O.x, O.y, 8);
+        R.y = __funnelshift_r(O.y, next, 8);
+    }
+    // neighbour sums offset by 2*dims*smax, byte-wise
+    const int smax = max_spin(g.two_S);
+    const uint32_t off = 0x01010101u * (uint32_t)smax;
+    uint32_t nlo = add_bytes(Lf.x, off) + add_bytes(R.x, off) + add_bytes(Yn.x, off) + add_bytes(Ys.x, off);
+    uint32_t nhi = add_bytes(Lf.y, off) + add_bytes(R.y, off) + add_bytes(Yn.y, off) + add_bytes(Ys.y, off);
+    if (g.dims == 3) {
+        nlo += add_bytes(Zd.x, off) + add_bytes(Zu.x, off);
+        nhi += add_bytes(Zd.y, off) + add_bytes(Zu.y, off);
+    }
+    const int noff = 2 * g.dims * smax;
+    const uint32_t g0 = r * g.G + ((8u * k) >> SH);  // first Philox group of the chunk
+    constexpr int kCalls = 8 >> SH;
+    U4 u[kCalls];
+#pragma unroll
+    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
+    uint32_t out_lo = 0, out_hi = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t sw = q < 4 ? S.x : S.y, nw = q < 4 ? nlo : nhi, ow = q < 4 ? O.x : O.y;
+        const int sh8 = 8 * (q & 3);
+        const int s_old = (int)(int8_t)(sw >> sh8);
+        const int n = (int)((nw >> sh8) & 0xFFu) - noff;
+        const int k_old = state_of_spin(g.two_S, s_old);
+        int k_new;
+        uint32_t u_acc;
+        if (SH == 2) {
+            k_new = 1 - k_old;
+            u_acc = word_of(u[q >> 2], q & 3);
+        } else {
+            const int w = 2 * (q & 1);
+            u_acc = word_of(u[q >> 1], w);
+            const uint32_t u_prop = word_of(u[q >> 1], w + 1);
+            k_new = k_old + 1 + (int)(((uint64_t)u_prop * (uint64_t)g.two_S) >> 32);
+            if (k_new > g.two_S) k_new -= g.two_S + 1;
+        }
+        const int s_new = spin_of_state(g.two_S, k_new);
+        const TabEntry e = stab[(s_new - s_old + g.dsmax) * g.nn + (n + g.nmax)];
+        const int s_fin = (e.always || u_acc < e.thr) ? s_new : s_old;
+        const uint32_t b = ((uint32_t)s_fin & 0xFFu) << sh8;
+        if (q < 4) out_lo |= b;
+        else out_hi |= b;
+        if (colour == 1) {
+            const int so = (int)(int8_t)(ow >> sh8);
+            acc.bond += (long long)(s_fin * n);
+            acc.mag += s_fin + so;
+            acc.up += (s_fin > 0) + (so > 0);
+        }
+    }
+    *reinterpret_cast<uint2 *>(dst + (uint64_t)colour * g.plane + (uint64_t)r * half + 8 * k) =
+        make_uint2(out_lo, out_hi);
+    if (colour == 0) *reinterpret_cast<uint2 *>(dst + g.plane + (uint64_t)r * half + 8 * k) = O;
+}
+
+template <int SH>
+__global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int off)
+{
+    __shared__ TabEntry stab[kMaxTab];
+    __shared__ long long red[kThreads / 32];
+    for (int i = threadIdx.x; i < g.tab_n; i += blockDim.x) stab[i] = g.tab[i];
+    __syncthreads();
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+    const uint32_t cpr = g.half >> 3;  // 8-site chunks per plane row
+    const uint64_t total = (uint64_t)g.rows * cpr;
+    const View3 v = view3(g);
+    Acc3 acc;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        wide3_chunk<SH>(v, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+    if (colour == 1) {
+        unsigned long long *slot = series_slot(g.ctrl, sweep);
+        long long v;
+        v = block_sum_ll(acc.bond, red);
+        if (threadIdx.x == 0) add_counter(slot + 0, v);
+        v = block_sum_ll(acc.mag, red);
+        if (threadIdx.x == 0) add_counter(slot + 1, v);
+        v = block_sum_ll(acc.up, red);
+        if (threadIdx.x == 0) add_counter(slot + 2, v);
+    }
+}
+
+// Batched form: a persistent grid takes (lattice, item) pairs from an
+// atomic counter; an item is kItemChunks x kThreads chunks of one colour of
+// one lattice.  The lattice's descriptor and table are reloaded only when a
+// CTA moves to another lattice (items are ordered by lattice).
+constexpr int kItemChunks = 4;
+
+__global__ void __launch_bounds__(kThreads) k_batch_wide3(const Geom *geoms, const uint2 *items, int n_items,
+                                                         unsigned *next_item, int colour)
+{
+    __shared__ TabEntry stab[kMaxTab];
+    __shared__ long long red[kThreads / 32];
+    __shared__ Geom sg;
+    __shared__ int cur;
+    int loaded = -1;
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = cur;
+        if (it >= n_items) break;
+        const uint2 w = items[it];
+        if ((int)w.x != loaded) {
+            if (threadIdx.x < sizeof(Geom) / 4)
+                reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
+                    reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
+            __syncthreads();
+            for (int i = threadIdx.x; i < sg.tab_n; i += blockDim.x) stab[i] = sg.tab[i];
+            loaded = (int)w.x;
+            __syncthreads();
+        }
+        // register copies: no aliasing with shared-memory stores
+        const View3 g = view3(sg);
+        Ctrl *const ctrl = sg.ctrl;
+        const bool spin_half = sg.sh == 2;
+        const unsigned long long sweep = ctrl->sweep;
+        PhiloxPre pp;
+        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
+        const uint32_t cpr = g.half >> 3;
+        const uint64_t total = (uint64_t)g.rows * cpr;
+        Acc3 acc;
+#pragma unroll 1
+        for (int c = 0; c < kItemChunks; ++c) {
+            const uint64_t t = ((uint64_t)w.y * kItemChunks + (uint64_t)c) * kThreads + threadIdx.x;
+            if (t >= total) break;
+            if (spin_half)
+                wide3_chunk<2>(g, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+            else
+                wide3_chunk<1>(g, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+        }
+        if (colour == 1) {
+            unsigned long long *slot = series_slot(ctrl, sweep);
+            long long v;
+            v = block_sum_ll(acc.bond, red);
+            if (threadIdx.x == 0) add_counter(slot + 0, v);
+            v = block_sum_ll(acc.mag, red);
+            if (threadIdx.x == 0) add_counter(slot + 1, v);
+            v = block_sum_ll(acc.up, red);
+            if (threadIdx.x == 0) add_counter(slot + 2, v);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int wide3_items(const Geom &g)
+{
+    const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
+    const uint64_t per = (uint64_t)kItemChunks * kThreads;
+    return (int)((chunks + per - 1) / per);
+}
+
+int batch_wide3_grid()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide3, kThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                               int colour, int grid, cudaStream_t st)
+{
+    k_batch_wide3<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    return cudaGetLastError();
+}
+
+bool wide3_supported(const Geom &g)
+{
+    return g.model == LAT_ISING && (g.dims == 3 || g.two_S >= 2) && (g.L % 16) == 0 &&
+           g.bits[0] == nullptr && g.tab_n <= kMaxTab;
+}
+
+cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st)
+{
+    static int resident[2] = {0, 0};
+    const int which = g.two_S == 1 ? 0 : 1;
+    if (resident[which] == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (which == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide3_half<2>, kThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide3_half<1>, kThreads, 0);
+        resident[which] = sms * (per > 0 ? per : 1);
+    }
+    const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((chunks + kThreads - 1) / kThreads,
+                                                        (uint64_t)resident[which]);
+    for (int colour = 0; colour < 2; ++colour) {
+        if (which == 0) k_wide3_half<2><<<blocks, kThreads, 0, st>>>(g, colour, off);
+        else k_wide3_half<1><<<blocks, kThreads, 0, st>>>(g, colour, off);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace lat

@@ -274,6 +274,12 @@ cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
 bool bitpacked_supported(const Geom &g);
 bool wide_supported(const Geom &g);
 cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st);
+bool wide3_supported(const Geom &g);
+cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
+int wide3_items(const Geom &g);   // batch items of one colour of one lattice
+int batch_wide3_grid();
+cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                               int colour, int grid, cudaStream_t st);
 int wide_chunks(const Geom &g);
 // batched engine
 Geom tiled_geom(const Geom &g);

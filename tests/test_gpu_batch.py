@@ -2,8 +2,9 @@
 bit where each would end alone, and where the oracle ends.
 
 Mixed batches cover the one-launch tiled sweep (2D spin-1/2, L % 32 == 0,
-Ising and North-East), the two-launch generic sweep (3D, spin-S, other L),
-lattices dropping out at different sweep counts, and graph replays.
+Ising and North-East), the two-launch wide sweep (3D or spin-S Ising,
+L % 16 == 0), the two-launch generic sweep (other sizes), lattices dropping
+out at different sweep counts, and graph replays.
 """
 import numpy as np
 import pytest
@@ -24,6 +25,10 @@ MIX = [
     (2, 20, 1, lt.NE, 0.0, 0.0, 0.45, 22, lt.INIT_EQUILIBRIUM, 45),
     (2, 288, 1, lt.NE, 0.5, -1.0, 1.5, 23, lt.INIT_RANDOM, 9),
     (2, 32, 1, lt.ISING, 1.0, 0.0, 3.5, 24, lt.INIT_RANDOM, 1),
+    (3, 16, 2, lt.ISING, 1.0, 0.0, 3.0, 31, lt.INIT_RANDOM, 40),
+    (3, 32, 1, lt.ISING, 1.0, 0.05, 4.2, 32, lt.INIT_COLD, 35),
+    (2, 48, 3, lt.ISING, 0.9, -0.2, 5.0, 33, lt.INIT_RANDOM, 66),
+    (3, 16, 7, lt.ISING, 1.0, 0.0, 30.0, 34, lt.INIT_RANDOM, 12),
 ]
 
 

@@ -90,6 +90,15 @@ def test_2d_spin_S(two_S):
     run_pair(2, 12, two_S, lt.ISING, 0.9, -0.1, 1.7 * two_S, 5, lt.INIT_RANDOM, 30)
 
 
+@pytest.mark.parametrize("dims,L,two_S", [(3, 16, 1), (3, 16, 2), (3, 32, 3), (3, 16, 8),
+                                          (2, 16, 2), (2, 48, 4), (2, 64, 7), (3, 48, 2)])
+def test_wide_three_d_and_spin_S(dims, L, two_S):
+    T = 2.0 * max(1, two_S) ** 1.2
+    for kernel in (lt.KERNEL_WIDE, lt.KERNEL_AUTO):
+        run_pair(dims, L, two_S, lt.ISING, 1.0, 0.15, T, 13 + L + two_S, lt.INIT_RANDOM, 15,
+                 kernel=kernel)
+
+
 @pytest.mark.parametrize("L", [4, 16, 48, 64, 288])
 @pytest.mark.parametrize("c", [0.05, 0.3, 0.45, 0.7])
 def test_north_east_c_mode(L, c):
@@ -173,9 +182,10 @@ def test_full_size_2d_L4096_random(kernel):
     run_pair(2, 4096, 1, lt.ISING, 1.0, 0.0, 2.0, 7, lt.INIT_RANDOM, 3, kernel=kernel)
 
 
-def test_full_size_3d_L256_spin_one():
+@pytest.mark.parametrize("kernel", [lt.KERNEL_GENERIC, lt.KERNEL_WIDE])
+def test_full_size_3d_L256_spin_one(kernel):
     # 3D spin-1, L=256, T=2.0 + 7*(2/15), uniform random start (seed 11).
-    run_pair(3, 256, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, 11, lt.INIT_RANDOM, 1)
+    run_pair(3, 256, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, 11, lt.INIT_RANDOM, 1, kernel=kernel)
 
 
 @pytest.mark.parametrize("kernel", [lt.KERNEL_TILED, lt.KERNEL_WIDE])
