@@ -89,9 +89,13 @@ enum lattice_kernel {
     LAT_KERNEL_GENERIC = 1, /* two launches per sweep, one per colour; any model */
     LAT_KERNEL_TILED = 2,   /* one launch per sweep, shared-memory tiles with halo
                                recompute; 2D spin-1/2 (Ising and North-East), L % 32 == 0 */
-    LAT_KERNEL_WIDE = 3     /* two launches per sweep, several sites per thread: 2D
+    LAT_KERNEL_WIDE = 3,    /* two launches per sweep, several sites per thread: 2D
                                spin-1/2 (Ising and North-East, L % 32 == 0), or Ising
                                in 3D / with spin S > 1/2 (L % 16 == 0) */
+    LAT_KERNEL_RESIDENT = 4 /* one launch for many sweeps: one CTA holds the whole
+                               lattice in shared memory; 2D spin-1/2 (Ising and
+                               North-East), L % 32 == 0, L^2 (+ L^2/4 for North-East)
+                               bytes <= 220 KiB, i.e. L <= 448 (Ising) / 416 (NE) */
 };
 
 typedef struct lattice lattice_t;
@@ -213,8 +217,11 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream);
 /* Schedule n more sweeps of lat in the next lattice_batch_run. */
 int lattice_batch_add(lattice_batch_t *b, lattice_t *lat, int64_t n);
 /* Run every scheduled sweep; returns after queueing (lattice_synchronize
- * or lattice_batch_synchronize waits).  Lattices with fewer remaining
- * sweeps drop out of later launches. */
+ * or lattice_batch_synchronize waits: each lattice's stream is made to wait
+ * for the batch).  Lattices with fewer remaining sweeps drop out of later
+ * launches.  2D spin-1/2 lattices with L <= 128 (under LAT_KERNEL_AUTO) or
+ * set to LAT_KERNEL_RESIDENT run as resident CTAs, one per lattice, for all
+ * their sweeps, concurrently with the others. */
 int lattice_batch_run(lattice_batch_t *b);
 int lattice_batch_synchronize(lattice_batch_t *b);
 void lattice_batch_destroy(lattice_batch_t *b);

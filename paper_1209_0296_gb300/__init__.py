@@ -15,12 +15,13 @@ from ._lib import LatticeError, LatticeRequest, LatticeResult, check, load
 
 __all__ = ["Lattice", "Batch", "Server", "LatticeError", "load", "threshold_table",
            "ISING", "NE", "INIT_COLD", "INIT_RANDOM", "INIT_EQUILIBRIUM", "INT8", "BITPACKED",
-           "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED", "KERNEL_WIDE"]
+           "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED", "KERNEL_WIDE",
+           "KERNEL_RESIDENT"]
 
 ISING, NE = 0, 1
 INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
 INT8, BITPACKED = 0, 1
-KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_WIDE = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_WIDE, KERNEL_RESIDENT = 0, 1, 2, 3, 4
 
 
 def _stream_handle(stream) -> int:

@@ -5,7 +5,9 @@
 // two persistent launches (colour 0, colour 1) over (lattice, item) pairs of
 // the wide 3D / spin-S kernel and two over (lattice, chunk) pairs of the
 // generic kernel, then one small kernel that advances every lattice's sweep
-// counter.  Steps
+// counter.  Small 2D spin-1/2 lattices instead run as resident CTAs (one CTA
+// per lattice holding it in shared memory for all its sweeps) on a side
+// stream, concurrently with the step loop of the others.  Steps
 // with the same set of lattices are captured once in a CUDA graph and
 // replayed.  Every lattice keeps its own seed, table and sweep counter, so
 // its result is bit-identical to running it alone.
@@ -31,6 +33,14 @@ struct lattice_batch {
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, wide colour 0 / 1
     unsigned *d_counters = nullptr;
     int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0;
+    // resident lattices
+    cudaStream_t res_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_done = nullptr;   // end of a run: each lattice's stream waits on it
+    Geom *d_res_geoms = nullptr;
+    int res_geoms_cap = 0;
+    long long *d_res_n = nullptr;
+    int res_n_cap = 0;
 };
 
 namespace {
@@ -38,6 +48,8 @@ namespace {
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
 constexpr int kCounters = 6;
+constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
+constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
 
 template <typename T>
 int grow(T **p, int &cap, int need, cudaStream_t st)
@@ -121,6 +133,51 @@ int run_steps(lattice_batch *b, const Shape &sh, int64_t steps)
     return LAT_OK;
 }
 
+bool runs_resident(const lattice *lt)
+{
+    if (!resident_supported(lt->geom)) return false;
+    if (choose_kernel(lt) == LAT_KERNEL_RESIDENT) return true;
+    return lt->kernel == LAT_KERNEL_AUTO && lt->P.L <= kResidentMaxL;
+}
+
+// Launch the resident lattices on the side stream (after the work already
+// on the batch stream) and record the join event.
+int run_resident(lattice_batch *b, const std::vector<std::pair<lattice *, int64_t>> &res)
+{
+    const int n = (int)res.size();
+    std::vector<Geom> geoms((size_t)n);
+    std::vector<long long> counts((size_t)n);
+    size_t smem = 0;
+    long long most = 0;
+    for (int i = 0; i < n; ++i) {
+        geoms[(size_t)i] = tiled_geom(res[(size_t)i].first->geom);
+        counts[(size_t)i] = (long long)res[(size_t)i].second;
+        smem = std::max(smem, resident_smem_bytes(res[(size_t)i].first->geom));
+        most = std::max(most, counts[(size_t)i]);
+    }
+    int rc = grow(&b->d_res_geoms, b->res_geoms_cap, n, b->stream);
+    if (rc == LAT_OK) rc = grow(&b->d_res_n, b->res_n_cap, n, b->stream);
+    if (rc != LAT_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (b->res_stream == nullptr) e = cudaStreamCreateWithFlags(&b->res_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && b->ev_fork == nullptr) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && b->ev_join == nullptr) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_res_geoms, geoms.data(), (size_t)n * sizeof(Geom), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_res_n, counts.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host vectors go out of scope
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->res_stream, b->ev_fork, 0);
+    for (long long done = 0; done < most && e == cudaSuccess; done += kResidentChunk)
+        e = launch_batch_resident(b->d_res_geoms, b->d_res_n, n, done, kResidentChunk, smem, b->res_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->res_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch resident launch");
+    return LAT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -173,6 +230,15 @@ int lattice_batch_run(lattice_batch_t *b)
         int rc = ensure_series(pr.first, (unsigned long long)(pr.first->sweeps + pr.second));
         if (rc != LAT_OK) return rc;
     }
+    // Small lattices: resident CTAs on the side stream.
+    std::vector<std::pair<lattice *, int64_t>> res, rest;
+    for (auto &pr : work) (runs_resident(pr.first) ? res : rest).push_back(pr);
+    if (!res.empty()) {
+        int rc = run_resident(b, res);
+        if (rc != LAT_OK) return rc;
+    }
+    for (auto &pr : res) pr.first->sweeps += pr.second;
+    work.swap(rest);
     // Run in phases: all lattices until the smallest remaining count is
     // done, then drop it, and so on.
     std::sort(work.begin(), work.end(), [](const auto &a, const auto &c) { return a.second > c.second; });
@@ -233,6 +299,16 @@ int lattice_batch_run(lattice_batch_t *b)
         --n_active;
     }
     for (auto &pr : work) pr.first->sweeps += pr.second;
+    cudaError_t e = cudaSuccess;
+    if (!res.empty()) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    // Order later work on each lattice's own stream after the batch.
+    if (e == cudaSuccess && b->ev_done == nullptr) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, b->stream);
+    for (auto *list : {&work, &res})
+        for (auto &pr : *list)
+            if (e == cudaSuccess && pr.first->stream != b->stream)
+                e = cudaStreamWaitEvent(pr.first->stream, b->ev_done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch join");
     return LAT_OK;
 }
 
@@ -240,6 +316,7 @@ int lattice_batch_synchronize(lattice_batch_t *b)
 {
     if (b == nullptr) return LAT_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && b->res_stream) e = cudaStreamSynchronize(b->res_stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch synchronize");
     return LAT_OK;
 }
@@ -252,6 +329,13 @@ void lattice_batch_destroy(lattice_batch_t *b)
     dev_free(b->d_items, b->stream);
     dev_free(b->d_ctrls, b->stream);
     dev_free(b->d_counters, b->stream);
+    if (b->res_stream) cudaStreamSynchronize(b->res_stream);
+    dev_free(b->d_res_geoms, b->stream);
+    dev_free(b->d_res_n, b->stream);
+    if (b->res_stream) cudaStreamDestroy(b->res_stream);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
 }

@@ -201,6 +201,7 @@ int choose_kernel(const lattice *lt)
     if (lt->kernel == LAT_KERNEL_GENERIC) return LAT_KERNEL_GENERIC;
     if (lt->kernel == LAT_KERNEL_TILED && tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
     if (lt->kernel == LAT_KERNEL_WIDE && any_wide(lt->geom)) return LAT_KERNEL_WIDE;
+    if (lt->kernel == LAT_KERNEL_RESIDENT && resident_supported(lt->geom)) return LAT_KERNEL_RESIDENT;
     if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel != 0) return lt->tuned_kernel;
     if (any_wide(lt->geom)) return LAT_KERNEL_WIDE;
     if (tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
@@ -209,9 +210,23 @@ int choose_kernel(const lattice *lt)
 
 // Queue k sweeps with sweep offsets 0..k-1 relative to ctrl->sweep, then
 // advance ctrl->sweep by k.  Used directly and under stream capture.
-int enqueue_sweeps(lattice *lt, int k, cudaStream_t st)
+// Sweeps per resident launch (a launch runs about a microsecond per sweep at
+// L = 64, so this bounds one kernel to well under a second).
+constexpr int64_t kResidentChunk = 1 << 16;
+
+int enqueue_sweeps(lattice *lt, int64_t k, cudaStream_t st)
 {
     const int kern = choose_kernel(lt);
+    if (kern == LAT_KERNEL_RESIDENT) {
+        for (int64_t off = 0; off < k; off += kResidentChunk) {
+            const int m = (int)std::min<int64_t>(kResidentChunk, k - off);
+            cudaError_t e = launch_sweep_resident(lt->geom, (int)off, m, st);
+            if (e != cudaSuccess) return cuda_fail(e, "resident sweep launch");
+        }
+        cudaError_t e = launch_advance(lt->ctrl, (unsigned long long)k, st);
+        if (e != cudaSuccess) return cuda_fail(e, "advance launch");
+        return LAT_OK;
+    }
     for (int off = 0; off < k; ++off) {
         cudaError_t e;
         if (lt->P.layout == LAT_BITPACKED) {
@@ -263,10 +278,14 @@ static int ensure_graph(lattice *lt)
 // ---------------------------------------------------------------------------
 // Autotuner for LAT_KERNEL_AUTO on 2D spin-1/2 lattices: the first sweep call
 // with enough sweeps times a few of them with each candidate (the wide
-// two-launch kernel, the tiled one-launch kernel at two tile heights) and
-// keeps the fastest.  The timed sweeps are the caller's own sweeps: every
-// kernel produces the same bits, so tuning changes no result.  Choices are
-// cached per (model, L) for the life of the process.
+// two-launch kernel, the tiled one-launch kernel at two tile heights and,
+// when the lattice fits one CTA, the resident kernel) and keeps the fastest.
+// Each candidate is timed the way the sweep loop will run it: the resident
+// kernel as one launch, the others as a replayed CUDA graph (after one
+// untimed replay), so launch overheads count as they will.  The timed sweeps
+// are the caller's own sweeps: every kernel produces the same bits, so
+// tuning changes no result.  Choices are cached per (model, L) for the life
+// of the process.
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneChoice {
@@ -274,7 +293,43 @@ struct TuneChoice {
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, TuneChoice> g_tune;
-constexpr int kTuneSweeps = 3;
+constexpr int kTuneSweeps = 4;
+
+// Time kTuneSweeps sweeps of the current candidate after kTuneSweeps untimed
+// ones (2 * kTuneSweeps sweeps in all, enqueued on the lattice's stream).
+int time_candidate(lattice *lt, cudaEvent_t ev0, cudaEvent_t ev1, float &ms)
+{
+    cudaGraphExec_t exec = nullptr;
+    int rc = LAT_OK;
+    const bool graphed = choose_kernel(lt) != LAT_KERNEL_RESIDENT;
+    if (graphed) {
+        if (lt->cap_stream == nullptr &&
+            cudaStreamCreateWithFlags(&lt->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return LAT_ECUDA;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(lt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return LAT_ECUDA;
+        rc = enqueue_sweeps(lt, kTuneSweeps, lt->cap_stream);
+        const cudaError_t e = cudaStreamEndCapture(lt->cap_stream, &graph);
+        if (rc == LAT_OK && e != cudaSuccess) rc = LAT_ECUDA;
+        if (rc == LAT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = LAT_ECUDA;
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != LAT_OK) return rc;
+    }
+    for (int rep = 0; rep < 2 && rc == LAT_OK; ++rep) {
+        if (rep == 1 && cudaEventRecord(ev0, lt->stream) != cudaSuccess) rc = LAT_ECUDA;
+        if (rc == LAT_OK) {
+            if (graphed) rc = cudaGraphLaunch(exec, lt->stream) == cudaSuccess ? LAT_OK : LAT_ECUDA;
+            else rc = enqueue_sweeps(lt, kTuneSweeps, lt->stream);
+        }
+    }
+    if (rc == LAT_OK && cudaEventRecord(ev1, lt->stream) != cudaSuccess) rc = LAT_ECUDA;
+    if (rc == LAT_OK && cudaEventSynchronize(ev1) != cudaSuccess) rc = LAT_ECUDA;
+    if (rc == LAT_OK && cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) rc = LAT_ECUDA;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (rc == LAT_ECUDA) return cuda_fail(cudaGetLastError(), "autotune");
+    return rc;
+}
 }  // namespace
 
 static int autotune(lattice *lt, int64_t &left)
@@ -289,9 +344,10 @@ static int autotune(lattice *lt, int64_t &left)
             return LAT_OK;
         }
     }
-    const TuneChoice cands[] = {{LAT_KERNEL_WIDE, 0}, {LAT_KERNEL_TILED, 64}, {LAT_KERNEL_TILED, 32}};
-    const int n_c = (int)(sizeof cands / sizeof cands[0]);
-    if (left < (int64_t)(n_c * (kTuneSweeps + 1))) return LAT_OK;  // too short to tune now
+    const TuneChoice all[] = {{LAT_KERNEL_WIDE, 0}, {LAT_KERNEL_TILED, 64}, {LAT_KERNEL_TILED, 32},
+                              {LAT_KERNEL_RESIDENT, 0}};
+    const int n_c = resident_supported(lt->geom) ? 4 : 3;
+    if (left < (int64_t)(n_c * 2 * kTuneSweeps)) return LAT_OK;  // too short to tune now
     cudaEvent_t ev[2];
     if (cudaEventCreate(&ev[0]) != cudaSuccess) return LAT_OK;
     if (cudaEventCreate(&ev[1]) != cudaSuccess) {
@@ -299,33 +355,25 @@ static int autotune(lattice *lt, int64_t &left)
         return LAT_OK;
     }
     float best = 1e30f;
-    TuneChoice pick = cands[0];
+    TuneChoice pick = all[0];
     const int keep_tile = lt->tile_h;
-    for (int c = 0; c < n_c; ++c) {
-        lt->tuned_kernel = cands[c].kernel;
-        lt->tile_h = cands[c].tile_h;
-        // one untimed sweep (first launch of this kernel), then the timed ones
-        int rc = enqueue_sweeps(lt, 1, lt->stream);
-        if (rc == LAT_OK && cudaEventRecord(ev[0], lt->stream) != cudaSuccess) rc = LAT_ECUDA;
-        if (rc == LAT_OK) rc = enqueue_sweeps(lt, kTuneSweeps, lt->stream);
-        if (rc == LAT_OK && cudaEventRecord(ev[1], lt->stream) != cudaSuccess) rc = LAT_ECUDA;
-        if (rc == LAT_OK && cudaEventSynchronize(ev[1]) != cudaSuccess) rc = LAT_ECUDA;
+    int rc = LAT_OK;
+    for (int c = 0; c < n_c && rc == LAT_OK; ++c) {
+        lt->tuned_kernel = all[c].kernel;
+        lt->tile_h = all[c].tile_h;
         float ms = 0.f;
-        if (rc == LAT_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) rc = LAT_ECUDA;
-        if (rc != LAT_OK) {
-            cudaEventDestroy(ev[0]);
-            cudaEventDestroy(ev[1]);
-            return rc;
-        }
-        lt->sweeps += kTuneSweeps + 1;
-        left -= kTuneSweeps + 1;
+        rc = time_candidate(lt, ev[0], ev[1], ms);
+        if (rc != LAT_OK) break;
+        lt->sweeps += 2 * kTuneSweeps;
+        left -= 2 * kTuneSweeps;
         if (ms < best) {
             best = ms;
-            pick = cands[c];
+            pick = all[c];
         }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
+    if (rc != LAT_OK) return rc;
     lt->tuned_kernel = pick.kernel;
     lt->tile_h = keep_tile ? keep_tile : pick.tile_h;
     lt->graph_valid = false;
@@ -349,7 +397,8 @@ int sweep_impl(lattice *lt, int64_t n)
         n -= lt->sweeps - before;   // sweeps already done (and counted) by the tuner
         if (left == 0) return LAT_OK;
     }
-    const int gk = lt->graph_sweeps;
+    // The resident kernel runs many sweeps per launch: no graph needed.
+    const int gk = choose_kernel(lt) == LAT_KERNEL_RESIDENT ? 0 : lt->graph_sweeps;
     if (gk > 0 && left >= gk) {
         rc = ensure_graph(lt);
         if (rc != LAT_OK) return rc;
@@ -360,7 +409,7 @@ int sweep_impl(lattice *lt, int64_t n)
         }
     }
     if (left > 0) {
-        rc = enqueue_sweeps(lt, (int)left, lt->stream);
+        rc = enqueue_sweeps(lt, left, lt->stream);
         if (rc != LAT_OK) return rc;
     }
     lt->sweeps += n;
@@ -748,10 +797,11 @@ int lattice_device_spins(lattice_t *lt, void **dev_ptr, size_t *bytes)
 int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sweeps_per_graph)
 {
     if (lt == nullptr) return LAT_EINVAL;
-    if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_WIDE) return LAT_EINVAL;
+    if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_RESIDENT) return LAT_EINVAL;
     if (tile_w < 0 || tile_h < 0 || sweeps_per_graph < 0) return LAT_EINVAL;
     if (kernel == LAT_KERNEL_TILED && !tiled_supported(lt->geom)) return LAT_ENOTSUP;
     if (kernel == LAT_KERNEL_WIDE && !any_wide(lt->geom)) return LAT_ENOTSUP;
+    if (kernel == LAT_KERNEL_RESIDENT && !resident_supported(lt->geom)) return LAT_ENOTSUP;
     if (!tile_shape_ok(tile_w, tile_h)) return LAT_EINVAL;
     lt->kernel = kernel;
     lt->tile_w = tile_w;

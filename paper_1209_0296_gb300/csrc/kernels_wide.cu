@@ -41,10 +41,42 @@ struct Counts {
     int bond = 0, mag = 0, up = 0, unfl = 0;
 };
 
-// Sweep colour `colour` of the 16-site chunk k of plane row y.
-template <bool kNE>
+// W consecutive 4-byte words (4W same-colour sites) from p.
+template <int W>
+LAT_D void load_words(const int8_t *p, uint32_t (&v)[W])
+{
+    if constexpr (W == 4) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else if constexpr (W == 2) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        v[0] = *reinterpret_cast<const uint32_t *>(p);
+    }
+}
+
+template <int W>
+LAT_D void store_words(int8_t *p, const uint32_t (&v)[W])
+{
+    if constexpr (W == 4) *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+    else if constexpr (W == 2) *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+    else *reinterpret_cast<uint32_t *>(p) = v[0];
+}
+
+// Sweep colour `colour` of the chunk k (4W sites, W Philox groups) of plane
+// row y.  The two-launch kernel uses W = 4 (16 sites, one 16-byte load per
+// row); the resident kernel uses smaller W on small lattices, for more
+// threads with shorter dependency chains.  kInPlace: both buffers are the
+// same array (the resident kernel), so colour 0 does not copy the colour-1
+// sites.
+template <bool kNE, bool kInPlace = false, int W = 4, bool kPre = false>
 LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsigned long long sweep,
-                      const PhiloxPre &pp, int y, int k, Counts &cnt)
+                      const PhiloxPre &pp, int y, int k, Counts &cnt, const U4 *upre = nullptr)
 {
     const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
     int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
@@ -55,36 +87,33 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
     const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
     const uint32_t nwr = half >> 2;  // 4-byte words per plane row
     auto row = [&](int c, int r) { return src + (uint64_t)c * g.plane + (uint64_t)r * half; };
-    const uint4 S4 = *reinterpret_cast<const uint4 *>(row(colour, y) + 16 * k);
-    const uint4 O4 = *reinterpret_cast<const uint4 *>(row(oc, y) + 16 * k);
-    const uint4 U4v = *reinterpret_cast<const uint4 *>(row(oc, ym) + 16 * k);   // north
-    const uint4 D4v = *reinterpret_cast<const uint4 *>(row(oc, yp) + 16 * k);   // south
+    uint32_t S[W], O[W], U[W], D[W];
+    load_words<W>(row(colour, y) + 4 * W * k, S);
+    load_words<W>(row(oc, y) + 4 * W * k, O);
+    load_words<W>(row(oc, ym) + 4 * W * k, U);   // north
+    load_words<W>(row(oc, yp) + 4 * W * k, D);   // south
     const bool p1 = ((colour + y) & 1) != 0;
     uint32_t adj;
     {
-        const uint32_t w = p1 ? (uint32_t)(4 * k + 4) : (uint32_t)(4 * k - 1 + nwr);
+        const uint32_t w = p1 ? (uint32_t)(W * k + W) : (uint32_t)(W * k - 1 + nwr);
         adj = reinterpret_cast<const uint32_t *>(row(oc, y))[w % nwr];
     }
-    const uint32_t S[4] = {S4.x, S4.y, S4.z, S4.w};
-    const uint32_t O[4] = {O4.x, O4.y, O4.z, O4.w};
-    const uint32_t U[4] = {U4v.x, U4v.y, U4v.z, U4v.w};
-    const uint32_t D[4] = {D4v.x, D4v.y, D4v.z, D4v.w};
-    uint32_t Lf[4], R[4];
+    uint32_t Lf[W], R[W];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < W; ++w) {
         if (!p1) {  // x = 2j: west is j-1 of the other plane, east is j
             Lf[w] = __funnelshift_l(w == 0 ? adj : O[w - 1], O[w], 8);
             R[w] = O[w];
         } else {    // x = 2j+1: west is j, east is j+1
             Lf[w] = O[w];
-            R[w] = __funnelshift_r(O[w], w == 3 ? adj : O[w + 1], 8);
+            R[w] = __funnelshift_r(O[w], w == W - 1 ? adj : O[w + 1], 8);
         }
     }
-    uint32_t t[4][4], locked[4];
+    uint32_t t[W][4], locked[W];
     bool need = false;
     const char *tb = reinterpret_cast<const char *>(sthr);
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < W; ++w) {
         const uint32_t s1 = U[w] ^ D[w] ^ Lf[w];
         const uint32_t c1 = (U[w] & D[w]) | (U[w] & Lf[w]) | (D[w] & Lf[w]);
         const uint32_t b0 = s1 ^ R[w];
@@ -98,7 +127,7 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
         t[w][3] = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
         locked[w] = 0;
-        if (kNE) {
+        if constexpr (kNE) {
             // §III.B: north (U) and east (R) must be up; a locked site needs
             // no draw (t' all ones) and its flip is masked off below.
             locked[w] = U[w] | R[w];
@@ -111,21 +140,26 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
     }
     // An item that needs no draw has t' = all ones at every site, so any u
     // accepts exactly as "no draw" would.
-    U4 u[4] = {U4{0, 0, 0, 0}, U4{0, 0, 0, 0}, U4{0, 0, 0, 0}, U4{0, 0, 0, 0}};
-    if (need) {
-        const uint32_t g0 = (uint32_t)y * g.G + 4u * (uint32_t)k;
+    U4 u[W];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)colour);
+    for (int w = 0; w < W; ++w) u[w] = U4{0, 0, 0, 0};
+    if constexpr (kPre) {   // draws made by the caller (same groups, same counters)
+#pragma unroll
+        for (int w = 0; w < W; ++w) u[w] = upre[w];
+    } else if (need) {
+        const uint32_t g0 = (uint32_t)y * g.G + (uint32_t)(W * k);
+#pragma unroll
+        for (int w = 0; w < W; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)colour);
     }
-    uint32_t Sn[4], chg = 0;
+    uint32_t Sn[W], chg = 0;
     const uint32_t M1 = 0x02020202u;
     uint32_t ue = 0, dn = 0;
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < W; ++w) {
         const uint32_t acc = (u[w].x <= t[w][0] ? 1u : 0u) | (u[w].y <= t[w][1] ? 2u : 0u) |
                              (u[w].z <= t[w][2] ? 4u : 0u) | (u[w].w <= t[w][3] ? 8u : 0u);
         uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu;  // 0xFE at flipped sites
-        if (kNE) {
+        if constexpr (kNE) {
             F &= ~locked[w];
             chg |= ((((F >> 1) & 0x01010101u) * 0x01020408u) >> 24 & 0xFu) << (8 * w);
         }
@@ -137,32 +171,45 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             dn += (Sn[w] & M1) + (O[w] & M1);  // 2 per down spin, both planes
         }
     }
-    *reinterpret_cast<uint4 *>(dst + (uint64_t)colour * g.plane + (uint64_t)y * half + 16 * k) =
-        make_uint4(Sn[0], Sn[1], Sn[2], Sn[3]);
-    if (colour == 0)
-        *reinterpret_cast<uint4 *>(dst + (uint64_t)g.plane + (uint64_t)y * half + 16 * k) = O4;
+    store_words<W>(dst + (uint64_t)colour * g.plane + (uint64_t)y * half + 4 * W * k, Sn);
+    if (colour == 0 && !kInPlace) store_words<W>(dst + (uint64_t)g.plane + (uint64_t)y * half + 4 * W * k, O);
     int unfl = 0;
-    if (kNE) {
-        // persistence bytes of the 4 groups (bit q = site 4m+q)
-        uint32_t *fp = reinterpret_cast<uint32_t *>(g.flags + ((uint64_t)colour * L + y) * g.G + 4u * k);
-        const uint32_t f = *fp | chg;
-        *fp = f;
-        if (colour == 1) {
-            const uint32_t fo =
-                *reinterpret_cast<const uint32_t *>(g.flags + ((uint64_t)oc * L + y) * g.G + 4u * k);
-            unfl = 32 - __popc(f) - __popc(fo);
+    if constexpr (kNE) {
+        // persistence bytes of the W groups (bit q = site 4m+q)
+        uint8_t *fb = g.flags + ((uint64_t)colour * L + y) * g.G + (uint64_t)(W * k);
+        const uint8_t *fob = g.flags + ((uint64_t)oc * L + y) * g.G + (uint64_t)(W * k);
+        uint32_t f, fo = 0;
+        if constexpr (W == 4) {
+            uint32_t *fp = reinterpret_cast<uint32_t *>(fb);
+            f = *fp | chg;
+            *fp = f;
+            if (colour == 1) fo = *reinterpret_cast<const uint32_t *>(fob);
+        } else if constexpr (W == 2) {
+            uint16_t *fp = reinterpret_cast<uint16_t *>(fb);
+            f = (uint32_t)*fp | chg;
+            *fp = (uint16_t)f;
+            if (colour == 1) fo = *reinterpret_cast<const uint16_t *>(fob);
+        } else {
+            f = (uint32_t)*fb | chg;
+            *fb = (uint8_t)f;
+            if (colour == 1) fo = *fob;
         }
+        if (colour == 1) unfl = 8 * W - __popc(f) - __popc(fo);
     }
     if (colour == 1) {
         const int d2 = byte_sum(dn);
-        cnt.bond += 64 - byte_sum(ue);
-        cnt.mag += 32 - d2;
-        cnt.up += 32 - (d2 >> 1);
+        cnt.bond += 16 * W - byte_sum(ue);
+        cnt.mag += 8 * W - d2;
+        cnt.up += 8 * W - (d2 >> 1);
         cnt.unfl += unfl;
     }
 }
 
-LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, bool ne, int (*red)[4])
+// Add the block's counters to the sweep's slot (bond, mag, up[, unflipped]).
+// Warp sums go to shared memory and warp 0 adds them up.  32-bit partial
+// sums are enough: a block's |bond| is at most 2 per site it updated, and a
+// block never updates 2^30 sites in one call.
+LAT_D void flush_slot(unsigned long long *slot, const Counts &c, bool ne, int (*red)[4])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = __reduce_add_sync(0xffffffffu, c.bond);
@@ -176,12 +223,20 @@ LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, 
         red[warp][3] = rf;
     }
     __syncthreads();
-    if (threadIdx.x < (ne ? 4 : 3)) {
-        long long s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        add_counter(series_slot(g.ctrl, sweep) + threadIdx.x, s);
+    if (warp == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        const int b = __reduce_add_sync(0xffffffffu, in ? red[lane][0] : 0);
+        const int m = __reduce_add_sync(0xffffffffu, in ? red[lane][1] : 0);
+        const int u = __reduce_add_sync(0xffffffffu, in ? red[lane][2] : 0);
+        const int f = __reduce_add_sync(0xffffffffu, in ? red[lane][3] : 0);
+        if (lane < (ne ? 4 : 3)) add_counter(slot + lane, (long long)(lane == 0 ? b : lane == 1 ? m : lane == 2 ? u : f));
     }
     __syncthreads();
+}
+
+LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, bool ne, int (*red)[4])
+{
+    flush_slot(series_slot(g.ctrl, sweep), c, ne, red);
 }
 
 template <bool kNE>
@@ -204,6 +259,132 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
          t += (uint64_t)gridDim.x * blockDim.x)
         wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
     if (colour == 1) flush(v, sweep, cnt, kNE, red);
+}
+
+// Resident form for lattices that fit in one CTA's shared memory (§III.A
+// with the whole lattice as the block's tile): the CTA loads the spins (and
+// the North-East persistence bytes) once, runs n sweeps in place -- an
+// in-place checkerboard update is exact because a colour reads only the
+// other colour, and __syncthreads() is the barrier between the two -- and
+// writes the final state to s[(sweep + n) & 1].  One launch replaces 2n.
+constexpr int kResThreads = 512;
+constexpr size_t kResMaxBytes = 220 * 1024;
+
+// One lattice, n_sweeps sweeps, by the whole CTA.  g may live in shared
+// memory (the batched kernel): the sweep loop reads only register copies.
+// advance: the CTA also moves the lattice's sweep counter on by n_sweeps.
+template <bool kNE, int W>
+LAT_D void resident_body(const Geom &g, int off, int n_sweeps, bool advance, uint4 *res_smem, uint32_t *sthr,
+                         int (*red)[4])
+{
+    int8_t *sp = reinterpret_cast<int8_t *>(res_smem);
+    const uint64_t n16 = g.N >> 4;                       // N % 16 == 0 (L % 32 == 0)
+    const uint64_t f16 = kNE ? ((uint64_t)2 * g.rows * g.G) >> 4 : 0;  // flag bytes / 16
+    uint4 *fl4 = res_smem + n16;
+    const unsigned long long sweep0 = g.ctrl->sweep + (unsigned long long)off;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(g.s[sweep0 & 1]);
+        for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) res_smem[i] = src[i];
+        if constexpr (kNE) {
+            const uint4 *fsrc = reinterpret_cast<const uint4 *>(g.flags);
+            for (uint64_t i = threadIdx.x; i < f16; i += blockDim.x) fl4[i] = fsrc[i];
+        }
+    }
+    if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
+    __syncthreads();
+    SweepView v = sweep_view(g);
+    v.s0 = sp;
+    v.s1 = sp;
+    v.flags = reinterpret_cast<uint8_t *>(fl4);
+    const uint32_t cpr = g.half / (4 * W);
+    const uint32_t total = (uint32_t)g.L * cpr;
+    unsigned long long *slot0 = series_slot(g.ctrl, sweep0);  // slots of consecutive sweeps are contiguous
+    // With at most one chunk per thread and colour, a thread draws both
+    // colours' numbers at the start of the sweep: the colour-1 draws do not
+    // depend on the colour-0 result, so their Philox chain leaves the
+    // critical path.
+    const bool one = W == 1 && total <= blockDim.x;   // (register budget: narrow chunks only)
+    const int y1 = (int)(threadIdx.x / cpr), k1 = (int)(threadIdx.x % cpr);
+    for (int s = 0; s < n_sweeps; ++s) {
+        const unsigned long long sweep = sweep0 + (unsigned long long)s;
+        PhiloxPre pp;
+        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+        Counts cnt;
+        if (W == 1 && one) {
+            const bool act = threadIdx.x < total;
+            U4 u0[W], u1[W];
+            if (act) {
+                const uint32_t g0 = (uint32_t)y1 * g.G + (uint32_t)(W * k1);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    u0[w] = philox_item(pp, g0 + (uint32_t)w, 0u);
+                    u1[w] = philox_item(pp, g0 + (uint32_t)w, 1u);
+                }
+                wide_chunk<kNE, true, W, true>(v, sthr, 0, sweep, pp, y1, k1, cnt, u0);
+            }
+            __syncthreads();
+            if (act) wide_chunk<kNE, true, W, true>(v, sthr, 1, sweep, pp, y1, k1, cnt, u1);
+        } else {
+            for (uint32_t t = threadIdx.x; t < total; t += blockDim.x)
+                wide_chunk<kNE, true, W>(v, sthr, 0, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < total; t += blockDim.x)
+                wide_chunk<kNE, true, W>(v, sthr, 1, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+        }
+        flush_slot(slot0 + 4ull * (unsigned)s, cnt, kNE, red);   // ends with __syncthreads()
+    }
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(g.s[(sweep0 + (unsigned long long)n_sweeps) & 1]);
+        for (uint64_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = res_smem[i];
+        if constexpr (kNE) {
+            uint4 *fdst = reinterpret_cast<uint4 *>(g.flags);
+            for (uint64_t i = threadIdx.x; i < f16; i += blockDim.x) fdst[i] = fl4[i];
+        }
+    }
+    if (advance) {
+        __syncthreads();   // every thread has read the old counter long before
+        if (threadIdx.x == 0) g.ctrl->sweep = sweep0 + (unsigned long long)n_sweeps;
+    }
+}
+
+template <bool kNE, int W>
+__global__ void __launch_bounds__(kResThreads, 1) k_resident(Geom g, int off, int n_sweeps)
+{
+    extern __shared__ uint4 res_smem[];
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kResThreads / 32][4];
+    resident_body<kNE, W>(g, off, n_sweeps, false, res_smem, sthr, red);
+}
+
+// Batched form: CTA i sweeps lattice i (descriptor geoms[i]) by
+// min(chunk, n[i] - done) sweeps and advances its counter; lattices of
+// either model and width share the launch.
+__global__ void __launch_bounds__(kResThreads, 1) k_batch_resident(const Geom *geoms, const long long *n,
+                                                                   long long done, int chunk)
+{
+    extern __shared__ uint4 res_smem[];
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kResThreads / 32][4];
+    __shared__ Geom sg;
+    const long long left = n[blockIdx.x] - done;
+    if (left <= 0) return;   // uniform over the CTA
+    const int m = (int)(left < (long long)chunk ? left : (long long)chunk);
+    if (threadIdx.x < sizeof(Geom) / 4)
+        reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] = reinterpret_cast<const uint32_t *>(&geoms[blockIdx.x])[threadIdx.x];
+    __syncthreads();
+    const bool narrow = (uint64_t)sg.L * (sg.half >> 2) <= (uint64_t)kResThreads;
+    if (sg.model == LAT_NE) {
+        if (narrow) resident_body<true, 1>(sg, 0, m, true, res_smem, sthr, red);
+        else resident_body<true, 4>(sg, 0, m, true, res_smem, sthr, red);
+    } else {
+        if (narrow) resident_body<false, 1>(sg, 0, m, true, res_smem, sthr, red);
+        else resident_body<false, 4>(sg, 0, m, true, res_smem, sthr, red);
+    }
+}
+
+size_t resident_bytes(const Geom &g)
+{
+    return (size_t)g.N + (g.model == LAT_NE ? (size_t)2 * g.rows * g.G : 0);
 }
 
 }  // namespace
@@ -245,5 +426,53 @@ cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st)
     }
     return cudaSuccess;
 }
+
+}  // namespace lat
+
+namespace lat {
+
+bool resident_supported(const Geom &g)
+{
+    return wide_supported(g) && resident_bytes(g) <= kResMaxBytes;
+}
+
+cudaError_t launch_sweep_resident(const Geom &g, int off, int n_sweeps, cudaStream_t st)
+{
+    const Geom k = tiled_geom(g);
+    const size_t smem = resident_bytes(g);
+    // Sites per thread: 4 (W = 1) while that keeps every thread busy, else 16.
+    const bool narrow = (uint64_t)g.L * (g.half >> 2) <= (uint64_t)kResThreads;
+    const int m = (g.model == LAT_NE ? 2 : 0) + (narrow ? 1 : 0);
+    static bool attr[4] = {false, false, false, false};
+    void (*fn[4])(Geom, int, int) = {k_resident<false, 4>, k_resident<false, 1>, k_resident<true, 4>,
+                                     k_resident<true, 1>};
+    if (!attr[m]) {
+        cudaError_t e = cudaFuncSetAttribute(fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResMaxBytes);
+        if (e != cudaSuccess) return e;
+        attr[m] = true;
+    }
+    fn[m]<<<1, kResThreads, smem, st>>>(k, off, n_sweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace lat
+
+namespace lat {
+
+cudaError_t launch_batch_resident(const Geom *geoms, const long long *n, int n_lat, long long done, int chunk,
+                                  size_t smem, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kResMaxBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_batch_resident<<<n_lat, kResThreads, smem, st>>>(geoms, n, done, chunk);
+    return cudaGetLastError();
+}
+
+size_t resident_smem_bytes(const Geom &g) { return resident_bytes(g); }
 
 }  // namespace lat

@@ -274,6 +274,12 @@ cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
 bool bitpacked_supported(const Geom &g);
 bool wide_supported(const Geom &g);
 cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st);
+bool resident_supported(const Geom &g);
+cudaError_t launch_sweep_resident(const Geom &g, int off, int n_sweeps, cudaStream_t st);
+size_t resident_smem_bytes(const Geom &g);
+// geoms: compact-table descriptors (tiled_geom); n[i]: sweeps for lattice i
+cudaError_t launch_batch_resident(const Geom *geoms, const long long *n, int n_lat, long long done, int chunk,
+                                  size_t smem, cudaStream_t st);
 bool wide3_supported(const Geom &g);
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
 int wide3_items(const Geom &g);   // batch items of one colour of one lattice

@@ -106,3 +106,67 @@ def test_batch_rejects_bitpacked_and_bad_arguments():
     with pytest.raises(lt.LatticeError):
         b.add(_make(MIX[0]), -1)
     b.run()  # empty run is a no-op
+
+
+def test_many_small_lattices_resident():
+    # 160 small 2D spin-1/2 lattices (resident CTAs) with uneven sweep counts,
+    # next to two lattices on the step loop; every one equals its solo run,
+    # a sample equals the oracle.
+    rng = np.random.default_rng(5)
+    cfgs = []
+    for i in range(160):
+        L = int(rng.choice([32, 64, 96, 128]))
+        if i % 3 == 0:
+            cfgs.append((2, L, 1, lt.NE, 0.0, 0.0, float(rng.uniform(0.05, 0.45)), 1000 + i,
+                         lt.INIT_EQUILIBRIUM, int(rng.integers(1, 90))))
+        else:
+            cfgs.append((2, L, 1, lt.ISING, 1.0, float(rng.uniform(-0.2, 0.2)), float(rng.uniform(1.5, 3.5)),
+                         1000 + i, lt.INIT_RANDOM, int(rng.integers(1, 90))))
+    cfgs.append((2, 512, 1, lt.ISING, 1.0, 0.0, 2.3, 7, lt.INIT_RANDOM, 50))
+    cfgs.append((3, 16, 2, lt.ISING, 1.0, 0.0, 3.0, 8, lt.INIT_RANDOM, 70))
+    lats = [_make(c) for c in cfgs]
+    b = lt.Batch()
+    for g, c in zip(lats, cfgs):
+        b.add(g, c[-1])
+    b.run()
+    b.synchronize()
+    for i, (g, c) in enumerate(zip(lats, cfgs)):
+        n = c[-1]
+        spins, flags, done = g.get_state()
+        assert done == n
+        solo = _make(c)
+        solo.set_kernel(lt.KERNEL_WIDE)
+        solo.sweep(n)
+        s2, f2, _ = solo.get_state()
+        assert np.array_equal(spins, s2), c
+        assert np.array_equal(flags, f2), c
+        for k in ("bond", "mag", "up", "unflipped"):
+            assert np.array_equal(g.series(0, n)[k], solo.series(0, n)[k]), (c, k)
+        solo.close()
+        if i % 37 == 0:
+            o = oracle.Lattice(*c[:7], seed=c[7], init=c[8])
+            o.sweep(n)
+            assert np.array_equal(spins, o.spins), c
+    b.close()
+
+
+def test_explicit_resident_in_batch_and_stream_order():
+    # Lattices on their own streams, the batch on another: with no batch
+    # synchronise, work on a lattice's stream still sees the batch's result.
+    import torch
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    cfgs = [(2, 256, 1, lt.ISING, 1.0, 0.0, 2.269185, 41, lt.INIT_RANDOM, 33),
+            (2, 64, 1, lt.NE, 0.0, 0.0, 0.1, 42, lt.INIT_EQUILIBRIUM, 20),
+            (2, 1024, 1, lt.ISING, 1.0, 0.0, 2.5, 43, lt.INIT_RANDOM, 12)]
+    lats = [lt.Lattice(*c[:7], seed=c[7], init=c[8], stream=sa) for c in cfgs]
+    lats[0].set_kernel(lt.KERNEL_RESIDENT)
+    b = lt.Batch(stream=sb)
+    for g, c in zip(lats, cfgs):
+        b.add(g, c[-1])
+    b.run()
+    for g, c in zip(lats, cfgs):
+        g.sweep(3)            # queued on the lattice's stream after the batch
+        o = oracle.Lattice(*c[:7], seed=c[7], init=c[8])
+        o.sweep(c[-1] + 3)
+        assert np.array_equal(g.get_spins(), o.spins), c
+    b.close()

@@ -217,3 +217,60 @@ def test_never_accept_table_falls_back_to_generic():
         g.set_kernel(lt.KERNEL_TILED)
     assert e.value.code == -6
     run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 0.3, 3, lt.INIT_RANDOM, 20)
+
+
+# ---- resident kernel: the whole lattice in one CTA's shared memory ----------
+
+def test_config_L64_cold_1000_sweeps_resident():
+    run_pair(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, 1234, lt.INIT_COLD, 1000,
+             kernel=lt.KERNEL_RESIDENT)
+
+
+@pytest.mark.parametrize("L", [32, 64, 96, 128, 224, 448])
+def test_resident_ising(L):
+    # odd sweep counts per call: the final state alternates between buffers
+    run_pair(2, L, 1, lt.ISING, 1.0, 0.1, 2.4, 300 + L, lt.INIT_RANDOM, 45,
+             kernel=lt.KERNEL_RESIDENT, chunks=[7, 1, 30, 7])
+
+
+@pytest.mark.parametrize("L,c", [(32, 0.3), (64, 0.05), (160, 0.2), (416, 0.45)])
+def test_resident_north_east(L, c):
+    run_pair(2, L, 1, lt.NE, 0.0, 0.0, c, 400 + L, lt.INIT_EQUILIBRIUM, 41,
+             kernel=lt.KERNEL_RESIDENT, chunks=[1, 13, 27])
+
+
+def test_resident_north_east_with_field():
+    run_pair(2, 96, 1, lt.NE, 0.5, -1.0, 1.5, 23, lt.INIT_RANDOM, 20, kernel=lt.KERNEL_RESIDENT)
+
+
+def test_resident_interleaved_with_other_kernels():
+    # sweeps alternate between the resident, wide and tiled kernels on one
+    # lattice; the chain must be the oracle's
+    for model, Tc, init in ((lt.ISING, 2.269185, lt.INIT_RANDOM), (lt.NE, 0.2, lt.INIT_EQUILIBRIUM)):
+        J = 1.0 if model == lt.ISING else 0.0
+        o = oracle.Lattice(2, 128, 1, model, J, 0.0, Tc, seed=77, init=init)
+        g = lt.Lattice(2, 128, 1, model, J, 0.0, Tc, seed=77, init=init)
+        ser_o = o.sweep(60)
+        for kern, n in ((lt.KERNEL_RESIDENT, 9), (lt.KERNEL_WIDE, 5), (lt.KERNEL_RESIDENT, 20),
+                        (lt.KERNEL_TILED, 3), (lt.KERNEL_RESIDENT, 23)):
+            g.set_kernel(kern)
+            g.sweep(n)
+        spins, flags, n = g.get_state()
+        assert n == 60
+        assert np.array_equal(spins, o.spins)
+        if model == lt.NE:
+            assert np.array_equal(flags, o.flags)
+        ser = g.series(0, 60)
+        for k in ("bond", "mag", "up") + (("unflipped",) if model == lt.NE else ()):
+            assert np.array_equal(ser[k], ser_o[k]), k
+        g.close()
+
+
+def test_resident_rejects_what_does_not_fit():
+    for args in ((2, 480, 1, lt.ISING, 1.0, 0.0, 2.0), (2, 448, 1, lt.NE, 0.0, 0.0, 0.2),
+                 (3, 32, 1, lt.ISING, 1.0, 0.0, 4.0), (2, 64, 2, lt.ISING, 1.0, 0.0, 2.0),
+                 (2, 80, 1, lt.ISING, 1.0, 0.0, 2.0)):
+        g = lt.Lattice(*args, seed=1, init=lt.INIT_RANDOM)
+        with pytest.raises(lt.LatticeError):
+            g.set_kernel(lt.KERNEL_RESIDENT)
+        g.close()
