@@ -199,8 +199,9 @@ def run_gpu(args):
     lats = {lay: [lt.Lattice(2, L, 1, lt.ISING, 1.0, 0.0, T, seed=SEED, init=lt.INIT_RANDOM,
                              layout=lt.INT8 if lay == "int8" else lt.BITPACKED, stream=stream)
                   for T in TEMPS] for lay in LAYOUTS}
+    int8_kernel = {"auto": lt.KERNEL_AUTO, "wide": lt.KERNEL_WIDE, "tiled": lt.KERNEL_TILED}[args.int8_kernel]
     for g in lats["int8"]:
-        g.set_kernel(lt.KERNEL_AUTO, 0, args.tile_h, args.graph)
+        g.set_kernel(int8_kernel, 0, args.tile_h, args.graph)
     all_lats = lats["int8"] + lats["bitpacked"]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
 
@@ -315,6 +316,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_serving:
         extra["batched"] = batched_bench()
         extra["served"] = served_bench()
+    if rank == 0 and world == 1 and not args.no_other:
+        extra["other_configs"] = other_configs(dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "updates/ns", "n_gpus": world,
@@ -322,7 +325,8 @@ def run_gpu(args):
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "lattices": n_lat, "sweeps_per_step": S,
-                           "layouts": list(LAYOUTS), "int8_kernel": kname + " (autotuned)",
+                           "layouts": list(LAYOUTS),
+                           "int8_kernel": kname + (" (autotuned)" if args.int8_kernel == "auto" else " (fixed)"),
                            "int8_updates_per_ns": len(TEMPS) * S * L * L * args.steps / (ms_int8 * 1e6),
                            "tile": [256, kinfo["tile_h"]] if kname == "tiled" else None,
                            "sweeps_per_graph": gk,
@@ -352,12 +356,15 @@ def run_profile(args):
     torch.cuda.set_device(0)
     if args.profile_model == "ne":
         g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, 0.3, seed=21, init=lt.INIT_EQUILIBRIUM)
+    elif args.profile_model == "ising3d":   # 3D spin-1 at T = 2 + 7 * 2/15, random start (seed 11)
+        g = lt.Lattice(3, args.profile_L, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, seed=11,
+                       init=lt.INIT_RANDOM)
     else:
         g = lt.Lattice(2, args.profile_L, 1, lt.ISING, 1.0, 0.0, TEMPS[0], seed=SEED,
                        init=lt.INIT_RANDOM,
                        layout=lt.BITPACKED if args.profile_layout == "bitpacked" else lt.INT8)
     kern = {"auto": lt.KERNEL_AUTO, "tiled": lt.KERNEL_TILED, "wide": lt.KERNEL_WIDE,
-            "generic": lt.KERNEL_GENERIC}[args.profile_kernel]
+            "generic": lt.KERNEL_GENERIC, "resident": lt.KERNEL_RESIDENT}[args.profile_kernel]
     if args.profile_layout == "bitpacked":
         kern = lt.KERNEL_AUTO
     g.set_kernel(kern, 0, args.tile_h, 1 << 30)  # direct launches, no graphs
@@ -493,6 +500,92 @@ def served_bench(n_req=256, sweep_scale=0.01, load=None):
     return out
 
 
+def _timed_sweeps(torch, stream, lats, n, flush):
+    """Device time (s) of n sweeps of each lattice, L2 flushed first."""
+    with torch.cuda.stream(stream):
+        for g in lats:
+            g.sweep(2)                 # warm: tuner, graphs
+        flush.fill_(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for g in lats:
+            g.sweep(n)
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def other_configs(dev):
+    """The other named workloads at their full lattice sizes, for context
+    (each a short timed run; the parity tests cover their bits)."""
+    import torch
+    import paper_1209_0296_gb300 as lt
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    hbm, _, _ = peaks()
+    out = {}
+    names = {lt.KERNEL_TILED: "tiled", lt.KERNEL_WIDE: "wide", lt.KERNEL_GENERIC: "generic",
+             lt.KERNEL_RESIDENT: "resident"}
+
+    # L = 64, cold start, T = 2.269185, seed 1234, 1000 sweeps
+    g = lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=1234, init=lt.INIT_COLD, stream=stream)
+    g.sweep(100)
+    t = _timed_sweeps(torch, stream, [g], 1000, flush)
+    out["L64_cold_1000_sweeps"] = {"us_per_sweep": t / 1000 * 1e6, "updates_per_ns": 64 * 64 * 1000 / t / 1e9,
+                                   "kernel": names.get(g.get_kernel()["kernel"], "?")}
+    g.close()
+
+    # 3D spin-1, L = 256, 16 temperatures in [2, 4], random start (seed 11)
+    Ts = [2.0 + k * 2.0 / 15 for k in range(16)]
+    lats = [lt.Lattice(3, 256, 2, lt.ISING, 1.0, 0.0, T, seed=11, init=lt.INIT_RANDOM, stream=stream) for T in Ts]
+    n = 20
+    t_solo = _timed_sweeps(torch, stream, lats[:1], n, flush)
+    b = lt.Batch(stream=stream)
+    for gg in lats:
+        b.add(gg, 2)
+    b.run()
+    flush.fill_(4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for gg in lats:
+        b.add(gg, n)
+    b.run()
+    e1.record(stream)
+    e1.synchronize()
+    t_b = e0.elapsed_time(e1) * 1e-3
+    N3 = 256 ** 3
+    out["3d_spin1_L256_16T"] = {"solo_updates_per_ns": N3 * n / t_solo / 1e9,
+                                "batched_updates_per_ns": 16 * N3 * n / t_b / 1e9,
+                                "solo_alg_GBps": 2.0 * N3 * n / t_solo / 1e9, "sweeps": n,
+                                "kernel": names.get(lats[0].get_kernel()["kernel"], "?")}
+    b.close()
+    for gg in lats:
+        gg.close()
+
+    # North-East, L = 8192, c in {0.05, 0.1, 0.2, 0.3}, equilibrium start (seed 21)
+    lats = [lt.Lattice(2, 8192, 1, lt.NE, 0.0, 0.0, c, seed=21, init=lt.INIT_EQUILIBRIUM, stream=stream)
+            for c in (0.05, 0.1, 0.2, 0.3)]
+    n = 20
+    t = _timed_sweeps(torch, stream, lats, n, flush)
+    N4 = 8192 * 8192
+    out["NE_L8192_4c"] = {"updates_per_ns": 4 * N4 * n / t / 1e9,
+                          "alg_GBps": 2.25 * 4 * N4 * n / t / 1e9, "hbm_frac": 2.25 * 4 * N4 * n / t / 1e9 / hbm,
+                          "sweeps": n, "kernel": names.get(lats[0].get_kernel()["kernel"], "?")}
+    for gg in lats:
+        gg.close()
+
+    # one 2D Ising lattice far larger than L2: L = 32768 (1 GiB per buffer)
+    g = lt.Lattice(2, 32768, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=7, init=lt.INIT_RANDOM, stream=stream)
+    n = 10
+    t = _timed_sweeps(torch, stream, [g], n, flush)
+    N5 = 32768 * 32768
+    out["L32768_int8"] = {"updates_per_ns": N5 * n / t / 1e9, "alg_GBps": 2.0 * N5 * n / t / 1e9,
+                          "hbm_frac": 2.0 * N5 * n / t / 1e9 / hbm, "sweeps": n,
+                          "kernel": names.get(g.get_kernel()["kernel"], "?")}
+    g.close()
+    return out
+
+
 def load_profile_numbers(kname):
     """Per-sweep DRAM traffic and instruction count of the chosen kernel,
     from the committed ncu summary (empty when absent)."""
@@ -524,15 +617,19 @@ def main():
     ap.add_argument("--sweeps", type=int, default=1000, help="sweeps per lattice per step")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tile-h", type=int, default=0)
+    ap.add_argument("--int8-kernel", default="auto", choices=["auto", "wide", "tiled"],
+                    help="int8 sweep kernel (auto = the library's autotuner; a fixed choice keeps "
+                         "a profiled run on the kernel the plain run picks)")
     ap.add_argument("--graph", type=int, default=0, help="sweeps per CUDA graph (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-other", action="store_true", help="skip the timings of the other named workloads")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
     ap.add_argument("--profile-L", type=int, default=L)
-    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne"])
-    ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic"])
+    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d"])
+    ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic", "resident"])
     ap.add_argument("--profile-layout", default="int8", choices=["int8", "bitpacked"])
     args = ap.parse_args()
     if args.profile:
