@@ -149,6 +149,27 @@ int lattice_observables(lattice_t *lat, double *E, double *M, double *density,
 int lattice_series(lattice_t *lat, int64_t first, int64_t count, int64_t *bond,
                    int64_t *mag, int64_t *up, int64_t *unflipped);
 
+/* Spin-spin autocorrelation (§III.B, the Phi(t) equation):
+ *   Phi(t) = (1/N) sum_i [s_i(t) s_i(0) - m^2] / (1 - m^2),  m = <s_i> = 2c - 1,
+ * with the sum over sites read as the mean, so that Phi(0) = 1 for +-1 spins.
+ * lattice_set_reference stores the current configuration as s(0) (a device
+ * copy: N bytes, or the bit-packed size) and returns in *ref_sweep (may be
+ * NULL) the sweeps done at that moment.  From then on every sweep also
+ * records, in the same kernels as the other counters, the exact overlap
+ *   overlap = sum_i s_i(t) s_i(0)      (int64)
+ * of the state after that sweep.  A later call replaces the reference;
+ * lattice_clear_reference frees it and stops the recording.  Neither
+ * set_state nor set_spins changes the reference. */
+int lattice_set_reference(lattice_t *lat, int64_t *ref_sweep);
+int lattice_clear_reference(lattice_t *lat);
+/* Copy the overlaps of sweeps [first, first+count) (global sweep indexes as in
+ * lattice_series; first >= the reference's ref_sweep) to overlap[] and, if phi
+ * is not NULL, Phi = (overlap/N - m^2) / (1 - m^2) to phi[] (|m| < 1 required,
+ * LAT_EINVAL otherwise).  NULL arrays are skipped.  LAT_ENOENT if no reference
+ * is set, LAT_ERANGE if the range is not recorded. */
+int lattice_autocorrelation(lattice_t *lat, int64_t first, int64_t count, double m,
+                            int64_t *overlap, double *phi);
+
 /* Copy the N = L^dims spins (int8, x fastest, spin values) to host_out,
  * whatever the layout (waits for the stream). */
 int lattice_get_spins(lattice_t *lat, int8_t *host_out);

@@ -64,6 +64,8 @@ def _load():
             lib.oracle_measure.argtypes = [ctypes.c_int, ctypes.c_int, i8p, u8p,
                                            i64p, i64p, i64p, i64p]
             lib.oracle_measure.restype = None
+            lib.oracle_overlap.argtypes = [ctypes.c_int64, i8p, i8p]
+            lib.oracle_overlap.restype = ctypes.c_int64
             lib.oracle_metropolis_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
                                                         ctypes.POINTER(ctypes.c_uint32)]
             lib.oracle_metropolis_threshold.restype = ctypes.c_int
@@ -121,13 +123,34 @@ class Lattice:
         self.spins = np.zeros(self.N, dtype=np.int8)
         self.flags = np.zeros(self.N, dtype=np.uint8)
         self.sweep_index = 0
+        self.ref = None          # s(0) of the autocorrelation (§III.B, Phi(t))
         rc = _load().oracle_init(dims, L, two_S, model, self.J, self.h, self.T_or_c,
                                  self.seed, init, self.spins)
         if rc != 0:
             raise ValueError("oracle_init rejected the parameters")
 
+    def set_reference(self):
+        """Take the current configuration as s(0) of the autocorrelation."""
+        self.ref = self.spins.copy()
+
+    def overlap(self):
+        """sum_i s_i * s_i(0) of the current configuration (needs a reference)."""
+        return int(_load().oracle_overlap(self.N, self.spins, self.ref))
+
     def sweep(self, n: int):
-        """Advance n sweeps; returns dict of per-sweep int64 series (bond, mag, up, unflipped)."""
+        """Advance n sweeps; returns dict of per-sweep int64 series (bond, mag, up,
+        unflipped, and "overlap" = sum_i s_i(t) s_i(0) when a reference is set)."""
+        if self.ref is not None:
+            out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped", "overlap")}
+            for k in range(n):      # one sweep at a time, the overlap after each
+                one = self._sweep(1)
+                for key in ("bond", "mag", "up", "unflipped"):
+                    out[key][k] = one[key][0]
+                out["overlap"][k] = self.overlap()
+            return out
+        return self._sweep(n)
+
+    def _sweep(self, n: int):
         out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
         rc = _load().oracle_sweep(self.dims, self.L, self.two_S, self.model, self.J, self.h,
                                   self.T_or_c, self.seed, self.spins,

@@ -342,5 +342,15 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
     return 0;
 }
 
+/* Overlap of a configuration with a reference one, sum_i s_i * ref_i: the  */
+/* numerator of the spin-spin autocorrelation Phi(t) of §III.B (the sum      */
+/* over sites i of s_i(t) s_i(0)).  Both arrays in the same site order.      */
+int64_t oracle_overlap(int64_t n, const int8_t *s, const int8_t *ref)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) c += (int64_t)s[i] * (int64_t)ref[i];
+    return c;
+}
+
 /* Number of distinct 32-bit words this oracle needs from Philox per call. */
 int oracle_sites_per_draw(int two_S) { return two_S == 1 ? 4 : 2; }

@@ -73,6 +73,31 @@ class Lattice:
               "lattice_series")
         return out
 
+    def set_reference(self) -> int:
+        """Store the current configuration as s(0) of the autocorrelation;
+        returns the sweeps done at that moment."""
+        r = ctypes.c_int64()
+        check(self._lib.lattice_set_reference(self._h, ctypes.byref(r)), "lattice_set_reference")
+        return r.value
+
+    def clear_reference(self):
+        check(self._lib.lattice_clear_reference(self._h), "lattice_clear_reference")
+
+    def autocorrelation(self, first: int, count: int | None = None, m: float | None = None):
+        """Exact overlaps sum_i s_i(t) s_i(0) of sweeps [first, first+count)
+        and Phi(t) with polarisation m (default 2c - 1 for a North-East
+        lattice in c-mode; Phi omitted when m is unknown)."""
+        if count is None:
+            count = self.sweeps() - first
+        if m is None and self.model == NE and self.J == 0.0 and self.h == 0.0:
+            m = 2.0 * self.T_or_c - 1.0
+        ov = np.zeros(count, dtype=np.int64)
+        phi = np.zeros(count, dtype=np.float64) if m is not None else None
+        check(self._lib.lattice_autocorrelation(self._h, int(first), int(count),
+                                                0.0 if m is None else float(m), _ptr(ov), _ptr(phi)),
+              "lattice_autocorrelation")
+        return (ov, phi) if phi is not None else (ov, None)
+
     def get_spins(self, out=None):
         if out is None:
             out = np.empty(self.N, dtype=np.int8)

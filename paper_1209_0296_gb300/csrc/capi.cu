@@ -132,6 +132,9 @@ static size_t flag_bytes(const Params &P)
     return 2 * rows * G;
 }
 
+// Bit-packed layout: two colour planes of L rows of bw words.
+static size_t bits_bytes(const Params &P) { return (size_t)2 * P.L * (((size_t)P.L / 2 + 31) / 32) * 4; }
+
 size_t footprint_bytes(const Params &P)
 {
     size_t b = 2 * (size_t)P.N;                             // int8 spins, double-buffered
@@ -151,17 +154,22 @@ int ensure_series(lattice *lt, unsigned long long need)
     if (slots <= lt->series_cap && lt->series != nullptr) return LAT_OK;
     unsigned long long cap = lt->series_cap ? lt->series_cap : 64;
     while (cap < slots) cap *= 2;
-    const size_t bytes = (size_t)cap * 4 * sizeof(unsigned long long);
+    // [cap][4] counters, then [cap] reference overlaps (the autocorrelation)
+    const size_t bytes = (size_t)cap * 5 * sizeof(unsigned long long);
     void *p = nullptr;
     cudaError_t e = dev_alloc(&p, bytes, lt->stream);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "series alloc");
+    unsigned long long *np = (unsigned long long *)p;
     e = cudaMemsetAsync(p, 0, bytes, lt->stream);
     if (e == cudaSuccess && lt->series != nullptr)
-        e = cudaMemcpyAsync(p, lt->series, (size_t)lt->series_cap * 4 * sizeof(unsigned long long),
+        e = cudaMemcpyAsync(np, lt->series, (size_t)lt->series_cap * 4 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToDevice, lt->stream);
+    if (e == cudaSuccess && lt->series != nullptr)
+        e = cudaMemcpyAsync(np + 4 * cap, lt->series + 4 * lt->series_cap,
+                            (size_t)lt->series_cap * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                            lt->stream);
     if (e == cudaSuccess)
-        e = launch_set_ctrl(lt->ctrl, (unsigned long long)lt->sweeps, (unsigned long long *)p, base,
-                            cap, lt->stream);
+        e = launch_set_ctrl(lt->ctrl, (unsigned long long)lt->sweeps, np, base, cap, np + 4 * cap, lt->stream);
     if (e != cudaSuccess) {
         dev_free(p, lt->stream);
         return cuda_fail(e, "series grow");
@@ -431,6 +439,8 @@ static void release(lattice *lt)
     dev_free(lt->ctrl, st);
     dev_free(lt->series, st);
     dev_free(lt->scratch4, st);
+    dev_free(lt->ref, st);
+    dev_free(lt->ref_bits, st);
     delete lt;
 }
 
@@ -631,6 +641,71 @@ int lattice_series(lattice_t *lt, int64_t first, int64_t count, int64_t *bond, i
     return LAT_OK;
 }
 
+int lattice_set_reference(lattice_t *lt, int64_t *ref_sweep)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    cudaStream_t st = lt->stream;
+    cudaError_t e = cudaSuccess;
+    if (lt->P.layout == LAT_BITPACKED) {
+        if (lt->ref_bits == nullptr) e = dev_alloc((void **)&lt->ref_bits, bits_bytes(lt->P), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lt->ref_bits, lt->bits[lt->sweeps & 1], bits_bytes(lt->P), cudaMemcpyDeviceToDevice,
+                                st);
+        lt->geom.ref_bits = lt->ref_bits;
+    } else {
+        if (lt->ref == nullptr) e = dev_alloc((void **)&lt->ref, (size_t)lt->P.N, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lt->ref, lt->spins[lt->sweeps & 1], (size_t)lt->P.N, cudaMemcpyDeviceToDevice, st);
+        lt->geom.ref = lt->ref;
+    }
+    if (e != cudaSuccess) {
+        lt->geom.ref = nullptr;
+        lt->geom.ref_bits = nullptr;
+        lt->ref_sweep = -1;
+        return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "set reference");
+    }
+    lt->ref_sweep = lt->sweeps;
+    lt->graph_valid = false;   // the descriptor captured in a graph changed
+    if (ref_sweep) *ref_sweep = lt->ref_sweep;
+    return LAT_OK;
+}
+
+int lattice_clear_reference(lattice_t *lt)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    dev_free(lt->ref, lt->stream);
+    dev_free(lt->ref_bits, lt->stream);
+    lt->ref = nullptr;
+    lt->ref_bits = nullptr;
+    lt->geom.ref = nullptr;
+    lt->geom.ref_bits = nullptr;
+    lt->ref_sweep = -1;
+    lt->graph_valid = false;
+    return LAT_OK;
+}
+
+int lattice_autocorrelation(lattice_t *lt, int64_t first, int64_t count, double m, int64_t *overlap,
+                            double *phi)
+{
+    if (lt == nullptr || first < 0 || count < 0) return LAT_EINVAL;
+    if (lt->ref_sweep < 0) return LAT_ENOENT;
+    if (phi != nullptr && !(std::fabs(m) < 1.0)) return LAT_EINVAL;
+    if (first < lt->series_first || first < lt->ref_sweep || first + count > lt->sweeps) return LAT_ERANGE;
+    if (count == 0) return LAT_OK;
+    std::vector<long long> buf((size_t)count);
+    cudaError_t e = cudaMemcpyAsync(buf.data(),
+                                    lt->series + 4 * lt->series_cap + (unsigned long long)(first - lt->series_first),
+                                    (size_t)count * sizeof(long long), cudaMemcpyDeviceToHost, lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "autocorrelation copy");
+    const double N = (double)lt->P.N, m2 = m * m;
+    for (int64_t k = 0; k < count; ++k) {
+        if (overlap) overlap[k] = buf[(size_t)k];
+        if (phi) phi[k] = ((double)buf[(size_t)k] / N - m2) / (1.0 - m2);
+    }
+    return LAT_OK;
+}
+
 int lattice_get_spins(lattice_t *lt, int8_t *host_out)
 {
     if (lt == nullptr || host_out == nullptr) return LAT_EINVAL;
@@ -776,7 +851,9 @@ int lattice_info(lattice_t *lt, int64_t *sweeps, int64_t *n_sites, int64_t *devi
     if (n_sites) *n_sites = (int64_t)lt->P.N;
     if (device_bytes)
         *device_bytes = (int64_t)(footprint_bytes(lt->P) +
-                                  (size_t)lt->series_cap * 4 * sizeof(long long));
+                                  (size_t)lt->series_cap * 5 * sizeof(long long) +
+                                  (lt->ref ? (size_t)lt->P.N : 0) +
+                                  (lt->ref_bits ? bits_bytes(lt->P) : 0));
     return LAT_OK;
 }
 

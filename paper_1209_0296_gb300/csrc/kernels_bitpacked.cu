@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_bits_half(Geom g, int colour, int 
     const int L = g.L;
     const uint32_t bw = g.bw;
     const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    long long bond = 0, mag = 0, up = 0, unfl = 0;
+    long long bond = 0, mag = 0, up = 0, unfl = 0, acf = 0;
     if (t < (uint64_t)L * bw) {
         const int y = (int)(t / bw);
         const int k = (int)(t % bw);
@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(kThreads) k_bits_half(Geom g, int colour, int 
             mag = 64 - 2 * downs;
             up = 64 - downs;
             unfl = 64 - (int)fl_c_pop - (int)fl_o_pop;
+            if (g.ref_bits != nullptr) {   // overlap with the reference: 64 - 2 * (# differing)
+                const uint32_t r1 = g.ref_bits[((uint64_t)1 * L + y) * bw + k];
+                const uint32_t r0 = g.ref_bits[(uint64_t)y * bw + k];
+                acf = 64 - 2 * (__popc(Sn ^ r1) + __popc(O ^ r0));
+            }
         }
     }
     if (colour == 1) {
@@ -169,6 +174,10 @@ __global__ void __launch_bounds__(kThreads) k_bits_half(Geom g, int colour, int 
         if (kNE) {
             v = block_sum_ll(unfl, red);
             if (threadIdx.x == 0) add_counter(slot + 3, v);
+        }
+        if (g.ref_bits != nullptr) {
+            v = block_sum_ll(acf, red);
+            if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), v);
         }
     }
 }

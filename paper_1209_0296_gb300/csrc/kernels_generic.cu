@@ -49,7 +49,7 @@ __global__ void k_init(Geom g, int init, uint32_t thr_c)
 
 // Partial per-sweep counters of one thread.
 struct Part {
-    long long bond = 0, mag = 0, up = 0, unfl = 0;
+    long long bond = 0, mag = 0, up = 0, unfl = 0, acf = 0;
 };
 
 // Sweep the colour-`colour` sites of Philox group t = (row r, group m) of
@@ -120,6 +120,7 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
             const int so = dst[io];
             pt.mag += s_fin + so;
             pt.up += (s_fin > 0) + (so > 0);
+            if (g.ref != nullptr) pt.acf += s_fin * g.ref[i] + so * g.ref[io];
         }
     }
     if (fl_c != nullptr) {
@@ -146,6 +147,10 @@ LAT_D void flush_counters(const Geom &g, unsigned long long sweep, const Part &p
     if (threadIdx.x == 0) add_counter(slot + 2, v);
     v = block_sum_ll(pt.unfl, red);
     if (threadIdx.x == 0) add_counter(slot + 3, v);
+    if (g.ref != nullptr) {
+        v = block_sum_ll(pt.acf, red);
+        if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), v);
+    }
 }
 
 // One colour of one sweep (thread = Philox group).  Colour 0 reads buffer
@@ -272,12 +277,13 @@ __global__ void k_to_planar(Geom g, const int8_t *linear, int8_t *planar)
 __global__ void k_advance(Ctrl *ctrl, unsigned long long k) { ctrl->sweep += k; }
 
 __global__ void k_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
-                           unsigned long long base, unsigned long long cap)
+                           unsigned long long base, unsigned long long cap, unsigned long long *acf)
 {
     ctrl->sweep = sweep;
     ctrl->series = series;
     ctrl->series_base = base;
     ctrl->series_cap = cap;
+    ctrl->acf = acf;
 }
 
 unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -359,9 +365,10 @@ cudaError_t launch_advance(Ctrl *ctrl, unsigned long long k, cudaStream_t st)
 }
 
 cudaError_t launch_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
-                            unsigned long long base, unsigned long long cap, cudaStream_t st)
+                            unsigned long long base, unsigned long long cap, unsigned long long *acf,
+                            cudaStream_t st)
 {
-    k_set_ctrl<<<1, 1, 0, st>>>(ctrl, sweep, series, base, cap);
+    k_set_ctrl<<<1, 1, 0, st>>>(ctrl, sweep, series, base, cap, acf);
     return cudaGetLastError();
 }
 

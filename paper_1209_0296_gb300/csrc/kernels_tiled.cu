@@ -178,7 +178,7 @@ LAT_D void do_pair(const Tile &t, const uint32_t *sthr, const PhiloxPre &pp, int
 // sized for tile_h; red: [kWarps][4] ints.  Called by every thread.
 template <bool kNE>
 LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, int tile_h, int off,
-                      unsigned char *smem_raw, int (*red)[4])
+                      unsigned char *smem_raw, int (*red)[5])
 {
     const int L = g.L;
     const int half = L >> 1;            // sites per plane row
@@ -289,8 +289,9 @@ LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, i
     // accumulators: ue counts 2 per unequal bond around a colour-1 site, dn
     // counts 2 per down spin; they are summed once at the end.
     const uint32_t M1 = 0x02020202u;
-    uint32_t ue = 0, dn = 0;
+    uint32_t ue = 0, dn = 0, dr = 0;   // dr: 2 per site differing from the reference
     int items = 0, unfl = 0;
+    const bool has_ref = g.ref != nullptr;
     for (int ry = warp; ry < th; ry += 2 * kWarps) {
         const bool two = ry + kWarps < th;
         const int gy = y0 + ry, gyb = y0 + ry + kWarps;
@@ -304,6 +305,11 @@ LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, i
             *reinterpret_cast<uint32_t *>(dst + g.plane + (size_t)gy * row_bytes + 4 * (size_t)(w0 + lane)) = nva;
             ue += ((ia.U ^ nva) & M1) + ((ia.D ^ nva) & M1) + ((ia.Lf ^ nva) & M1) + ((ia.R ^ nva) & M1);
             dn += (nva & M1) + (t.at(0, ry, lane) & M1);
+            if (has_ref) {
+                const size_t o = (size_t)gy * row_bytes + 4 * (size_t)(w0 + lane);
+                dr += ((nva ^ *reinterpret_cast<const uint32_t *>(g.ref + g.plane + o)) & M1) +
+                      ((t.at(0, ry, lane) ^ *reinterpret_cast<const uint32_t *>(g.ref + o)) & M1);
+            }
             ++items;
             if (kNE) {
                 uint8_t *fp = g.flags + (size_t)g.rows * wpr + (size_t)gy * wpr + w0 + lane;
@@ -315,6 +321,11 @@ LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, i
                 *reinterpret_cast<uint32_t *>(dst + g.plane + (size_t)gyb * row_bytes + 4 * (size_t)(w0 + lane)) = nvb;
                 ue += ((ib.U ^ nvb) & M1) + ((ib.D ^ nvb) & M1) + ((ib.Lf ^ nvb) & M1) + ((ib.R ^ nvb) & M1);
                 dn += (nvb & M1) + (t.at(0, ry + kWarps, lane) & M1);
+                if (has_ref) {
+                    const size_t o = (size_t)gyb * row_bytes + 4 * (size_t)(w0 + lane);
+                    dr += ((nvb ^ *reinterpret_cast<const uint32_t *>(g.ref + g.plane + o)) & M1) +
+                          ((t.at(0, ry + kWarps, lane) ^ *reinterpret_cast<const uint32_t *>(g.ref + o)) & M1);
+                }
                 ++items;
                 if (kNE) {
                     uint8_t *fp = g.flags + (size_t)g.rows * wpr + (size_t)gyb * wpr + w0 + lane;
@@ -331,17 +342,20 @@ LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, i
     const int bond = 16 * items - byte_sum(ue);
     const int mag = 8 * items - d2;
     const int up = 8 * items - (d2 >> 1);
+    const int acf = 8 * items - byte_sum(dr);   // overlap with the reference, both planes
 
     // ---- per-sweep counters: warp reduce, then one atomic per CTA and counter
     const int rb = __reduce_add_sync(0xffffffffu, bond);
     const int rm = __reduce_add_sync(0xffffffffu, mag);
     const int ru = __reduce_add_sync(0xffffffffu, up);
     const int rf = kNE ? __reduce_add_sync(0xffffffffu, unfl) : 0;
+    const int ra = has_ref ? __reduce_add_sync(0xffffffffu, acf) : 0;
     if (lane == 0) {
         red[warp][0] = rb;
         red[warp][1] = rm;
         red[warp][2] = ru;
         red[warp][3] = rf;
+        red[warp][4] = ra;
     }
     __syncthreads();
     if (threadIdx.x < (kNE ? 4 : 3)) {
@@ -349,6 +363,11 @@ LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, i
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
         add_counter(series_slot(g.ctrl, sweep) + threadIdx.x, s);
+    } else if (has_ref && threadIdx.x == 4) {
+        long long s = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += red[w][4];
+        add_counter(acf_slot(g.ctrl, sweep), s);
     }
 }
 
@@ -359,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(TiledArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t sthr[16];
-    __shared__ int red[kWarps][4];
+    __shared__ int red[kWarps][5];
     if (threadIdx.x < 16) sthr[threadIdx.x] = a.g.thr16[threadIdx.x];
     sweep_tile<kNE>(sweep_view(a.g), sthr, blockIdx.x, blockIdx.y, a.tile_h, a.off, smem_raw, red);
 }
@@ -380,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_tiled(const Geom *geoms, con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Geom sg;
     __shared__ uint32_t sthr[16];
-    __shared__ int red[kWarps][4];
+    __shared__ int red[kWarps][5];
     __shared__ int cur;
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);

@@ -38,7 +38,7 @@ LAT_D int byte_sum(uint32_t x)
 }
 
 struct Counts {
-    int bond = 0, mag = 0, up = 0, unfl = 0;
+    int bond = 0, mag = 0, up = 0, unfl = 0, acf = 0;
 };
 
 // W consecutive 4-byte words (4W same-colour sites) from p.
@@ -202,6 +202,16 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         cnt.mag += 8 * W - d2;
         cnt.up += 8 * W - (d2 >> 1);
         cnt.unfl += unfl;
+        if (g.ref != nullptr) {
+            // overlap with the reference over both planes' 8W sites:
+            // 8W - 2 * (# sites that differ); 0x02 marks a differing byte
+            uint32_t R1[W], R0[W], dr = 0;
+            load_words<W>(g.ref + g.plane + (uint64_t)y * half + 4 * W * k, R1);
+            load_words<W>(g.ref + (uint64_t)y * half + 4 * W * k, R0);
+#pragma unroll
+            for (int w = 0; w < W; ++w) dr += ((Sn[w] ^ R1[w]) & M1) + ((O[w] ^ R0[w]) & M1);
+            cnt.acf += 8 * W - byte_sum(dr);
+        }
     }
 }
 
@@ -209,18 +219,22 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
 // Warp sums go to shared memory and warp 0 adds them up.  32-bit partial
 // sums are enough: a block's |bond| is at most 2 per site it updated, and a
 // block never updates 2^30 sites in one call.
-LAT_D void flush_slot(unsigned long long *slot, const Counts &c, bool ne, int (*red)[4])
+// acf: the sweep's autocorrelation slot, or null when no reference is set.
+LAT_D void flush_slot(unsigned long long *slot, unsigned long long *acf, const Counts &c, bool ne,
+                      int (*red)[5])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = __reduce_add_sync(0xffffffffu, c.bond);
     const int rm = __reduce_add_sync(0xffffffffu, c.mag);
     const int ru = __reduce_add_sync(0xffffffffu, c.up);
     const int rf = __reduce_add_sync(0xffffffffu, c.unfl);
+    const int ra = acf ? __reduce_add_sync(0xffffffffu, c.acf) : 0;
     if (lane == 0) {
         red[warp][0] = rb;
         red[warp][1] = rm;
         red[warp][2] = ru;
         red[warp][3] = rf;
+        red[warp][4] = ra;
     }
     __syncthreads();
     if (warp == 0) {
@@ -230,20 +244,24 @@ LAT_D void flush_slot(unsigned long long *slot, const Counts &c, bool ne, int (*
         const int u = __reduce_add_sync(0xffffffffu, in ? red[lane][2] : 0);
         const int f = __reduce_add_sync(0xffffffffu, in ? red[lane][3] : 0);
         if (lane < (ne ? 4 : 3)) add_counter(slot + lane, (long long)(lane == 0 ? b : lane == 1 ? m : lane == 2 ? u : f));
+        if (acf) {
+            const int a = __reduce_add_sync(0xffffffffu, in ? red[lane][4] : 0);
+            if (lane == 0) add_counter(acf, (long long)a);
+        }
     }
     __syncthreads();
 }
 
-LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, bool ne, int (*red)[4])
+LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, bool ne, int (*red)[5])
 {
-    flush_slot(series_slot(g.ctrl, sweep), c, ne, red);
+    flush_slot(series_slot(g.ctrl, sweep), g.ref ? acf_slot(g.ctrl, sweep) : nullptr, c, ne, red);
 }
 
 template <bool kNE>
 __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
 {
     __shared__ uint32_t sthr[16];
-    __shared__ int red[kThreads / 32][4];
+    __shared__ int red[kThreads / 32][5];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
     __syncthreads();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
@@ -275,7 +293,7 @@ constexpr size_t kResMaxBytes = 220 * 1024;
 // advance: the CTA also moves the lattice's sweep counter on by n_sweeps.
 template <bool kNE, int W>
 LAT_D void resident_body(const Geom &g, int off, int n_sweeps, bool advance, uint4 *res_smem, uint32_t *sthr,
-                         int (*red)[4])
+                         int (*red)[5])
 {
     int8_t *sp = reinterpret_cast<int8_t *>(res_smem);
     const uint64_t n16 = g.N >> 4;                       // N % 16 == 0 (L % 32 == 0)
@@ -299,6 +317,7 @@ LAT_D void resident_body(const Geom &g, int off, int n_sweeps, bool advance, uin
     const uint32_t cpr = g.half / (4 * W);
     const uint32_t total = (uint32_t)g.L * cpr;
     unsigned long long *slot0 = series_slot(g.ctrl, sweep0);  // slots of consecutive sweeps are contiguous
+    unsigned long long *acf0 = g.ref ? acf_slot(g.ctrl, sweep0) : nullptr;
     // With at most one chunk per thread and colour, a thread draws both
     // colours' numbers at the start of the sweep: the colour-1 draws do not
     // depend on the colour-0 result, so their Philox chain leaves the
@@ -331,7 +350,7 @@ LAT_D void resident_body(const Geom &g, int off, int n_sweeps, bool advance, uin
             for (uint32_t t = threadIdx.x; t < total; t += blockDim.x)
                 wide_chunk<kNE, true, W>(v, sthr, 1, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
         }
-        flush_slot(slot0 + 4ull * (unsigned)s, cnt, kNE, red);   // ends with __syncthreads()
+        flush_slot(slot0 + 4ull * (unsigned)s, acf0 ? acf0 + (unsigned)s : nullptr, cnt, kNE, red);  // ends with __syncthreads()
     }
     {
         uint4 *dst = reinterpret_cast<uint4 *>(g.s[(sweep0 + (unsigned long long)n_sweeps) & 1]);
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(Geom g, int off, in
 {
     extern __shared__ uint4 res_smem[];
     __shared__ uint32_t sthr[16];
-    __shared__ int red[kResThreads / 32][4];
+    __shared__ int red[kResThreads / 32][5];
     resident_body<kNE, W>(g, off, n_sweeps, false, res_smem, sthr, red);
 }
 
@@ -364,7 +383,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_batch_resident(const Geom *g
 {
     extern __shared__ uint4 res_smem[];
     __shared__ uint32_t sthr[16];
-    __shared__ int red[kResThreads / 32][4];
+    __shared__ int red[kResThreads / 32][5];
     __shared__ Geom sg;
     const long long left = n[blockIdx.x] - done;
     if (left <= 0) return;   // uniform over the CTA

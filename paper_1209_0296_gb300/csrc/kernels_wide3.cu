@@ -34,7 +34,7 @@ LAT_D uint32_t add_bytes(uint32_t a, uint32_t b)
 }
 
 struct Acc3 {
-    long long bond = 0, mag = 0, up = 0;
+    long long bond = 0, mag = 0, up = 0, acf = 0;
 };
 
 // The fields of a Geom that this kernel reads, small enough for registers.
@@ -43,6 +43,7 @@ struct View3 {
     uint32_t G, rows, half;
     uint64_t plane;
     int8_t *s0, *s1;
+    const int8_t *ref;
 };
 
 LAT_D View3 view3(const Geom &g)
@@ -60,6 +61,7 @@ LAT_D View3 view3(const Geom &g)
     v.plane = g.plane;
     v.s0 = g.s[0];
     v.s1 = g.s[1];
+    v.ref = g.ref;
     return v;
 }
 
@@ -120,6 +122,12 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
 #pragma unroll
     for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
     uint32_t out_lo = 0, out_hi = 0;
+    uint2 RS = make_uint2(0u, 0u), RO = RS;   // reference words (colour 1 only)
+    const bool has_ref = colour == 1 && g.ref != nullptr;
+    if (has_ref) {
+        RS = *reinterpret_cast<const uint2 *>(g.ref + g.plane + (uint64_t)r * half + 8 * k);
+        RO = *reinterpret_cast<const uint2 *>(g.ref + (uint64_t)r * half + 8 * k);
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const uint32_t sw = q < 4 ? S.x : S.y, nw = q < 4 ? nlo : nhi, ow = q < 4 ? O.x : O.y;
@@ -150,6 +158,11 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
             acc.bond += (long long)(s_fin * n);
             acc.mag += s_fin + so;
             acc.up += (s_fin > 0) + (so > 0);
+            if (has_ref) {
+                const int rs = (int)(int8_t)((q < 4 ? RS.x : RS.y) >> sh8);
+                const int ro = (int)(int8_t)((q < 4 ? RO.x : RO.y) >> sh8);
+                acc.acf += s_fin * rs + so * ro;
+            }
         }
     }
     *reinterpret_cast<uint2 *>(dst + (uint64_t)colour * g.plane + (uint64_t)r * half + 8 * k) =
@@ -183,6 +196,10 @@ __global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int
         if (threadIdx.x == 0) add_counter(slot + 1, v);
         v = block_sum_ll(acc.up, red);
         if (threadIdx.x == 0) add_counter(slot + 2, v);
+        if (g.ref != nullptr) {
+            v = block_sum_ll(acc.acf, red);
+            if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), v);
+        }
     }
 }
 
@@ -243,6 +260,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_wide3(const Geom *geoms, con
             if (threadIdx.x == 0) add_counter(slot + 1, v);
             v = block_sum_ll(acc.up, red);
             if (threadIdx.x == 0) add_counter(slot + 2, v);
+            if (g.ref != nullptr) {
+                v = block_sum_ll(acc.acf, red);
+                if (threadIdx.x == 0) add_counter(acf_slot(ctrl, sweep), v);
+            }
         }
         __syncthreads();
     }

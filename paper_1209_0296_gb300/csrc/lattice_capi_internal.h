@@ -54,8 +54,11 @@ struct lattice {
     uint32_t *bits[2] = {nullptr, nullptr};
     lat::TabEntry *tab = nullptr;
     lat::Ctrl *ctrl = nullptr;
-    unsigned long long *series = nullptr;
+    unsigned long long *series = nullptr;  // [series_cap][4] counters, then [series_cap] overlaps
     unsigned long long series_cap = 0;   // sweeps the buffer can hold (from series_first)
+    int8_t *ref = nullptr;               // reference state s(0), int8 planar layout
+    uint32_t *ref_bits = nullptr;        // reference state s(0), bit-packed layout
+    int64_t ref_sweep = -1;              // sweeps done when the reference was taken (-1: none)
     unsigned long long *scratch4 = nullptr;
     std::vector<lat::TabEntry> host_tab;
     int64_t sweeps = 0;        // sweeps done (global index of the next sweep)

@@ -140,6 +140,7 @@ struct Ctrl {
     unsigned long long series_cap;   // sweeps the series buffer can hold
     unsigned int error;              // device error word (0 = none)
     unsigned int pad;
+    unsigned long long *acf;         // [series_cap] sum_i s_i(t) s_i(ref), same indexing
 };
 
 #if defined(__CUDACC__)
@@ -147,6 +148,14 @@ struct Ctrl {
 LAT_D unsigned long long *series_slot(const Ctrl *c, unsigned long long sweep)
 {
     return c->series + 4ull * (sweep - c->series_base);
+}
+
+// Autocorrelation slot of global sweep `sweep`: the overlap of the state
+// after that sweep with the stored reference state (written only while a
+// reference is set).
+LAT_D unsigned long long *acf_slot(const Ctrl *c, unsigned long long sweep)
+{
+    return c->acf + (sweep - c->series_base);
 }
 #endif
 
@@ -178,6 +187,11 @@ struct Geom {
     // North-East persistence: one byte per Philox group of 4 same-colour
     // sites, bit q = site 4m+q ever changed: flags[(c * rows + r) * G + m].
     uint8_t *flags;
+    // Reference state s(0) for the autocorrelation (§III.B, the Phi(t)
+    // equation): a copy in the int8 planar layout (ref) or the bit-packed one
+    // (ref_bits); null when no reference is set.
+    const int8_t *ref;
+    const uint32_t *ref_bits;
     Ctrl *ctrl;
     // Compact acceptance table for 2D spin-1/2 (tiled and bit-packed
     // kernels): index (self down) << 3 | (# down neighbours).
@@ -195,6 +209,7 @@ struct SweepView {
     int8_t *s0, *s1;
     uint32_t key0, key1;
     uint8_t *flags;
+    const int8_t *ref;
     Ctrl *ctrl;
 };
 
@@ -211,6 +226,7 @@ LAT_HD SweepView sweep_view(const Geom &g)
     v.key0 = g.key0;
     v.key1 = g.key1;
     v.flags = g.flags;
+    v.ref = g.ref;
     v.ctrl = g.ctrl;
     return v;
 }
@@ -262,7 +278,8 @@ cudaError_t launch_half_sweep_generic(const Geom &g, int colour, int off, cudaSt
 cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out4, cudaStream_t st);
 cudaError_t launch_advance(Ctrl *ctrl, unsigned long long k, cudaStream_t st);
 cudaError_t launch_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
-                            unsigned long long base, unsigned long long cap, cudaStream_t st);
+                            unsigned long long base, unsigned long long cap, unsigned long long *acf,
+                            cudaStream_t st);
 bool tiled_supported(const Geom &g);
 cudaError_t launch_sweep_tiled(const Geom &g, int tile_w, int tile_h, int off, cudaStream_t st);
 cudaError_t launch_pack_bits(const Geom &g, const int8_t *planar, uint32_t *bits, cudaStream_t st);
