@@ -149,7 +149,7 @@ int lattice_observables(lattice_t *lat, double *E, double *M, double *density,
 int lattice_series(lattice_t *lat, int64_t first, int64_t count, int64_t *bond,
                    int64_t *mag, int64_t *up, int64_t *unflipped);
 
-/* Spin-spin autocorrelation (§III.B, the Phi(t) equation):
+/* Spin-spin autocorrelation (§III.B, Eq. 4):
  *   Phi(t) = (1/N) sum_i [s_i(t) s_i(0) - m^2] / (1 - m^2),  m = <s_i> = 2c - 1,
  * with the sum over sites read as the mean, so that Phi(0) = 1 for +-1 spins.
  * lattice_set_reference stores the current configuration as s(0) (a device
@@ -275,8 +275,8 @@ typedef struct lattice_result {
  * (so work of requests that arrived at different times shares launches),
  * then retires finished lattices (freeing their memory) and admits waiting
  * requests.  Every result is bit-identical to running its lattice alone.
- * This is continuous batching in the sense of the spec: admission
- * happens between rounds, never by stopping resident work. */
+ * This is continuous batching: admission happens between rounds, never
+ * by stopping resident work. */
 int lattice_server_create(lattice_server_t **out, size_t hbm_budget_bytes, int max_slots,
                           int chunk_sweeps);
 /* Non-blocking; *id identifies the request. LAT_EINVAL for a bad request,

@@ -343,7 +343,7 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
 }
 
 /* Overlap of a configuration with a reference one, sum_i s_i * ref_i: the  */
-/* numerator of the spin-spin autocorrelation Phi(t) of §III.B (the sum      */
+/* numerator of the spin-spin autocorrelation Phi(t), §III.B Eq. 4 (the sum */
 /* over sites i of s_i(t) s_i(0)).  Both arrays in the same site order.      */
 int64_t oracle_overlap(int64_t n, const int8_t *s, const int8_t *ref)
 {

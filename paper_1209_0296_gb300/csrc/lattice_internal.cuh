@@ -187,8 +187,8 @@ struct Geom {
     // North-East persistence: one byte per Philox group of 4 same-colour
     // sites, bit q = site 4m+q ever changed: flags[(c * rows + r) * G + m].
     uint8_t *flags;
-    // Reference state s(0) for the autocorrelation (§III.B, the Phi(t)
-    // equation): a copy in the int8 planar layout (ref) or the bit-packed one
+    // Reference state s(0) for the autocorrelation Phi(t) (§III.B, Eq. 4):
+    // a copy in the int8 planar layout (ref) or the bit-packed one
     // (ref_bits); null when no reference is set.
     const int8_t *ref;
     const uint32_t *ref_bits;

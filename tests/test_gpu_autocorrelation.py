@@ -1,4 +1,4 @@
-"""Spin-spin autocorrelation on the GPU (§III.B, the Phi(t) equation): the
+"""Spin-spin autocorrelation on the GPU (§III.B, Eq. 4): the
 per-sweep overlap sum_i s_i(t) s_i(0) recorded inside every sweep kernel
 must equal the oracle's, integer for integer, for every kernel, layout and
 model, in the batched engine too; Phi follows from it on the host."""
