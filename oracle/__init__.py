@@ -64,6 +64,11 @@ def _load():
             lib.oracle_measure.argtypes = [ctypes.c_int, ctypes.c_int, i8p, u8p,
                                            i64p, i64p, i64p, i64p]
             lib.oracle_measure.restype = None
+            lib.oracle_rsite_sweep.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                               ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4
+            lib.oracle_rsite_sweep.restype = ctypes.c_int
             lib.oracle_overlap.argtypes = [ctypes.c_int64, i8p, i8p]
             lib.oracle_overlap.restype = ctypes.c_int64
             lib.oracle_metropolis_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
@@ -149,6 +154,35 @@ class Lattice:
                 out["overlap"][k] = self.overlap()
             return out
         return self._sweep(n)
+
+    def rsite_sweep(self, n: int, tile: int, lam: int):
+        """Advance n sweeps of the paper's random-sub-lattice, random-site
+        algorithm (§III.B) with b x b sub-lattices and lam picks per round;
+        returns the per-sweep series (and "overlap" when a reference is set)."""
+        keys = ("bond", "mag", "up", "unflipped")
+        if self.ref is not None:
+            out = {k: np.zeros(n, dtype=np.int64) for k in keys + ("overlap",)}
+            for k in range(n):
+                one = self._rsite(1, tile, lam)
+                for key in keys:
+                    out[key][k] = one[key][0]
+                out["overlap"][k] = self.overlap()
+            return out
+        return self._rsite(n, tile, lam)
+
+    def _rsite(self, n, tile, lam):
+        if self.dims != 2 or self.two_S != 1:
+            raise ValueError("the random-site algorithm is 2D spin-1/2")
+        out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
+        rc = _load().oracle_rsite_sweep(self.L, self.model, self.J, self.h, self.T_or_c, self.seed,
+                                        int(tile), int(lam), self.spins,
+                                        _ptr(self.flags) if self.model == NE else None,
+                                        self.sweep_index, n, _ptr(out["bond"]), _ptr(out["mag"]),
+                                        _ptr(out["up"]), _ptr(out["unflipped"]))
+        if rc != 0:
+            raise ValueError("oracle_rsite_sweep rejected the parameters")
+        self.sweep_index += n
+        return out
 
     def _sweep(self, n: int):
         out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}

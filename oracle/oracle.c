@@ -342,6 +342,146 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The paper's own North-East GPU algorithm (§III.B, the second algorithm:   */
+/* steps 3-10, Figs. 4-5): random sub-lattices and random sites instead of   */
+/* a checkerboard, to keep the serial relaxation dynamics.  2D spin-1/2.     */
+/*                                                                           */
+/* The lattice is cut into Q = (L/b)^2 square sub-lattices of P = b*b spins  */
+/* (step 3).  One sweep is two launches (steps 9-10); in each launch every   */
+/* sub-lattice (step 5: each is picked by exactly one block) makes q rounds  */
+/* of lambda concurrent random picks with q * lambda = P/2 (steps 6-8).      */
+/* Sites outside a sub-lattice (its boundary, step 5) keep the values they   */
+/* had when the launch started.                                              */
+/*                                                                           */
+/* Readings taken here (the paper leaves them open):                         */
+/*  - Pick p = r*lambda + i (round r, thread i) of launch l in sweep t of    */
+/*    sub-lattice B (row-major over sub-lattices) draws Philox with counter  */
+/*    (B*P/2 + p, t lo, t hi, 4 + l); word 0 picks the site,                 */
+/*    floor(w0 * P / 2^32) in row-major order inside the sub-lattice, and    */
+/*    word 1 is the acceptance draw.  The block-to-sub-lattice permutation  */
+/*    of step 5 changes nothing (every sub-lattice is processed once per     */
+/*    launch, blocks do not interact within one) and is the identity.       */
+/*  - The lambda picks of a round are concurrent: each is decided from the   */
+/*    state at the start of the round; when several pick the same site, the  */
+/*    lowest thread index's outcome is kept.                                 */
+/*  - A neighbour inside the sub-lattice is read live; one outside it from   */
+/*    the launch's frozen input.  With one sub-lattice (b = L) every        */
+/*    neighbour is inside, so Q = lambda = 1 is serial random-site           */
+/*    Metropolis, the paper's reference limit.                               */
+/*  - Move rule and thresholds as in oracle_sweep: flip, the North-East      */
+/*    constraint, accept without a draw when allowed by "always", else iff   */
+/*    u < thr.  Persistence flags as in oracle_sweep.                        */
+/* ------------------------------------------------------------------------ */
+static int rsite_accept(const params_t *p, int model, int s_old, int s_new, int n, uint32_t u)
+{
+    uint32_t thr;
+    int accept;
+    if (model == 1 && p->cmode) {
+        double pr = (s_new > s_old) ? p->c / (1.0 - p->c) : (1.0 - p->c) / p->c;
+        accept = oracle_probability_threshold(pr, &thr);
+    } else {
+        double dE = oracle_delta_energy(p->J, p->h, s_new - s_old, n);
+        accept = oracle_metropolis_threshold(dE, p->T, &thr);
+    }
+    if (!accept) accept = (u < thr);
+    return accept;
+}
+
+int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
+                       uint64_t seed, int b, int lambda, int8_t *s, uint8_t *flag,
+                       int64_t sweep0, int64_t nsweeps, int64_t *bond,
+                       int64_t *mag, int64_t *up, int64_t *unflipped)
+{
+    params_t p;
+    if (setup(&p, 2, L, 1, model, J, h, T_or_c, seed)) return -1;
+    if (model == 1 && flag == NULL) return -1;
+    if (b < 2 || (b & (b - 1)) != 0 || L % b != 0) return -1;
+    const int64_t P = (int64_t)b * b;
+    if (lambda < 1 || (P / 2) % lambda != 0) return -1;
+    const int64_t q = P / 2 / lambda;
+    const int nt = L / b;
+    int8_t *src = (int8_t *)malloc((size_t)p.N);
+    int8_t *loc = (int8_t *)malloc((size_t)P);
+    int8_t *nv = (int8_t *)malloc((size_t)lambda);
+    int64_t *pick = (int64_t *)malloc(sizeof(int64_t) * (size_t)lambda);
+    if (!src || !loc || !nv || !pick) {
+        free(src); free(loc); free(nv); free(pick);
+        return -1;
+    }
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int64_t t = sweep0; t < sweep0 + nsweeps; ++t) {
+        for (int launch = 0; launch < 2; ++launch) {
+            memcpy(src, s, (size_t)p.N);               /* the launch's input */
+            for (int ty = 0; ty < nt; ++ty)
+                for (int tx = 0; tx < nt; ++tx) {
+                    const int64_t B = (int64_t)ty * nt + tx;
+                    const int x0 = tx * b, y0 = ty * b;
+                    for (int ly = 0; ly < b; ++ly)
+                        for (int lx = 0; lx < b; ++lx)
+                            loc[ly * b + lx] = src[site_index(&p, x0 + lx, y0 + ly, 0)];
+                    for (int64_t r = 0; r < q; ++r) {
+                        /* every pick of the round decided from the same state */
+                        for (int i = 0; i < lambda; ++i) {
+                            const int64_t pk = r * lambda + i;
+                            uint32_t ctr[4] = {(uint32_t)(B * (P / 2) + pk),
+                                               (uint32_t)((uint64_t)t & 0xffffffffu),
+                                               (uint32_t)((uint64_t)t >> 32),
+                                               (uint32_t)(4 + launch)};
+                            uint32_t w[4];
+                            oracle_philox4x32_10(ctr, key, w);
+                            const int64_t site = (int64_t)(((uint64_t)w[0] * (uint64_t)P) >> 32);
+                            const int lx = (int)(site % b), ly = (int)(site / b);
+                            int nb[4];   /* north, east, south, west */
+                            const int dx[4] = {0, 1, 0, -1}, dy[4] = {-1, 0, 1, 0};
+                            for (int d = 0; d < 4; ++d) {
+                                const int X = ((x0 + lx + dx[d]) % L + L) % L;
+                                const int Y = ((y0 + ly + dy[d]) % L + L) % L;
+                                if (X >= x0 && X < x0 + b && Y >= y0 && Y < y0 + b)
+                                    nb[d] = loc[(Y - y0) * b + (X - x0)];
+                                else
+                                    nb[d] = src[site_index(&p, X, Y, 0)];
+                            }
+                            const int s_old = loc[site], s_new = -s_old;
+                            int allowed = 1;
+                            if (model == 1) allowed = (nb[0] == 1 && nb[1] == 1);
+                            const int n = nb[0] + nb[1] + nb[2] + nb[3];
+                            nv[i] = (int8_t)((allowed && rsite_accept(&p, model, s_old, s_new, n, w[1]))
+                                                 ? s_new : s_old);
+                            pick[i] = site;
+                        }
+                        /* apply: the first pick of a site wins */
+                        for (int i = 0; i < lambda; ++i) {
+                            int first = 1;
+                            for (int j = 0; j < i; ++j)
+                                if (pick[j] == pick[i]) first = 0;
+                            if (!first) continue;
+                            if (nv[i] != loc[pick[i]]) {
+                                loc[pick[i]] = nv[i];
+                                if (flag != NULL) {
+                                    const int lx = (int)(pick[i] % b), ly = (int)(pick[i] / b);
+                                    flag[site_index(&p, x0 + lx, y0 + ly, 0)] = 1;
+                                }
+                            }
+                        }
+                    }
+                    for (int ly = 0; ly < b; ++ly)
+                        for (int lx = 0; lx < b; ++lx)
+                            s[site_index(&p, x0 + lx, y0 + ly, 0)] = loc[ly * b + lx];
+                }
+        }
+        int64_t bb, m, nu, nf;
+        oracle_measure(2, L, s, flag, &bb, &m, &nu, &nf);
+        const int64_t k = t - sweep0;
+        if (bond) bond[k] = bb;
+        if (mag) mag[k] = m;
+        if (up) up[k] = nu;
+        if (unflipped) unflipped[k] = nf;
+    }
+    free(src); free(loc); free(nv); free(pick);
+    return 0;
+}
+
 /* Overlap of a configuration with a reference one, sum_i s_i * ref_i: the  */
 /* numerator of the spin-spin autocorrelation Phi(t), §III.B Eq. 4 (the sum */
 /* over sites i of s_i(t) s_i(0)).  Both arrays in the same site order.      */
