@@ -574,6 +574,16 @@ def other_configs(dev):
     for gg in lats:
         gg.close()
 
+    # the paper's own North-East algorithm (random sub-lattices and sites):
+    # L = 8192, c = 0.42, 32x32 sub-lattices, 16 picks per round
+    g = lt.Lattice(2, 8192, 1, lt.NE, 0.0, 0.0, 0.42, seed=21, init=lt.INIT_EQUILIBRIUM, stream=stream)
+    g.set_dynamics(lt.DYNAMICS_RANDOM_SITE, 32, 16)
+    n = 3
+    t = _timed_sweeps(torch, stream, [g], n, flush)
+    out["NE_L8192_random_site_b32_lambda16"] = {"updates_per_ns": N4 * n / t / 1e9, "sweeps": n,
+                                                "us_per_sweep": t / n * 1e6}
+    g.close()
+
     # one 2D Ising lattice far larger than L2: L = 32768 (1 GiB per buffer)
     g = lt.Lattice(2, 32768, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=7, init=lt.INIT_RANDOM, stream=stream)
     n = 10
