@@ -83,6 +83,12 @@ enum lattice_layout {
     LAT_INT8 = 0,      /* one int8 spin per site */
     LAT_BITPACKED = 1  /* spin-1/2, 2D only: one bit per site, colour-separated planes */
 };
+/* Sweep dynamics for lattice_set_dynamics. */
+enum lattice_dynamics {
+    LAT_DYNAMICS_CHECKERBOARD = 0, /* colour 0 then colour 1 (§III.A steps 5-8); the default */
+    LAT_DYNAMICS_RANDOM_SITE = 1   /* the paper's random-sub-lattice, random-site algorithm
+                                      (§III.B, second algorithm) */
+};
 /* Kernel selection for lattice_set_kernel (tests and the autotuner). */
 enum lattice_kernel {
     LAT_KERNEL_AUTO = 0,    /* library choice (tuned tile shape when eligible) */
@@ -161,6 +167,26 @@ int lattice_series(lattice_t *lat, int64_t first, int64_t count, int64_t *bond,
  * lattice_clear_reference frees it and stops the recording.  Neither
  * set_state nor set_spins changes the reference. */
 int lattice_set_reference(lattice_t *lat, int64_t *ref_sweep);
+
+/* Choose the sweep dynamics of later lattice_sweep calls.
+ * LAT_DYNAMICS_RANDOM_SITE is the paper's own North-East GPU algorithm
+ * (§III.B, steps 3-10, Figs. 4-5), for 2D spin-1/2 int8 lattices of either
+ * model: the lattice is cut into tile x tile sub-lattices (tile a power of two
+ * in [8, 256] dividing L); one sweep is two launches, and in each launch
+ * every sub-lattice makes q rounds of lambda concurrent random picks
+ * (lambda a power of two, 1 <= lambda <= min(1024, tile^2/2), q * lambda =
+ * tile^2/2), with its boundary frozen at the launch's start.  Randomness:
+ * pick p of launch l in sweep t of sub-lattice B (row-major) draws Philox
+ * with counter (B*tile^2/2 + p, t lo, t hi, 4 + l); word 0 picks the site,
+ * word 1 the acceptance.  Picks of one round are decided from the state at
+ * the round's start; of several picks of one site the lowest thread index's
+ * is kept.  tile = L (one sub-lattice) with lambda = 1 is serial random-site
+ * Metropolis.  Allocates one more lattice-sized buffer (N bytes) the first
+ * time.  Counters, persistence and the autocorrelation are recorded as for
+ * the checkerboard.  LAT_ENOTSUP for 3D, spin-S or bit-packed lattices,
+ * LAT_EINVAL for other tile / lambda values.  Such lattices cannot join a
+ * batch (lattice_batch_add: LAT_ENOTSUP). */
+int lattice_set_dynamics(lattice_t *lat, int dynamics, int tile, int lambda);
 int lattice_clear_reference(lattice_t *lat);
 /* Copy the overlaps of sweeps [first, first+count) (global sweep indexes as in
  * lattice_series; first >= the reference's ref_sweep) to overlap[] and, if phi

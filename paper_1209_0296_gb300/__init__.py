@@ -16,12 +16,13 @@ from ._lib import LatticeError, LatticeRequest, LatticeResult, check, load
 __all__ = ["Lattice", "Batch", "Server", "LatticeError", "load", "threshold_table",
            "ISING", "NE", "INIT_COLD", "INIT_RANDOM", "INIT_EQUILIBRIUM", "INT8", "BITPACKED",
            "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED", "KERNEL_WIDE",
-           "KERNEL_RESIDENT"]
+           "KERNEL_RESIDENT", "DYNAMICS_CHECKERBOARD", "DYNAMICS_RANDOM_SITE"]
 
 ISING, NE = 0, 1
 INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
 INT8, BITPACKED = 0, 1
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_WIDE, KERNEL_RESIDENT = 0, 1, 2, 3, 4
+DYNAMICS_CHECKERBOARD, DYNAMICS_RANDOM_SITE = 0, 1
 
 
 def _stream_handle(stream) -> int:
@@ -79,6 +80,12 @@ class Lattice:
         r = ctypes.c_int64()
         check(self._lib.lattice_set_reference(self._h, ctypes.byref(r)), "lattice_set_reference")
         return r.value
+
+    def set_dynamics(self, dynamics=0, tile: int = 32, lam: int = 16):
+        """DYNAMICS_CHECKERBOARD (default) or DYNAMICS_RANDOM_SITE with
+        tile x tile sub-lattices and lam picks per round."""
+        check(self._lib.lattice_set_dynamics(self._h, int(dynamics), int(tile), int(lam)),
+              "lattice_set_dynamics")
 
     def clear_reference(self):
         check(self._lib.lattice_clear_reference(self._h), "lattice_clear_reference")

@@ -206,7 +206,7 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
 int lattice_batch_add(lattice_batch_t *b, lattice_t *lt, int64_t n)
 {
     if (b == nullptr || lt == nullptr || n < 0) return LAT_EINVAL;
-    if (lt->P.layout == LAT_BITPACKED) return LAT_ENOTSUP;
+    if (lt->P.layout == LAT_BITPACKED || lt->dynamics != LAT_DYNAMICS_CHECKERBOARD) return LAT_ENOTSUP;
     if (n == 0) return LAT_OK;
     for (auto &pr : b->pending)
         if (pr.first == lt) {

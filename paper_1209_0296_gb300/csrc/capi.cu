@@ -224,6 +224,15 @@ constexpr int64_t kResidentChunk = 1 << 16;
 
 int enqueue_sweeps(lattice *lt, int64_t k, cudaStream_t st)
 {
+    if (lt->dynamics == LAT_DYNAMICS_RANDOM_SITE) {
+        for (int64_t off = 0; off < k; ++off) {
+            cudaError_t e = launch_sweep_rsite(lt->geom, lt->rs_scratch, lt->rs_tile, lt->rs_lambda, (int)off, st);
+            if (e != cudaSuccess) return cuda_fail(e, "random-site sweep launch");
+        }
+        cudaError_t e = launch_advance(lt->ctrl, (unsigned long long)k, st);
+        if (e != cudaSuccess) return cuda_fail(e, "advance launch");
+        return LAT_OK;
+    }
     const int kern = choose_kernel(lt);
     if (kern == LAT_KERNEL_RESIDENT) {
         for (int64_t off = 0; off < k; off += kResidentChunk) {
@@ -398,7 +407,7 @@ int sweep_impl(lattice *lt, int64_t n)
     if (rc != LAT_OK) return rc;
     int64_t left = n;
     if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel == 0 && lt->P.layout == LAT_INT8 &&
-        wide_supported(lt->geom) && tiled_supported(lt->geom)) {
+        lt->dynamics == LAT_DYNAMICS_CHECKERBOARD && wide_supported(lt->geom) && tiled_supported(lt->geom)) {
         const int64_t before = lt->sweeps;
         rc = autotune(lt, left);
         if (rc != LAT_OK) return rc;
@@ -406,7 +415,8 @@ int sweep_impl(lattice *lt, int64_t n)
         if (left == 0) return LAT_OK;
     }
     // The resident kernel runs many sweeps per launch: no graph needed.
-    const int gk = choose_kernel(lt) == LAT_KERNEL_RESIDENT ? 0 : lt->graph_sweeps;
+    const int gk = (lt->dynamics == LAT_DYNAMICS_CHECKERBOARD && choose_kernel(lt) == LAT_KERNEL_RESIDENT)
+                       ? 0 : lt->graph_sweeps;
     if (gk > 0 && left >= gk) {
         rc = ensure_graph(lt);
         if (rc != LAT_OK) return rc;
@@ -441,6 +451,7 @@ static void release(lattice *lt)
     dev_free(lt->scratch4, st);
     dev_free(lt->ref, st);
     dev_free(lt->ref_bits, st);
+    dev_free(lt->rs_scratch, st);
     delete lt;
 }
 
@@ -670,6 +681,28 @@ int lattice_set_reference(lattice_t *lt, int64_t *ref_sweep)
     return LAT_OK;
 }
 
+int lattice_set_dynamics(lattice_t *lt, int dynamics, int tile, int lambda)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    if (dynamics == LAT_DYNAMICS_CHECKERBOARD) {
+        lt->dynamics = dynamics;
+        lt->graph_valid = false;
+        return LAT_OK;
+    }
+    if (dynamics != LAT_DYNAMICS_RANDOM_SITE) return LAT_EINVAL;
+    if (lt->P.dims != 2 || lt->P.two_S != 1 || lt->P.layout != LAT_INT8) return LAT_ENOTSUP;
+    if (!rsite_params_ok(lt->geom, tile, lambda)) return LAT_EINVAL;
+    if (lt->rs_scratch == nullptr) {
+        cudaError_t e = dev_alloc((void **)&lt->rs_scratch, (size_t)lt->P.N, lt->stream);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "random-site scratch");
+    }
+    lt->dynamics = dynamics;
+    lt->rs_tile = tile;
+    lt->rs_lambda = lambda;
+    lt->graph_valid = false;
+    return LAT_OK;
+}
+
 int lattice_clear_reference(lattice_t *lt)
 {
     if (lt == nullptr) return LAT_EINVAL;
@@ -853,7 +886,8 @@ int lattice_info(lattice_t *lt, int64_t *sweeps, int64_t *n_sites, int64_t *devi
         *device_bytes = (int64_t)(footprint_bytes(lt->P) +
                                   (size_t)lt->series_cap * 5 * sizeof(long long) +
                                   (lt->ref ? (size_t)lt->P.N : 0) +
-                                  (lt->ref_bits ? bits_bytes(lt->P) : 0));
+                                  (lt->ref_bits ? bits_bytes(lt->P) : 0) +
+                                  (lt->rs_scratch ? (size_t)lt->P.N : 0));
     return LAT_OK;
 }
 

@@ -59,6 +59,9 @@ struct lattice {
     int8_t *ref = nullptr;               // reference state s(0), int8 planar layout
     uint32_t *ref_bits = nullptr;        // reference state s(0), bit-packed layout
     int64_t ref_sweep = -1;              // sweeps done when the reference was taken (-1: none)
+    int dynamics = 0;                    // LAT_DYNAMICS_*
+    int rs_tile = 0, rs_lambda = 0;      // random-site sub-lattice side and picks per round
+    int8_t *rs_scratch = nullptr;        // random-site: output of the first launch of a sweep
     unsigned long long *scratch4 = nullptr;
     std::vector<lat::TabEntry> host_tab;
     int64_t sweeps = 0;        // sweeps done (global index of the next sweep)
