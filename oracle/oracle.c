@@ -355,13 +355,15 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
 /* had when the launch started.                                              */
 /*                                                                           */
 /* Readings taken here (the paper leaves them open):                         */
-/*  - Pick p = r*lambda + i (round r, thread i) of launch l in sweep t of    */
-/*    sub-lattice B (row-major over sub-lattices) draws Philox with counter  */
-/*    (B*P/2 + p, t lo, t hi, 4 + l); word 0 picks the site,                 */
-/*    floor(w0 * P / 2^32) in row-major order inside the sub-lattice, and    */
-/*    word 1 is the acceptance draw.  The block-to-sub-lattice permutation  */
-/*    of step 5 changes nothing (every sub-lattice is processed once per     */
-/*    launch, blocks do not interact within one) and is the identity.       */
+/*  - Thread i of sub-lattice B (row-major over sub-lattices) makes one     */
+/*    Philox call per two rounds: in launch l of sweep t, rounds 2k and 2k+1 */
+/*    share the call with counter (B*C + k*lambda + i, t lo, t hi, 4 + l),   */
+/*    C = ceil(q/2)*lambda calls per sub-lattice; round r uses words         */
+/*    w = 2*(r & 1) (the site, floor(w * P / 2^32) row-major inside the      */
+/*    sub-lattice) and w + 1 (the acceptance draw).  The block-to-           */
+/*    sub-lattice permutation of step 5 changes nothing (every sub-lattice  */
+/*    is processed once per launch, blocks do not interact within one) and  */
+/*    is the identity.                                                       */
 /*  - The lambda picks of a round are concurrent: each is decided from the   */
 /*    state at the start of the round; when several pick the same site, the  */
 /*    lowest thread index's outcome is kept.                                 */
@@ -400,6 +402,7 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
     const int64_t P = (int64_t)b * b;
     if (lambda < 1 || (P / 2) % lambda != 0) return -1;
     const int64_t q = P / 2 / lambda;
+    const int64_t calls = (q + 1) / 2 * lambda;   /* Philox calls per sub-lattice and launch */
     const int nt = L / b;
     int8_t *src = (int8_t *)malloc((size_t)p.N);
     int8_t *loc = (int8_t *)malloc((size_t)P);
@@ -423,14 +426,14 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
                     for (int64_t r = 0; r < q; ++r) {
                         /* every pick of the round decided from the same state */
                         for (int i = 0; i < lambda; ++i) {
-                            const int64_t pk = r * lambda + i;
-                            uint32_t ctr[4] = {(uint32_t)(B * (P / 2) + pk),
+                            uint32_t ctr[4] = {(uint32_t)(B * calls + (r / 2) * lambda + i),
                                                (uint32_t)((uint64_t)t & 0xffffffffu),
                                                (uint32_t)((uint64_t)t >> 32),
                                                (uint32_t)(4 + launch)};
                             uint32_t w[4];
                             oracle_philox4x32_10(ctr, key, w);
-                            const int64_t site = (int64_t)(((uint64_t)w[0] * (uint64_t)P) >> 32);
+                            const int ws = 2 * (int)(r & 1);
+                            const int64_t site = (int64_t)(((uint64_t)w[ws] * (uint64_t)P) >> 32);
                             const int lx = (int)(site % b), ly = (int)(site / b);
                             int nb[4];   /* north, east, south, west */
                             const int dx[4] = {0, 1, 0, -1}, dy[4] = {-1, 0, 1, 0};
@@ -446,7 +449,7 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
                             int allowed = 1;
                             if (model == 1) allowed = (nb[0] == 1 && nb[1] == 1);
                             const int n = nb[0] + nb[1] + nb[2] + nb[3];
-                            nv[i] = (int8_t)((allowed && rsite_accept(&p, model, s_old, s_new, n, w[1]))
+                            nv[i] = (int8_t)((allowed && rsite_accept(&p, model, s_old, s_new, n, w[ws + 1]))
                                                  ? s_new : s_old);
                             pick[i] = site;
                         }
