@@ -355,7 +355,8 @@ def run_profile(args):
     import paper_1209_0296_gb300 as lt
     torch.cuda.set_device(0)
     if args.profile_model == "ne":
-        g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, 0.3, seed=21, init=lt.INIT_EQUILIBRIUM)
+        c = 0.42 if args.profile_dynamics == "random-site" else 0.3
+        g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, c, seed=21, init=lt.INIT_EQUILIBRIUM)
     elif args.profile_model == "ising3d":   # 3D spin-1 at T = 2 + 7 * 2/15, random start (seed 11)
         g = lt.Lattice(3, args.profile_L, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, seed=11,
                        init=lt.INIT_RANDOM)
@@ -368,6 +369,8 @@ def run_profile(args):
     if args.profile_layout == "bitpacked":
         kern = lt.KERNEL_AUTO
     g.set_kernel(kern, 0, args.tile_h, 1 << 30)  # direct launches, no graphs
+    if args.profile_dynamics == "random-site":
+        g.set_dynamics(lt.DYNAMICS_RANDOM_SITE, args.profile_tile, args.profile_lambda)
     g.sweep(args.profile)
     g.synchronize()
     print("profile run: %d sweeps of L=%d (%s), kernel %s" % (args.profile, args.profile_L,
@@ -641,6 +644,9 @@ def main():
     ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d"])
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic", "resident"])
     ap.add_argument("--profile-layout", default="int8", choices=["int8", "bitpacked"])
+    ap.add_argument("--profile-dynamics", default="checkerboard", choices=["checkerboard", "random-site"])
+    ap.add_argument("--profile-tile", type=int, default=32, help="random-site sub-lattice side")
+    ap.add_argument("--profile-lambda", type=int, default=16, help="random-site picks per round")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

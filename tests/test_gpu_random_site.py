@@ -42,7 +42,8 @@ def rs_pair(L, model, Tc, tile, lam, nsweeps, seed=5, chunks=None, ref=True):
 
 
 @pytest.mark.parametrize("L,tile,lam", [(64, 32, 16), (64, 8, 32), (64, 8, 1), (64, 16, 4),
-                                        (128, 16, 64), (64, 32, 512), (32, 32, 4), (256, 128, 1024)])
+                                        (128, 16, 64), (64, 32, 512), (32, 32, 4), (256, 128, 1024),
+                                        (24, 8, 4), (8, 8, 2), (40, 8, 16)])
 @pytest.mark.parametrize("model,Tc", [(lt.NE, 0.42), (lt.ISING, 2.3)])
 def test_random_site_matches_oracle(L, tile, lam, model, Tc):
     rs_pair(L, model, Tc, tile, lam, 6, seed=L + tile + lam, chunks=[1, 5])
