@@ -33,8 +33,11 @@ LAT_D uint32_t add_bytes(uint32_t a, uint32_t b)
     return ((a & 0x7F7F7F7Fu) + (b & 0x7F7F7F7Fu)) ^ ((a ^ b) & 0x80808080u);
 }
 
+// Per-thread partial sums.  32 bits suffice: a thread sees at most
+// 2^32 / (resident threads) sites (< 2^17), each adding at most 6*S*S <= 96
+// to |bond|.
 struct Acc3 {
-    long long bond = 0, mag = 0, up = 0, acf = 0;
+    int bond = 0, mag = 0, up = 0, acf = 0;
 };
 
 // The fields of a Geom that this kernel reads, small enough for registers.
@@ -65,11 +68,18 @@ LAT_D View3 view3(const Geom &g)
     return v;
 }
 
-// Colour `colour` of the 8-site chunk k of plane row r = y + L*z.
-template <int SH>
+// Colour `colour` of the 8-site chunk k of plane row r = y + L*z.  TS and
+// D fix two_S and dims at compile time (0: read them from g), which turns
+// the spin/state maps, the proposal and the table index into constants.
+template <int SH, int TS, int D>
 LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigned long long sweep,
                        const PhiloxPre &pp, uint32_t r, uint32_t k, Acc3 &acc)
 {
+    const int two_S = TS ? TS : g.two_S;
+    const int dims = D ? D : g.dims;
+    const int dsmax = TS ? 2 * max_spin(TS) : g.dsmax;
+    const int nmax = (TS && D) ? 2 * D * max_spin(TS) : g.nmax;
+    const int nn = (TS && D) ? 2 * nmax + 1 : g.nn;
     const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
     int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
     if (colour == 1) src = dst;
@@ -85,7 +95,7 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
     const uint2 Yn = *reinterpret_cast<const uint2 *>(row(oc, ym) + 8 * k);
     const uint2 Ys = *reinterpret_cast<const uint2 *>(row(oc, yp) + 8 * k);
     uint2 Zd = make_uint2(0u, 0u), Zu = make_uint2(0u, 0u);
-    if (g.dims == 3) {
+    if (dims == 3) {
         const uint32_t zm = (uint32_t)(y + L * (z == 0 ? L - 1 : z - 1));
         const uint32_t zp = (uint32_t)(y + L * (z == L - 1 ? 0 : z + 1));
         Zd = *reinterpret_cast<const uint2 *>(row(oc, zm) + 8 * k);
@@ -107,15 +117,15 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
         R.y = __funnelshift_r(O.y, next, 8);
     }
     // neighbour sums offset by 2*dims*smax, byte-wise
-    const int smax = max_spin(g.two_S);
+    const int smax = max_spin(two_S);
     const uint32_t off = 0x01010101u * (uint32_t)smax;
     uint32_t nlo = add_bytes(Lf.x, off) + add_bytes(R.x, off) + add_bytes(Yn.x, off) + add_bytes(Ys.x, off);
     uint32_t nhi = add_bytes(Lf.y, off) + add_bytes(R.y, off) + add_bytes(Yn.y, off) + add_bytes(Ys.y, off);
-    if (g.dims == 3) {
+    if (dims == 3) {
         nlo += add_bytes(Zd.x, off) + add_bytes(Zu.x, off);
         nhi += add_bytes(Zd.y, off) + add_bytes(Zu.y, off);
     }
-    const int noff = 2 * g.dims * smax;
+    const int noff = 2 * dims * smax;
     const uint32_t g0 = r * g.G + ((8u * k) >> SH);  // first Philox group of the chunk
     constexpr int kCalls = 8 >> SH;
     U4 u[kCalls];
@@ -134,28 +144,28 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
         const int sh8 = 8 * (q & 3);
         const int s_old = (int)(int8_t)(sw >> sh8);
         const int n = (int)((nw >> sh8) & 0xFFu) - noff;
-        const int k_old = state_of_spin(g.two_S, s_old);
-        int k_new;
+        int s_new;
         uint32_t u_acc;
         if (SH == 2) {
-            k_new = 1 - k_old;
+            s_new = -s_old;   // spin-1/2: the flip
             u_acc = word_of(u[q >> 2], q & 3);
         } else {
             const int w = 2 * (q & 1);
             u_acc = word_of(u[q >> 1], w);
             const uint32_t u_prop = word_of(u[q >> 1], w + 1);
-            k_new = k_old + 1 + (int)(((uint64_t)u_prop * (uint64_t)g.two_S) >> 32);
-            if (k_new > g.two_S) k_new -= g.two_S + 1;
+            const int k_old = state_of_spin(two_S, s_old);
+            int k_new = k_old + 1 + (int)(((uint64_t)u_prop * (uint64_t)two_S) >> 32);
+            if (k_new > two_S) k_new -= two_S + 1;
+            s_new = spin_of_state(two_S, k_new);
         }
-        const int s_new = spin_of_state(g.two_S, k_new);
-        const TabEntry e = stab[(s_new - s_old + g.dsmax) * g.nn + (n + g.nmax)];
+        const TabEntry e = stab[(s_new - s_old + dsmax) * nn + (n + nmax)];
         const int s_fin = (e.always || u_acc < e.thr) ? s_new : s_old;
         const uint32_t b = ((uint32_t)s_fin & 0xFFu) << sh8;
         if (q < 4) out_lo |= b;
         else out_hi |= b;
         if (colour == 1) {
             const int so = (int)(int8_t)(ow >> sh8);
-            acc.bond += (long long)(s_fin * n);
+            acc.bond += s_fin * n;
             acc.mag += s_fin + so;
             acc.up += (s_fin > 0) + (so > 0);
             if (has_ref) {
@@ -170,7 +180,7 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
     if (colour == 0) *reinterpret_cast<uint2 *>(dst + g.plane + (uint64_t)r * half + 8 * k) = O;
 }
 
-template <int SH>
+template <int SH, int TS, int D>
 __global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int off)
 {
     __shared__ TabEntry stab[kMaxTab];
@@ -186,18 +196,18 @@ __global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int
     Acc3 acc;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
          t += (uint64_t)gridDim.x * blockDim.x)
-        wide3_chunk<SH>(v, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+        wide3_chunk<SH, TS, D>(v, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
     if (colour == 1) {
         unsigned long long *slot = series_slot(g.ctrl, sweep);
         long long v;
-        v = block_sum_ll(acc.bond, red);
+        v = block_sum_ll((long long)acc.bond, red);
         if (threadIdx.x == 0) add_counter(slot + 0, v);
-        v = block_sum_ll(acc.mag, red);
+        v = block_sum_ll((long long)acc.mag, red);
         if (threadIdx.x == 0) add_counter(slot + 1, v);
-        v = block_sum_ll(acc.up, red);
+        v = block_sum_ll((long long)acc.up, red);
         if (threadIdx.x == 0) add_counter(slot + 2, v);
         if (g.ref != nullptr) {
-            v = block_sum_ll(acc.acf, red);
+            v = block_sum_ll((long long)acc.acf, red);
             if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), v);
         }
     }
@@ -235,7 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_wide3(const Geom *geoms, con
         // register copies: no aliasing with shared-memory stores
         const View3 g = view3(sg);
         Ctrl *const ctrl = sg.ctrl;
-        const bool spin_half = sg.sh == 2;
+        const bool spin_half = sg.sh == 2;   // wide3 takes 2D spin-1/2 never, so this is 3D
+        const bool spin_one3 = sg.two_S == 2 && sg.dims == 3;
         const unsigned long long sweep = ctrl->sweep;
         PhiloxPre pp;
         philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
@@ -246,22 +257,22 @@ __global__ void __launch_bounds__(kThreads) k_batch_wide3(const Geom *geoms, con
         for (int c = 0; c < kItemChunks; ++c) {
             const uint64_t t = ((uint64_t)w.y * kItemChunks + (uint64_t)c) * kThreads + threadIdx.x;
             if (t >= total) break;
-            if (spin_half)
-                wide3_chunk<2>(g, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
-            else
-                wide3_chunk<1>(g, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+            const uint32_t rr = (uint32_t)(t / cpr), kk = (uint32_t)(t % cpr);
+            if (spin_half) wide3_chunk<2, 1, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
+            else if (spin_one3) wide3_chunk<1, 2, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
+            else wide3_chunk<1, 0, 0>(g, stab, colour, sweep, pp, rr, kk, acc);
         }
         if (colour == 1) {
             unsigned long long *slot = series_slot(ctrl, sweep);
             long long v;
-            v = block_sum_ll(acc.bond, red);
+            v = block_sum_ll((long long)acc.bond, red);
             if (threadIdx.x == 0) add_counter(slot + 0, v);
-            v = block_sum_ll(acc.mag, red);
+            v = block_sum_ll((long long)acc.mag, red);
             if (threadIdx.x == 0) add_counter(slot + 1, v);
-            v = block_sum_ll(acc.up, red);
+            v = block_sum_ll((long long)acc.up, red);
             if (threadIdx.x == 0) add_counter(slot + 2, v);
             if (g.ref != nullptr) {
-                v = block_sum_ll(acc.acf, red);
+                v = block_sum_ll((long long)acc.acf, red);
                 if (threadIdx.x == 0) add_counter(acf_slot(ctrl, sweep), v);
             }
         }
@@ -303,22 +314,23 @@ bool wide3_supported(const Geom &g)
 
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st)
 {
-    static int resident[2] = {0, 0};
-    const int which = g.two_S == 1 ? 0 : 1;
+    // instantiations: 3D spin-1/2, 3D spin-1, 2D spin-1, any other spin-S
+    const int which = g.two_S == 1 ? 0 : (g.two_S == 2 ? (g.dims == 3 ? 1 : 2) : 3);
+    using K = void (*)(Geom, int, int);
+    const K kern[4] = {k_wide3_half<2, 1, 3>, k_wide3_half<1, 2, 3>, k_wide3_half<1, 2, 2>, k_wide3_half<1, 0, 0>};
+    static int resident[4] = {0, 0, 0, 0};
     if (resident[which] == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (which == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide3_half<2>, kThreads, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide3_half<1>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern[which], kThreads, 0);
         resident[which] = sms * (per > 0 ? per : 1);
     }
     const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
     const unsigned blocks = (unsigned)std::min<uint64_t>((chunks + kThreads - 1) / kThreads,
                                                         (uint64_t)resident[which]);
     for (int colour = 0; colour < 2; ++colour) {
-        if (which == 0) k_wide3_half<2><<<blocks, kThreads, 0, st>>>(g, colour, off);
-        else k_wide3_half<1><<<blocks, kThreads, 0, st>>>(g, colour, off);
+        kern[which]<<<blocks, kThreads, 0, st>>>(g, colour, off);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
