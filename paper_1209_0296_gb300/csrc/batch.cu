@@ -1,16 +1,17 @@
 // batch.cu -- the batched engine behind lattice_batch_*: many lattices of
-// any sizes and models advanced together.  Each sweep step is one
-// persistent-grid launch over the (lattice, tile) items of every 2D
-// spin-1/2 lattice (one fused sweep per tile) plus, for the other lattices,
-// two persistent launches (colour 0, colour 1) over (lattice, item) pairs of
-// the wide 3D / spin-S kernel and two over (lattice, chunk) pairs of the
-// generic kernel, then one small kernel that advances every lattice's sweep
-// counter.  Small 2D spin-1/2 lattices instead run as resident CTAs (one CTA
-// per lattice holding it in shared memory for all its sweeps) on a side
-// stream, concurrently with the step loop of the others.  Steps
-// with the same set of lattices are captured once in a CUDA graph and
-// replayed.  Every lattice keeps its own seed, table and sweep counter, so
-// its result is bit-identical to running it alone.
+// any sizes and models advanced together.  Each sweep step is a set of
+// persistent-grid launches over work lists: two (colour 0, colour 1) per
+// model over (lattice, item) pairs of the 2D spin-1/2 wide kernel, one over
+// (lattice, tile) items of lattices set to the fused tiled kernel, two over
+// (lattice, item) pairs of the 3D / spin-S wide kernel and two over
+// (lattice, chunk) pairs of the generic kernel; then one small kernel
+// advances every lattice's sweep counter.  Small 2D spin-1/2 lattices
+// instead run as resident CTAs (one CTA per lattice holding it in shared
+// memory for all its sweeps) on a side stream, concurrently with the step
+// loop of the others.  Steps with the same set of lattices are captured
+// once in a CUDA graph and replayed.  Every lattice keeps its own seed,
+// table and sweep counter, so its result is bit-identical to running it
+// alone.
 #include <algorithm>
 #include <map>
 #include <new>
@@ -30,9 +31,11 @@ struct lattice_batch {
     int items_cap = 0;
     Ctrl **d_ctrls = nullptr;
     int ctrls_cap = 0;
-    // next item of: Ising tiles, NE tiles, generic colour 0 / 1, wide colour 0 / 1
+    // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S wide
+    // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1
     unsigned *d_counters = nullptr;
     int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0;
+    int grid_wide2[2] = {0, 0};   // 2D wide, Ising / North-East
     // resident lattices
     cudaStream_t res_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -47,7 +50,7 @@ namespace {
 
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
-constexpr int kCounters = 6;
+constexpr int kCounters = 10;
 constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
 constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
 
@@ -66,11 +69,11 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
     return LAT_OK;
 }
 
-// Item counts of the current active set: tiles of Ising lattices, tiles of
-// North-East lattices, wide items, then generic chunks, in that order in
-// d_items.
+// Item counts of the current active set, in this order in d_items: tiles
+// of Ising lattices, tiles of North-East lattices, 2D wide items of Ising
+// and of North-East lattices, 3D / spin-S wide items, generic chunks.
 struct Shape {
-    int n_lat, n_ising, n_ne, n_wide, n_gen;
+    int n_lat, n_ising, n_ne, n_w2[2], n_wide, n_gen;
 };
 
 // Queue `steps` sweep steps of the current active set.
@@ -84,7 +87,14 @@ int enqueue_steps(lattice_batch *b, const Shape &sh, int steps, cudaStream_t st)
         if (e == cudaSuccess && sh.n_ne > 0)
             e = launch_batch_tiled(b->d_geoms, b->d_items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
                                    std::min(b->grid_tiled_ne, sh.n_ne), true, st);
-        const uint2 *wide = b->d_items + sh.n_ising + sh.n_ne;
+        const uint2 *w2 = b->d_items + sh.n_ising + sh.n_ne;
+        for (int m = 0; m < 2; ++m) {   // Ising, then North-East: colour 0, then colour 1
+            for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_w2[m] > 0; ++colour)
+                e = launch_batch_wide(b->d_geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
+                                      m == 1, std::min(b->grid_wide2[m], sh.n_w2[m]), st);
+            w2 += sh.n_w2[m];
+        }
+        const uint2 *wide = w2;
         for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide > 0; ++colour)
             e = launch_batch_wide3(b->d_geoms, wide, sh.n_wide, b->d_counters + 4 + colour, colour,
                                    std::min(b->grid_wide, sh.n_wide), st);
@@ -199,6 +209,8 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     b->grid_tiled_ne = batch_tiled_grid(true);
     b->grid_generic = batch_generic_grid();
     b->grid_wide = batch_wide3_grid();
+    b->grid_wide2[0] = batch_wide_grid(false);
+    b->grid_wide2[1] = batch_wide_grid(true);
     *out = b;
     return LAT_OK;
 }
@@ -249,20 +261,26 @@ int lattice_batch_run(lattice_batch_t *b)
         if (steps > 0) {
             std::vector<Geom> geoms(n_active);
             std::vector<Ctrl *> ctrls(n_active);
-            std::vector<uint2> tiled, tiled_ne, wide, gen;
+            std::vector<uint2> tiled, tiled_ne, w2[2], wide, gen;
             for (size_t i = 0; i < n_active; ++i) {
                 lattice *lt = work[i].first;
                 geoms[i] = tiled_geom(lt->geom);
                 ctrls[i] = lt->ctrl;
-                // 2D spin-1/2 lattices whose own sweep is tiled or wide share the
-                // tiled item list; 3D and spin-S Ising lattices with L % 16 == 0
-                // take the wide items; the rest (odd sizes, an explicit generic
-                // choice) go to the generic chunks.
-                const bool generic = choose_kernel(lt) == LAT_KERNEL_GENERIC;
-                if (!generic && tiled_supported(lt->geom)) {
+                // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
+                // the tiled items when their kernel is the tiled one; 3D and
+                // spin-S Ising lattices with L % 16 == 0 take the 3D wide items;
+                // the rest (other sizes, an explicit generic choice) go to the
+                // generic chunks.
+                const int kern = choose_kernel(lt);
+                const bool generic = kern == LAT_KERNEL_GENERIC;
+                if (!generic && tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) {
                     const int nt = tiles_of(lt->geom, 0);
                     auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
                     for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+                } else if (!generic && wide_supported(lt->geom)) {
+                    const int nw = wide_items(lt->geom);
+                    auto &dst = w2[lt->P.model == LAT_NE ? 1 : 0];
+                    for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
                 } else if (!generic && wide3_supported(lt->geom)) {
                     const int nw = wide3_items(lt->geom);
                     for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
@@ -272,9 +290,12 @@ int lattice_batch_run(lattice_batch_t *b)
                     for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
                 }
             }
-            Shape sh{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), (int)wide.size(), (int)gen.size()};
+            Shape sh{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
+                     (int)wide.size(), (int)gen.size()};
             std::vector<uint2> items(tiled);
             items.insert(items.end(), tiled_ne.begin(), tiled_ne.end());
+            items.insert(items.end(), w2[0].begin(), w2[0].end());
+            items.insert(items.end(), w2[1].begin(), w2[1].end());
             items.insert(items.end(), wide.begin(), wide.end());
             items.insert(items.end(), gen.begin(), gen.end());
             int rc = grow(&b->d_geoms, b->geoms_cap, (int)n_active, b->stream);

@@ -279,6 +279,55 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     if (colour == 1) flush(v, sweep, cnt, kNE, red);
 }
 
+// Batched form: a persistent grid takes (lattice, item) pairs from an
+// atomic counter; an item is kItemChunks x kThreads chunks of one colour of
+// one lattice.  The descriptor and table are reloaded only when a CTA moves
+// to another lattice (items are ordered by lattice); the sweep works on a
+// register copy of the descriptor.
+constexpr int kItemChunks = 4;
+
+template <bool kNE>
+__global__ void __launch_bounds__(kThreads) k_batch_wide(const Geom *geoms, const uint2 *items, int n_items,
+                                                        unsigned *next_item, int colour)
+{
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kThreads / 32][5];
+    __shared__ Geom sg;
+    __shared__ int cur;
+    int loaded = -1;
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = cur;
+        if (it >= n_items) break;
+        const uint2 w = items[it];
+        if ((int)w.x != loaded) {
+            if (threadIdx.x < sizeof(Geom) / 4)
+                reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
+                    reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
+            loaded = (int)w.x;
+            __syncthreads();
+        }
+        const SweepView v = sweep_view(sg);
+        const unsigned long long sweep = v.ctrl->sweep;
+        PhiloxPre pp;
+        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), v.key0, v.key1);
+        const uint32_t cpr = v.half >> 4;
+        const uint32_t total = (uint32_t)v.L * cpr;
+        Counts cnt;
+#pragma unroll 1
+        for (int c = 0; c < kItemChunks; ++c) {
+            const uint32_t t = (w.y * (uint32_t)kItemChunks + (uint32_t)c) * kThreads + threadIdx.x;
+            if (t >= total) break;
+            wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+        }
+        if (colour == 1) flush(v, sweep, cnt, kNE, red);   // ends with __syncthreads()
+        __syncthreads();
+    }
+}
+
 // Resident form for lattices that fit in one CTA's shared memory (§III.A
 // with the whole lattice as the block's tile): the CTA loads the spins (and
 // the North-East persistence bytes) once, runs n sweeps in place -- an
@@ -493,5 +542,35 @@ cudaError_t launch_batch_resident(const Geom *geoms, const long long *n, int n_l
 }
 
 size_t resident_smem_bytes(const Geom &g) { return resident_bytes(g); }
+
+}  // namespace lat
+
+namespace lat {
+
+int wide_items(const Geom &g)
+{
+    const uint64_t chunks = (uint64_t)g.L * (g.half >> 4);
+    const uint64_t per = (uint64_t)kItemChunks * kThreads;
+    return (int)((chunks + per - 1) / per);
+}
+
+int batch_wide_grid(bool ne)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ne) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide<true>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide<false>, kThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
+                              bool ne, int grid, cudaStream_t st)
+{
+    if (ne) k_batch_wide<true><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    else k_batch_wide<false><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    return cudaGetLastError();
+}
 
 }  // namespace lat

@@ -300,6 +300,11 @@ size_t resident_smem_bytes(const Geom &g);
 // geoms: compact-table descriptors (tiled_geom); n[i]: sweeps for lattice i
 cudaError_t launch_batch_resident(const Geom *geoms, const long long *n, int n_lat, long long done, int chunk,
                                   size_t smem, cudaStream_t st);
+// Batched 2D spin-1/2 wide sweep (geoms: compact-table descriptors).
+int wide_items(const Geom &g);
+int batch_wide_grid(bool ne);
+cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
+                              bool ne, int grid, cudaStream_t st);
 bool wide3_supported(const Geom &g);
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
 int wide3_items(const Geom &g);   // batch items of one colour of one lattice
