@@ -817,9 +817,23 @@ static void flags_from_host(const lattice *lt, const uint8_t *in, std::vector<ui
 int lattice_set_spins(lattice_t *lt, const int8_t *host_in)
 {
     if (lt == nullptr || host_in == nullptr) return LAT_EINVAL;
-    if (!spins_allowed(lt->P, host_in)) return LAT_EINVAL;
-    cudaError_t e = put_spins(lt, host_in);
-    // The caller's buffer may be reused as soon as we return.
+    // Upload into the idle buffer and check the values there (on the device,
+    // not by a host scan of N bytes); only then convert into the current
+    // buffer, so a rejected array leaves the lattice unchanged.
+    const int par = (int)(lt->sweeps & 1);
+    int8_t *lin = (lt->P.layout == LAT_BITPACKED) ? lt->spins[1] : lt->spins[par ^ 1];
+    int8_t *dst = (lt->P.layout == LAT_BITPACKED) ? lt->spins[0] : lt->spins[par];
+    unsigned long long bad = 0;
+    cudaError_t e = cudaMemcpyAsync(lin, host_in, (size_t)lt->P.N, cudaMemcpyHostToDevice, lt->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lt->scratch4, 0, sizeof(unsigned long long), lt->stream);
+    if (e == cudaSuccess) e = launch_count_bad(lt->geom, lin, lt->scratch4, lt->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, lt->scratch4, sizeof bad, cudaMemcpyDeviceToHost, lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);   // the caller may reuse host_in now
+    if (e != cudaSuccess) return cuda_fail(e, "set spins");
+    if (bad != 0) return LAT_EINVAL;
+    e = launch_to_planar(lt->geom, lin, dst, lt->stream);
+    if (e == cudaSuccess && lt->P.layout == LAT_BITPACKED) e = launch_pack_bits(lt->geom, dst, lt->bits[par], lt->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set spins");
     return LAT_OK;

@@ -5,6 +5,8 @@
 // Spins use the checkerboard-planar int8 layout described in Geom.
 #include <cmath>
 
+#include <algorithm>
+
 #include "lattice_internal.cuh"
 
 namespace lat {
@@ -274,6 +276,21 @@ __global__ void k_to_planar(Geom g, const int8_t *linear, int8_t *planar)
     planar[planar_index(g, x, y, z)] = linear[i];
 }
 
+// Count the bytes of an uploaded spin array that are not allowed spin
+// values (|v| > smax, or the wrong parity for half-integer S).
+__global__ void __launch_bounds__(kThreads) k_count_bad(Geom g, const int8_t *s, unsigned long long *out)
+{
+    __shared__ long long red[kThreads / 32];
+    const int smax = max_spin(g.two_S), odd = g.two_S & 1;
+    long long bad = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < g.N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int v = s[i];
+        bad += (v < -smax) | (v > smax) | (odd & ((v + g.two_S) & 1));
+    }
+    const long long t = block_sum_ll(bad, red);
+    if (threadIdx.x == 0 && t != 0) atomicAdd(out, (unsigned long long)t);
+}
+
 __global__ void k_advance(Ctrl *ctrl, unsigned long long k) { ctrl->sweep += k; }
 
 __global__ void k_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
@@ -349,6 +366,13 @@ cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long lon
 cudaError_t launch_to_linear(const Geom &g, const int8_t *planar, int8_t *linear, cudaStream_t st)
 {
     k_to_linear<<<blocks_for(g.N), kThreads, 0, st>>>(g, planar, linear);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_bad(const Geom &g, const int8_t *spins, unsigned long long *out, cudaStream_t st)
+{
+    const unsigned blocks = std::min<unsigned>(blocks_for(g.N), 4096u);
+    k_count_bad<<<blocks, kThreads, 0, st>>>(g, spins, out);
     return cudaGetLastError();
 }
 

@@ -286,6 +286,8 @@ cudaError_t launch_pack_bits(const Geom &g, const int8_t *planar, uint32_t *bits
 cudaError_t launch_unpack_bits(const Geom &g, const uint32_t *bits, int8_t *planar, cudaStream_t st);
 // planar <-> x-fastest (linear) int8 spins
 cudaError_t launch_to_linear(const Geom &g, const int8_t *planar, int8_t *linear, cudaStream_t st);
+// out[0] += number of bytes of spins[0 .. N) that are not allowed values.
+cudaError_t launch_count_bad(const Geom &g, const int8_t *spins, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_to_planar(const Geom &g, const int8_t *linear, int8_t *planar, cudaStream_t st);
 cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
 bool bitpacked_supported(const Geom &g);

@@ -162,6 +162,31 @@ def test_set_spins_roundtrip_and_validation():
     assert np.array_equal(g.get_spins(), s)
     with pytest.raises(lt.LatticeError):
         g.set_spins(np.full(216, 2, dtype=np.int8))
+    assert np.array_equal(g.get_spins(), s)          # a rejected array changes nothing
+    # one bad byte among good ones; odd parity for half-integer spin; bit-packed
+    bad = s.copy()
+    bad[100] = -2
+    with pytest.raises(lt.LatticeError):
+        g.set_spins(bad)
+    assert np.array_equal(g.get_spins(), s)
+    h = lt.Lattice(2, 8, 3, lt.ISING, 1.0, 0.0, 4.0, seed=1, init=lt.INIT_RANDOM)
+    good = rng.choice(np.array([-3, -1, 1, 3], dtype=np.int8), 64)
+    h.set_spins(good)
+    assert np.array_equal(h.get_spins(), good)
+    even = good.copy()
+    even[5] = 2
+    with pytest.raises(lt.LatticeError):
+        h.set_spins(even)
+    assert np.array_equal(h.get_spins(), good)
+    k = lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.0, seed=1, init=lt.INIT_RANDOM, layout=lt.BITPACKED)
+    pm = rng.choice(np.array([-1, 1], dtype=np.int8), 4096)
+    k.set_spins(pm)
+    assert np.array_equal(k.get_spins(), pm)
+    zero = pm.copy()
+    zero[7] = 0
+    with pytest.raises(lt.LatticeError):
+        k.set_spins(zero)
+    assert np.array_equal(k.get_spins(), pm)
 
 
 def test_allocation_failure_is_reported():
