@@ -50,6 +50,7 @@ namespace {
 
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
+constexpr int kGraphMinSteps = 128;
 constexpr int kCounters = 10;
 constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
 constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
@@ -76,45 +77,59 @@ struct Shape {
     int n_lat, n_ising, n_ne, n_w2[2], n_wide, n_gen;
 };
 
-// Queue `steps` sweep steps of the current active set.
-int enqueue_steps(lattice_batch *b, const Shape &sh, int steps, cudaStream_t st)
+// One phase of a run: its item counts and where its descriptors, items and
+// control pointers start in the batch's device arrays.
+struct Phase {
+    Shape sh;
+    int64_t steps;
+    const Geom *geoms;
+    const uint2 *items;
+    Ctrl *const *ctrls;
+};
+
+// Queue `steps` sweep steps of one phase.
+int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
 {
+    const Shape &sh = ph.sh;
     for (int s = 0; s < steps; ++s) {
         cudaError_t e = cudaSuccess;
         if (sh.n_ising > 0)
-            e = launch_batch_tiled(b->d_geoms, b->d_items, sh.n_ising, b->d_counters + 0, 0, 0,
+            e = launch_batch_tiled(ph.geoms, ph.items, sh.n_ising, b->d_counters + 0, 0, 0,
                                    std::min(b->grid_tiled_ising, sh.n_ising), false, st);
         if (e == cudaSuccess && sh.n_ne > 0)
-            e = launch_batch_tiled(b->d_geoms, b->d_items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
+            e = launch_batch_tiled(ph.geoms, ph.items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
                                    std::min(b->grid_tiled_ne, sh.n_ne), true, st);
-        const uint2 *w2 = b->d_items + sh.n_ising + sh.n_ne;
+        const uint2 *w2 = ph.items + sh.n_ising + sh.n_ne;
         for (int m = 0; m < 2; ++m) {   // Ising, then North-East: colour 0, then colour 1
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_w2[m] > 0; ++colour)
-                e = launch_batch_wide(b->d_geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
+                e = launch_batch_wide(ph.geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
                                       m == 1, std::min(b->grid_wide2[m], sh.n_w2[m]), st);
             w2 += sh.n_w2[m];
         }
         const uint2 *wide = w2;
         for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide > 0; ++colour)
-            e = launch_batch_wide3(b->d_geoms, wide, sh.n_wide, b->d_counters + 4 + colour, colour,
+            e = launch_batch_wide3(ph.geoms, wide, sh.n_wide, b->d_counters + 4 + colour, colour,
                                    std::min(b->grid_wide, sh.n_wide), st);
         const uint2 *gen = wide + sh.n_wide;
         if (e == cudaSuccess && sh.n_gen > 0)
-            e = launch_batch_generic(b->d_geoms, gen, sh.n_gen, b->d_counters + 2, 0, 0,
+            e = launch_batch_generic(ph.geoms, gen, sh.n_gen, b->d_counters + 2, 0, 0,
                                      std::min(b->grid_generic, sh.n_gen), st);
         if (e == cudaSuccess && sh.n_gen > 0)
-            e = launch_batch_generic(b->d_geoms, gen, sh.n_gen, b->d_counters + 3, 1, 0,
+            e = launch_batch_generic(ph.geoms, gen, sh.n_gen, b->d_counters + 3, 1, 0,
                                      std::min(b->grid_generic, sh.n_gen), st);
-        if (e == cudaSuccess) e = launch_batch_advance(b->d_ctrls, sh.n_lat, b->d_counters, kCounters, 1ull, st);
+        if (e == cudaSuccess) e = launch_batch_advance(ph.ctrls, sh.n_lat, b->d_counters, kCounters, 1ull, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     }
     return LAT_OK;
 }
 
-int run_steps(lattice_batch *b, const Shape &sh, int64_t steps)
+int run_steps(lattice_batch *b, const Phase &ph)
 {
-    int64_t left = steps;
-    if (left >= kGraphSteps) {
+    int64_t left = ph.steps;
+    // A graph pays for its capture and instantiation (milliseconds) only
+    // over many replays; short runs (a serving round) launch directly,
+    // which the host enqueues faster than the device drains them.
+    if (left >= kGraphMinSteps) {
         if (b->cap_stream == nullptr) {
             cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
             if (e != cudaSuccess) return cuda_fail(e, "batch capture stream");
@@ -123,7 +138,7 @@ int run_steps(lattice_batch *b, const Shape &sh, int64_t steps)
         cudaGraphExec_t exec = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "batch begin capture");
-        int rc = enqueue_steps(b, sh, kGraphSteps, b->cap_stream);
+        int rc = enqueue_steps(b, ph, kGraphSteps, b->cap_stream);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (rc != LAT_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -139,7 +154,7 @@ int run_steps(lattice_batch *b, const Shape &sh, int64_t steps)
         cudaGraphExecDestroy(exec);  // safe: destruction waits for no launch; launches stay valid
         if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
     }
-    if (left > 0) return enqueue_steps(b, sh, (int)left, b->stream);
+    if (left > 0) return enqueue_steps(b, ph, (int)left, b->stream);
     return LAT_OK;
 }
 
@@ -235,10 +250,16 @@ int lattice_batch_run(lattice_batch_t *b)
     std::vector<std::pair<lattice *, int64_t>> work;
     work.swap(b->pending);
     if (work.empty()) return LAT_OK;
-    // Lattices must have no work in flight on their own streams.
+    // Lattices must have no work in flight on their own streams (each
+    // distinct stream is synchronised once: lattices often share one).
+    std::vector<cudaStream_t> synced;
     for (auto &pr : work) {
-        cudaError_t e = cudaStreamSynchronize(pr.first->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+        cudaStream_t ls = pr.first->stream;
+        if (std::find(synced.begin(), synced.end(), ls) == synced.end()) {
+            cudaError_t e = cudaStreamSynchronize(ls);
+            if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+            synced.push_back(ls);
+        }
         int rc = ensure_series(pr.first, (unsigned long long)(pr.first->sweeps + pr.second));
         if (rc != LAT_OK) return rc;
     }
@@ -252,72 +273,86 @@ int lattice_batch_run(lattice_batch_t *b)
     for (auto &pr : res) pr.first->sweeps += pr.second;
     work.swap(rest);
     // Run in phases: all lattices until the smallest remaining count is
-    // done, then drop it, and so on.
+    // done, then drop it, and so on.  Every phase's descriptors and items are
+    // built first and uploaded together, so the phases are queued back to
+    // back with no host synchronisation between them.
     std::sort(work.begin(), work.end(), [](const auto &a, const auto &c) { return a.second > c.second; });
+    std::vector<Geom> all_geoms;
+    std::vector<Ctrl *> all_ctrls;
+    std::vector<uint2> all_items;
+    struct Spec {
+        Shape sh;
+        int64_t steps;
+        size_t geom_off, item_off;
+    };
+    std::vector<Spec> specs;
     int64_t done = 0;
-    size_t n_active = work.size();
-    while (n_active > 0) {
+    for (size_t n_active = work.size(); n_active > 0; --n_active) {
         const int64_t steps = work[n_active - 1].second - done;
-        if (steps > 0) {
-            std::vector<Geom> geoms(n_active);
-            std::vector<Ctrl *> ctrls(n_active);
-            std::vector<uint2> tiled, tiled_ne, w2[2], wide, gen;
-            for (size_t i = 0; i < n_active; ++i) {
-                lattice *lt = work[i].first;
-                geoms[i] = tiled_geom(lt->geom);
-                ctrls[i] = lt->ctrl;
-                // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
-                // the tiled items when their kernel is the tiled one; 3D and
-                // spin-S Ising lattices with L % 16 == 0 take the 3D wide items;
-                // the rest (other sizes, an explicit generic choice) go to the
-                // generic chunks.
-                const int kern = choose_kernel(lt);
-                const bool generic = kern == LAT_KERNEL_GENERIC;
-                if (!generic && tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) {
-                    const int nt = tiles_of(lt->geom, 0);
-                    auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
-                    for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-                } else if (!generic && wide_supported(lt->geom)) {
-                    const int nw = wide_items(lt->geom);
-                    auto &dst = w2[lt->P.model == LAT_NE ? 1 : 0];
-                    for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-                } else if (!generic && wide3_supported(lt->geom)) {
-                    const int nw = wide3_items(lt->geom);
-                    for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
-                } else {
-                    const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
-                    const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
-                    for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
-                }
+        if (steps <= 0) continue;
+        const size_t g0 = all_geoms.size();
+        std::vector<uint2> tiled, tiled_ne, w2[2], wide, gen;
+        for (size_t i = 0; i < n_active; ++i) {
+            lattice *lt = work[i].first;
+            all_geoms.push_back(tiled_geom(lt->geom));
+            all_ctrls.push_back(lt->ctrl);
+            // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
+            // the tiled items when their kernel is the tiled one; 3D and
+            // spin-S Ising lattices with L % 16 == 0 take the 3D wide items;
+            // the rest (other sizes, an explicit generic choice) go to the
+            // generic chunks.  Item lattice indexes are local to the phase.
+            const int kern = choose_kernel(lt);
+            const bool generic = kern == LAT_KERNEL_GENERIC;
+            if (!generic && tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) {
+                const int nt = tiles_of(lt->geom, 0);
+                auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
+                for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+            } else if (!generic && wide_supported(lt->geom)) {
+                const int nw = wide_items(lt->geom);
+                auto &dst = w2[lt->P.model == LAT_NE ? 1 : 0];
+                for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+            } else if (!generic && wide3_supported(lt->geom)) {
+                const int nw = wide3_items(lt->geom);
+                for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
+            } else {
+                const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
+                const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
+                for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
             }
-            Shape sh{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                     (int)wide.size(), (int)gen.size()};
-            std::vector<uint2> items(tiled);
-            items.insert(items.end(), tiled_ne.begin(), tiled_ne.end());
-            items.insert(items.end(), w2[0].begin(), w2[0].end());
-            items.insert(items.end(), w2[1].begin(), w2[1].end());
-            items.insert(items.end(), wide.begin(), wide.end());
-            items.insert(items.end(), gen.begin(), gen.end());
-            int rc = grow(&b->d_geoms, b->geoms_cap, (int)n_active, b->stream);
-            if (rc == LAT_OK) rc = grow(&b->d_items, b->items_cap, (int)items.size(), b->stream);
-            if (rc == LAT_OK) rc = grow(&b->d_ctrls, b->ctrls_cap, (int)n_active, b->stream);
-            if (rc != LAT_OK) return rc;
-            cudaError_t e = cudaMemcpyAsync(b->d_geoms, geoms.data(), n_active * sizeof(Geom),
-                                            cudaMemcpyHostToDevice, b->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(uint2),
-                                    cudaMemcpyHostToDevice, b->stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(b->d_ctrls, ctrls.data(), n_active * sizeof(Ctrl *),
-                                    cudaMemcpyHostToDevice, b->stream);
-            // The host vectors go out of scope: make the copies complete first.
-            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "batch upload");
-            rc = run_steps(b, sh, steps);
-            if (rc != LAT_OK) return rc;
-            done += steps;
         }
-        --n_active;
+        Spec sp;
+        sp.sh = Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
+                      (int)wide.size(), (int)gen.size()};
+        sp.steps = steps;
+        sp.geom_off = g0;
+        sp.item_off = all_items.size();
+        for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &wide, &gen})
+            all_items.insert(all_items.end(), v->begin(), v->end());
+        specs.push_back(sp);
+        done += steps;
+    }
+    if (!specs.empty()) {
+        int rc = grow(&b->d_geoms, b->geoms_cap, (int)all_geoms.size(), b->stream);
+        if (rc == LAT_OK) rc = grow(&b->d_items, b->items_cap, (int)all_items.size(), b->stream);
+        if (rc == LAT_OK) rc = grow(&b->d_ctrls, b->ctrls_cap, (int)all_ctrls.size(), b->stream);
+        if (rc != LAT_OK) return rc;
+        cudaError_t e = cudaMemcpyAsync(b->d_geoms, all_geoms.data(), all_geoms.size() * sizeof(Geom),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_items, all_items.data(), all_items.size() * sizeof(uint2),
+                                cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_ctrls, all_ctrls.data(), all_ctrls.size() * sizeof(Ctrl *),
+                                cudaMemcpyHostToDevice, b->stream);
+        // The host vectors go out of scope: make the copies complete first.
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+        for (const Spec &sp : specs) {
+            const Phase ph{sp.sh, sp.steps, b->d_geoms + sp.geom_off, b->d_items + sp.item_off,
+                           b->d_ctrls + sp.geom_off};
+            rc = run_steps(b, ph);
+            if (rc != LAT_OK) return rc;
+        }
     }
     for (auto &pr : work) pr.first->sweeps += pr.second;
     cudaError_t e = cudaSuccess;
