@@ -69,6 +69,14 @@ def _load():
                                                ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4
             lib.oracle_rsite_sweep.restype = ctypes.c_int
+            lib.oracle_sweep_couplings.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_uint64, i8p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4
+            lib.oracle_sweep_couplings.restype = ctypes.c_int
+            lib.oracle_measure_couplings.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
+                                                     ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4
+            lib.oracle_measure_couplings.restype = None
             lib.oracle_overlap.argtypes = [ctypes.c_int64, i8p, i8p]
             lib.oracle_overlap.restype = ctypes.c_int64
             lib.oracle_metropolis_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
@@ -129,10 +137,22 @@ class Lattice:
         self.flags = np.zeros(self.N, dtype=np.uint8)
         self.sweep_index = 0
         self.ref = None          # s(0) of the autocorrelation (§III.B, Phi(t))
+        self.eps = None          # per-bond signs (Eq. 1 couplings J_ij = J * eps), or None
         rc = _load().oracle_init(dims, L, two_S, model, self.J, self.h, self.T_or_c,
                                  self.seed, init, self.spins)
         if rc != 0:
             raise ValueError("oracle_init rejected the parameters")
+
+    def set_couplings(self, eps):
+        """Per-bond signs: eps[d*N + i] = +-1 for the bond from linear site i
+        to its +e_d neighbour (Eq. 1 with J_ij = J * eps); None for uniform."""
+        if eps is None:
+            self.eps = None
+            return
+        e = np.ascontiguousarray(eps, dtype=np.int8).reshape(-1)
+        if e.size != self.dims * self.N or not np.all(np.abs(e) == 1):
+            raise ValueError("couplings must be dims*N values of +-1")
+        self.eps = e
 
     def set_reference(self):
         """Take the current configuration as s(0) of the autocorrelation."""
@@ -171,8 +191,8 @@ class Lattice:
         return self._rsite(n, tile, lam)
 
     def _rsite(self, n, tile, lam):
-        if self.dims != 2 or self.two_S != 1:
-            raise ValueError("the random-site algorithm is 2D spin-1/2")
+        if self.dims != 2 or self.two_S != 1 or self.eps is not None:
+            raise ValueError("the random-site algorithm is 2D spin-1/2 with uniform couplings")
         out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
         rc = _load().oracle_rsite_sweep(self.L, self.model, self.J, self.h, self.T_or_c, self.seed,
                                         int(tile), int(lam), self.spins,
@@ -186,11 +206,11 @@ class Lattice:
 
     def _sweep(self, n: int):
         out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
-        rc = _load().oracle_sweep(self.dims, self.L, self.two_S, self.model, self.J, self.h,
-                                  self.T_or_c, self.seed, self.spins,
-                                  _ptr(self.flags) if self.model == NE else None,
-                                  self.sweep_index, n, _ptr(out["bond"]), _ptr(out["mag"]),
-                                  _ptr(out["up"]), _ptr(out["unflipped"]))
+        rc = _load().oracle_sweep_couplings(self.dims, self.L, self.two_S, self.model, self.J, self.h,
+                                            self.T_or_c, self.seed, self.spins,
+                                            _ptr(self.flags) if self.model == NE else None,
+                                            _ptr(self.eps), self.sweep_index, n, _ptr(out["bond"]),
+                                            _ptr(out["mag"]), _ptr(out["up"]), _ptr(out["unflipped"]))
         if rc != 0:
             raise ValueError("oracle_sweep rejected the parameters")
         self.sweep_index += n
@@ -198,10 +218,10 @@ class Lattice:
 
     def measure(self):
         b, m, u, f = (ctypes.c_int64() for _ in range(4))
-        _load().oracle_measure(self.dims, self.L, self.spins,
-                               _ptr(self.flags) if self.model == NE else None,
-                               ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
-                               ctypes.byref(f))
+        _load().oracle_measure_couplings(self.dims, self.L, self.spins,
+                                         _ptr(self.flags) if self.model == NE else None, _ptr(self.eps),
+                                         ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
+                                         ctypes.byref(f))
         return dict(bond=b.value, mag=m.value, up=u.value, unflipped=f.value)
 
     def energy(self, bond, mag):

@@ -149,6 +149,7 @@ typedef struct {
     int cmode;
     uint64_t seed;
     int64_t N;
+    const int8_t *eps;   /* per-bond signs (Eq. 1's J_ij / J), or NULL: all +1 */
 } params_t;
 
 static int64_t site_index(const params_t *p, int x, int y, int z)
@@ -168,6 +169,7 @@ static int setup(params_t *p, int dims, int L, int two_S, int model, double J,
     if (two_S < 1 || two_S > 8) return -1;
     if (model != 0 && model != 1) return -1;
     if (model == 1 && (dims != 2 || two_S != 1)) return -1;
+    p->eps = NULL;
     p->dims = dims; p->L = L; p->two_S = two_S; p->model = model;
     p->J = J; p->h = h; p->seed = seed;
     p->N = (int64_t)L * L * (dims == 3 ? L : 1);
@@ -183,14 +185,26 @@ static int setup(params_t *p, int dims, int L, int two_S, int model, double J,
     return 0;
 }
 
-/* Sum of the 2*dims nearest-neighbour spins of (x,y,z), periodic. */
+/* Sign of the bond from site (x,y,z) to its +e_d neighbour: eps[d*N + i]  */
+/* with i the linear index of (x,y,z) (Eq. 1 with J_ij = J * eps), or +1.   */
+static int bond_sign(const params_t *p, int x, int y, int z, int d)
+{
+    if (p->eps == NULL) return 1;
+    return p->eps[(int64_t)d * p->N + site_index(p, x, y, z)];
+}
+
+/* Sum over the 2*dims nearest neighbours j of (x,y,z) of eps_ij * s_j,      */
+/* periodic (with no couplings set: the plain neighbour sum).               */
 static int neighbour_sum(const params_t *p, const int8_t *s, int x, int y,
                          int z)
 {
-    int n = s[site_index(p, x - 1, y, z)] + s[site_index(p, x + 1, y, z)] +
-            s[site_index(p, x, y - 1, z)] + s[site_index(p, x, y + 1, z)];
+    int n = bond_sign(p, x - 1, y, z, 0) * s[site_index(p, x - 1, y, z)] +
+            bond_sign(p, x, y, z, 0) * s[site_index(p, x + 1, y, z)] +
+            bond_sign(p, x, y - 1, z, 1) * s[site_index(p, x, y - 1, z)] +
+            bond_sign(p, x, y, z, 1) * s[site_index(p, x, y + 1, z)];
     if (p->dims == 3)
-        n += s[site_index(p, x, y, z - 1)] + s[site_index(p, x, y, z + 1)];
+        n += bond_sign(p, x, y, z - 1, 2) * s[site_index(p, x, y, z - 1)] +
+             bond_sign(p, x, y, z, 2) * s[site_index(p, x, y, z + 1)];
     return n;
 }
 
@@ -230,13 +244,17 @@ int oracle_init(int dims, int L, int two_S, int model, double J, double h,
 /*   mag  = sum_i s_i;  up = #{s_i > 0};  unflipped = #{flag_i == 0}         */
 /* E = -J*bond - h*mag (Eq. 2 with a field).                                 */
 /* ------------------------------------------------------------------------ */
-void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
-                    int64_t *bond, int64_t *mag, int64_t *up,
-                    int64_t *unflipped)
+/* With couplings (eps != NULL) the bond sum is weighted:                    */
+/*   bond = sum over sites i and directions d of eps_{i,d} s_i s_{i+e_d}.    */
+void oracle_measure_couplings(int dims, int L, const int8_t *s, const uint8_t *flag,
+                              const int8_t *eps, int64_t *bond, int64_t *mag,
+                              int64_t *up, int64_t *unflipped)
 {
     params_t p;
     memset(&p, 0, sizeof p);
     p.dims = dims; p.L = L;
+    p.N = (int64_t)L * L * (dims == 3 ? L : 1);
+    p.eps = eps;
     int Lz = (dims == 3) ? L : 1;
     int64_t b = 0, m = 0, nu = 0, nf = 0;
     for (int z = 0; z < Lz; ++z)
@@ -244,14 +262,21 @@ void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
             for (int x = 0; x < L; ++x) {
                 int64_t i = site_index(&p, x, y, z);
                 int si = s[i];
-                b += si * s[site_index(&p, x + 1, y, z)];
-                b += si * s[site_index(&p, x, y + 1, z)];
-                if (dims == 3) b += si * s[site_index(&p, x, y, z + 1)];
+                b += bond_sign(&p, x, y, z, 0) * si * s[site_index(&p, x + 1, y, z)];
+                b += bond_sign(&p, x, y, z, 1) * si * s[site_index(&p, x, y + 1, z)];
+                if (dims == 3) b += bond_sign(&p, x, y, z, 2) * si * s[site_index(&p, x, y, z + 1)];
                 m += si;
                 nu += (si > 0);
                 nf += (flag == NULL) ? 0 : (flag[i] == 0);
             }
     *bond = b; *mag = m; *up = nu; *unflipped = nf;
+}
+
+void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
+                    int64_t *bond, int64_t *mag, int64_t *up,
+                    int64_t *unflipped)
+{
+    oracle_measure_couplings(dims, L, s, flag, NULL, bond, mag, up, unflipped);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -262,13 +287,19 @@ void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
 /* After each sweep the four observables are recorded (NULL skips one).     */
 /* flag may be NULL for the Ising model.                                     */
 /* ------------------------------------------------------------------------ */
-int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
-                 double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
-                 int64_t sweep0, int64_t nsweeps, int64_t *bond,
-                 int64_t *mag, int64_t *up, int64_t *unflipped)
+/* eps: per-bond signs (Eq. 1 with J_ij = J * eps_ij, nearest neighbours),  */
+/* eps[d*N + i] for the bond from linear site i to its +e_d neighbour; NULL */
+/* for uniform couplings.  Ising model only.                                */
+int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, double h,
+                           double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
+                           const int8_t *eps, int64_t sweep0, int64_t nsweeps,
+                           int64_t *bond, int64_t *mag, int64_t *up,
+                           int64_t *unflipped)
 {
     params_t p;
     if (setup(&p, dims, L, two_S, model, J, h, T_or_c, seed)) return -1;
+    if (eps != NULL && model != 0) return -1;
+    p.eps = eps;
     if (model == 1 && flag == NULL) return -1;
     const int sh = (two_S == 1) ? 2 : 1;               /* sites per draw: 4 or 2 */
     const int64_t half = L / 2;
@@ -332,7 +363,7 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
                     }
         }
         int64_t b, m, nu, nf;
-        oracle_measure(dims, L, s, flag, &b, &m, &nu, &nf);
+        oracle_measure_couplings(dims, L, s, flag, eps, &b, &m, &nu, &nf);
         int64_t k = t - sweep0;
         if (bond) bond[k] = b;
         if (mag) mag[k] = m;
@@ -340,6 +371,15 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
         if (unflipped) unflipped[k] = nf;
     }
     return 0;
+}
+
+int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
+                 double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
+                 int64_t sweep0, int64_t nsweeps, int64_t *bond,
+                 int64_t *mag, int64_t *up, int64_t *unflipped)
+{
+    return oracle_sweep_couplings(dims, L, two_S, model, J, h, T_or_c, seed, s, flag, NULL,
+                                  sweep0, nsweeps, bond, mag, up, unflipped);
 }
 
 /* ------------------------------------------------------------------------ */
