@@ -168,6 +168,20 @@ int lattice_series(lattice_t *lat, int64_t first, int64_t count, int64_t *bond,
  * set_state nor set_spins changes the reference. */
 int lattice_set_reference(lattice_t *lat, int64_t *ref_sweep);
 
+/* Per-bond couplings (Eq. 1: H = -sum_<ij> J_ij s_i s_j - h sum_i s_i with
+ * J_ij = J * eps_ij, eps_ij = +-1: the Edwards-Anderson +-J spin glass).
+ * bond_signs holds dims * N int8 values of +-1: bond_signs[d*N + i] is eps
+ * for the bond from site i (x fastest) to its +e_d neighbour (periodic).
+ * NULL restores uniform couplings.  From then on lattice_series' bond[k] is
+ * the weighted sum over bonds of eps_ij s_i s_j, so E = -J*bond - h*mag as
+ * before.  Ising model, int8 layout, checkerboard dynamics only
+ * (LAT_ENOTSUP otherwise); LAT_EINVAL for values other than +-1.  Such
+ * lattices sweep with the 2D wide kernel (2D spin-1/2) or the generic one;
+ * the tiled, resident, bit-packed and random-site paths are not available
+ * (lattice_set_kernel answers LAT_ENOTSUP).  Uses N bytes of device memory;
+ * a checkpoint (lattice_get_state) does not include the couplings. */
+int lattice_set_couplings(lattice_t *lat, const int8_t *bond_signs);
+
 /* Choose the sweep dynamics of later lattice_sweep calls.
  * LAT_DYNAMICS_RANDOM_SITE is the paper's own North-East GPU algorithm
  * (§III.B, steps 3-10, Figs. 4-5), for 2D spin-1/2 int8 lattices of either

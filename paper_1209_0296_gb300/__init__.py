@@ -81,6 +81,17 @@ class Lattice:
         check(self._lib.lattice_set_reference(self._h, ctypes.byref(r)), "lattice_set_reference")
         return r.value
 
+    def set_couplings(self, bond_signs=None):
+        """Per-bond coupling signs (dims*N int8 of +-1, bond_signs[d*N + i]
+        for site i and its +e_d neighbour); None for uniform couplings."""
+        if bond_signs is None:
+            check(self._lib.lattice_set_couplings(self._h, None), "lattice_set_couplings")
+            return
+        a = np.ascontiguousarray(bond_signs, dtype=np.int8).reshape(-1)
+        if a.size != self.dims * self.N:
+            raise ValueError("need dims*N coupling signs")
+        check(self._lib.lattice_set_couplings(self._h, _ptr(a)), "lattice_set_couplings")
+
     def set_dynamics(self, dynamics=0, tile: int = 32, lam: int = 16):
         """DYNAMICS_CHECKERBOARD (default) or DYNAMICS_RANDOM_SITE with
         tile x tile sub-lattices and lam picks per round."""

@@ -48,6 +48,7 @@ SIGNATURES = {
     "lattice_set_reference": (c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "lattice_clear_reference": (c_int, [c_void_p]),
     "lattice_set_dynamics": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "lattice_set_couplings": (c_int, [c_void_p, c_void_p]),
     "lattice_autocorrelation": (c_int, [c_void_p, c_int64, c_int64, ctypes.c_double, c_void_p, c_void_p]),
     "lattice_get_spins": (c_int, [c_void_p, c_void_p]),
     "lattice_set_spins": (c_int, [c_void_p, c_void_p]),

@@ -206,6 +206,9 @@ static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supporte
 int choose_kernel(const lattice *lt)
 {
     if (lt->P.layout == LAT_BITPACKED) return LAT_KERNEL_AUTO;  // bit-packed path
+    if (lt->geom.cpl != nullptr)   // per-bond couplings: the 2D wide kernel or the generic one
+        return (lt->kernel != LAT_KERNEL_GENERIC && wide_supported(lt->geom)) ? LAT_KERNEL_WIDE
+                                                                             : LAT_KERNEL_GENERIC;
     if (lt->kernel == LAT_KERNEL_GENERIC) return LAT_KERNEL_GENERIC;
     if (lt->kernel == LAT_KERNEL_TILED && tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
     if (lt->kernel == LAT_KERNEL_WIDE && any_wide(lt->geom)) return LAT_KERNEL_WIDE;
@@ -407,7 +410,8 @@ int sweep_impl(lattice *lt, int64_t n)
     if (rc != LAT_OK) return rc;
     int64_t left = n;
     if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel == 0 && lt->P.layout == LAT_INT8 &&
-        lt->dynamics == LAT_DYNAMICS_CHECKERBOARD && wide_supported(lt->geom) && tiled_supported(lt->geom)) {
+        lt->dynamics == LAT_DYNAMICS_CHECKERBOARD && lt->geom.cpl == nullptr && wide_supported(lt->geom) &&
+        tiled_supported(lt->geom)) {
         const int64_t before = lt->sweeps;
         rc = autotune(lt, left);
         if (rc != LAT_OK) return rc;
@@ -452,6 +456,7 @@ static void release(lattice *lt)
     dev_free(lt->ref, st);
     dev_free(lt->ref_bits, st);
     dev_free(lt->rs_scratch, st);
+    dev_free(lt->cpl, st);
     delete lt;
 }
 
@@ -690,7 +695,7 @@ int lattice_set_dynamics(lattice_t *lt, int dynamics, int tile, int lambda)
         return LAT_OK;
     }
     if (dynamics != LAT_DYNAMICS_RANDOM_SITE) return LAT_EINVAL;
-    if (lt->P.dims != 2 || lt->P.two_S != 1 || lt->P.layout != LAT_INT8) return LAT_ENOTSUP;
+    if (lt->P.dims != 2 || lt->P.two_S != 1 || lt->P.layout != LAT_INT8 || lt->cpl != nullptr) return LAT_ENOTSUP;
     if (!rsite_params_ok(lt->geom, tile, lambda)) return LAT_EINVAL;
     if (lt->rs_scratch == nullptr) {
         cudaError_t e = dev_alloc((void **)&lt->rs_scratch, (size_t)lt->P.N, lt->stream);
@@ -699,6 +704,51 @@ int lattice_set_dynamics(lattice_t *lt, int dynamics, int tile, int lambda)
     lt->dynamics = dynamics;
     lt->rs_tile = tile;
     lt->rs_lambda = lambda;
+    lt->graph_valid = false;
+    return LAT_OK;
+}
+
+int lattice_set_couplings(lattice_t *lt, const int8_t *bond_signs)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    if (bond_signs == nullptr) {
+        dev_free(lt->cpl, lt->stream);
+        lt->cpl = nullptr;
+        lt->geom.cpl = nullptr;
+        lt->graph_valid = false;
+        return LAT_OK;
+    }
+    const Params &P = lt->P;
+    if (P.model != LAT_ISING || P.layout != LAT_INT8 || lt->dynamics != LAT_DYNAMICS_CHECKERBOARD)
+        return LAT_ENOTSUP;
+    const uint64_t N = P.N;
+    for (uint64_t i = 0; i < (uint64_t)P.dims * N; ++i)
+        if (bond_signs[i] != 1 && bond_signs[i] != -1) return LAT_EINVAL;
+    // One byte per site (planar layout): bit 2d = bond to -e_d negative,
+    // bit 2d+1 = bond to +e_d negative; the -e_d bond is the +e_d bond of
+    // the neighbour behind.
+    const int L = P.L;
+    std::vector<uint8_t> host((size_t)N);
+    for (uint64_t i = 0; i < N; ++i) {
+        const int x = (int)(i % (uint64_t)L), y = (int)((i / (uint64_t)L) % (uint64_t)L);
+        const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
+        const int c[3] = {x, y, z};
+        uint32_t b = 0;
+        for (int d = 0; d < P.dims; ++d) {
+            int nb[3] = {x, y, z};
+            nb[d] = (c[d] + L - 1) % L;
+            const uint64_t back = (uint64_t)nb[0] + (uint64_t)L * ((uint64_t)nb[1] + (uint64_t)L * (uint64_t)nb[2]);
+            if (bond_signs[(uint64_t)d * N + back] < 0) b |= 1u << (2 * d);
+            if (bond_signs[(uint64_t)d * N + i] < 0) b |= 1u << (2 * d + 1);
+        }
+        host[planar_index(lt->geom, x, y, z)] = (uint8_t)b;
+    }
+    cudaError_t e = cudaSuccess;
+    if (lt->cpl == nullptr) e = dev_alloc((void **)&lt->cpl, (size_t)N, lt->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lt->cpl, host.data(), (size_t)N, cudaMemcpyHostToDevice, lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);   // host buffer goes out of scope
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "set couplings");
+    lt->geom.cpl = lt->cpl;
     lt->graph_valid = false;
     return LAT_OK;
 }

@@ -84,9 +84,18 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
         const uint64_t i = addr(g, x, y, z);
         const uint64_t io = (uint64_t)(1 - colour) * g.plane + (uint64_t)r * g.half + (uint64_t)j;
         const int s_old = src[i];
-        int n = src[addr(g, x - 1, y, z)] + src[addr(g, x + 1, y, z)] +
-                src[addr(g, x, y - 1, z)] + src[addr(g, x, y + 1, z)];
-        if (g.dims == 3) n += src[addr(g, x, y, z - 1)] + src[addr(g, x, y, z + 1)];
+        int n;
+        if (g.cpl == nullptr) {
+            n = src[addr(g, x - 1, y, z)] + src[addr(g, x + 1, y, z)] + src[addr(g, x, y - 1, z)] +
+                src[addr(g, x, y + 1, z)];
+            if (g.dims == 3) n += src[addr(g, x, y, z - 1)] + src[addr(g, x, y, z + 1)];
+        } else {   // Eq. 1 couplings: sum of eps_ij * s_j
+            const uint32_t cb = g.cpl[i];
+            auto sg = [&](int bit, int v) { return ((cb >> bit) & 1u) ? -v : v; };
+            n = sg(0, src[addr(g, x - 1, y, z)]) + sg(1, src[addr(g, x + 1, y, z)]) +
+                sg(2, src[addr(g, x, y - 1, z)]) + sg(3, src[addr(g, x, y + 1, z)]);
+            if (g.dims == 3) n += sg(4, src[addr(g, x, y, z - 1)]) + sg(5, src[addr(g, x, y, z + 1)]);
+        }
         const int k_old = state_of_spin(g.two_S, s_old);
         int k_new;
         uint32_t u_acc;
@@ -229,9 +238,13 @@ __global__ void __launch_bounds__(kThreads) k_measure(Geom g, const int8_t *sp, 
         const int x = (int)(i % (uint64_t)L);
         const int y = (int)((i / (uint64_t)L) % (uint64_t)L);
         const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
-        const int s = sp[planar_index(g, x, y, z)];
-        int nf = sp[addr(g, x + 1, y, z)] + sp[addr(g, x, y + 1, z)];
-        if (g.dims == 3) nf += sp[addr(g, x, y, z + 1)];
+        const uint64_t pi = planar_index(g, x, y, z);
+        const int s = sp[pi];
+        // forward bonds (+x, +y, +z), weighted by their coupling signs
+        const uint32_t cb = g.cpl != nullptr ? g.cpl[pi] : 0u;
+        auto sg = [&](int bit, int v) { return ((cb >> bit) & 1u) ? -v : v; };
+        int nf = sg(1, sp[addr(g, x + 1, y, z)]) + sg(3, sp[addr(g, x, y + 1, z)]);
+        if (g.dims == 3) nf += sg(5, sp[addr(g, x, y, z + 1)]);
         bond = (long long)s * nf;
         mag = s;
         up = s > 0;

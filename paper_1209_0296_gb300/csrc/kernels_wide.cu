@@ -109,6 +109,20 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             R[w] = __funnelshift_r(O[w], w == W - 1 ? adj : O[w + 1], 8);
         }
     }
+    if (g.cpl != nullptr) {
+        // Eq. 1 couplings: a negative bond enters the energy as a flipped
+        // neighbour, so XOR 0xFE (+1 <-> -1) into that neighbour's byte
+        uint32_t C[W];
+        load_words<W>(reinterpret_cast<const int8_t *>(g.cpl) + (uint64_t)colour * g.plane + (uint64_t)y * half +
+                          4 * W * k, C);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            Lf[w] ^= ((C[w] >> 0) & 0x01010101u) * 0xFEu;
+            R[w] ^= ((C[w] >> 1) & 0x01010101u) * 0xFEu;
+            U[w] ^= ((C[w] >> 2) & 0x01010101u) * 0xFEu;
+            D[w] ^= ((C[w] >> 3) & 0x01010101u) * 0xFEu;
+        }
+    }
     uint32_t t[W][4], locked[W];
     bool need = false;
     const char *tb = reinterpret_cast<const char *>(sthr);
@@ -501,7 +515,7 @@ namespace lat {
 
 bool resident_supported(const Geom &g)
 {
-    return wide_supported(g) && resident_bytes(g) <= kResMaxBytes;
+    return wide_supported(g) && g.cpl == nullptr && resident_bytes(g) <= kResMaxBytes;
 }
 
 cudaError_t launch_sweep_resident(const Geom &g, int off, int n_sweeps, cudaStream_t st)

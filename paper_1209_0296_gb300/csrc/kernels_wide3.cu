@@ -309,7 +309,7 @@ cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_item
 bool wide3_supported(const Geom &g)
 {
     return g.model == LAT_ISING && (g.dims == 3 || g.two_S >= 2) && (g.L % 16) == 0 &&
-           g.bits[0] == nullptr && g.tab_n <= kMaxTab;
+           g.bits[0] == nullptr && g.cpl == nullptr && g.tab_n <= kMaxTab;
 }
 
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st)

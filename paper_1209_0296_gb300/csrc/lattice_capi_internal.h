@@ -62,6 +62,7 @@ struct lattice {
     int dynamics = 0;                    // LAT_DYNAMICS_*
     int rs_tile = 0, rs_lambda = 0;      // random-site sub-lattice side and picks per round
     int8_t *rs_scratch = nullptr;        // random-site: output of the first launch of a sweep
+    uint8_t *cpl = nullptr;              // per-site coupling-sign bytes (see Geom::cpl)
     unsigned long long *scratch4 = nullptr;
     std::vector<lat::TabEntry> host_tab;
     int64_t sweeps = 0;        // sweeps done (global index of the next sweep)

@@ -192,6 +192,10 @@ struct Geom {
     // (ref_bits); null when no reference is set.
     const int8_t *ref;
     const uint32_t *ref_bits;
+    // Per-bond coupling signs (Eq. 1 with J_ij = J * eps_ij): one byte per
+    // site in the int8 planar layout, bit set = that bond is negative; bits
+    // 0..5 = the bonds to x-1, x+1, y-1, y+1, z-1, z+1.  Null: uniform J.
+    const uint8_t *cpl;
     Ctrl *ctrl;
     // Compact acceptance table for 2D spin-1/2 (tiled and bit-packed
     // kernels): index (self down) << 3 | (# down neighbours).
@@ -210,6 +214,7 @@ struct SweepView {
     uint32_t key0, key1;
     uint8_t *flags;
     const int8_t *ref;
+    const uint8_t *cpl;
     Ctrl *ctrl;
 };
 
@@ -227,6 +232,7 @@ LAT_HD SweepView sweep_view(const Geom &g)
     v.key1 = g.key1;
     v.flags = g.flags;
     v.ref = g.ref;
+    v.cpl = g.cpl;
     v.ctrl = g.ctrl;
     return v;
 }
