@@ -25,7 +25,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ISING, NE = 0, 1
+ISING, NE, POTTS = 0, 1, 2
 INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
 
 
@@ -77,6 +77,9 @@ def _load():
             lib.oracle_measure_couplings.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
                                                      ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4
             lib.oracle_measure_couplings.restype = None
+            lib.oracle_measure_potts.argtypes = [ctypes.c_int, ctypes.c_int, i8p] + \
+                [ctypes.POINTER(ctypes.c_int64)] * 3
+            lib.oracle_measure_potts.restype = None
             lib.oracle_overlap.argtypes = [ctypes.c_int64, i8p, i8p]
             lib.oracle_overlap.restype = ctypes.c_int64
             lib.oracle_metropolis_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
@@ -218,6 +221,10 @@ class Lattice:
 
     def measure(self):
         b, m, u, f = (ctypes.c_int64() for _ in range(4))
+        if self.model == POTTS:
+            _load().oracle_measure_potts(self.dims, self.L, self.spins, ctypes.byref(b), ctypes.byref(m),
+                                         ctypes.byref(u))
+            return dict(bond=b.value, mag=m.value, up=u.value, unflipped=0)
         _load().oracle_measure_couplings(self.dims, self.L, self.spins,
                                          _ptr(self.flags) if self.model == NE else None, _ptr(self.eps),
                                          ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),

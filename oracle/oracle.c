@@ -167,7 +167,7 @@ static int setup(params_t *p, int dims, int L, int two_S, int model, double J,
     if (dims != 2 && dims != 3) return -1;
     if (L < 2 || (L & 1)) return -1;
     if (two_S < 1 || two_S > 8) return -1;
-    if (model != 0 && model != 1) return -1;
+    if (model != 0 && model != 1 && model != 2) return -1;
     if (model == 1 && (dims != 2 || two_S != 1)) return -1;
     p->eps = NULL;
     p->dims = dims; p->L = L; p->two_S = two_S; p->model = model;
@@ -222,6 +222,15 @@ int oracle_init(int dims, int L, int two_S, int model, double J, double h,
     for (int64_t i = 0; i < p.N; ++i) {
         uint32_t u = draw_word(seed, (uint32_t)(i >> 2), 0, 2, (int)(i & 3));
         int k;
+        if (model == 2) {                              /* Potts: the state label */
+            if (init == 0) k = 0;
+            else if (init == 1)
+                k = (two_S == 1) ? ((u < 0x80000000u) ? 0 : 1)
+                                 : (int)(((uint64_t)u * (uint64_t)(two_S + 1)) >> 32);
+            else return -1;
+            s[i] = (int8_t)k;
+            continue;
+        }
         if (init == 0) {
             k = two_S;                                 /* all spins up */
         } else if (init == 1) {
@@ -272,6 +281,31 @@ void oracle_measure_couplings(int dims, int L, const int8_t *s, const uint8_t *f
     *bond = b; *mag = m; *up = nu; *unflipped = nf;
 }
 
+/* Potts observables (q states, labels 0..q-1):                             */
+/*   bond = number of bonds (i, i+e_d) with equal ends, mag = number of      */
+/*   sites in state 0, up = number of sites in another state; so that        */
+/*   E = -J*bond - h*mag for H = -J sum delta(s_i,s_j) - h sum delta(s_i,0). */
+void oracle_measure_potts(int dims, int L, const int8_t *s, int64_t *bond,
+                          int64_t *mag, int64_t *up)
+{
+    params_t p;
+    memset(&p, 0, sizeof p);
+    p.dims = dims; p.L = L;
+    int Lz = (dims == 3) ? L : 1;
+    int64_t b = 0, m = 0, nu = 0;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int si = s[site_index(&p, x, y, z)];
+                b += (si == s[site_index(&p, x + 1, y, z)]);
+                b += (si == s[site_index(&p, x, y + 1, z)]);
+                if (dims == 3) b += (si == s[site_index(&p, x, y, z + 1)]);
+                m += (si == 0);
+                nu += (si != 0);
+            }
+    *bond = b; *mag = m; *up = nu;
+}
+
 void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
                     int64_t *bond, int64_t *mag, int64_t *up,
                     int64_t *unflipped)
@@ -318,7 +352,7 @@ int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, doub
                         uint32_t g = (uint32_t)(r * G + (j >> sh));
 
                         int s_old = s[i];
-                        int k_old = oracle_state_of_spin(two_S, s_old);
+                        int k_old = (model == 2) ? s_old : oracle_state_of_spin(two_S, s_old);
                         int k_new;
                         uint32_t u_acc;
                         if (two_S == 1) {
@@ -334,7 +368,27 @@ int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, doub
                                                   (uint64_t)two_S) >> 32);
                             k_new = (k_old + step) % (two_S + 1);
                         }
-                        int s_new = oracle_spin_of_state(two_S, k_new);
+                        int s_new = (model == 2) ? k_new : oracle_spin_of_state(two_S, k_new);
+
+                        /* Potts (q = two_S + 1 states): H = -J sum delta(s_i,s_j)
+                         * - h sum delta(s_i,0); the move changes the number of
+                         * equal neighbours by dn and the state-0 count by df. */
+                        if (model == 2) {
+                            int dn = 0;
+                            const int nb[6] = {
+                                s[site_index(&p, x - 1, y, z)], s[site_index(&p, x + 1, y, z)],
+                                s[site_index(&p, x, y - 1, z)], s[site_index(&p, x, y + 1, z)],
+                                dims == 3 ? s[site_index(&p, x, y, z - 1)] : 0,
+                                dims == 3 ? s[site_index(&p, x, y, z + 1)] : 0};
+                            for (int d = 0; d < 2 * dims; ++d) dn += (nb[d] == s_new) - (nb[d] == s_old);
+                            const int df = (s_new == 0) - (s_old == 0);
+                            const double dE = -(J * (double)dn) - h * (double)df;
+                            uint32_t thr;
+                            int accept = oracle_metropolis_threshold(dE, p.T, &thr);
+                            if (!accept) accept = (u_acc < thr);
+                            if (accept) s[i] = (int8_t)s_new;
+                            continue;
+                        }
 
                         /* North-East constraint (§III.B): both the north
                          * (x, y-1) and the east (x+1, y) neighbours up. */
@@ -362,8 +416,9 @@ int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, doub
                         }
                     }
         }
-        int64_t b, m, nu, nf;
-        oracle_measure_couplings(dims, L, s, flag, eps, &b, &m, &nu, &nf);
+        int64_t b, m, nu, nf = 0;
+        if (model == 2) oracle_measure_potts(dims, L, s, &b, &m, &nu);
+        else oracle_measure_couplings(dims, L, s, flag, eps, &b, &m, &nu, &nf);
         int64_t k = t - sweep0;
         if (bond) bond[k] = b;
         if (mag) mag[k] = m;
