@@ -73,7 +73,10 @@ enum lattice_status {
     LAT_ENOENT = -8    /* unknown id */
 };
 
-enum lattice_model { LAT_ISING = 0, LAT_NE = 1 };
+/* LAT_POTTS: the q-state Potts model, H = -J sum_<ij> delta(s_i, s_j) -
+ * h sum_i delta(s_i, 0), with q = two_S + 1 states (2..9) stored as the
+ * labels 0..q-1 (the paper's §III.C: the method suits the Potts model). */
+enum lattice_model { LAT_ISING = 0, LAT_NE = 1, LAT_POTTS = 2 };
 enum lattice_init {
     LAT_INIT_COLD = 0,        /* every spin at its top value (+1 for spin-1/2) */
     LAT_INIT_RANDOM = 1,      /* uniform over the 2S+1 values */
@@ -117,7 +120,9 @@ typedef struct lattice_server lattice_server_t;
  *   dims     2 or 3
  *   L        even, >= 2, L^dims < 2^32
  *   two_S    1..8 (2 * spin); North-East and the bit-packed layout need 1
- *   model    LAT_ISING or LAT_NE (North-East needs dims = 2)
+ *   model    LAT_ISING, LAT_NE (North-East needs dims = 2) or LAT_POTTS
+ *            (q = two_S + 1 states; init COLD = all state 0, RANDOM =
+ *            uniform labels; for q = 2 the Ising draws, state 0 <-> up)
  *   J, h     coupling and field of H above
  *   T_or_c   temperature (> 0) in energy units, or, for LAT_NE with
  *            J = h = 0, the concentration c in (0, 1)

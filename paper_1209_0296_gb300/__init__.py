@@ -14,11 +14,11 @@ import numpy as np
 from ._lib import LatticeError, LatticeRequest, LatticeResult, check, load
 
 __all__ = ["Lattice", "Batch", "Server", "LatticeError", "load", "threshold_table",
-           "ISING", "NE", "INIT_COLD", "INIT_RANDOM", "INIT_EQUILIBRIUM", "INT8", "BITPACKED",
+           "ISING", "NE", "POTTS", "INIT_COLD", "INIT_RANDOM", "INIT_EQUILIBRIUM", "INT8", "BITPACKED",
            "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED", "KERNEL_WIDE",
            "KERNEL_RESIDENT", "DYNAMICS_CHECKERBOARD", "DYNAMICS_RANDOM_SITE"]
 
-ISING, NE = 0, 1
+ISING, NE, POTTS = 0, 1, 2
 INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
 INT8, BITPACKED = 0, 1
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_WIDE, KERNEL_RESIDENT = 0, 1, 2, 3, 4

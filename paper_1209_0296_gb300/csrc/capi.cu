@@ -57,6 +57,24 @@ void dev_free(void *p, cudaStream_t st)
 // ---------------------------------------------------------------------------
 void build_table(const Params &P, std::vector<TabEntry> &tab, int &dsmax, int &nmax, int &nn)
 {
+    if (P.model == LAT_POTTS) {
+        // Potts: index (df + 1) * nn + (dn + nmax) with dn the change in the
+        // number of equal neighbours (|dn| <= 2*dims) and df the change in
+        // the state-0 indicator; dE = -(J*dn) - h*df.
+        dsmax = 1;
+        nmax = 2 * P.dims;
+        nn = 2 * nmax + 1;
+        tab.assign((size_t)3 * nn, TabEntry{0u, 0u});
+        for (int df = -1; df <= 1; ++df)
+            for (int dn = -nmax; dn <= nmax; ++dn) {
+                const double dE = -(P.J * (double)dn) - P.h * (double)df;
+                TabEntry e{0u, 0u};
+                if (dE <= 0.0) e.always = 1u;
+                else e.thr = (uint32_t)std::floor(std::ldexp(std::exp(-dE / P.T), 32));
+                tab[(size_t)(df + 1) * nn + (dn + nmax)] = e;
+            }
+        return;
+    }
     const int smax = max_spin(P.two_S);
     dsmax = 2 * smax;
     nmax = 2 * P.dims * smax;
@@ -92,7 +110,7 @@ int validate(int dims, int L, int two_S, int model, double J, double h, double T
     if (dims != 2 && dims != 3) return LAT_EINVAL;
     if (L < 2 || (L & 1)) return LAT_EINVAL;
     if (two_S < 1 || two_S > 8) return LAT_EINVAL;
-    if (model != LAT_ISING && model != LAT_NE) return LAT_EINVAL;
+    if (model != LAT_ISING && model != LAT_NE && model != LAT_POTTS) return LAT_EINVAL;
     if (model == LAT_NE && (dims != 2 || two_S != 1)) return LAT_EINVAL;
     if (!std::isfinite(J) || !std::isfinite(h) || !std::isfinite(T_or_c)) return LAT_EINVAL;
     const double N = std::pow((double)L, (double)dims);
@@ -107,7 +125,7 @@ int validate(int dims, int L, int two_S, int model, double J, double h, double T
         return LAT_EINVAL;
     if (init == LAT_INIT_EQUILIBRIUM && !cmode) return LAT_EINVAL;
     if (layout != LAT_INT8 && layout != LAT_BITPACKED) return LAT_EINVAL;
-    if (layout == LAT_BITPACKED && (dims != 2 || two_S != 1)) return LAT_ENOTSUP;
+    if (layout == LAT_BITPACKED && (dims != 2 || two_S != 1 || model == LAT_POTTS)) return LAT_ENOTSUP;
     P.dims = dims;
     P.L = L;
     P.two_S = two_S;
@@ -695,7 +713,9 @@ int lattice_set_dynamics(lattice_t *lt, int dynamics, int tile, int lambda)
         return LAT_OK;
     }
     if (dynamics != LAT_DYNAMICS_RANDOM_SITE) return LAT_EINVAL;
-    if (lt->P.dims != 2 || lt->P.two_S != 1 || lt->P.layout != LAT_INT8 || lt->cpl != nullptr) return LAT_ENOTSUP;
+    if (lt->P.dims != 2 || lt->P.two_S != 1 || lt->P.layout != LAT_INT8 || lt->cpl != nullptr ||
+        lt->P.model == LAT_POTTS)
+        return LAT_ENOTSUP;
     if (!rsite_params_ok(lt->geom, tile, lambda)) return LAT_EINVAL;
     if (lt->rs_scratch == nullptr) {
         cudaError_t e = dev_alloc((void **)&lt->rs_scratch, (size_t)lt->P.N, lt->stream);
@@ -806,6 +826,11 @@ int lattice_get_spins(lattice_t *lt, int8_t *host_out)
 static bool spins_allowed(const Params &P, const int8_t *s)
 {
     // Branch-free scan (vectorises): count values outside the allowed set.
+    if (P.model == LAT_POTTS) {
+        uint64_t bad = 0;
+        for (uint64_t i = 0; i < P.N; ++i) bad += (uint64_t)((s[i] < 0) | (s[i] > P.two_S));
+        return bad == 0;
+    }
     const int smax = max_spin(P.two_S);
     const int odd = P.two_S & 1;
     uint64_t bad = 0;

@@ -215,7 +215,7 @@ cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st)
 
 bool bitpacked_supported(const Geom &g)
 {
-    if (!(g.dims == 2 && g.two_S == 1 && (g.L % 64) == 0)) return false;
+    if (!(g.dims == 2 && g.two_S == 1 && (g.L % 64) == 0) || g.model == LAT_POTTS) return false;
     for (int k = 0; k < 16; ++k) {
         if ((k & 7) > 4) continue;
         if (!((g.always16 >> k) & 1u) && g.thr16[k] == 0u) return false;

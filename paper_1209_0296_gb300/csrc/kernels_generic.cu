@@ -35,17 +35,17 @@ __global__ void k_init(Geom g, int init, uint32_t thr_c)
         const uint32_t w = word_of(u, k);
         int st;
         if (init == LAT_INIT_COLD) {
-            st = g.two_S;
+            st = g.model == LAT_POTTS ? 0 : g.two_S;
         } else if (init == LAT_INIT_RANDOM) {
-            st = (g.two_S == 1) ? (w < 0x80000000u ? 1 : 0)
-                                : (int)(((uint64_t)w * (uint64_t)(g.two_S + 1)) >> 32);
+            if (g.two_S == 1) st = (w < 0x80000000u) == (g.model != LAT_POTTS) ? 1 : 0;   // Potts: state 0 <-> up
+            else st = (int)(((uint64_t)w * (uint64_t)(g.two_S + 1)) >> 32);
         } else {
             st = (w < thr_c) ? 1 : 0;
         }
         const int x = (int)(i % (uint64_t)g.L);
         const int y = (int)((i / (uint64_t)g.L) % (uint64_t)g.L);
         const int z = (int)(i / ((uint64_t)g.L * (uint64_t)g.L));
-        g.s[0][planar_index(g, x, y, z)] = (int8_t)spin_of_state(g.two_S, st);
+        g.s[0][planar_index(g, x, y, z)] = (int8_t)(g.model == LAT_POTTS ? st : spin_of_state(g.two_S, st));
     }
 }
 
@@ -96,7 +96,8 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
                 sg(2, src[addr(g, x, y - 1, z)]) + sg(3, src[addr(g, x, y + 1, z)]);
             if (g.dims == 3) n += sg(4, src[addr(g, x, y, z - 1)]) + sg(5, src[addr(g, x, y, z + 1)]);
         }
-        const int k_old = state_of_spin(g.two_S, s_old);
+        const bool potts = g.model == LAT_POTTS;
+        const int k_old = potts ? s_old : state_of_spin(g.two_S, s_old);
         int k_new;
         uint32_t u_acc;
         if (g.two_S == 1) {
@@ -110,7 +111,37 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
             k_new = k_old + step;
             if (k_new > g.two_S) k_new -= g.two_S + 1;
         }
-        const int s_new = spin_of_state(g.two_S, k_new);
+        const int s_new = potts ? k_new : spin_of_state(g.two_S, k_new);
+        if (potts) {
+            // Potts: dn = change in equal neighbours, df = change in the
+            // state-0 indicator (labels are stored as the spin bytes)
+            int nb[6];
+            nb[0] = src[addr(g, x - 1, y, z)];
+            nb[1] = src[addr(g, x + 1, y, z)];
+            nb[2] = src[addr(g, x, y - 1, z)];
+            nb[3] = src[addr(g, x, y + 1, z)];
+            nb[4] = g.dims == 3 ? src[addr(g, x, y, z - 1)] : -1;
+            nb[5] = g.dims == 3 ? src[addr(g, x, y, z + 1)] : -1;
+            int dn = 0;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) dn += (nb[d] == s_new) - (nb[d] == s_old);
+            const int df = (s_new == 0) - (s_old == 0);
+            const TabEntry e = stab[(df + 1) * g.nn + (dn + g.nmax)];
+            int s_fin = s_old;
+            if (e.always || u_acc < e.thr) s_fin = s_new;
+            dst[i] = (int8_t)s_fin;
+            if (colour == 0) dst[io] = src[io];
+            if (measure) {
+                int eq = 0;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) eq += nb[d] == s_fin;
+                pt.bond += eq;
+                const int so = dst[io];
+                pt.mag += (s_fin == 0) + (so == 0);
+                pt.up += (s_fin != 0) + (so != 0);
+            }
+            continue;
+        }
         bool allowed = true;
         if (g.model == LAT_NE) {
             // §III.B: north (x, y-1) and east (x+1, y) must both be up.
@@ -240,14 +271,22 @@ __global__ void __launch_bounds__(kThreads) k_measure(Geom g, const int8_t *sp, 
         const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
         const uint64_t pi = planar_index(g, x, y, z);
         const int s = sp[pi];
-        // forward bonds (+x, +y, +z), weighted by their coupling signs
-        const uint32_t cb = g.cpl != nullptr ? g.cpl[pi] : 0u;
-        auto sg = [&](int bit, int v) { return ((cb >> bit) & 1u) ? -v : v; };
-        int nf = sg(1, sp[addr(g, x + 1, y, z)]) + sg(3, sp[addr(g, x, y + 1, z)]);
-        if (g.dims == 3) nf += sg(5, sp[addr(g, x, y, z + 1)]);
-        bond = (long long)s * nf;
-        mag = s;
-        up = s > 0;
+        if (g.model == LAT_POTTS) {   // equal forward bonds, state-0 count, others
+            int eq = (sp[addr(g, x + 1, y, z)] == s) + (sp[addr(g, x, y + 1, z)] == s);
+            if (g.dims == 3) eq += sp[addr(g, x, y, z + 1)] == s;
+            bond = eq;
+            mag = s == 0;
+            up = s != 0;
+        } else {
+            // forward bonds (+x, +y, +z), weighted by their coupling signs
+            const uint32_t cb = g.cpl != nullptr ? g.cpl[pi] : 0u;
+            auto sg = [&](int bit, int v) { return ((cb >> bit) & 1u) ? -v : v; };
+            int nf = sg(1, sp[addr(g, x + 1, y, z)]) + sg(3, sp[addr(g, x, y + 1, z)]);
+            if (g.dims == 3) nf += sg(5, sp[addr(g, x, y, z + 1)]);
+            bond = (long long)s * nf;
+            mag = s;
+            up = s > 0;
+        }
         if (g.flags != nullptr) {
             const int c = (x + y + z) & 1;
             const uint32_t r = (uint32_t)y + (uint32_t)L * (uint32_t)z;
@@ -298,7 +337,8 @@ __global__ void __launch_bounds__(kThreads) k_count_bad(Geom g, const int8_t *s,
     long long bad = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < g.N; i += (uint64_t)gridDim.x * blockDim.x) {
         const int v = s[i];
-        bad += (v < -smax) | (v > smax) | (odd & ((v + g.two_S) & 1));
+        if (g.model == LAT_POTTS) bad += (v < 0) | (v > g.two_S);
+        else bad += (v < -smax) | (v > smax) | (odd & ((v + g.two_S) & 1));
     }
     const long long t = block_sum_ll(bad, red);
     if (threadIdx.x == 0 && t != 0) atomicAdd(out, (unsigned long long)t);

@@ -491,7 +491,9 @@ RsPlan plan(int L, int b, int lambda)
 
 bool rsite_params_ok(const Geom &g, int b, int lambda)
 {
-    if (g.dims != 2 || g.two_S != 1 || g.bits[0] != nullptr || g.cpl != nullptr || g.tab_n > kMaxTab) return false;
+    if (g.dims != 2 || g.two_S != 1 || g.bits[0] != nullptr || g.cpl != nullptr || g.tab_n > kMaxTab ||
+        g.model == LAT_POTTS)
+        return false;
     if (b < 8 || b > 256 || (b & (b - 1)) != 0 || (g.L % b) != 0) return false;
     const int half_p = b * b / 2;
     if (lambda < 1 || lambda > 1024 || (lambda & (lambda - 1)) != 0 || lambda > half_p) return false;

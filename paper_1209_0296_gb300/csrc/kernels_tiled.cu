@@ -435,7 +435,7 @@ bool tile_shape_ok(int tile_w, int tile_h)
 bool tiled_supported(const Geom &g)
 {
     if (!(g.dims == 2 && g.two_S == 1 && g.bits[0] == nullptr && (g.L % 32) == 0)) return false;
-    if (g.cpl != nullptr) return false;   // per-bond couplings: generic and wide kernels only
+    if (g.cpl != nullptr || g.model == LAT_POTTS) return false;   // per-bond couplings: generic and wide kernels only
     // Every non-always entry must have thr >= 1 (t' = thr - 1 >= 0).
     for (int k = 0; k < 16; ++k) {
         if ((k & 7) > 4) continue;

@@ -474,6 +474,7 @@ size_t resident_bytes(const Geom &g)
 bool wide_supported(const Geom &g)
 {
     if (!(g.dims == 2 && g.two_S == 1 && g.bits[0] == nullptr && (g.L % 32) == 0)) return false;
+    if (g.model == LAT_POTTS) return false;
     for (int k = 0; k < 16; ++k) {
         if ((k & 7) > 4) continue;
         if (!((g.always16 >> k) & 1u) && g.thr16[k] == 0u) return false;

@@ -1,0 +1,91 @@
+"""q-state Potts model on the GPU (generic kernel, solo and batched):
+labels and counters must equal the oracle's bit for bit; unsupported paths
+are refused."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1209_0296_gb300 as lt
+
+pytestmark = pytest.mark.gpu
+
+
+def potts_pair(dims, L, q, J, h, T, seed, n, init=lt.INIT_RANDOM, chunks=None):
+    o = oracle.Lattice(dims, L, q - 1, oracle.POTTS, J, h, T, seed=seed, init=init)
+    g = lt.Lattice(dims, L, q - 1, lt.POTTS, J, h, T, seed=seed, init=init)
+    try:
+        assert np.array_equal(g.get_spins(), o.spins), "initial labels differ"
+        ser_o = o.sweep(n)
+        for c in (chunks or [n]):
+            g.sweep(c)
+        assert np.array_equal(g.get_spins(), o.spins)
+        ser = g.series(0, n)
+        for k in ("bond", "mag", "up"):
+            assert np.array_equal(ser[k], ser_o[k]), k
+        m = o.measure()
+        obs = g.observables()
+        N = L ** dims
+        assert obs["E"] == pytest.approx((-J * m["bond"] - h * m["mag"]) / N, abs=1e-12)
+        assert obs["M"] == pytest.approx(m["mag"] / N, abs=1e-15)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 9])
+@pytest.mark.parametrize("dims,L", [(2, 16), (2, 64), (2, 30), (3, 8), (3, 16)])
+def test_potts_matches_oracle(q, dims, L):
+    potts_pair(dims, L, q, 1.0, 0.2, 0.9 if dims == 2 else 1.6, 3 * q + L, 15, chunks=[2, 13])
+
+
+@pytest.mark.parametrize("init", [lt.INIT_COLD, lt.INIT_RANDOM])
+def test_potts_critical_q3(init):
+    import math
+    potts_pair(2, 128, 3, 1.0, 0.0, 1 / math.log(1 + math.sqrt(3)), 5, 40, init=init)
+
+
+def test_potts_batch_with_ising():
+    cfg_p = [(2, 64, 3, 1.0, 0.0, 1.0, 21, 30), (3, 16, 4, 1.0, 0.1, 1.5, 22, 17), (2, 32, 2, 1.0, 0.0, 1.1, 23, 25)]
+    lats, ors = [], []
+    for dims, L, q, J, h, T, seed, n in cfg_p:
+        lats.append(lt.Lattice(dims, L, q - 1, lt.POTTS, J, h, T, seed=seed, init=lt.INIT_RANDOM))
+        ors.append(oracle.Lattice(dims, L, q - 1, oracle.POTTS, J, h, T, seed=seed, init=oracle.INIT_RANDOM))
+    ising = lt.Lattice(2, 128, 1, lt.ISING, 1.0, 0.0, 2.3, seed=24, init=lt.INIT_RANDOM)
+    b = lt.Batch()
+    for g, c in zip(lats, cfg_p):
+        b.add(g, c[-1])
+    b.add(ising, 20)
+    b.run()
+    b.synchronize()
+    for g, o, c in zip(lats, ors, cfg_p):
+        ser_o = o.sweep(c[-1])
+        assert np.array_equal(g.get_spins(), o.spins), c
+        assert np.array_equal(g.series(0, c[-1])["bond"], ser_o["bond"]), c
+    oi = oracle.Lattice(2, 128, 1, oracle.ISING, 1.0, 0.0, 2.3, seed=24, init=oracle.INIT_RANDOM)
+    oi.sweep(20)
+    assert np.array_equal(ising.get_spins(), oi.spins)
+    b.close()
+
+
+def test_potts_labels_and_refusals():
+    g = lt.Lattice(2, 16, 2, lt.POTTS, 1.0, 0.0, 1.0, seed=1, init=lt.INIT_RANDOM)
+    labels = np.random.default_rng(0).integers(0, 3, 256).astype(np.int8)
+    g.set_spins(labels)
+    assert np.array_equal(g.get_spins(), labels)
+    for bad in (3, -1):
+        x = labels.copy()
+        x[9] = bad
+        with pytest.raises(lt.LatticeError):
+            g.set_spins(x)
+    assert np.array_equal(g.get_spins(), labels)
+    for kern in (lt.KERNEL_TILED, lt.KERNEL_WIDE, lt.KERNEL_RESIDENT):
+        with pytest.raises(lt.LatticeError):
+            g.set_kernel(kern)
+    g.close()
+    q2 = lt.Lattice(2, 64, 1, lt.POTTS, 1.0, 0.0, 1.0, seed=1, init=lt.INIT_RANDOM)
+    with pytest.raises(lt.LatticeError):
+        q2.set_dynamics(lt.DYNAMICS_RANDOM_SITE, 16, 16)
+    with pytest.raises(lt.LatticeError):
+        q2.set_couplings(np.ones(2 * 4096, dtype=np.int8))
+    q2.close()
+    with pytest.raises(lt.LatticeError):
+        lt.Lattice(2, 64, 1, lt.POTTS, 1.0, 0.0, 1.0, seed=1, layout=lt.BITPACKED)
