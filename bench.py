@@ -587,6 +587,26 @@ def other_configs(dev):
                                                 "us_per_sweep": t / n * 1e6}
     g.close()
 
+    # a +-J spin glass (Eq. 1 with random bond signs, half negative), L = 4096
+    g = lt.Lattice(2, 4096, 1, lt.ISING, 1.0, 0.0, 1.0, seed=7, init=lt.INIT_RANDOM, stream=stream)
+    g.set_couplings(np.where(np.random.default_rng(5).random(2 * 4096 * 4096) < 0.5, -1, 1).astype(np.int8))
+    n = 20
+    t = _timed_sweeps(torch, stream, [g], n, flush)
+    out["spin_glass_pmJ_L4096"] = {"updates_per_ns": 4096 * 4096 * n / t / 1e9, "sweeps": n,
+                                   "alg_GBps": 3.0 * 4096 * 4096 * n / t / 1e9,
+                                   "kernel": names.get(g.get_kernel()["kernel"], "?")}
+    g.close()
+
+    # the q = 3 Potts model at its critical point, L = 4096
+    import math
+    g = lt.Lattice(2, 4096, 2, lt.POTTS, 1.0, 0.0, 1.0 / math.log(1.0 + math.sqrt(3.0)), seed=7,
+                   init=lt.INIT_RANDOM, stream=stream)
+    n = 10
+    t = _timed_sweeps(torch, stream, [g], n, flush)
+    out["potts_q3_L4096_Tc"] = {"updates_per_ns": 4096 * 4096 * n / t / 1e9, "sweeps": n,
+                                "kernel": names.get(g.get_kernel()["kernel"], "?")}
+    g.close()
+
     # one 2D Ising lattice far larger than L2: L = 32768 (1 GiB per buffer)
     g = lt.Lattice(2, 32768, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=7, init=lt.INIT_RANDOM, stream=stream)
     n = 10

@@ -299,15 +299,16 @@ int lattice_batch_run(lattice_batch_t *b)
             // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
             // the tiled items when their kernel is the tiled one; 3D and
             // spin-S Ising lattices with L % 16 == 0 take the 3D wide items;
-            // the rest (other sizes, an explicit generic choice) go to the
-            // generic chunks.  Item lattice indexes are local to the phase.
+            // the rest (other sizes, per-bond couplings, an explicit generic
+            // choice) go to the generic chunks.  Item lattice indexes are
+            // local to the phase.
             const int kern = choose_kernel(lt);
             const bool generic = kern == LAT_KERNEL_GENERIC;
             if (!generic && tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) {
                 const int nt = tiles_of(lt->geom, 0);
                 auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
                 for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else if (!generic && wide_supported(lt->geom)) {
+            } else if (!generic && wide_supported(lt->geom) && lt->geom.cpl == nullptr) {
                 const int nw = wide_items(lt->geom);
                 auto &dst = w2[lt->P.model == LAT_NE ? 1 : 0];
                 for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));

@@ -74,7 +74,7 @@ LAT_D void store_words(int8_t *p, const uint32_t (&v)[W])
 // threads with shorter dependency chains.  kInPlace: both buffers are the
 // same array (the resident kernel), so colour 0 does not copy the colour-1
 // sites.
-template <bool kNE, bool kInPlace = false, int W = 4, bool kPre = false>
+template <bool kNE, bool kInPlace = false, int W = 4, bool kPre = false, bool kCpl = false>
 LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsigned long long sweep,
                       const PhiloxPre &pp, int y, int k, Counts &cnt, const U4 *upre = nullptr)
 {
@@ -109,7 +109,7 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             R[w] = __funnelshift_r(O[w], w == W - 1 ? adj : O[w + 1], 8);
         }
     }
-    if (g.cpl != nullptr) {
+    if constexpr (kCpl) {
         // Eq. 1 couplings: a negative bond enters the energy as a flipped
         // neighbour, so XOR 0xFE (+1 <-> -1) into that neighbour's byte
         uint32_t C[W];
@@ -271,7 +271,7 @@ LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, 
     flush_slot(series_slot(g.ctrl, sweep), g.ref ? acf_slot(g.ctrl, sweep) : nullptr, c, ne, red);
 }
 
-template <bool kNE>
+template <bool kNE, bool kCpl>
 __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
 {
     __shared__ uint32_t sthr[16];
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     const uint64_t total = (uint64_t)g.L * cpr;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
          t += (uint64_t)gridDim.x * blockDim.x)
-        wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+        wide_chunk<kNE, false, 4, false, kCpl>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
     if (colour == 1) flush(v, sweep, cnt, kNE, red);
 }
 
@@ -487,23 +487,22 @@ int wide_chunks(const Geom &g) { return (int)(((uint64_t)g.L * (g.half >> 4) + k
 cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st)
 {
     const Geom k = tiled_geom(g);  // compact table in t' = thr - 1 form
-    // one wave: SMs x resident CTAs per SM (queried once per model)
-    static int resident[2] = {0, 0};
-    const int m = g.model == LAT_NE ? 1 : 0;
+    // instantiations: Ising, North-East, Ising with per-bond couplings
+    const int m = g.model == LAT_NE ? 1 : (g.cpl != nullptr ? 2 : 0);
+    using K = void (*)(Geom, int, int);
+    const K kern[3] = {k_wide_half<false, false>, k_wide_half<true, false>, k_wide_half<false, true>};
+    // one wave: SMs x resident CTAs per SM (queried once per instantiation)
+    static int resident[3] = {0, 0, 0};
     if (resident[m] == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (m) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide_half<true>, kThreads, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wide_half<false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern[m], kThreads, 0);
         resident[m] = sms * (per > 0 ? per : 1);
     }
     const unsigned blocks = (unsigned)std::min<long long>(wide_chunks(g), resident[m]);
     for (int colour = 0; colour < 2; ++colour) {
-        if (g.model == LAT_NE)
-            k_wide_half<true><<<blocks, kThreads, 0, st>>>(k, colour, off);
-        else
-            k_wide_half<false><<<blocks, kThreads, 0, st>>>(k, colour, off);
+        kern[m]<<<blocks, kThreads, 0, st>>>(k, colour, off);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
