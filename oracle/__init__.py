@@ -74,6 +74,16 @@ def _load():
                                                    ctypes.c_uint64, i8p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4
             lib.oracle_sweep_couplings.restype = ctypes.c_int
+            lib.oracle_sweep_disorder.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_uint64, i8p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 5
+            lib.oracle_sweep_disorder.restype = ctypes.c_int
+            lib.oracle_measure_disorder.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p] + \
+                [ctypes.POINTER(ctypes.c_int64)] * 5
+            lib.oracle_measure_disorder.restype = None
             lib.oracle_measure_couplings.argtypes = [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
                                                      ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4
             lib.oracle_measure_couplings.restype = None
@@ -141,6 +151,7 @@ class Lattice:
         self.sweep_index = 0
         self.ref = None          # s(0) of the autocorrelation (§III.B, Phi(t))
         self.eps = None          # per-bond signs (Eq. 1 couplings J_ij = J * eps), or None
+        self.eta = None          # per-site field signs (Eq. 1 fields B_i = h * eta), or None
         rc = _load().oracle_init(dims, L, two_S, model, self.J, self.h, self.T_or_c,
                                  self.seed, init, self.spins)
         if rc != 0:
@@ -156,6 +167,16 @@ class Lattice:
         if e.size != self.dims * self.N or not np.all(np.abs(e) == 1):
             raise ValueError("couplings must be dims*N values of +-1")
         self.eps = e
+
+    def set_fields(self, eta):
+        """Per-site field signs eta_i = +-1 (B_i = h * eta_i); None for uniform."""
+        if eta is None:
+            self.eta = None
+            return
+        e = np.ascontiguousarray(eta, dtype=np.int8).reshape(-1)
+        if e.size != self.N or not np.all(np.abs(e) == 1):
+            raise ValueError("fields must be N values of +-1")
+        self.eta = e
 
     def set_reference(self):
         """Take the current configuration as s(0) of the autocorrelation."""
@@ -194,7 +215,7 @@ class Lattice:
         return self._rsite(n, tile, lam)
 
     def _rsite(self, n, tile, lam):
-        if self.dims != 2 or self.two_S != 1 or self.eps is not None:
+        if self.dims != 2 or self.two_S != 1 or self.eps is not None or self.eta is not None:
             raise ValueError("the random-site algorithm is 2D spin-1/2 with uniform couplings")
         out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
         rc = _load().oracle_rsite_sweep(self.L, self.model, self.J, self.h, self.T_or_c, self.seed,
@@ -208,12 +229,14 @@ class Lattice:
         return out
 
     def _sweep(self, n: int):
-        out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
-        rc = _load().oracle_sweep_couplings(self.dims, self.L, self.two_S, self.model, self.J, self.h,
-                                            self.T_or_c, self.seed, self.spins,
-                                            _ptr(self.flags) if self.model == NE else None,
-                                            _ptr(self.eps), self.sweep_index, n, _ptr(out["bond"]),
-                                            _ptr(out["mag"]), _ptr(out["up"]), _ptr(out["unflipped"]))
+        """Series also carry "field" = sum_i eta_i s_i (= mag without field signs)."""
+        out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped", "field")}
+        rc = _load().oracle_sweep_disorder(self.dims, self.L, self.two_S, self.model, self.J, self.h,
+                                           self.T_or_c, self.seed, self.spins,
+                                           _ptr(self.flags) if self.model == NE else None,
+                                           _ptr(self.eps), _ptr(self.eta), self.sweep_index, n,
+                                           _ptr(out["bond"]), _ptr(out["mag"]), _ptr(out["up"]),
+                                           _ptr(out["unflipped"]), _ptr(out["field"]))
         if rc != 0:
             raise ValueError("oracle_sweep rejected the parameters")
         self.sweep_index += n
@@ -225,13 +248,15 @@ class Lattice:
             _load().oracle_measure_potts(self.dims, self.L, self.spins, ctypes.byref(b), ctypes.byref(m),
                                          ctypes.byref(u))
             return dict(bond=b.value, mag=m.value, up=u.value, unflipped=0)
-        _load().oracle_measure_couplings(self.dims, self.L, self.spins,
-                                         _ptr(self.flags) if self.model == NE else None, _ptr(self.eps),
-                                         ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
-                                         ctypes.byref(f))
-        return dict(bond=b.value, mag=m.value, up=u.value, unflipped=f.value)
+        fs = ctypes.c_int64()
+        _load().oracle_measure_disorder(self.dims, self.L, self.spins,
+                                        _ptr(self.flags) if self.model == NE else None, _ptr(self.eps),
+                                        _ptr(self.eta), ctypes.byref(b), ctypes.byref(m), ctypes.byref(u),
+                                        ctypes.byref(f), ctypes.byref(fs))
+        return dict(bond=b.value, mag=m.value, up=u.value, unflipped=f.value, field=fs.value)
 
     def energy(self, bond, mag):
+        """E = -J*bond - h*mag; with field signs pass the series' "field" as mag."""
         J, h = self.J, self.h
         if self.model == NE and J == 0.0 and h == 0.0:
             J, h = 0.0, -1.0

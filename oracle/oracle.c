@@ -150,6 +150,7 @@ typedef struct {
     uint64_t seed;
     int64_t N;
     const int8_t *eps;   /* per-bond signs (Eq. 1's J_ij / J), or NULL: all +1 */
+    const int8_t *eta;   /* per-site field signs (Eq. 1's B_i / h), or NULL: all +1 */
 } params_t;
 
 static int64_t site_index(const params_t *p, int x, int y, int z)
@@ -170,6 +171,7 @@ static int setup(params_t *p, int dims, int L, int two_S, int model, double J,
     if (model != 0 && model != 1 && model != 2) return -1;
     if (model == 1 && (dims != 2 || two_S != 1)) return -1;
     p->eps = NULL;
+    p->eta = NULL;
     p->dims = dims; p->L = L; p->two_S = two_S; p->model = model;
     p->J = J; p->h = h; p->seed = seed;
     p->N = (int64_t)L * L * (dims == 3 ? L : 1);
@@ -253,8 +255,26 @@ int oracle_init(int dims, int L, int two_S, int model, double J, double h,
 /*   mag  = sum_i s_i;  up = #{s_i > 0};  unflipped = #{flag_i == 0}         */
 /* E = -J*bond - h*mag (Eq. 2 with a field).                                 */
 /* ------------------------------------------------------------------------ */
+void oracle_measure_couplings(int dims, int L, const int8_t *s, const uint8_t *flag,
+                              const int8_t *eps, int64_t *bond, int64_t *mag,
+                              int64_t *up, int64_t *unflipped);
+
 /* With couplings (eps != NULL) the bond sum is weighted:                    */
-/*   bond = sum over sites i and directions d of eps_{i,d} s_i s_{i+e_d}.    */
+/*   bond = sum over sites i and directions d of eps_{i,d} s_i s_{i+e_d};    */
+/* with field signs eta (may be NULL) field = sum_i eta_i s_i, so that       */
+/* E = -J*bond - h*field (Eq. 1 with J_ij = J eps_ij, B_i = h eta_i).        */
+void oracle_measure_disorder(int dims, int L, const int8_t *s, const uint8_t *flag,
+                             const int8_t *eps, const int8_t *eta, int64_t *bond,
+                             int64_t *mag, int64_t *up, int64_t *unflipped,
+                             int64_t *field)
+{
+    int64_t fs = 0;
+    const int64_t N = (int64_t)L * L * (dims == 3 ? L : 1);
+    for (int64_t i = 0; i < N; ++i) fs += (eta == NULL ? 1 : eta[i]) * (int64_t)s[i];
+    if (field) *field = fs;
+    oracle_measure_couplings(dims, L, s, flag, eps, bond, mag, up, unflipped);
+}
+
 void oracle_measure_couplings(int dims, int L, const int8_t *s, const uint8_t *flag,
                               const int8_t *eps, int64_t *bond, int64_t *mag,
                               int64_t *up, int64_t *unflipped)
@@ -324,16 +344,19 @@ void oracle_measure(int dims, int L, const int8_t *s, const uint8_t *flag,
 /* eps: per-bond signs (Eq. 1 with J_ij = J * eps_ij, nearest neighbours),  */
 /* eps[d*N + i] for the bond from linear site i to its +e_d neighbour; NULL */
 /* for uniform couplings.  Ising model only.                                */
-int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, double h,
-                           double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
-                           const int8_t *eps, int64_t sweep0, int64_t nsweeps,
-                           int64_t *bond, int64_t *mag, int64_t *up,
-                           int64_t *unflipped)
+/* eta: per-site field signs (B_i = h * eta_i), or NULL for a uniform field; */
+/* field[k] (may be NULL) receives sum_i eta_i s_i after each sweep.         */
+int oracle_sweep_disorder(int dims, int L, int two_S, int model, double J, double h,
+                          double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
+                          const int8_t *eps, const int8_t *eta, int64_t sweep0,
+                          int64_t nsweeps, int64_t *bond, int64_t *mag, int64_t *up,
+                          int64_t *unflipped, int64_t *field)
 {
     params_t p;
     if (setup(&p, dims, L, two_S, model, J, h, T_or_c, seed)) return -1;
-    if (eps != NULL && model != 0) return -1;
+    if ((eps != NULL || eta != NULL) && model != 0) return -1;
     p.eps = eps;
+    p.eta = eta;
     if (model == 1 && flag == NULL) return -1;
     const int sh = (two_S == 1) ? 2 : 1;               /* sites per draw: 4 or 2 */
     const int64_t half = L / 2;
@@ -406,7 +429,8 @@ int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, doub
                             accept = oracle_probability_threshold(pr, &thr);
                         } else {
                             int n = neighbour_sum(&p, s, x, y, z);
-                            double dE = oracle_delta_energy(J, h, s_new - s_old, n);
+                            const double hi = (eta == NULL || eta[i] > 0) ? h : -h;   /* B_i */
+                            double dE = oracle_delta_energy(J, hi, s_new - s_old, n);
                             accept = oracle_metropolis_threshold(dE, p.T, &thr);
                         }
                         if (!accept) accept = (u_acc < thr);
@@ -416,9 +440,10 @@ int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, doub
                         }
                     }
         }
-        int64_t b, m, nu, nf = 0;
+        int64_t b, m, nu, nf = 0, fs = 0;
         if (model == 2) oracle_measure_potts(dims, L, s, &b, &m, &nu);
-        else oracle_measure_couplings(dims, L, s, flag, eps, &b, &m, &nu, &nf);
+        else oracle_measure_disorder(dims, L, s, flag, eps, eta, &b, &m, &nu, &nf, &fs);
+        if (field) field[t - sweep0] = fs;
         int64_t k = t - sweep0;
         if (bond) bond[k] = b;
         if (mag) mag[k] = m;
@@ -426,6 +451,16 @@ int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, doub
         if (unflipped) unflipped[k] = nf;
     }
     return 0;
+}
+
+int oracle_sweep_couplings(int dims, int L, int two_S, int model, double J, double h,
+                           double T_or_c, uint64_t seed, int8_t *s, uint8_t *flag,
+                           const int8_t *eps, int64_t sweep0, int64_t nsweeps,
+                           int64_t *bond, int64_t *mag, int64_t *up,
+                           int64_t *unflipped)
+{
+    return oracle_sweep_disorder(dims, L, two_S, model, J, h, T_or_c, seed, s, flag, eps, NULL,
+                                 sweep0, nsweeps, bond, mag, up, unflipped, NULL);
 }
 
 int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,

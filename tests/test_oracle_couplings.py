@@ -113,3 +113,58 @@ def test_measure_matches_a_recount():
     bond = (e[0] * s * np.roll(s, -1, axis=2)).sum() + (e[1] * s * np.roll(s, -1, axis=1)).sum() + \
         (e[2] * s * np.roll(s, -1, axis=0)).sum()
     assert o.measure()["bond"] == int(bond)
+
+
+# ---- per-site field signs (Eq. 1's B_i = h * eta_i) -----------------------
+
+@pytest.mark.parametrize("dims,L", [(2, 8), (3, 6)])
+def test_gauge_invariance_with_random_fields(dims, L):
+    # tau maps eps_ij -> tau_i tau_j eps_ij and eta_i -> tau_i eta_i: every
+    # move keeps its energy change, so the chain is tau*s(t) with h != 0 too
+    rng = np.random.default_rng(100 + L)
+    N = L ** dims
+    eps = rng.choice(np.array([-1, 1], dtype=np.int8), dims * N)
+    eta = rng.choice(np.array([-1, 1], dtype=np.int8), N)
+    tau = rng.choice(np.array([-1, 1], dtype=np.int8), N)
+    a = _lat(dims, L, 1, 1.0, 0.7, 1.4, 33, eps)
+    a.set_fields(eta)
+    b = _lat(dims, L, 1, 1.0, 0.7, 1.4, 33, _gauge(dims, L, eps, tau), spins=a.spins * tau)
+    b.set_fields(eta * tau)
+    for _ in range(5):
+        sa, sb = a.sweep(3), b.sweep(3)
+        assert np.array_equal(b.spins, a.spins * tau)
+        assert np.array_equal(sa["bond"], sb["bond"])
+        assert np.array_equal(sa["field"], sb["field"])
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+def test_uniform_field_signs_reduce_to_the_plain_field(sign):
+    a = _lat(2, 8, 1, 1.0, 0.4, 1.7, 6)
+    a.set_fields(np.full(64, sign, dtype=np.int8))
+    b = _lat(2, 8, 1, 1.0, 0.4 * sign, 1.7, 6)
+    sa, sb = a.sweep(10), b.sweep(10)
+    assert np.array_equal(a.spins, b.spins)
+    assert np.array_equal(sa["field"], sign * sb["mag"])
+
+
+def test_enumeration_random_bonds_and_fields():
+    rng = np.random.default_rng(12)
+    eps = rng.choice(np.array([-1, 1], dtype=np.int8), 32)
+    eta = rng.choice(np.array([-1, 1], dtype=np.int8), 16)
+    J, h, T = 1.0, 0.6, 1.6
+    L, N = 4, 16
+    states = np.arange(1 << N, dtype=np.int64)
+    s = (((states[:, None] >> np.arange(N)) & 1) * 2 - 1).astype(np.int64)
+    e = eps.reshape(2, N).astype(np.int64)
+    idx = np.arange(N)
+    x, y = idx % L, idx // L
+    bond = (e[0] * s * s[:, ((x + 1) % L) + L * y]).sum(1) + (e[1] * s * s[:, x + L * ((y + 1) % L)]).sum(1)
+    E = -J * bond - h * (s * eta.astype(np.int64)).sum(1)
+    w = np.exp(-(E - E.min()) / T)
+    E_ex = (w * E).sum() / w.sum() / N
+    o = _lat(2, 4, 1, J, h, T, 14, eps)
+    o.set_fields(eta)
+    o.sweep(1000)
+    ser = o.sweep(150000)
+    ev, de = _mean_and_error((-J * ser["bond"] - h * ser["field"]) / N)
+    assert abs(ev - E_ex) < 5 * de + 1e-4, (ev, E_ex, de)
