@@ -142,7 +142,8 @@ int lattice_create(lattice_t **out, int dims, int L, int two_S, int model,
 int lattice_sweep(lattice_t *lat, int64_t n);
 
 /* Per-site observables of the current configuration (waits for the
- * stream): E/N = (-J*bond - h*mag)/N, M/N, up density, and persistence =
+ * stream): E/N = (-J*bond - h*mag)/N (mag replaced by the field sum while
+ * per-site field signs are set), M/N, up density, and persistence =
  * fraction of sites that never changed since creation or the last
  * lattice_set_state (North-East only; NaN for Ising).  NULL outputs are
  * skipped.  For North-East in c-mode E uses J = 0, h = -1. */
@@ -183,9 +184,28 @@ int lattice_set_reference(lattice_t *lat, int64_t *ref_sweep);
  * (LAT_ENOTSUP otherwise); LAT_EINVAL for values other than +-1.  Such
  * lattices sweep with the 2D wide kernel (2D spin-1/2) or the generic one;
  * the tiled, resident, bit-packed and random-site paths are not available
- * (lattice_set_kernel answers LAT_ENOTSUP).  Uses N bytes of device memory;
- * a checkpoint (lattice_get_state) does not include the couplings. */
+ * (lattice_set_kernel answers LAT_ENOTSUP).  Uses N bytes of device memory
+ * (shared with the field signs below); a checkpoint (lattice_get_state)
+ * does not include the couplings.  Waits for the stream. */
 int lattice_set_couplings(lattice_t *lat, const int8_t *bond_signs);
+
+/* Per-site random fields (Eq. 1 with B_i = h * eta_i, eta_i = +-1: the
+ * random-field Ising model with a bimodal field).  field_signs holds N int8
+ * values of +-1, field_signs[i] = eta for site i (x fastest); NULL restores
+ * the uniform field.  Couplings and field signs are independent: setting
+ * or clearing one keeps the other.  From then on every sweep also records
+ *   field = sum_i eta_i s_i       (int64, lattice_field_series)
+ * and lattice_observables reports E/N = (-J*bond - h*field)/N.  Same
+ * restrictions as lattice_set_couplings; such lattices sweep with the
+ * generic kernel only (in a batch too).  The acceptance table gains a
+ * second half for -h.  Waits for the stream; LAT_EINVAL for values other
+ * than +-1. */
+int lattice_set_fields(lattice_t *lat, const int8_t *field_signs);
+
+/* Copy the recorded field sums of sweeps [first, first+count) to field[]
+ * (int64).  LAT_ENOENT when no field signs are set; LAT_ERANGE unless the
+ * range was swept with the current field signs and is recorded. */
+int lattice_field_series(lattice_t *lat, int64_t first, int64_t count, int64_t *field);
 
 /* Choose the sweep dynamics of later lattice_sweep calls.
  * LAT_DYNAMICS_RANDOM_SITE is the paper's own North-East GPU algorithm

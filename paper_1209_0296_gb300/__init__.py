@@ -92,6 +92,26 @@ class Lattice:
             raise ValueError("need dims*N coupling signs")
         check(self._lib.lattice_set_couplings(self._h, _ptr(a)), "lattice_set_couplings")
 
+    def set_fields(self, field_signs=None):
+        """Per-site field signs eta_i = +-1 (N int8, x fastest; B_i = h *
+        eta_i); None for the uniform field."""
+        if field_signs is None:
+            check(self._lib.lattice_set_fields(self._h, None), "lattice_set_fields")
+            return
+        a = np.ascontiguousarray(field_signs, dtype=np.int8).reshape(-1)
+        if a.size != self.N:
+            raise ValueError("need N field signs")
+        check(self._lib.lattice_set_fields(self._h, _ptr(a)), "lattice_set_fields")
+
+    def field_series(self, first: int, count: int | None = None):
+        """Recorded sums sum_i eta_i s_i of sweeps [first, first+count)."""
+        if count is None:
+            count = self.sweeps() - first
+        out = np.zeros(count, dtype=np.int64)
+        check(self._lib.lattice_field_series(self._h, int(first), int(count), _ptr(out)),
+              "lattice_field_series")
+        return out
+
     def set_dynamics(self, dynamics=0, tile: int = 32, lam: int = 16):
         """DYNAMICS_CHECKERBOARD (default) or DYNAMICS_RANDOM_SITE with
         tile x tile sub-lattices and lam picks per round."""

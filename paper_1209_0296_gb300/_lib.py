@@ -49,6 +49,8 @@ SIGNATURES = {
     "lattice_clear_reference": (c_int, [c_void_p]),
     "lattice_set_dynamics": (c_int, [c_void_p, c_int, c_int, c_int]),
     "lattice_set_couplings": (c_int, [c_void_p, c_void_p]),
+    "lattice_set_fields": (c_int, [c_void_p, c_void_p]),
+    "lattice_field_series": (c_int, [c_void_p, c_int64, c_int64, c_void_p]),
     "lattice_autocorrelation": (c_int, [c_void_p, c_int64, c_int64, ctypes.c_double, c_void_p, c_void_p]),
     "lattice_get_spins": (c_int, [c_void_p, c_void_p]),
     "lattice_set_spins": (c_int, [c_void_p, c_void_p]),

@@ -75,6 +75,7 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
 // and of North-East lattices, 3D / spin-S wide items, generic chunks.
 struct Shape {
     int n_lat, n_ising, n_ne, n_w2[2], n_wide, n_gen;
+    int tab_gen;   // largest table among the generic lattices
 };
 
 // One phase of a run: its item counts and where its descriptors, items and
@@ -113,10 +114,10 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
         const uint2 *gen = wide + sh.n_wide;
         if (e == cudaSuccess && sh.n_gen > 0)
             e = launch_batch_generic(ph.geoms, gen, sh.n_gen, b->d_counters + 2, 0, 0,
-                                     std::min(b->grid_generic, sh.n_gen), st);
+                                     std::min(b->grid_generic, sh.n_gen), sh.tab_gen, st);
         if (e == cudaSuccess && sh.n_gen > 0)
             e = launch_batch_generic(ph.geoms, gen, sh.n_gen, b->d_counters + 3, 1, 0,
-                                     std::min(b->grid_generic, sh.n_gen), st);
+                                     std::min(b->grid_generic, sh.n_gen), sh.tab_gen, st);
         if (e == cudaSuccess) e = launch_batch_advance(ph.ctrls, sh.n_lat, b->d_counters, kCounters, 1ull, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     }
@@ -292,6 +293,7 @@ int lattice_batch_run(lattice_batch_t *b)
         if (steps <= 0) continue;
         const size_t g0 = all_geoms.size();
         std::vector<uint2> tiled, tiled_ne, w2[2], wide, gen;
+        int tab_gen = 0;
         for (size_t i = 0; i < n_active; ++i) {
             lattice *lt = work[i].first;
             all_geoms.push_back(tiled_geom(lt->geom));
@@ -319,11 +321,12 @@ int lattice_batch_run(lattice_batch_t *b)
                 const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
                 const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
                 for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
+                tab_gen = std::max(tab_gen, lt->geom.tab_n);
             }
         }
         Spec sp;
         sp.sh = Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                      (int)wide.size(), (int)gen.size()};
+                      (int)wide.size(), (int)gen.size(), tab_gen};
         sp.steps = steps;
         sp.geom_off = g0;
         sp.item_off = all_items.size();

@@ -172,8 +172,9 @@ int ensure_series(lattice *lt, unsigned long long need)
     if (slots <= lt->series_cap && lt->series != nullptr) return LAT_OK;
     unsigned long long cap = lt->series_cap ? lt->series_cap : 64;
     while (cap < slots) cap *= 2;
-    // [cap][4] counters, then [cap] reference overlaps (the autocorrelation)
-    const size_t bytes = (size_t)cap * 5 * sizeof(unsigned long long);
+    // [cap][4] counters, then [cap] reference overlaps (the autocorrelation),
+    // then [cap] field sums
+    const size_t bytes = (size_t)cap * 6 * sizeof(unsigned long long);
     void *p = nullptr;
     cudaError_t e = dev_alloc(&p, bytes, lt->stream);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "series alloc");
@@ -182,12 +183,13 @@ int ensure_series(lattice *lt, unsigned long long need)
     if (e == cudaSuccess && lt->series != nullptr)
         e = cudaMemcpyAsync(np, lt->series, (size_t)lt->series_cap * 4 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToDevice, lt->stream);
-    if (e == cudaSuccess && lt->series != nullptr)
-        e = cudaMemcpyAsync(np + 4 * cap, lt->series + 4 * lt->series_cap,
+    for (int sec = 4; sec < 6 && e == cudaSuccess && lt->series != nullptr; ++sec)
+        e = cudaMemcpyAsync(np + sec * cap, lt->series + sec * lt->series_cap,
                             (size_t)lt->series_cap * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                             lt->stream);
     if (e == cudaSuccess)
-        e = launch_set_ctrl(lt->ctrl, (unsigned long long)lt->sweeps, np, base, cap, np + 4 * cap, lt->stream);
+        e = launch_set_ctrl(lt->ctrl, (unsigned long long)lt->sweeps, np, base, cap, np + 4 * cap, np + 5 * cap,
+                            lt->stream);
     if (e != cudaSuccess) {
         dev_free(p, lt->stream);
         return cuda_fail(e, "series grow");
@@ -224,6 +226,7 @@ static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supporte
 int choose_kernel(const lattice *lt)
 {
     if (lt->P.layout == LAT_BITPACKED) return LAT_KERNEL_AUTO;  // bit-packed path
+    if (lt->has_fields) return LAT_KERNEL_GENERIC;   // per-site field signs: the generic kernel only
     if (lt->geom.cpl != nullptr)   // per-bond couplings: the 2D wide kernel or the generic one
         return (lt->kernel != LAT_KERNEL_GENERIC && wide_supported(lt->geom)) ? LAT_KERNEL_WIDE
                                                                              : LAT_KERNEL_GENERIC;
@@ -538,7 +541,7 @@ int create_impl(lattice_t **out, int dims, int L, int two_S, int model, double J
     }
     if (e == cudaSuccess) e = dev_alloc((void **)&lt->tab, tab.size() * sizeof(TabEntry), st);
     if (e == cudaSuccess) e = dev_alloc((void **)&lt->ctrl, sizeof(Ctrl), st);
-    if (e == cudaSuccess) e = dev_alloc((void **)&lt->scratch4, 4 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = dev_alloc((void **)&lt->scratch4, 8 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) {
         rc = (e == cudaErrorMemoryAllocation) ? LAT_ENOMEM : cuda_fail(e, "alloc");
         release(lt);
@@ -613,20 +616,26 @@ static int current_planar(lattice *lt, int8_t **cur, int8_t **scratch)
     return LAT_OK;
 }
 
-static int current_counters(lattice *lt, long long c[4])
+// bond, mag, up, unflipped and the field sum of the current state: the
+// last recorded sweep's counters, or measured when no sweep is recorded
+// (or the couplings or field signs changed after it).
+static int current_counters(lattice *lt, long long c[5])
 {
     cudaError_t e;
-    if (lt->sweeps > lt->series_first) {
-        e = cudaMemcpyAsync(c, lt->series + 4ull * (unsigned long long)(lt->sweeps - 1 - lt->series_first),
-                            4 * sizeof(long long), cudaMemcpyDeviceToHost, lt->stream);
+    if (lt->sweeps > lt->series_first && lt->sweeps > lt->disorder_from) {
+        const unsigned long long k = (unsigned long long)(lt->sweeps - 1 - lt->series_first);
+        e = cudaMemcpyAsync(c, lt->series + 4ull * k, 4 * sizeof(long long), cudaMemcpyDeviceToHost, lt->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c + 4, lt->series + 5 * lt->series_cap + k, sizeof(long long),
+                                cudaMemcpyDeviceToHost, lt->stream);
     } else {
         int8_t *cur = nullptr;
         int rc = current_planar(lt, &cur, nullptr);
         if (rc != LAT_OK) return rc;
-        e = cudaMemsetAsync(lt->scratch4, 0, 4 * sizeof(long long), lt->stream);
+        e = cudaMemsetAsync(lt->scratch4, 0, 5 * sizeof(long long), lt->stream);
         if (e == cudaSuccess) e = launch_measure(lt->geom, cur, lt->scratch4, lt->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c, lt->scratch4, 4 * sizeof(long long), cudaMemcpyDeviceToHost,
+            e = cudaMemcpyAsync(c, lt->scratch4, 5 * sizeof(long long), cudaMemcpyDeviceToHost,
                                 lt->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
@@ -637,7 +646,7 @@ static int current_counters(lattice *lt, long long c[4])
 int lattice_observables(lattice_t *lt, double *E, double *M, double *density, double *persistence)
 {
     if (lt == nullptr) return LAT_EINVAL;
-    long long c[4];
+    long long c[5];
     int rc = current_counters(lt, c);
     if (rc != LAT_OK) return rc;
     const double N = (double)lt->P.N;
@@ -646,7 +655,9 @@ int lattice_observables(lattice_t *lt, double *E, double *M, double *density, do
         J = 0.0;
         h = -1.0;
     }
-    if (E) *E = (-J * (double)c[0] - h * (double)c[1]) / N;
+    // Eq. 1: the field term is -h sum_i eta_i s_i (eta = 1 without field signs)
+    const double fs = lt->has_fields ? (double)c[4] : (double)c[1];
+    if (E) *E = (-J * (double)c[0] - h * fs) / N;
     if (M) *M = (double)c[1] / N;
     if (density) *density = (double)c[2] / N;
     if (persistence) *persistence = (lt->P.model == LAT_NE) ? (double)c[3] / N : NAN;
@@ -728,27 +739,83 @@ int lattice_set_dynamics(lattice_t *lt, int dynamics, int tile, int lambda)
     return LAT_OK;
 }
 
-int lattice_set_couplings(lattice_t *lt, const int8_t *bond_signs)
+// Upload the host disorder bytes (or drop the device copy when every byte
+// is zero) and rebuild the acceptance table: a second half for -h follows
+// the first while field signs are set.
+static int apply_disorder(lattice *lt)
 {
-    if (lt == nullptr) return LAT_EINVAL;
-    if (bond_signs == nullptr) {
-        dev_free(lt->cpl, lt->stream);
-        lt->cpl = nullptr;
-        lt->geom.cpl = nullptr;
-        lt->graph_valid = false;
-        return LAT_OK;
+    cudaStream_t st = lt->stream;
+    cudaError_t e = cudaStreamSynchronize(st);   // no queued sweep may read the old table or bytes
+    if (e != cudaSuccess) return cuda_fail(e, "disorder sync");
+    std::vector<TabEntry> tab;
+    int dsmax, nmax, nn;
+    build_table(lt->P, tab, dsmax, nmax, nn);
+    if (lt->has_fields) {
+        Params Pm = lt->P;
+        Pm.h = -Pm.h;
+        std::vector<TabEntry> neg;
+        build_table(Pm, neg, dsmax, nmax, nn);
+        tab.insert(tab.end(), neg.begin(), neg.end());
     }
+    if ((int)tab.size() != lt->geom.tab_n) {
+        TabEntry *t = nullptr;
+        e = dev_alloc((void **)&t, tab.size() * sizeof(TabEntry), st);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "table alloc");
+        dev_free(lt->tab, st);
+        lt->tab = t;
+        lt->geom.tab = t;
+        lt->geom.tab_n = (int)tab.size();
+    }
+    e = cudaMemcpyAsync(lt->tab, tab.data(), tab.size() * sizeof(TabEntry), cudaMemcpyHostToDevice, st);
+    const bool any = lt->has_bonds || lt->has_fields;
+    if (e == cudaSuccess && any) {
+        if (lt->cpl == nullptr) e = dev_alloc((void **)&lt->cpl, (size_t)lt->P.N, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lt->cpl, lt->dis_host.data(), (size_t)lt->P.N, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host vectors go out of scope
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "set disorder");
+    if (!any) {
+        dev_free(lt->cpl, st);
+        lt->cpl = nullptr;
+        lt->dis_host.clear();
+    }
+    lt->geom.cpl = lt->cpl;
+    lt->disorder_from = lt->sweeps;
+    lt->graph_valid = false;
+    return LAT_OK;
+}
+
+// Checks shared by the coupling and field setters: Ising, int8 layout,
+// checkerboard dynamics.
+static int disorder_ok(const lattice *lt)
+{
     const Params &P = lt->P;
     if (P.model != LAT_ISING || P.layout != LAT_INT8 || lt->dynamics != LAT_DYNAMICS_CHECKERBOARD)
         return LAT_ENOTSUP;
+    return LAT_OK;
+}
+
+int lattice_set_couplings(lattice_t *lt, const int8_t *bond_signs)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    const Params &P = lt->P;
     const uint64_t N = P.N;
+    if (bond_signs == nullptr) {
+        if (!lt->has_bonds) return LAT_OK;
+        for (auto &b : lt->dis_host) b &= 0x40u;   // keep the field signs
+        lt->has_bonds = false;
+        return apply_disorder(lt);
+    }
+    int rc = disorder_ok(lt);
+    if (rc != LAT_OK) return rc;
     for (uint64_t i = 0; i < (uint64_t)P.dims * N; ++i)
         if (bond_signs[i] != 1 && bond_signs[i] != -1) return LAT_EINVAL;
     // One byte per site (planar layout): bit 2d = bond to -e_d negative,
     // bit 2d+1 = bond to +e_d negative; the -e_d bond is the +e_d bond of
     // the neighbour behind.
     const int L = P.L;
-    std::vector<uint8_t> host((size_t)N);
+    if (lt->dis_host.size() != (size_t)N) lt->dis_host.assign((size_t)N, 0u);
     for (uint64_t i = 0; i < N; ++i) {
         const int x = (int)(i % (uint64_t)L), y = (int)((i / (uint64_t)L) % (uint64_t)L);
         const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
@@ -761,15 +828,53 @@ int lattice_set_couplings(lattice_t *lt, const int8_t *bond_signs)
             if (bond_signs[(uint64_t)d * N + back] < 0) b |= 1u << (2 * d);
             if (bond_signs[(uint64_t)d * N + i] < 0) b |= 1u << (2 * d + 1);
         }
-        host[planar_index(lt->geom, x, y, z)] = (uint8_t)b;
+        uint8_t &dst = lt->dis_host[planar_index(lt->geom, x, y, z)];
+        dst = (uint8_t)((dst & 0x40u) | b);
     }
-    cudaError_t e = cudaSuccess;
-    if (lt->cpl == nullptr) e = dev_alloc((void **)&lt->cpl, (size_t)N, lt->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(lt->cpl, host.data(), (size_t)N, cudaMemcpyHostToDevice, lt->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);   // host buffer goes out of scope
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "set couplings");
-    lt->geom.cpl = lt->cpl;
-    lt->graph_valid = false;
+    lt->has_bonds = true;
+    return apply_disorder(lt);
+}
+
+int lattice_set_fields(lattice_t *lt, const int8_t *field_signs)
+{
+    if (lt == nullptr) return LAT_EINVAL;
+    const Params &P = lt->P;
+    const uint64_t N = P.N;
+    if (field_signs == nullptr) {
+        if (!lt->has_fields) return LAT_OK;
+        for (auto &b : lt->dis_host) b &= 0x3fu;   // keep the coupling signs
+        lt->has_fields = false;
+        return apply_disorder(lt);
+    }
+    int rc = disorder_ok(lt);
+    if (rc != LAT_OK) return rc;
+    for (uint64_t i = 0; i < N; ++i)
+        if (field_signs[i] != 1 && field_signs[i] != -1) return LAT_EINVAL;
+    const int L = P.L;
+    if (lt->dis_host.size() != (size_t)N) lt->dis_host.assign((size_t)N, 0u);
+    for (uint64_t i = 0; i < N; ++i) {
+        const int x = (int)(i % (uint64_t)L), y = (int)((i / (uint64_t)L) % (uint64_t)L);
+        const int z = (int)(i / ((uint64_t)L * (uint64_t)L));
+        uint8_t &dst = lt->dis_host[planar_index(lt->geom, x, y, z)];
+        dst = (uint8_t)((dst & 0x3fu) | (field_signs[i] < 0 ? 0x40u : 0u));
+    }
+    lt->has_fields = true;
+    rc = apply_disorder(lt);
+    if (rc == LAT_OK) lt->fields_from = lt->sweeps;
+    return rc;
+}
+
+int lattice_field_series(lattice_t *lt, int64_t first, int64_t count, int64_t *field)
+{
+    if (lt == nullptr || first < 0 || count < 0) return LAT_EINVAL;
+    if (!lt->has_fields) return LAT_ENOENT;
+    if (first < lt->series_first || first < lt->fields_from || first + count > lt->sweeps) return LAT_ERANGE;
+    if (count == 0 || field == nullptr) return LAT_OK;
+    cudaError_t e = cudaMemcpyAsync(field,
+                                    lt->series + 5 * lt->series_cap + (unsigned long long)(first - lt->series_first),
+                                    (size_t)count * sizeof(int64_t), cudaMemcpyDeviceToHost, lt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lt->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "field series copy");
     return LAT_OK;
 }
 
@@ -963,6 +1068,8 @@ int lattice_set_state(lattice_t *lt, const int8_t *spins, const uint8_t *flags, 
     lt->series_cap = 0;
     lt->sweeps = sweeps;
     lt->series_first = sweeps;
+    lt->disorder_from = sweeps;
+    lt->fields_from = sweeps;
     return ensure_series(lt, (unsigned long long)sweeps + 64);
 }
 
@@ -973,7 +1080,7 @@ int lattice_info(lattice_t *lt, int64_t *sweeps, int64_t *n_sites, int64_t *devi
     if (n_sites) *n_sites = (int64_t)lt->P.N;
     if (device_bytes)
         *device_bytes = (int64_t)(footprint_bytes(lt->P) +
-                                  (size_t)lt->series_cap * 5 * sizeof(long long) +
+                                  (size_t)lt->series_cap * 6 * sizeof(long long) +
                                   (lt->ref ? (size_t)lt->P.N : 0) +
                                   (lt->ref_bits ? bits_bytes(lt->P) : 0) +
                                   (lt->rs_scratch ? (size_t)lt->P.N : 0));
@@ -1000,7 +1107,7 @@ int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sw
     if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_RESIDENT) return LAT_EINVAL;
     if (tile_w < 0 || tile_h < 0 || sweeps_per_graph < 0) return LAT_EINVAL;
     if (kernel == LAT_KERNEL_TILED && !tiled_supported(lt->geom)) return LAT_ENOTSUP;
-    if (kernel == LAT_KERNEL_WIDE && !any_wide(lt->geom)) return LAT_ENOTSUP;
+    if (kernel == LAT_KERNEL_WIDE && (!any_wide(lt->geom) || lt->has_fields)) return LAT_ENOTSUP;
     if (kernel == LAT_KERNEL_RESIDENT && !resident_supported(lt->geom)) return LAT_ENOTSUP;
     if (!tile_shape_ok(tile_w, tile_h)) return LAT_EINVAL;
     lt->kernel = kernel;

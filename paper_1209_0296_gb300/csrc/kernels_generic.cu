@@ -51,7 +51,7 @@ __global__ void k_init(Geom g, int init, uint32_t thr_c)
 
 // Partial per-sweep counters of one thread.
 struct Part {
-    long long bond = 0, mag = 0, up = 0, unfl = 0, acf = 0;
+    long long bond = 0, mag = 0, up = 0, unfl = 0, acf = 0, fld = 0;
 };
 
 // Sweep the colour-`colour` sites of Philox group t = (row r, group m) of
@@ -85,16 +85,18 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
         const uint64_t io = (uint64_t)(1 - colour) * g.plane + (uint64_t)r * g.half + (uint64_t)j;
         const int s_old = src[i];
         int n;
+        int fo = 0;   // table half: the -h entries for a site with eta_i = -1
         if (g.cpl == nullptr) {
             n = src[addr(g, x - 1, y, z)] + src[addr(g, x + 1, y, z)] + src[addr(g, x, y - 1, z)] +
                 src[addr(g, x, y + 1, z)];
             if (g.dims == 3) n += src[addr(g, x, y, z - 1)] + src[addr(g, x, y, z + 1)];
-        } else {   // Eq. 1 couplings: sum of eps_ij * s_j
+        } else {   // Eq. 1 disorder: sum of eps_ij * s_j, and the sign of B_i
             const uint32_t cb = g.cpl[i];
             auto sg = [&](int bit, int v) { return ((cb >> bit) & 1u) ? -v : v; };
             n = sg(0, src[addr(g, x - 1, y, z)]) + sg(1, src[addr(g, x + 1, y, z)]) +
                 sg(2, src[addr(g, x, y - 1, z)]) + sg(3, src[addr(g, x, y + 1, z)]);
             if (g.dims == 3) n += sg(4, src[addr(g, x, y, z - 1)]) + sg(5, src[addr(g, x, y, z + 1)]);
+            if ((cb >> 6) & 1u) fo = (2 * g.dsmax + 1) * g.nn;
         }
         const bool potts = g.model == LAT_POTTS;
         const int k_old = potts ? s_old : state_of_spin(g.two_S, s_old);
@@ -149,7 +151,7 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
         }
         int s_fin = s_old;
         if (allowed) {
-            const TabEntry e = stab[(s_new - s_old + g.dsmax) * g.nn + (n + g.nmax)];
+            const TabEntry e = stab[fo + (s_new - s_old + g.dsmax) * g.nn + (n + g.nmax)];
             if (e.always || u_acc < e.thr) {
                 s_fin = s_new;
                 if (s_new != s_old) flips |= 1u << q;
@@ -163,6 +165,8 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
             pt.mag += s_fin + so;
             pt.up += (s_fin > 0) + (so > 0);
             if (g.ref != nullptr) pt.acf += s_fin * g.ref[i] + so * g.ref[io];
+            if (g.cpl != nullptr)
+                pt.fld += (((g.cpl[i] >> 6) & 1u) ? -s_fin : s_fin) + (((g.cpl[io] >> 6) & 1u) ? -so : so);
         }
     }
     if (fl_c != nullptr) {
@@ -192,6 +196,10 @@ LAT_D void flush_counters(const Geom &g, unsigned long long sweep, const Part &p
     if (g.ref != nullptr) {
         v = block_sum_ll(pt.acf, red);
         if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), v);
+    }
+    if (g.cpl != nullptr) {
+        v = block_sum_ll(pt.fld, red);
+        if (threadIdx.x == 0) add_counter(fld_slot(g.ctrl, sweep), v);
     }
 }
 
@@ -258,12 +266,13 @@ __global__ void k_batch_advance(Ctrl *const *ctrls, int n, unsigned *counters, i
 
 // Counters of a configuration from their definitions (before the first
 // sweep and after set_state): bond = sum over sites and directions of
-// s_i s_{i+e_d}; mag; up; unflipped (from the persistence bytes).
+// eps s_i s_{i+e_d}; mag; up; unflipped (from the persistence bytes); the
+// field sum sum_i eta_i s_i.
 __global__ void __launch_bounds__(kThreads) k_measure(Geom g, const int8_t *sp, unsigned long long *out)
 {
     __shared__ long long red[kThreads / 32];
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    long long bond = 0, mag = 0, up = 0, unfl = 0;
+    long long bond = 0, mag = 0, up = 0, unfl = 0, fld = 0;
     if (i < g.N) {
         const int L = g.L;
         const int x = (int)(i % (uint64_t)L);
@@ -286,6 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_measure(Geom g, const int8_t *sp, 
             bond = (long long)s * nf;
             mag = s;
             up = s > 0;
+            fld = ((cb >> 6) & 1u) ? -s : s;
         }
         if (g.flags != nullptr) {
             const int c = (x + y + z) & 1;
@@ -304,6 +314,8 @@ __global__ void __launch_bounds__(kThreads) k_measure(Geom g, const int8_t *sp, 
     if (threadIdx.x == 0) add_counter(out + 2, v);
     v = block_sum_ll(unfl, red);
     if (threadIdx.x == 0) add_counter(out + 3, v);
+    v = block_sum_ll(fld, red);
+    if (threadIdx.x == 0) add_counter(out + 4, v);
 }
 
 __global__ void k_to_linear(Geom g, const int8_t *planar, int8_t *linear)
@@ -347,13 +359,15 @@ __global__ void __launch_bounds__(kThreads) k_count_bad(Geom g, const int8_t *s,
 __global__ void k_advance(Ctrl *ctrl, unsigned long long k) { ctrl->sweep += k; }
 
 __global__ void k_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
-                           unsigned long long base, unsigned long long cap, unsigned long long *acf)
+                           unsigned long long base, unsigned long long cap, unsigned long long *acf,
+                           unsigned long long *fld)
 {
     ctrl->sweep = sweep;
     ctrl->series = series;
     ctrl->series_base = base;
     ctrl->series_cap = cap;
     ctrl->acf = acf;
+    ctrl->fld = fld;
 }
 
 unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
@@ -379,15 +393,17 @@ cudaError_t launch_half_sweep_generic(const Geom &g, int colour, int off, cudaSt
 }
 
 cudaError_t launch_batch_generic(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                                 int colour, int off, int grid, cudaStream_t st)
+                                 int colour, int off, int grid, int tab_max, cudaStream_t st)
 {
-    // dynamic shared memory for the largest table (two_S <= 8, 3D): 2465 entries
-    const size_t smem = 2465 * sizeof(TabEntry);
+    // The largest table (two_S <= 8, 3D) has 2465 entries, twice that with
+    // per-site field signs.
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_batch_half_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_batch_half_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * 2465 * sizeof(TabEntry)));
         attr = true;
     }
+    const size_t smem = (size_t)tab_max * sizeof(TabEntry);
     k_batch_half_sweep<<<grid, kThreads, smem, st>>>(geoms, items, n_items, next_item, colour, off);
     return cudaGetLastError();
 }
@@ -410,9 +426,9 @@ cudaError_t launch_batch_advance(Ctrl *const *ctrls, int n, unsigned *counters, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out4, cudaStream_t st)
+cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out5, cudaStream_t st)
 {
-    k_measure<<<blocks_for(g.N), kThreads, 0, st>>>(g, spins, out4);
+    k_measure<<<blocks_for(g.N), kThreads, 0, st>>>(g, spins, out5);
     return cudaGetLastError();
 }
 
@@ -443,9 +459,9 @@ cudaError_t launch_advance(Ctrl *ctrl, unsigned long long k, cudaStream_t st)
 
 cudaError_t launch_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
                             unsigned long long base, unsigned long long cap, unsigned long long *acf,
-                            cudaStream_t st)
+                            unsigned long long *fld, cudaStream_t st)
 {
-    k_set_ctrl<<<1, 1, 0, st>>>(ctrl, sweep, series, base, cap, acf);
+    k_set_ctrl<<<1, 1, 0, st>>>(ctrl, sweep, series, base, cap, acf, fld);
     return cudaGetLastError();
 }
 

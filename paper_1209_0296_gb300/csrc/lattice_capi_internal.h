@@ -54,7 +54,8 @@ struct lattice {
     uint32_t *bits[2] = {nullptr, nullptr};
     lat::TabEntry *tab = nullptr;
     lat::Ctrl *ctrl = nullptr;
-    unsigned long long *series = nullptr;  // [series_cap][4] counters, then [series_cap] overlaps
+    // [series_cap][4] counters, then [series_cap] overlaps, then [series_cap] field sums
+    unsigned long long *series = nullptr;
     unsigned long long series_cap = 0;   // sweeps the buffer can hold (from series_first)
     int8_t *ref = nullptr;               // reference state s(0), int8 planar layout
     uint32_t *ref_bits = nullptr;        // reference state s(0), bit-packed layout
@@ -62,7 +63,12 @@ struct lattice {
     int dynamics = 0;                    // LAT_DYNAMICS_*
     int rs_tile = 0, rs_lambda = 0;      // random-site sub-lattice side and picks per round
     int8_t *rs_scratch = nullptr;        // random-site: output of the first launch of a sweep
-    uint8_t *cpl = nullptr;              // per-site coupling-sign bytes (see Geom::cpl)
+    uint8_t *cpl = nullptr;              // per-site disorder bytes (see Geom::cpl); null when all zero
+    std::vector<uint8_t> dis_host;       // host copy of the disorder bytes (empty: none set)
+    bool has_bonds = false;              // coupling signs set
+    bool has_fields = false;             // field signs set (the table then has a -h half)
+    int64_t disorder_from = 0;           // sweeps done when the couplings or field signs last changed
+    int64_t fields_from = 0;             // sweeps done when the field signs were last set
     unsigned long long *scratch4 = nullptr;
     std::vector<lat::TabEntry> host_tab;
     int64_t sweeps = 0;        // sweeps done (global index of the next sweep)

@@ -141,6 +141,7 @@ struct Ctrl {
     unsigned int error;              // device error word (0 = none)
     unsigned int pad;
     unsigned long long *acf;         // [series_cap] sum_i s_i(t) s_i(ref), same indexing
+    unsigned long long *fld;         // [series_cap] sum_i eta_i s_i (per-site field signs), same indexing
 };
 
 #if defined(__CUDACC__)
@@ -156,6 +157,13 @@ LAT_D unsigned long long *series_slot(const Ctrl *c, unsigned long long sweep)
 LAT_D unsigned long long *acf_slot(const Ctrl *c, unsigned long long sweep)
 {
     return c->acf + (sweep - c->series_base);
+}
+
+// Field-sum slot of global sweep `sweep`: sum_i eta_i s_i over the state
+// after that sweep (written by the kernels that read per-site disorder).
+LAT_D unsigned long long *fld_slot(const Ctrl *c, unsigned long long sweep)
+{
+    return c->fld + (sweep - c->series_base);
 }
 #endif
 
@@ -192,9 +200,11 @@ struct Geom {
     // (ref_bits); null when no reference is set.
     const int8_t *ref;
     const uint32_t *ref_bits;
-    // Per-bond coupling signs (Eq. 1 with J_ij = J * eps_ij): one byte per
-    // site in the int8 planar layout, bit set = that bond is negative; bits
-    // 0..5 = the bonds to x-1, x+1, y-1, y+1, z-1, z+1.  Null: uniform J.
+    // Per-site disorder of Eq. 1 (J_ij = J * eps_ij, B_i = h * eta_i): one
+    // byte per site in the int8 planar layout.  Bits 0..5 = the bonds to
+    // x-1, x+1, y-1, y+1, z-1, z+1, set = that eps_ij is -1; bit 6 set =
+    // eta_i is -1, whose acceptance entries sit in a second table half
+    // (for -h) right after the first.  Null: uniform J and h.
     const uint8_t *cpl;
     Ctrl *ctrl;
     // Compact acceptance table for 2D spin-1/2 (tiled and bit-packed
@@ -281,11 +291,12 @@ LAT_D void add_counter(unsigned long long *slot, long long v)
 namespace lat {
 cudaError_t launch_init(const Geom &g, int init, double c, cudaStream_t st);
 cudaError_t launch_half_sweep_generic(const Geom &g, int colour, int off, cudaStream_t st);
-cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out4, cudaStream_t st);
+// out[0..4] += bond, mag, up, unflipped, field sum (sum_i eta_i s_i)
+cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out5, cudaStream_t st);
 cudaError_t launch_advance(Ctrl *ctrl, unsigned long long k, cudaStream_t st);
 cudaError_t launch_set_ctrl(Ctrl *ctrl, unsigned long long sweep, unsigned long long *series,
                             unsigned long long base, unsigned long long cap, unsigned long long *acf,
-                            cudaStream_t st);
+                            unsigned long long *fld, cudaStream_t st);
 bool tiled_supported(const Geom &g);
 cudaError_t launch_sweep_tiled(const Geom &g, int tile_w, int tile_h, int off, cudaStream_t st);
 cudaError_t launch_pack_bits(const Geom &g, const int8_t *planar, uint32_t *bits, cudaStream_t st);
@@ -326,8 +337,9 @@ int tiles_of(const Geom &g, int tile_h);
 int batch_tiled_grid(bool ne);
 cudaError_t launch_batch_tiled(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
                                int tile_h, int off, int grid, bool ne, cudaStream_t st);
+// tab_max: the largest tab_n among the lattices of the items
 cudaError_t launch_batch_generic(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                                 int colour, int off, int grid, cudaStream_t st);
+                                 int colour, int off, int grid, int tab_max, cudaStream_t st);
 int batch_generic_grid();
 cudaError_t launch_batch_advance(Ctrl *const *ctrls, int n, unsigned *counters, int n_counters,
                                  unsigned long long k, cudaStream_t st);
