@@ -597,6 +597,17 @@ def other_configs(dev):
                                    "kernel": names.get(g.get_kernel()["kernel"], "?")}
     g.close()
 
+    # the random-field Ising model (Eq. 1 with B_i = h * eta_i, eta_i = +-1
+    # at random), L = 4096, h = J, T = 2
+    g = lt.Lattice(2, 4096, 1, lt.ISING, 1.0, 1.0, 2.0, seed=7, init=lt.INIT_RANDOM, stream=stream)
+    g.set_fields(np.where(np.random.default_rng(6).random(4096 * 4096) < 0.5, -1, 1).astype(np.int8))
+    n = 20
+    t = _timed_sweeps(torch, stream, [g], n, flush)
+    out["random_field_ising_L4096"] = {"updates_per_ns": 4096 * 4096 * n / t / 1e9, "sweeps": n,
+                                       "alg_GBps": 3.0 * 4096 * 4096 * n / t / 1e9,
+                                       "kernel": names.get(g.get_kernel()["kernel"], "?")}
+    g.close()
+
     # the q = 3 Potts model at its critical point, L = 4096
     import math
     g = lt.Lattice(2, 4096, 2, lt.POTTS, 1.0, 0.0, 1.0 / math.log(1.0 + math.sqrt(3.0)), seed=7,

@@ -196,10 +196,10 @@ int lattice_set_couplings(lattice_t *lat, const int8_t *bond_signs);
  * or clearing one keeps the other.  From then on every sweep also records
  *   field = sum_i eta_i s_i       (int64, lattice_field_series)
  * and lattice_observables reports E/N = (-J*bond - h*field)/N.  Same
- * restrictions as lattice_set_couplings; such lattices sweep with the
- * generic kernel only (in a batch too).  The acceptance table gains a
- * second half for -h.  Waits for the stream; LAT_EINVAL for values other
- * than +-1. */
+ * restrictions as lattice_set_couplings; such lattices sweep with the 2D
+ * wide kernel (2D spin-1/2, L % 32 == 0) or the generic one, and in a
+ * batch with the generic one.  The acceptance table gains a second half
+ * for -h.  Waits for the stream; LAT_EINVAL for values other than +-1. */
 int lattice_set_fields(lattice_t *lat, const int8_t *field_signs);
 
 /* Copy the recorded field sums of sweeps [first, first+count) to field[]

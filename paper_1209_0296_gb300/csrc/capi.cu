@@ -226,10 +226,11 @@ static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supporte
 int choose_kernel(const lattice *lt)
 {
     if (lt->P.layout == LAT_BITPACKED) return LAT_KERNEL_AUTO;  // bit-packed path
-    if (lt->has_fields) return LAT_KERNEL_GENERIC;   // per-site field signs: the generic kernel only
-    if (lt->geom.cpl != nullptr)   // per-bond couplings: the 2D wide kernel or the generic one
-        return (lt->kernel != LAT_KERNEL_GENERIC && wide_supported(lt->geom)) ? LAT_KERNEL_WIDE
-                                                                             : LAT_KERNEL_GENERIC;
+    if (lt->geom.cpl != nullptr)   // per-site disorder: the 2D wide kernel or the generic one
+        return (lt->kernel != LAT_KERNEL_GENERIC && wide_supported(lt->geom) &&
+                (!lt->has_fields || lt->fields_wide_ok))
+                   ? LAT_KERNEL_WIDE
+                   : LAT_KERNEL_GENERIC;
     if (lt->kernel == LAT_KERNEL_GENERIC) return LAT_KERNEL_GENERIC;
     if (lt->kernel == LAT_KERNEL_TILED && tiled_supported(lt->geom)) return LAT_KERNEL_TILED;
     if (lt->kernel == LAT_KERNEL_WIDE && any_wide(lt->geom)) return LAT_KERNEL_WIDE;
@@ -275,7 +276,7 @@ int enqueue_sweeps(lattice *lt, int64_t k, cudaStream_t st)
         } else if (kern == LAT_KERNEL_TILED) {
             e = launch_sweep_tiled(lt->geom, lt->tile_w, lt->tile_h, off, st);
         } else if (kern == LAT_KERNEL_WIDE) {
-            e = wide_supported(lt->geom) ? launch_sweep_wide(lt->geom, off, st)
+            e = wide_supported(lt->geom) ? launch_sweep_wide(lt->geom, lt->has_fields, off, st)
                                          : launch_sweep_wide3(lt->geom, off, st);
         } else {
             e = launch_half_sweep_generic(lt->geom, 0, off, st);
@@ -750,11 +751,19 @@ static int apply_disorder(lattice *lt)
     std::vector<TabEntry> tab;
     int dsmax, nmax, nn;
     build_table(lt->P, tab, dsmax, nmax, nn);
+    lt->fields_wide_ok = false;
     if (lt->has_fields) {
         Params Pm = lt->P;
         Pm.h = -Pm.h;
         std::vector<TabEntry> neg;
         build_table(Pm, neg, dsmax, nmax, nn);
+        // the 2D wide kernel takes the -h entries in t' = thr - 1 form: no
+        // never-accept entry among the reachable ones
+        Geom probe = lt->geom;
+        compact_table(probe, neg.data());
+        lt->fields_wide_ok = true;
+        for (int k = 0; k < 16; ++k)
+            if ((k & 7) <= 4 && !((probe.always16 >> k) & 1u) && probe.thr16[k] == 0u) lt->fields_wide_ok = false;
         tab.insert(tab.end(), neg.begin(), neg.end());
     }
     if ((int)tab.size() != lt->geom.tab_n) {
@@ -1107,7 +1116,9 @@ int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sw
     if (kernel < LAT_KERNEL_AUTO || kernel > LAT_KERNEL_RESIDENT) return LAT_EINVAL;
     if (tile_w < 0 || tile_h < 0 || sweeps_per_graph < 0) return LAT_EINVAL;
     if (kernel == LAT_KERNEL_TILED && !tiled_supported(lt->geom)) return LAT_ENOTSUP;
-    if (kernel == LAT_KERNEL_WIDE && (!any_wide(lt->geom) || lt->has_fields)) return LAT_ENOTSUP;
+    if (kernel == LAT_KERNEL_WIDE &&
+        (!any_wide(lt->geom) || (lt->has_fields && !(wide_supported(lt->geom) && lt->fields_wide_ok))))
+        return LAT_ENOTSUP;
     if (kernel == LAT_KERNEL_RESIDENT && !resident_supported(lt->geom)) return LAT_ENOTSUP;
     if (!tile_shape_ok(tile_w, tile_h)) return LAT_EINVAL;
     lt->kernel = kernel;

@@ -38,7 +38,7 @@ LAT_D int byte_sum(uint32_t x)
 }
 
 struct Counts {
-    int bond = 0, mag = 0, up = 0, unfl = 0, acf = 0;
+    int bond = 0, mag = 0, up = 0, unfl = 0, acf = 0, fld = 0;
 };
 
 // W consecutive 4-byte words (4W same-colour sites) from p.
@@ -73,8 +73,10 @@ LAT_D void store_words(int8_t *p, const uint32_t (&v)[W])
 // row); the resident kernel uses smaller W on small lattices, for more
 // threads with shorter dependency chains.  kInPlace: both buffers are the
 // same array (the resident kernel), so colour 0 does not copy the colour-1
-// sites.
-template <bool kNE, bool kInPlace = false, int W = 4, bool kPre = false, bool kCpl = false>
+// sites.  kCpl: per-site disorder bytes (Eq. 1 couplings); kFld (with
+// kCpl): also per-site field signs, whose -h entries are table entries
+// 16..31, and the field sum sum_i eta_i s_i.
+template <bool kNE, bool kInPlace = false, int W = 4, bool kPre = false, bool kCpl = false, bool kFld = false>
 LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsigned long long sweep,
                       const PhiloxPre &pp, int y, int k, Counts &cnt, const U4 *upre = nullptr)
 {
@@ -109,10 +111,10 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             R[w] = __funnelshift_r(O[w], w == W - 1 ? adj : O[w + 1], 8);
         }
     }
+    uint32_t C[W];   // disorder bytes of the colour-c sites (kCpl)
     if constexpr (kCpl) {
         // Eq. 1 couplings: a negative bond enters the energy as a flipped
         // neighbour, so XOR 0xFE (+1 <-> -1) into that neighbour's byte
-        uint32_t C[W];
         load_words<W>(reinterpret_cast<const int8_t *>(g.cpl) + (uint64_t)colour * g.plane + (uint64_t)y * half +
                           4 * W * k, C);
 #pragma unroll
@@ -134,8 +136,8 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         const uint32_t b1 = c1 ^ (s1 & R[w]);
         const uint32_t b2 = c1 & s1 & R[w];
         // byte offset into the 16-entry table (index sd<<3 | nd, 4 bytes each)
-        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
-                             (S[w] & 0x20202020u);
+        uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (S[w] & 0x20202020u);
+        if constexpr (kFld) idx |= C[w] & 0x40404040u;   // eta_i = -1: the -h entries 16..31
         t[w][0] = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
         t[w][1] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
         t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
@@ -226,6 +228,15 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             for (int w = 0; w < W; ++w) dr += ((Sn[w] ^ R1[w]) & M1) + ((O[w] ^ R0[w]) & M1);
             cnt.acf += 8 * W - byte_sum(dr);
         }
+        if constexpr (kFld) {
+            // field sum over both planes' 8W sites: eta_i s_i is down when
+            // exactly one of (s_i down: bit 1, eta_i = -1: bit 6) holds
+            uint32_t C0[W], ed = 0;
+            load_words<W>(reinterpret_cast<const int8_t *>(g.cpl) + (uint64_t)y * half + 4 * W * k, C0);
+#pragma unroll
+            for (int w = 0; w < W; ++w) ed += ((Sn[w] ^ (C[w] >> 5)) & M1) + ((O[w] ^ (C0[w] >> 5)) & M1);
+            cnt.fld += 8 * W - byte_sum(ed);
+        }
     }
 }
 
@@ -271,12 +282,41 @@ LAT_D void flush(const SweepView &g, unsigned long long sweep, const Counts &c, 
     flush_slot(series_slot(g.ctrl, sweep), g.ref ? acf_slot(g.ctrl, sweep) : nullptr, c, ne, red);
 }
 
-template <bool kNE, bool kCpl>
+// Add one int per thread, summed over the block, to *dst (all threads call).
+LAT_D void flush_one(unsigned long long *dst, int v, int (*red)[5])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) red[warp][0] = r;
+    __syncthreads();
+    if (warp == 0) {
+        const int t = __reduce_add_sync(0xffffffffu, lane < (int)(blockDim.x >> 5) ? red[lane][0] : 0);
+        if (lane == 0) add_counter(dst, (long long)t);
+    }
+    __syncthreads();
+}
+
+// kFld: 32-entry table, entries 16..31 built from the -h half of the full
+// table (t' = thr - 1 form, all ones = always), index sd << 3 | nd as for
+// entries 0..15.
+template <bool kNE, bool kCpl, bool kFld>
 __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
 {
-    __shared__ uint32_t sthr[16];
+    __shared__ uint32_t sthr[kFld ? 32 : 16];
     __shared__ int red[kThreads / 32][5];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
+    if constexpr (kFld) {
+        if (threadIdx.x >= 16 && threadIdx.x < 32) {
+            const int k = threadIdx.x - 16, nd = k & 7;
+            uint32_t t = 0u;
+            if (nd <= 4) {
+                const int ds = (k >> 3) ? 2 : -2, n = 4 - 2 * nd;
+                const TabEntry e = g.tab[(2 * g.dsmax + 1) * g.nn + (ds + g.dsmax) * g.nn + (n + g.nmax)];
+                t = e.always ? 0xFFFFFFFFu : e.thr - 1u;
+            }
+            sthr[threadIdx.x] = t;
+        }
+    }
     __syncthreads();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     PhiloxPre pp;
@@ -289,8 +329,11 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     const uint64_t total = (uint64_t)g.L * cpr;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
          t += (uint64_t)gridDim.x * blockDim.x)
-        wide_chunk<kNE, false, 4, false, kCpl>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
-    if (colour == 1) flush(v, sweep, cnt, kNE, red);
+        wide_chunk<kNE, false, 4, false, kCpl, kFld>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+    if (colour == 1) {
+        flush(v, sweep, cnt, kNE, red);
+        if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);
+    }
 }
 
 // Batched form: a persistent grid takes (lattice, item) pairs from an
@@ -484,15 +527,17 @@ bool wide_supported(const Geom &g)
 
 int wide_chunks(const Geom &g) { return (int)(((uint64_t)g.L * (g.half >> 4) + kThreads - 1) / kThreads); }
 
-cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st)
+cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st)
 {
     const Geom k = tiled_geom(g);  // compact table in t' = thr - 1 form
-    // instantiations: Ising, North-East, Ising with per-bond couplings
-    const int m = g.model == LAT_NE ? 1 : (g.cpl != nullptr ? 2 : 0);
+    // instantiations: Ising, North-East, Ising with per-bond couplings,
+    // Ising with couplings and per-site field signs
+    const int m = g.model == LAT_NE ? 1 : (g.cpl != nullptr ? (fields ? 3 : 2) : 0);
     using K = void (*)(Geom, int, int);
-    const K kern[3] = {k_wide_half<false, false>, k_wide_half<true, false>, k_wide_half<false, true>};
+    const K kern[4] = {k_wide_half<false, false, false>, k_wide_half<true, false, false>,
+                       k_wide_half<false, true, false>, k_wide_half<false, true, true>};
     // one wave: SMs x resident CTAs per SM (queried once per instantiation)
-    static int resident[3] = {0, 0, 0};
+    static int resident[4] = {0, 0, 0, 0};
     if (resident[m] == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);

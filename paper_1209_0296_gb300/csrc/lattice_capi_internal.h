@@ -67,6 +67,7 @@ struct lattice {
     std::vector<uint8_t> dis_host;       // host copy of the disorder bytes (empty: none set)
     bool has_bonds = false;              // coupling signs set
     bool has_fields = false;             // field signs set (the table then has a -h half)
+    bool fields_wide_ok = false;         // the -h half suits the 2D wide kernel
     int64_t disorder_from = 0;           // sweeps done when the couplings or field signs last changed
     int64_t fields_from = 0;             // sweeps done when the field signs were last set
     unsigned long long *scratch4 = nullptr;

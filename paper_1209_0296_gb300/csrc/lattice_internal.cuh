@@ -309,7 +309,9 @@ cudaError_t launch_to_planar(const Geom &g, const int8_t *linear, int8_t *planar
 cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st);
 bool bitpacked_supported(const Geom &g);
 bool wide_supported(const Geom &g);
-cudaError_t launch_sweep_wide(const Geom &g, int off, cudaStream_t st);
+// fields: per-site field signs are set (g.cpl bit 6; the -h table half
+// follows the first in g.tab, with no never-accept entry)
+cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st);
 // The paper's random-sub-lattice, random-site sweep (kernels_rsite.cu).
 bool rsite_params_ok(const Geom &g, int b, int lambda);
 cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda, int off, cudaStream_t st);

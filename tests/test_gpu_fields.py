@@ -1,8 +1,8 @@
 """Per-site random fields (Eq. 1, B_i = h * eta_i with eta_i = +-1: the
 random-field Ising model) on the GPU, alone and together with per-bond
 couplings: lattices, counters and the field sums sum_i eta_i s_i must equal
-the oracle's bit for bit on the generic kernel (solo and batched) and
-through observables; the field signs survive changes of the couplings and
+the oracle's bit for bit on the 2D wide kernel, the generic kernel (solo
+and batched) and through observables; the field signs survive changes of the couplings and
 the other way round; unsupported combinations are refused."""
 import numpy as np
 import pytest
@@ -53,9 +53,30 @@ def fld_pair(dims, L, two_S, J, h, T, seed, n, bonds=False, kernel=lt.KERNEL_AUT
 
 @pytest.mark.parametrize("L", [32, 64, 96, 130])
 @pytest.mark.parametrize("bonds", [False, True])
-def test_2d_spin_half(L, bonds):
-    k = fld_pair(2, L, 1, 1.0, 0.8, 1.6, 10 + L, 25, bonds=bonds, chunks=[3, 22])
-    assert k == lt.KERNEL_GENERIC
+@pytest.mark.parametrize("kernel", [lt.KERNEL_AUTO, lt.KERNEL_GENERIC])
+def test_2d_spin_half(L, bonds, kernel):
+    k = fld_pair(2, L, 1, 1.0, 0.8, 1.6, 10 + L, 25, bonds=bonds, kernel=kernel, chunks=[3, 22])
+    wide = kernel == lt.KERNEL_AUTO and L % 32 == 0
+    assert k == (lt.KERNEL_WIDE if wide else lt.KERNEL_GENERIC)
+
+
+def test_wide_with_reference_and_graphs():
+    # a long run (graph replays) with the autocorrelation recorded as well
+    L, N = 128, 128 * 128
+    eta = _signs(N, 9)
+    o = oracle.Lattice(2, L, 1, oracle.ISING, 1.0, 1.1, 2.0, seed=9, init=oracle.INIT_RANDOM)
+    g = lt.Lattice(2, L, 1, lt.ISING, 1.0, 1.1, 2.0, seed=9, init=lt.INIT_RANDOM)
+    o.set_fields(eta)
+    g.set_fields(eta)
+    ref = o.spins.copy()
+    g.set_reference()
+    ser_o = o.sweep(70)
+    g.sweep(70)
+    assert g.get_kernel()["kernel"] == lt.KERNEL_WIDE
+    assert np.array_equal(g.get_spins(), o.spins)
+    assert np.array_equal(g.field_series(0, 70), ser_o["field"])
+    assert g.autocorrelation(69, 1)[0][0] == int(np.dot(o.spins.astype(np.int64), ref))
+    g.close()
 
 
 @pytest.mark.parametrize("dims,L,two_S", [(2, 50, 1), (3, 16, 1), (3, 10, 1), (2, 32, 2), (3, 8, 2), (2, 12, 3),
@@ -169,6 +190,11 @@ def test_refusals():
     with pytest.raises(lt.LatticeError):
         po.set_fields(eta)
     po.close()
+    w3 = lt.Lattice(3, 16, 1, lt.ISING, 1.0, 0.5, 4.0, seed=1, init=lt.INIT_RANDOM)
+    w3.set_fields(_signs(16 ** 3, 2))
+    with pytest.raises(lt.LatticeError):
+        w3.set_kernel(lt.KERNEL_WIDE)   # the 3D wide kernel reads no disorder
+    w3.close()
     bp = lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.0, seed=1, init=lt.INIT_RANDOM, layout=lt.BITPACKED)
     with pytest.raises(lt.LatticeError):
         bp.set_fields(eta)
@@ -179,9 +205,10 @@ def test_refusals():
     with pytest.raises(lt.LatticeError):
         g.set_fields(bad)
     g.set_fields(eta)
-    for kern in (lt.KERNEL_TILED, lt.KERNEL_RESIDENT, lt.KERNEL_WIDE):
+    for kern in (lt.KERNEL_TILED, lt.KERNEL_RESIDENT):
         with pytest.raises(lt.LatticeError):
             g.set_kernel(kern)
+    g.set_kernel(lt.KERNEL_WIDE)
     with pytest.raises(lt.LatticeError):
         g.set_dynamics(lt.DYNAMICS_RANDOM_SITE, 16, 16)
     g.close()
