@@ -92,6 +92,8 @@ def _load():
             lib.oracle_measure_potts.restype = None
             lib.oracle_overlap.argtypes = [ctypes.c_int64, i8p, i8p]
             lib.oracle_overlap.restype = ctypes.c_int64
+            lib.oracle_overlap_potts.argtypes = [ctypes.c_int64, i8p, i8p]
+            lib.oracle_overlap_potts.restype = ctypes.c_int64
             lib.oracle_metropolis_threshold.argtypes = [ctypes.c_double, ctypes.c_double,
                                                         ctypes.POINTER(ctypes.c_uint32)]
             lib.oracle_metropolis_threshold.restype = ctypes.c_int
@@ -183,7 +185,10 @@ class Lattice:
         self.ref = self.spins.copy()
 
     def overlap(self):
-        """sum_i s_i * s_i(0) of the current configuration (needs a reference)."""
+        """sum_i s_i * s_i(0) of the current configuration (needs a reference);
+        for the Potts model the number of sites with s_i = s_i(0)."""
+        if self.model == POTTS:
+            return int(_load().oracle_overlap_potts(self.N, self.spins, self.ref))
         return int(_load().oracle_overlap(self.N, self.spins, self.ref))
 
     def sweep(self, n: int):

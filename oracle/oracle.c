@@ -625,5 +625,17 @@ int64_t oracle_overlap(int64_t n, const int8_t *s, const int8_t *ref)
     return c;
 }
 
+/* Potts overlap with a reference configuration: the number of sites whose  */
+/* label equals the reference label, sum_i delta(s_i, ref_i).  Eq. 4 is     */
+/* written for spins; for labels the product s_i(t) s_i(0) has no meaning,   */
+/* and delta(s_i(t), s_i(0)) is the Potts counterpart (for q = 2 with        */
+/* sigma = 1 - 2s it is (N + sum_i sigma_i(t) sigma_i(0)) / 2).              */
+int64_t oracle_overlap_potts(int64_t n, const int8_t *s, const int8_t *ref)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) c += (s[i] == ref[i]) ? 1 : 0;
+    return c;
+}
+
 /* Number of distinct 32-bit words this oracle needs from Philox per call. */
 int oracle_sites_per_draw(int two_S) { return two_S == 1 ? 4 : 2; }

@@ -108,3 +108,38 @@ def test_baxter_critical_energy():
     ser = p.sweep(3000)
     u = (-J * ser["bond"] / 64 ** 2).mean()
     assert abs(u - (-J * (1 + 1 / math.sqrt(q)))) < 0.03, u
+
+
+# The Potts overlap with a reference state is the number of sites whose label
+# equals the reference label (the counterpart of Eq. 4's sum of s_i(t) s_i(0)).
+
+@pytest.mark.parametrize("dims,L", [(2, 10), (3, 4)])
+def test_overlap_q2_maps_to_the_ising_overlap(dims, L):
+    # sigma = 1 - 2s: sum sigma sigma' = 2 * #equal - N, along the mapped chains
+    J, h, T = 1.3, 0.2, 1.1
+    p = _potts(dims, L, 2, J, h, T, 23)
+    i = oracle.Lattice(dims, L, 1, oracle.ISING, J / 2, h / 2, T, seed=23, init=oracle.INIT_RANDOM)
+    p.set_reference()
+    i.set_reference()
+    N = L ** dims
+    sp, si = p.sweep(12), i.sweep(12)
+    assert np.array_equal(2 * sp["overlap"] - N, si["overlap"])
+
+
+@pytest.mark.parametrize("q", [3, 5])
+def test_overlap_zero_temperature_moves(q):
+    # J = h = 0: every site changes each sweep, so after one sweep no site
+    # keeps its reference label; after two a site is back with chance
+    # 1/(q-1) (the second move is uniform over the other q-1 labels)
+    L, N = 16, 256
+    p = _potts(2, L, q, 0.0, 0.0, 1.0, 5)
+    p.set_reference()
+    assert p.overlap() == N
+    back = []
+    for _ in range(300):
+        p.set_reference()
+        ser = p.sweep(2)
+        assert ser["overlap"][0] == 0
+        back.append(ser["overlap"][1])
+    m, dm = _mean_and_error(np.array(back, dtype=np.float64))
+    assert abs(m - N / (q - 1)) < 5 * dm, (m, dm)
