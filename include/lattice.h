@@ -169,7 +169,9 @@ int lattice_series(lattice_t *lat, int64_t first, int64_t count, int64_t *bond,
  * NULL) the sweeps done at that moment.  From then on every sweep also
  * records, in the same kernels as the other counters, the exact overlap
  *   overlap = sum_i s_i(t) s_i(0)      (int64)
- * of the state after that sweep.  A later call replaces the reference;
+ * of the state after that sweep.  For the Potts model the overlap is the
+ * number of sites whose label equals the reference label, and m = 1/sqrt(q)
+ * gives Phi = (overlap/N - 1/q) / (1 - 1/q).  A later call replaces the reference;
  * lattice_clear_reference frees it and stops the recording.  Neither
  * set_state nor set_spins changes the reference. */
 int lattice_set_reference(lattice_t *lat, int64_t *ref_sweep);

@@ -219,9 +219,10 @@ void compact_table(Geom &g, const TabEntry *host_tab)
     }
 }
 
-// LAT_KERNEL_WIDE covers two kernels: the 2D spin-1/2 one (kernels_wide.cu)
-// and the 3D / spin-S one (kernels_wide3.cu).
-static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supported(g); }
+// LAT_KERNEL_WIDE covers three kernels: the 2D spin-1/2 one
+// (kernels_wide.cu), the 3D / spin-S Ising one (kernels_wide3.cu) and the
+// Potts one (kernels_potts.cu).
+static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supported(g) || potts_supported(g); }
 
 int choose_kernel(const lattice *lt)
 {
@@ -276,8 +277,9 @@ int enqueue_sweeps(lattice *lt, int64_t k, cudaStream_t st)
         } else if (kern == LAT_KERNEL_TILED) {
             e = launch_sweep_tiled(lt->geom, lt->tile_w, lt->tile_h, off, st);
         } else if (kern == LAT_KERNEL_WIDE) {
-            e = wide_supported(lt->geom) ? launch_sweep_wide(lt->geom, lt->has_fields, off, st)
-                                         : launch_sweep_wide3(lt->geom, off, st);
+            e = wide_supported(lt->geom)    ? launch_sweep_wide(lt->geom, lt->has_fields, off, st)
+                : potts_supported(lt->geom) ? launch_sweep_potts(lt->geom, off, st)
+                                            : launch_sweep_wide3(lt->geom, off, st);
         } else {
             e = launch_half_sweep_generic(lt->geom, 0, off, st);
             if (e == cudaSuccess) e = launch_half_sweep_generic(lt->geom, 1, off, st);

@@ -141,6 +141,8 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
                 const int so = dst[io];
                 pt.mag += (s_fin == 0) + (so == 0);
                 pt.up += (s_fin != 0) + (so != 0);
+                // overlap of labels: sites in their reference state
+                if (g.ref != nullptr) pt.acf += (s_fin == g.ref[i]) + (so == g.ref[io]);
             }
             continue;
         }

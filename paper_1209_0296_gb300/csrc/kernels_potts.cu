@@ -1,0 +1,246 @@
+// kernels_potts.cu -- two launches per sweep (one per colour, the kernel
+// boundary being the device-wide barrier of §III.A steps 6-7) for the
+// q-state Potts model (§III.C: the method carries over to Potts spins),
+// int8 labels 0..q-1 in the checkerboard-planar layout, 2D or 3D, L a
+// multiple of 16.
+//
+// A thread owns 8 consecutive same-colour sites of one plane row (one
+// 8-byte load per row).  The equal-neighbour counts of the old and of the
+// proposed labels come from byte-wise equality masks of whole neighbour
+// words, and the table index (df + 1) * nn + (dn + nmax) is formed for the
+// 8 sites at once with byte-wise adds (every byte stays below 64, so no
+// carry crosses a byte).  Per site remain the proposal, one table lookup
+// and the acceptance compare.  Draws come from the same Philox groups as
+// the generic kernel (4 sites per call for q = 2, 2 for q >= 3).  Colour 0
+// reads s[sweep & 1] and writes the new colour-0 labels and a copy of the
+// colour-1 labels into s[(sweep+1) & 1]; colour 1 then updates that buffer
+// in place and reduces the sweep's counters (equal-neighbour bonds, sites
+// in state 0, the others, and the overlap with a reference state).
+#include <algorithm>
+
+#include "lattice_internal.cuh"
+
+namespace lat {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxTab = 39;   // 3 * (2 * nmax + 1) with nmax = 6 (3D)
+
+// 0x01 in every byte where a and b hold the same label, else 0x00 (labels
+// below 128: the XOR of two bytes plus 0x7F sets bit 7 exactly when they
+// differ, without a carry into the next byte).
+LAT_D uint32_t eq_bytes(uint32_t a, uint32_t b)
+{
+    return (~((a ^ b) + 0x7F7F7F7Fu) >> 7) & 0x01010101u;
+}
+
+LAT_D int byte_sum(uint32_t x)
+{
+    const uint32_t s = (x & 0x00FF00FFu) + ((x >> 8) & 0x00FF00FFu);
+    return (int)((s & 0xFFFFu) + (s >> 16));
+}
+
+// 0xFF in byte i for bit i of a 4-bit mask.
+LAT_D uint32_t spread4(uint32_t m) { return ((m * 0x00204081u) & 0x01010101u) * 0xFFu; }
+
+struct AccP {
+    int bond = 0, zero = 0, other = 0, acf = 0;
+};
+
+// The fields of a Geom that this kernel reads, small enough for registers.
+struct ViewP {
+    int L, two_S, nn, nmax;
+    uint32_t G, half;
+    uint64_t plane;
+    int8_t *s0, *s1;
+    const int8_t *ref;
+};
+
+LAT_D ViewP viewp(const Geom &g)
+{
+    ViewP v;
+    v.L = g.L;
+    v.two_S = g.two_S;
+    v.nn = g.nn;
+    v.nmax = g.nmax;
+    v.G = g.G;
+    v.half = g.half;
+    v.plane = g.plane;
+    v.s0 = g.s[0];
+    v.s1 = g.s[1];
+    v.ref = g.ref;
+    return v;
+}
+
+// Colour `colour` of the 8-site chunk k of plane row r = y + L*z.  SH:
+// log2(sites per Philox call), 2 for q = 2 and 1 otherwise; D: dimension.
+template <int SH, int D>
+LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigned long long sweep,
+                       const PhiloxPre &pp, uint32_t r, uint32_t k, AccP &acc)
+{
+    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
+    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
+    if (colour == 1) src = dst;
+    const int L = g.L;
+    const uint32_t half = g.half;
+    const int oc = 1 - colour;
+    const int y = (int)(r % (uint32_t)L), z = (int)(r / (uint32_t)L);
+    auto row = [&](int c, uint32_t rr) { return src + (uint64_t)c * g.plane + (uint64_t)rr * half; };
+    auto ld = [&](int c, uint32_t rr) { return *reinterpret_cast<const uint2 *>(row(c, rr) + 8 * k); };
+    const uint2 S = ld(colour, r);
+    const uint2 O = ld(oc, r);
+    // neighbours: west, east, north, south (and z-1, z+1 in 3D)
+    uint2 Nb[2 * D];
+    Nb[2] = ld(oc, (uint32_t)((y == 0 ? L - 1 : y - 1) + L * z));
+    Nb[3] = ld(oc, (uint32_t)((y == L - 1 ? 0 : y + 1) + L * z));
+    if constexpr (D == 3) {
+        Nb[4] = ld(oc, (uint32_t)(y + L * (z == 0 ? L - 1 : z - 1)));
+        Nb[5] = ld(oc, (uint32_t)(y + L * (z == L - 1 ? 0 : z + 1)));
+    }
+    // row-shifted neighbours: x = 2j + p with p = (colour + y + z) & 1
+    const bool p1 = ((colour + y + z) & 1) != 0;
+    const uint32_t nwr = half >> 2;
+    if (!p1) {  // west is j-1 of the other plane, east is j
+        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k - 1 + nwr) % nwr];
+        Nb[0] = make_uint2(__funnelshift_l(prev, O.x, 8), __funnelshift_l(O.x, O.y, 8));
+        Nb[1] = O;
+    } else {    // west is j, east is j+1
+        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k + 2) % nwr];
+        Nb[0] = O;
+        Nb[1] = make_uint2(__funnelshift_r(O.x, O.y, 8), __funnelshift_r(O.y, next, 8));
+    }
+    // proposals (§III.A step 4 for labels: a uniform other label)
+    const uint32_t g0 = r * g.G + ((8u * k) >> SH);   // first Philox group of the chunk
+    constexpr int kCalls = 8 >> SH;
+    U4 u[kCalls];
+#pragma unroll
+    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
+    uint2 Sn = make_uint2(0u, 0u);
+    if constexpr (SH == 2) {
+        Sn = make_uint2(S.x ^ 0x01010101u, S.y ^ 0x01010101u);   // q = 2: the other label
+    } else {
+        const uint32_t q1 = (uint32_t)g.two_S;   // q - 1
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t sw = q < 4 ? S.x : S.y;
+            const int sh8 = 8 * (q & 3);
+            const uint32_t k_old = (sw >> sh8) & 0xFFu;
+            const uint32_t u_prop = word_of(u[q >> 1], 2 * (q & 1) + 1);
+            uint32_t k_new = k_old + 1u + (uint32_t)(((uint64_t)u_prop * (uint64_t)q1) >> 32);
+            if (k_new > q1) k_new -= q1 + 1u;
+            if (q < 4) Sn.x |= k_new << sh8;
+            else Sn.y |= k_new << sh8;
+        }
+    }
+    // byte-wise table index: (df + 1) * nn + (dn + nmax), with
+    // dn = #equal(new) - #equal(old) and df = [new = 0] - [old = 0]
+    const uint32_t ones = 0x01010101u;
+    uint32_t c_old_lo = 0, c_old_hi = 0, c_new_lo = 0, c_new_hi = 0;
+#pragma unroll
+    for (int d = 0; d < 2 * D; ++d) {
+        c_old_lo += eq_bytes(Nb[d].x, S.x);
+        c_old_hi += eq_bytes(Nb[d].y, S.y);
+        c_new_lo += eq_bytes(Nb[d].x, Sn.x);
+        c_new_hi += eq_bytes(Nb[d].y, Sn.y);
+    }
+    const uint32_t nn = (uint32_t)g.nn, nmax = (uint32_t)g.nmax;
+    const uint32_t idx_lo = (eq_bytes(Sn.x, 0u) + ones - eq_bytes(S.x, 0u)) * nn + (c_new_lo + nmax * ones - c_old_lo);
+    const uint32_t idx_hi = (eq_bytes(Sn.y, 0u) + ones - eq_bytes(S.y, 0u)) * nn + (c_new_hi + nmax * ones - c_old_hi);
+    uint32_t am = 0;   // bit q: site q accepted
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t iw = q < 4 ? idx_lo : idx_hi;
+        const TabEntry e = stab[(iw >> (8 * (q & 3))) & 0xFFu];
+        const uint32_t u_acc = SH == 2 ? word_of(u[q >> 2], q & 3) : word_of(u[q >> 1], 2 * (q & 1));
+        if (e.always || u_acc < e.thr) am |= 1u << q;
+    }
+    const uint32_t m_lo = spread4(am & 0xFu), m_hi = spread4(am >> 4);
+    const uint2 Sf = make_uint2(S.x ^ ((S.x ^ Sn.x) & m_lo), S.y ^ ((S.y ^ Sn.y) & m_hi));
+    *reinterpret_cast<uint2 *>(dst + (uint64_t)colour * g.plane + (uint64_t)r * half + 8 * k) = Sf;
+    if (colour == 0) *reinterpret_cast<uint2 *>(dst + g.plane + (uint64_t)r * half + 8 * k) = O;
+    if (colour == 1) {
+        // every bond has exactly one colour-1 end
+        uint32_t eq = 0;
+#pragma unroll
+        for (int d = 0; d < 2 * D; ++d) eq += eq_bytes(Nb[d].x, Sf.x) + eq_bytes(Nb[d].y, Sf.y);
+        acc.bond += byte_sum(eq);
+        const int z0 = byte_sum(eq_bytes(Sf.x, 0u) + eq_bytes(Sf.y, 0u) + eq_bytes(O.x, 0u) + eq_bytes(O.y, 0u));
+        acc.zero += z0;
+        acc.other += 16 - z0;
+        if (g.ref != nullptr) {
+            const uint2 R1 = *reinterpret_cast<const uint2 *>(g.ref + g.plane + (uint64_t)r * half + 8 * k);
+            const uint2 R0 = *reinterpret_cast<const uint2 *>(g.ref + (uint64_t)r * half + 8 * k);
+            acc.acf += byte_sum(eq_bytes(Sf.x, R1.x) + eq_bytes(Sf.y, R1.y) + eq_bytes(O.x, R0.x) +
+                                eq_bytes(O.y, R0.y));
+        }
+    }
+}
+
+template <int SH, int D>
+__global__ void __launch_bounds__(kThreads) k_potts_half(Geom g, int colour, int off)
+{
+    __shared__ TabEntry stab[kMaxTab];
+    __shared__ long long red[kThreads / 32];
+    if (threadIdx.x < (unsigned)g.tab_n) stab[threadIdx.x] = g.tab[threadIdx.x];
+    __syncthreads();
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+    const uint32_t cpr = g.half >> 3;   // 8-site chunks per plane row
+    const uint64_t total = (uint64_t)g.rows * cpr;
+    const ViewP v = viewp(g);
+    AccP acc;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x)
+        potts_chunk<SH, D>(v, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+    if (colour == 1) {
+        unsigned long long *slot = series_slot(g.ctrl, sweep);
+        long long s;
+        s = block_sum_ll((long long)acc.bond, red);
+        if (threadIdx.x == 0) add_counter(slot + 0, s);
+        s = block_sum_ll((long long)acc.zero, red);
+        if (threadIdx.x == 0) add_counter(slot + 1, s);
+        s = block_sum_ll((long long)acc.other, red);
+        if (threadIdx.x == 0) add_counter(slot + 2, s);
+        if (g.ref != nullptr) {
+            s = block_sum_ll((long long)acc.acf, red);
+            if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), s);
+        }
+    }
+}
+
+}  // namespace
+
+bool potts_supported(const Geom &g)
+{
+    return g.model == LAT_POTTS && (g.L % 16) == 0 && g.bits[0] == nullptr && g.cpl == nullptr &&
+           g.tab_n <= kMaxTab && g.two_S <= 8;
+}
+
+cudaError_t launch_sweep_potts(const Geom &g, int off, cudaStream_t st)
+{
+    // instantiations: q = 2 and q >= 3, each in 2D and 3D
+    const int which = (g.two_S == 1 ? 0 : 2) + (g.dims == 3 ? 1 : 0);
+    using K = void (*)(Geom, int, int);
+    const K kern[4] = {k_potts_half<2, 2>, k_potts_half<2, 3>, k_potts_half<1, 2>, k_potts_half<1, 3>};
+    static int resident[4] = {0, 0, 0, 0};
+    if (resident[which] == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern[which], kThreads, 0);
+        resident[which] = sms * (per > 0 ? per : 1);
+    }
+    const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((chunks + kThreads - 1) / kThreads,
+                                                        (uint64_t)resident[which]);
+    for (int colour = 0; colour < 2; ++colour) {
+        kern[which]<<<blocks, kThreads, 0, st>>>(g, colour, off);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace lat

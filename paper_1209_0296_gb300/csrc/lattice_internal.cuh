@@ -327,6 +327,9 @@ int batch_wide_grid(bool ne);
 cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
                               bool ne, int grid, cudaStream_t st);
 bool wide3_supported(const Geom &g);
+// q-state Potts model, 8 sites per thread (kernels_potts.cu)
+bool potts_supported(const Geom &g);
+cudaError_t launch_sweep_potts(const Geom &g, int off, cudaStream_t st);
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
 int wide3_items(const Geom &g);   // batch items of one colour of one lattice
 int batch_wide3_grid();

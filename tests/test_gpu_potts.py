@@ -1,6 +1,7 @@
-"""q-state Potts model on the GPU (generic kernel, solo and batched):
-labels and counters must equal the oracle's bit for bit; unsupported paths
-are refused."""
+"""q-state Potts model on the GPU (the 8-sites-per-thread Potts kernel and
+the generic kernel, solo and batched): labels, counters and overlaps with a
+reference state must equal the oracle's bit for bit; unsupported paths are
+refused."""
 import numpy as np
 import pytest
 
@@ -10,11 +11,16 @@ import paper_1209_0296_gb300 as lt
 pytestmark = pytest.mark.gpu
 
 
-def potts_pair(dims, L, q, J, h, T, seed, n, init=lt.INIT_RANDOM, chunks=None):
+def potts_pair(dims, L, q, J, h, T, seed, n, init=lt.INIT_RANDOM, chunks=None, kernel=lt.KERNEL_AUTO,
+               ref=False):
     o = oracle.Lattice(dims, L, q - 1, oracle.POTTS, J, h, T, seed=seed, init=init)
     g = lt.Lattice(dims, L, q - 1, lt.POTTS, J, h, T, seed=seed, init=init)
     try:
+        g.set_kernel(kernel)
         assert np.array_equal(g.get_spins(), o.spins), "initial labels differ"
+        if ref:
+            o.set_reference()
+            g.set_reference()
         ser_o = o.sweep(n)
         for c in (chunks or [n]):
             g.sweep(c)
@@ -27,14 +33,37 @@ def potts_pair(dims, L, q, J, h, T, seed, n, init=lt.INIT_RANDOM, chunks=None):
         N = L ** dims
         assert obs["E"] == pytest.approx((-J * m["bond"] - h * m["mag"]) / N, abs=1e-12)
         assert obs["M"] == pytest.approx(m["mag"] / N, abs=1e-15)
+        if ref:
+            assert np.array_equal(g.autocorrelation(0, n)[0], ser_o["overlap"])
+        return g.get_kernel()["kernel"]
     finally:
         g.close()
 
 
 @pytest.mark.parametrize("q", [2, 3, 4, 9])
-@pytest.mark.parametrize("dims,L", [(2, 16), (2, 64), (2, 30), (3, 8), (3, 16)])
-def test_potts_matches_oracle(q, dims, L):
-    potts_pair(dims, L, q, 1.0, 0.2, 0.9 if dims == 2 else 1.6, 3 * q + L, 15, chunks=[2, 13])
+@pytest.mark.parametrize("dims,L", [(2, 16), (2, 64), (2, 30), (3, 8), (3, 16), (2, 48)])
+@pytest.mark.parametrize("kernel", [lt.KERNEL_AUTO, lt.KERNEL_GENERIC])
+def test_potts_matches_oracle(q, dims, L, kernel):
+    k = potts_pair(dims, L, q, 1.0, 0.2, 0.9 if dims == 2 else 1.6, 3 * q + L, 15, chunks=[2, 13], kernel=kernel)
+    fast = kernel == lt.KERNEL_AUTO and L % 16 == 0
+    assert k == (lt.KERNEL_WIDE if fast else lt.KERNEL_GENERIC)
+
+
+@pytest.mark.parametrize("q,dims,L", [(2, 2, 32), (3, 2, 48), (5, 3, 16), (3, 2, 30)])
+@pytest.mark.parametrize("kernel", [lt.KERNEL_AUTO, lt.KERNEL_GENERIC])
+def test_potts_overlap_series(q, dims, L, kernel):
+    potts_pair(dims, L, q, 1.0, 0.0, 1.2, 7 + q, 40, kernel=kernel, ref=True, chunks=[1, 39])
+
+
+def test_potts_long_run_graphs():
+    # graph replays (64 sweeps each at this size) and a direct tail
+    potts_pair(2, 64, 4, 1.0, -0.1, 0.8, 41, 150, chunks=[150])
+
+
+@pytest.mark.slow
+def test_potts_full_size_L4096_q3():
+    import math
+    potts_pair(2, 4096, 3, 1.0, 0.0, 1 / math.log(1 + math.sqrt(3)), 7, 2)
 
 
 @pytest.mark.parametrize("init", [lt.INIT_COLD, lt.INIT_RANDOM])
@@ -77,10 +106,15 @@ def test_potts_labels_and_refusals():
         with pytest.raises(lt.LatticeError):
             g.set_spins(x)
     assert np.array_equal(g.get_spins(), labels)
-    for kern in (lt.KERNEL_TILED, lt.KERNEL_WIDE, lt.KERNEL_RESIDENT):
+    for kern in (lt.KERNEL_TILED, lt.KERNEL_RESIDENT):
         with pytest.raises(lt.LatticeError):
             g.set_kernel(kern)
+    g.set_kernel(lt.KERNEL_WIDE)
     g.close()
+    odd = lt.Lattice(2, 30, 2, lt.POTTS, 1.0, 0.0, 1.0, seed=1, init=lt.INIT_RANDOM)
+    with pytest.raises(lt.LatticeError):
+        odd.set_kernel(lt.KERNEL_WIDE)   # L % 16 != 0: generic only
+    odd.close()
     q2 = lt.Lattice(2, 64, 1, lt.POTTS, 1.0, 0.0, 1.0, seed=1, init=lt.INIT_RANDOM)
     with pytest.raises(lt.LatticeError):
         q2.set_dynamics(lt.DYNAMICS_RANDOM_SITE, 16, 16)
