@@ -357,6 +357,10 @@ def run_profile(args):
     if args.profile_model == "ne":
         c = 0.42 if args.profile_dynamics == "random-site" else 0.3
         g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, c, seed=21, init=lt.INIT_EQUILIBRIUM)
+    elif args.profile_model == "potts":   # q = 3 Potts at T_c = 1 / ln(1 + sqrt 3), random start (seed 7)
+        import math
+        g = lt.Lattice(2, args.profile_L, 2, lt.POTTS, 1.0, 0.0, 1.0 / math.log(1.0 + math.sqrt(3.0)), seed=7,
+                       init=lt.INIT_RANDOM)
     elif args.profile_model == "ising3d":   # 3D spin-1 at T = 2 + 7 * 2/15, random start (seed 11)
         g = lt.Lattice(3, args.profile_L, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, seed=11,
                        init=lt.INIT_RANDOM)
@@ -672,7 +676,7 @@ def main():
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
     ap.add_argument("--profile-L", type=int, default=L)
-    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d"])
+    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d", "potts"])
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic", "resident"])
     ap.add_argument("--profile-layout", default="int8", choices=["int8", "bitpacked"])
     ap.add_argument("--profile-dynamics", default="checkerboard", choices=["checkerboard", "random-site"])

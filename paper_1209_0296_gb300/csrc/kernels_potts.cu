@@ -177,8 +177,11 @@ LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigne
     }
 }
 
+// Four CTAs per SM (64 registers) hide the Philox and load latencies better
+// than the two that the unbounded register allocation leaves room for; the
+// 3D q >= 3 form takes three (80 registers) to stay free of spills.
 template <int SH, int D>
-__global__ void __launch_bounds__(kThreads) k_potts_half(Geom g, int colour, int off)
+__global__ void __launch_bounds__(kThreads, (SH == 1 && D == 3) ? 3 : 4) k_potts_half(Geom g, int colour, int off)
 {
     __shared__ TabEntry stab[kMaxTab];
     __shared__ long long red[kThreads / 32];
