@@ -69,6 +69,12 @@ def _load():
                                                ctypes.c_int, ctypes.c_int, i8p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4
             lib.oracle_rsite_sweep.restype = ctypes.c_int
+            lib.oracle_rsite_sweep_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                       ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, i8p,
+                                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 4
+            lib.oracle_rsite_sweep_variant.restype = ctypes.c_int
             lib.oracle_sweep_couplings.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                    ctypes.c_uint64, i8p, ctypes.c_void_p, ctypes.c_void_p,
@@ -204,30 +210,32 @@ class Lattice:
             return out
         return self._sweep(n)
 
-    def rsite_sweep(self, n: int, tile: int, lam: int):
+    def rsite_sweep(self, n: int, tile: int, lam: int, balanced: bool = False):
         """Advance n sweeps of the paper's random-sub-lattice, random-site
-        algorithm (§III.B) with b x b sub-lattices and lam picks per round;
-        returns the per-sweep series (and "overlap" when a reference is set)."""
+        algorithm (§III.B) with b x b sub-lattices and lam picks per round
+        (balanced: its balance-preserving variant, single-colour rounds and
+        four launches per sweep); returns the per-sweep series (and
+        "overlap" when a reference is set)."""
         keys = ("bond", "mag", "up", "unflipped")
         if self.ref is not None:
             out = {k: np.zeros(n, dtype=np.int64) for k in keys + ("overlap",)}
             for k in range(n):
-                one = self._rsite(1, tile, lam)
+                one = self._rsite(1, tile, lam, balanced)
                 for key in keys:
                     out[key][k] = one[key][0]
                 out["overlap"][k] = self.overlap()
             return out
-        return self._rsite(n, tile, lam)
+        return self._rsite(n, tile, lam, balanced)
 
-    def _rsite(self, n, tile, lam):
+    def _rsite(self, n, tile, lam, balanced=False):
         if self.dims != 2 or self.two_S != 1 or self.eps is not None or self.eta is not None:
             raise ValueError("the random-site algorithm is 2D spin-1/2 with uniform couplings")
         out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped")}
-        rc = _load().oracle_rsite_sweep(self.L, self.model, self.J, self.h, self.T_or_c, self.seed,
-                                        int(tile), int(lam), self.spins,
-                                        _ptr(self.flags) if self.model == NE else None,
-                                        self.sweep_index, n, _ptr(out["bond"]), _ptr(out["mag"]),
-                                        _ptr(out["up"]), _ptr(out["unflipped"]))
+        rc = _load().oracle_rsite_sweep_variant(self.L, self.model, self.J, self.h, self.T_or_c, self.seed,
+                                                int(tile), int(lam), int(bool(balanced)), self.spins,
+                                                _ptr(self.flags) if self.model == NE else None,
+                                                self.sweep_index, n, _ptr(out["bond"]), _ptr(out["mag"]),
+                                                _ptr(out["up"]), _ptr(out["unflipped"]))
         if rc != 0:
             raise ValueError("oracle_rsite_sweep rejected the parameters")
         self.sweep_index += n

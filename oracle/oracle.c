@@ -504,6 +504,20 @@ int oracle_sweep(int dims, int L, int two_S, int model, double J, double h,
 /*  - Move rule and thresholds as in oracle_sweep: flip, the North-East      */
 /*    constraint, accept without a draw when allowed by "always", else iff   */
 /*    u < thr.  Persistence flags as in oracle_sweep.                        */
+/*                                                                           */
+/* The balance-preserving variant (§III.B, after Fig. 5: steps 6-9 changed) */
+/* picks the lambda sites of a round among one colour only, red and white   */
+/* rounds alternating, and takes four launches per sweep.  Its round count  */
+/* per launch is not legible in the paper; read here as q/2 (so a sweep     */
+/* still makes q*lambda*2 = P picks per sub-lattice, the time unit of the   */
+/* serial reference), which needs q/2 even.  Red is colour 0, (x+y) even,  */
+/* and goes first; a round of colour c uses the same Philox words as round */
+/* r of the plain algorithm, with the site word mapped into the P/2 sites  */
+/* of that colour: m = floor(w * P/2 / 2^32), row ly = m / (b/2), column   */
+/* lx = 2 (m mod b/2) + ((ly + c) & 1).  Launches 0..3 use tags 4..7.     */
+/* With one sub-lattice a round changes only non-interacting sites, each by */
+/* a Metropolis move, so the Boltzmann distribution is stationary for any  */
+/* lambda -- the paper's point for this variant.                            */
 /* ------------------------------------------------------------------------ */
 static int rsite_accept(const params_t *p, int model, int s_old, int s_new, int n, uint32_t u)
 {
@@ -520,10 +534,12 @@ static int rsite_accept(const params_t *p, int model, int s_old, int s_new, int 
     return accept;
 }
 
-int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
-                       uint64_t seed, int b, int lambda, int8_t *s, uint8_t *flag,
-                       int64_t sweep0, int64_t nsweeps, int64_t *bond,
-                       int64_t *mag, int64_t *up, int64_t *unflipped)
+/* balanced = 0: the algorithm of steps 3-10; 1: the balance-preserving    */
+/* variant described above.                                                  */
+int oracle_rsite_sweep_variant(int L, int model, double J, double h, double T_or_c,
+                               uint64_t seed, int b, int lambda, int balanced, int8_t *s,
+                               uint8_t *flag, int64_t sweep0, int64_t nsweeps, int64_t *bond,
+                               int64_t *mag, int64_t *up, int64_t *unflipped)
 {
     params_t p;
     if (setup(&p, 2, L, 1, model, J, h, T_or_c, seed)) return -1;
@@ -532,7 +548,10 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
     const int64_t P = (int64_t)b * b;
     if (lambda < 1 || (P / 2) % lambda != 0) return -1;
     const int64_t q = P / 2 / lambda;
-    const int64_t calls = (q + 1) / 2 * lambda;   /* Philox calls per sub-lattice and launch */
+    if (balanced && (q % 4) != 0) return -1;
+    const int launches = balanced ? 4 : 2;
+    const int64_t rounds = balanced ? q / 2 : q;        /* rounds per launch */
+    const int64_t calls = (rounds + 1) / 2 * lambda;   /* Philox calls per sub-lattice and launch */
     const int nt = L / b;
     int8_t *src = (int8_t *)malloc((size_t)p.N);
     int8_t *loc = (int8_t *)malloc((size_t)P);
@@ -544,7 +563,7 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
     }
     const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     for (int64_t t = sweep0; t < sweep0 + nsweeps; ++t) {
-        for (int launch = 0; launch < 2; ++launch) {
+        for (int launch = 0; launch < launches; ++launch) {
             memcpy(src, s, (size_t)p.N);               /* the launch's input */
             for (int ty = 0; ty < nt; ++ty)
                 for (int tx = 0; tx < nt; ++tx) {
@@ -553,7 +572,7 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
                     for (int ly = 0; ly < b; ++ly)
                         for (int lx = 0; lx < b; ++lx)
                             loc[ly * b + lx] = src[site_index(&p, x0 + lx, y0 + ly, 0)];
-                    for (int64_t r = 0; r < q; ++r) {
+                    for (int64_t r = 0; r < rounds; ++r) {
                         /* every pick of the round decided from the same state */
                         for (int i = 0; i < lambda; ++i) {
                             uint32_t ctr[4] = {(uint32_t)(B * calls + (r / 2) * lambda + i),
@@ -563,7 +582,14 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
                             uint32_t w[4];
                             oracle_philox4x32_10(ctr, key, w);
                             const int ws = 2 * (int)(r & 1);
-                            const int64_t site = (int64_t)(((uint64_t)w[ws] * (uint64_t)P) >> 32);
+                            int64_t site;
+                            if (!balanced) {
+                                site = (int64_t)(((uint64_t)w[ws] * (uint64_t)P) >> 32);
+                            } else {            /* round colour c = r & 1 */
+                                const int64_t m = (int64_t)(((uint64_t)w[ws] * (uint64_t)(P / 2)) >> 32);
+                                const int64_t row = m / (b / 2);
+                                site = row * b + 2 * (m % (b / 2)) + ((row + (r & 1)) & 1);
+                            }
                             const int lx = (int)(site % b), ly = (int)(site / b);
                             int nb[4];   /* north, east, south, west */
                             const int dx[4] = {0, 1, 0, -1}, dy[4] = {-1, 0, 1, 0};
@@ -613,6 +639,15 @@ int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
     }
     free(src); free(loc); free(nv); free(pick);
     return 0;
+}
+
+int oracle_rsite_sweep(int L, int model, double J, double h, double T_or_c,
+                       uint64_t seed, int b, int lambda, int8_t *s, uint8_t *flag,
+                       int64_t sweep0, int64_t nsweeps, int64_t *bond,
+                       int64_t *mag, int64_t *up, int64_t *unflipped)
+{
+    return oracle_rsite_sweep_variant(L, model, J, h, T_or_c, seed, b, lambda, 0, s, flag, sweep0,
+                                      nsweeps, bond, mag, up, unflipped);
 }
 
 /* Overlap of a configuration with a reference one, sum_i s_i * ref_i: the  */
