@@ -355,7 +355,7 @@ def run_profile(args):
     import paper_1209_0296_gb300 as lt
     torch.cuda.set_device(0)
     if args.profile_model == "ne":
-        c = 0.42 if args.profile_dynamics == "random-site" else 0.3
+        c = 0.42 if args.profile_dynamics != "checkerboard" else 0.3
         g = lt.Lattice(2, args.profile_L, 1, lt.NE, 0.0, 0.0, c, seed=21, init=lt.INIT_EQUILIBRIUM)
     elif args.profile_model == "potts":   # q = 3 Potts at T_c = 1 / ln(1 + sqrt 3), random start (seed 7)
         import math
@@ -373,8 +373,9 @@ def run_profile(args):
     if args.profile_layout == "bitpacked":
         kern = lt.KERNEL_AUTO
     g.set_kernel(kern, 0, args.tile_h, 1 << 30)  # direct launches, no graphs
-    if args.profile_dynamics == "random-site":
-        g.set_dynamics(lt.DYNAMICS_RANDOM_SITE, args.profile_tile, args.profile_lambda)
+    if args.profile_dynamics != "checkerboard":
+        g.set_dynamics(lt.DYNAMICS_RANDOM_SITE if args.profile_dynamics == "random-site"
+                       else lt.DYNAMICS_RANDOM_SITE_BALANCED, args.profile_tile, args.profile_lambda)
     g.sweep(args.profile)
     g.synchronize()
     print("profile run: %d sweeps of L=%d (%s), kernel %s" % (args.profile, args.profile_L,
@@ -591,6 +592,15 @@ def other_configs(dev):
                                                 "us_per_sweep": t / n * 1e6}
     g.close()
 
+    # its balance-preserving variant (single-colour rounds, four launches)
+    g = lt.Lattice(2, 8192, 1, lt.NE, 0.0, 0.0, 0.42, seed=21, init=lt.INIT_EQUILIBRIUM, stream=stream)
+    g.set_dynamics(lt.DYNAMICS_RANDOM_SITE_BALANCED, 32, 16)
+    n = 3
+    t = _timed_sweeps(torch, stream, [g], n, flush)
+    out["NE_L8192_random_site_balanced_b32_lambda16"] = {"updates_per_ns": N4 * n / t / 1e9, "sweeps": n,
+                                                         "us_per_sweep": t / n * 1e6}
+    g.close()
+
     # a +-J spin glass (Eq. 1 with random bond signs, half negative), L = 4096
     g = lt.Lattice(2, 4096, 1, lt.ISING, 1.0, 0.0, 1.0, seed=7, init=lt.INIT_RANDOM, stream=stream)
     g.set_couplings(np.where(np.random.default_rng(5).random(2 * 4096 * 4096) < 0.5, -1, 1).astype(np.int8))
@@ -679,7 +689,7 @@ def main():
     ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d", "potts"])
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic", "resident"])
     ap.add_argument("--profile-layout", default="int8", choices=["int8", "bitpacked"])
-    ap.add_argument("--profile-dynamics", default="checkerboard", choices=["checkerboard", "random-site"])
+    ap.add_argument("--profile-dynamics", default="checkerboard", choices=["checkerboard", "random-site", "random-site-balanced"])
     ap.add_argument("--profile-tile", type=int, default=32, help="random-site sub-lattice side")
     ap.add_argument("--profile-lambda", type=int, default=16, help="random-site picks per round")
     args = ap.parse_args()

@@ -89,8 +89,10 @@ enum lattice_layout {
 /* Sweep dynamics for lattice_set_dynamics. */
 enum lattice_dynamics {
     LAT_DYNAMICS_CHECKERBOARD = 0, /* colour 0 then colour 1 (§III.A steps 5-8); the default */
-    LAT_DYNAMICS_RANDOM_SITE = 1   /* the paper's random-sub-lattice, random-site algorithm
+    LAT_DYNAMICS_RANDOM_SITE = 1,  /* the paper's random-sub-lattice, random-site algorithm
                                       (§III.B, second algorithm) */
+    LAT_DYNAMICS_RANDOM_SITE_BALANCED = 2  /* its balance-preserving variant (§III.B, after
+                                              Fig. 5): single-colour rounds */
 };
 /* Kernel selection for lattice_set_kernel (tests and the autotuner). */
 enum lattice_kernel {
@@ -217,12 +219,22 @@ int lattice_field_series(lattice_t *lat, int64_t first, int64_t count, int64_t *
  * every sub-lattice makes q rounds of lambda concurrent random picks
  * (lambda a power of two, 1 <= lambda <= min(1024, tile^2/2), q * lambda =
  * tile^2/2), with its boundary frozen at the launch's start.  Randomness:
- * pick p of launch l in sweep t of sub-lattice B (row-major) draws Philox
- * with counter (B*tile^2/2 + p, t lo, t hi, 4 + l); word 0 picks the site,
- * word 1 the acceptance.  Picks of one round are decided from the state at
- * the round's start; of several picks of one site the lowest thread index's
- * is kept.  tile = L (one sub-lattice) with lambda = 1 is serial random-site
- * Metropolis.  Allocates one more lattice-sized buffer (N bytes) the first
+ * thread i of sub-lattice B (row-major) makes one Philox call per two
+ * rounds, rounds 2k and 2k+1 of launch l in sweep t sharing the counter
+ * (B*C + k*lambda + i, t lo, t hi, 4 + l) with C = ceil(q/2)*lambda; round r
+ * takes word 2(r&1) for the site (floor(w * tile^2 / 2^32), row-major) and
+ * word 2(r&1)+1 for the acceptance.  Picks of one round are decided from
+ * the state at the round's start; of several picks of one site the lowest
+ * thread index's is kept.  tile = L (one sub-lattice) with lambda = 1 is
+ * serial random-site Metropolis.
+ * LAT_DYNAMICS_RANDOM_SITE_BALANCED is the variant that keeps the weaker
+ * balance condition: four launches per sweep (tags 4..7), each making q/2
+ * rounds that alternate colour 0 (the paper's red) and colour 1 (white),
+ * starting with colour 0; a round's picks are drawn among the tile^2/2
+ * sites of its colour (m = floor(w * tile^2/2 / 2^32), row m / (tile/2),
+ * column 2 (m mod tile/2) + ((row + colour) & 1)).  It needs q/2 even
+ * (lambda <= tile^2/8).  With one sub-lattice it leaves the Boltzmann
+ * distribution stationary for any lambda.  Allocates one more lattice-sized buffer (N bytes) the first
  * time.  Counters, persistence and the autocorrelation are recorded as for
  * the checkerboard.  LAT_ENOTSUP for 3D, spin-S or bit-packed lattices,
  * LAT_EINVAL for other tile / lambda values.  Such lattices cannot join a

@@ -16,13 +16,14 @@ from ._lib import LatticeError, LatticeRequest, LatticeResult, check, load
 __all__ = ["Lattice", "Batch", "Server", "LatticeError", "load", "threshold_table",
            "ISING", "NE", "POTTS", "INIT_COLD", "INIT_RANDOM", "INIT_EQUILIBRIUM", "INT8", "BITPACKED",
            "KERNEL_AUTO", "KERNEL_GENERIC", "KERNEL_TILED", "KERNEL_WIDE",
-           "KERNEL_RESIDENT", "DYNAMICS_CHECKERBOARD", "DYNAMICS_RANDOM_SITE"]
+           "KERNEL_RESIDENT", "DYNAMICS_CHECKERBOARD", "DYNAMICS_RANDOM_SITE",
+           "DYNAMICS_RANDOM_SITE_BALANCED"]
 
 ISING, NE, POTTS = 0, 1, 2
 INIT_COLD, INIT_RANDOM, INIT_EQUILIBRIUM = 0, 1, 2
 INT8, BITPACKED = 0, 1
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_WIDE, KERNEL_RESIDENT = 0, 1, 2, 3, 4
-DYNAMICS_CHECKERBOARD, DYNAMICS_RANDOM_SITE = 0, 1
+DYNAMICS_CHECKERBOARD, DYNAMICS_RANDOM_SITE, DYNAMICS_RANDOM_SITE_BALANCED = 0, 1, 2
 
 
 def _stream_handle(stream) -> int:
@@ -113,8 +114,9 @@ class Lattice:
         return out
 
     def set_dynamics(self, dynamics=0, tile: int = 32, lam: int = 16):
-        """DYNAMICS_CHECKERBOARD (default) or DYNAMICS_RANDOM_SITE with
-        tile x tile sub-lattices and lam picks per round."""
+        """DYNAMICS_CHECKERBOARD (default), DYNAMICS_RANDOM_SITE or
+        DYNAMICS_RANDOM_SITE_BALANCED with tile x tile sub-lattices and lam
+        picks per round."""
         check(self._lib.lattice_set_dynamics(self._h, int(dynamics), int(tile), int(lam)),
               "lattice_set_dynamics")
 

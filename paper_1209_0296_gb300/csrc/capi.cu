@@ -250,9 +250,11 @@ constexpr int64_t kResidentChunk = 1 << 16;
 
 int enqueue_sweeps(lattice *lt, int64_t k, cudaStream_t st)
 {
-    if (lt->dynamics == LAT_DYNAMICS_RANDOM_SITE) {
+    if (lt->dynamics != LAT_DYNAMICS_CHECKERBOARD) {
+        const bool balanced = lt->dynamics == LAT_DYNAMICS_RANDOM_SITE_BALANCED;
         for (int64_t off = 0; off < k; ++off) {
-            cudaError_t e = launch_sweep_rsite(lt->geom, lt->rs_scratch, lt->rs_tile, lt->rs_lambda, (int)off, st);
+            cudaError_t e =
+                launch_sweep_rsite(lt->geom, lt->rs_scratch, lt->rs_tile, lt->rs_lambda, balanced, (int)off, st);
             if (e != cudaSuccess) return cuda_fail(e, "random-site sweep launch");
         }
         cudaError_t e = launch_advance(lt->ctrl, (unsigned long long)k, st);
@@ -726,11 +728,11 @@ int lattice_set_dynamics(lattice_t *lt, int dynamics, int tile, int lambda)
         lt->graph_valid = false;
         return LAT_OK;
     }
-    if (dynamics != LAT_DYNAMICS_RANDOM_SITE) return LAT_EINVAL;
+    if (dynamics != LAT_DYNAMICS_RANDOM_SITE && dynamics != LAT_DYNAMICS_RANDOM_SITE_BALANCED) return LAT_EINVAL;
     if (lt->P.dims != 2 || lt->P.two_S != 1 || lt->P.layout != LAT_INT8 || lt->cpl != nullptr ||
         lt->P.model == LAT_POTTS)
         return LAT_ENOTSUP;
-    if (!rsite_params_ok(lt->geom, tile, lambda)) return LAT_EINVAL;
+    if (!rsite_params_ok(lt->geom, tile, lambda, dynamics == LAT_DYNAMICS_RANDOM_SITE_BALANCED)) return LAT_EINVAL;
     if (lt->rs_scratch == nullptr) {
         cudaError_t e = dev_alloc((void **)&lt->rs_scratch, (size_t)lt->P.N, lt->stream);
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "random-site scratch");

@@ -25,6 +25,13 @@
 // one sub-lattice (b = L) the neighbours wrap inside it, so Q = lambda = 1
 // is serial random-site Metropolis.
 //
+// The balance-preserving variant (after Fig. 5) makes q/2 rounds per
+// launch, red (colour 0) and white (colour 1) alternating, each picking
+// among the P/2 sites of its colour (m = floor(w * P/2 / 2^32), row m / (b/2),
+// column 2 (m mod b/2) + ((row + colour) & 1)), and four launches per sweep
+// with tags 4..7; launches 0 and 2 write the scratch buffer, 1 and 3 write
+// s[(t+1) & 1].
+//
 // GPU mapping.  lambda <= 32: a group of lambda lanes owns one sub-lattice,
 // a warp holds 32/lambda groups (fewer when shared memory is short) and
 // a CTA several independent warps; collisions are resolved in the warp
@@ -48,6 +55,7 @@ struct RsArgs {
     Geom g;
     int8_t *scratch;    // launch 0 output, launch 1 input
     int b, logb, lambda, loglam, launch, off;
+    int balanced, rounds;   // balance-preserving variant; rounds per launch
     int per_warp, warps;    // lambda <= 32: sub-lattices per warp, warps per CTA
     int tile_bytes;         // shared-memory bytes of one staged sub-lattice
 };
@@ -179,11 +187,19 @@ LAT_D void store_tile(const Geom &g, int8_t *dst, const Tile &t, int x0, int y0,
 
 // Decide one pick from the tile as it stands: the site, its new value and
 // whether it changes.
+// colour < 0: a pick among all P sites; else among the P/2 sites of that
+// colour (the balance-preserving variant).
 template <bool kNE>
-LAT_D void decide(const Geom &g, const Tile &t, const TabEntry *stab, int b, int logb, uint32_t w_site,
-                  uint32_t w_acc, int &site, int8_t &nv, bool &chg)
+LAT_D void decide(const Geom &g, const Tile &t, const TabEntry *stab, int b, int logb, int colour,
+                  uint32_t w_site, uint32_t w_acc, int &site, int8_t &nv, bool &chg)
 {
-    site = (int)(((uint64_t)w_site * (uint64_t)(b * b)) >> 32);
+    if (colour < 0) {
+        site = (int)(((uint64_t)w_site * (uint64_t)(b * b)) >> 32);
+    } else {
+        const int m = (int)(((uint64_t)w_site * (uint64_t)(b * b / 2)) >> 32);
+        const int row = m >> (logb - 1);
+        site = (row << logb) + 2 * (m & ((b >> 1) - 1)) + ((row + colour) & 1);
+    }
     const int lx = site & (b - 1), ly = site >> logb;
     const int8_t *c = t.g + (ly + 1) * t.pitch + 4 + lx;
     const int s_old = c[0];
@@ -240,8 +256,10 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta) k_rsite_warp(RsArgs a)
     const int nt = L >> logb, Q = nt * nt;
     const bool whole = nt == 1;
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)a.off;
-    const int8_t *src = a.launch == 0 ? g.s[sweep & 1] : a.scratch;
-    int8_t *dst = a.launch == 0 ? a.scratch : g.s[(sweep + 1) & 1];
+    // odd launches read the scratch buffer and write s[(t+1) & 1]; even ones
+    // write the scratch buffer from s[t & 1] (launch 0) or s[(t+1) & 1]
+    const int8_t *src = (a.launch & 1) ? a.scratch : g.s[(sweep + (a.launch ? 1 : 0)) & 1];
+    int8_t *dst = (a.launch & 1) ? g.s[(sweep + 1) & 1] : a.scratch;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = a.per_warp;
     const int T0 = (blockIdx.x * a.warps + warp) * S;
@@ -264,17 +282,17 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta) k_rsite_warp(RsArgs a)
     const Tile t = tile_at(wbase + (size_t)(act ? grp : 0) * a.tile_bytes, b);
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
-    const int q = (P >> 1) >> a.loglam;
+    const int q = a.rounds;
     const uint32_t calls = (uint32_t)((q + 1) >> 1) << a.loglam;   // Philox calls per sub-lattice
     const uint32_t base = (uint32_t)T * calls + (uint32_t)me;
     const uint32_t tag = 4u + (uint32_t)a.launch;
-    auto round = [&](uint32_t w_site, uint32_t w_acc) {
+    auto round = [&](uint32_t w_site, uint32_t w_acc, int colour) {
         int key = -1 - lane;   // distinct for idle lanes
         int site = 0;
         int8_t nv = 0;
         bool chg = false;
         if (act) {
-            decide<kNE>(g, t, stab, b, logb, w_site, w_acc, site, nv, chg);
+            decide<kNE>(g, t, stab, b, logb, colour, w_site, w_acc, site, nv, chg);
             key = grp * P + site;
         }
         __syncwarp();                        // every read of the round is done
@@ -285,8 +303,8 @@ __global__ void __launch_bounds__(32 * kMaxWarpsPerCta) k_rsite_warp(RsArgs a)
     for (int r = 0; r < q; r += 2) {
         U4 w = U4{0u, 0u, 0u, 0u};
         if (act) w = philox_item(pp, base + ((uint32_t)(r >> 1) << a.loglam), tag);
-        round(w.x, w.y);
-        if (r + 1 < q) round(w.z, w.w);
+        round(w.x, w.y, a.balanced ? 0 : -1);
+        if (r + 1 < q) round(w.z, w.w, a.balanced ? 1 : -1);
     }
 
     for (int k = 0; k < S && T0 + k < Q; ++k) {
@@ -307,8 +325,10 @@ __global__ void __launch_bounds__(1024) k_rsite_block(RsArgs a)
     const int nt = L >> logb;
     const bool whole = nt == 1;
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)a.off;
-    const int8_t *src = a.launch == 0 ? g.s[sweep & 1] : a.scratch;
-    int8_t *dst = a.launch == 0 ? a.scratch : g.s[(sweep + 1) & 1];
+    // odd launches read the scratch buffer and write s[(t+1) & 1]; even ones
+    // write the scratch buffer from s[t & 1] (launch 0) or s[(t+1) & 1]
+    const int8_t *src = (a.launch & 1) ? a.scratch : g.s[(sweep + (a.launch ? 1 : 0)) & 1];
+    int8_t *dst = (a.launch & 1) ? g.s[(sweep + 1) & 1] : a.scratch;
     const int T = blockIdx.x;
     int x0, y0;
     tile_origin(T, nt, logb, x0, y0);
@@ -327,15 +347,15 @@ __global__ void __launch_bounds__(1024) k_rsite_block(RsArgs a)
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
     const int me = threadIdx.x;
-    const int q = (P >> 1) >> a.loglam;
+    const int q = a.rounds;
     const uint32_t calls = (uint32_t)((q + 1) >> 1) << a.loglam;
     const uint32_t base = (uint32_t)T * calls + (uint32_t)me;
     const uint32_t tag = 4u + (uint32_t)a.launch;
-    auto round = [&](uint32_t w_site, uint32_t w_acc) {
+    auto round = [&](uint32_t w_site, uint32_t w_acc, int colour) {
         int site;
         int8_t nv;
         bool chg;
-        decide<kNE>(g, t, stab, b, logb, w_site, w_acc, site, nv, chg);
+        decide<kNE>(g, t, stab, b, logb, colour, w_site, w_acc, site, nv, chg);
         __syncthreads();                     // every read of the round is done
         atomicMin(&own[site], (uint32_t)me);
         __syncthreads();
@@ -345,8 +365,8 @@ __global__ void __launch_bounds__(1024) k_rsite_block(RsArgs a)
     };
     for (int r = 0; r < q; r += 2) {
         const U4 w = philox_item(pp, base + ((uint32_t)(r >> 1) << a.loglam), tag);
-        round(w.x, w.y);
-        if (r + 1 < q) round(w.z, w.w);
+        round(w.x, w.y, a.balanced ? 0 : -1);
+        if (r + 1 < q) round(w.z, w.w, a.balanced ? 1 : -1);
     }
     __syncthreads();
     store_tile<kNE>(g, dst, t, x0, y0, b, threadIdx.x, blockDim.x);
@@ -489,7 +509,7 @@ RsPlan plan(int L, int b, int lambda)
 
 }  // namespace
 
-bool rsite_params_ok(const Geom &g, int b, int lambda)
+bool rsite_params_ok(const Geom &g, int b, int lambda, bool balanced)
 {
     if (g.dims != 2 || g.two_S != 1 || g.bits[0] != nullptr || g.cpl != nullptr || g.tab_n > kMaxTab ||
         g.model == LAT_POTTS)
@@ -497,10 +517,12 @@ bool rsite_params_ok(const Geom &g, int b, int lambda)
     if (b < 8 || b > 256 || (b & (b - 1)) != 0 || (g.L % b) != 0) return false;
     const int half_p = b * b / 2;
     if (lambda < 1 || lambda > 1024 || (lambda & (lambda - 1)) != 0 || lambda > half_p) return false;
+    if (balanced && ((half_p / lambda) % 4) != 0) return false;   // q/2 rounds per launch, q/2 even
     return plan(g.L, b, lambda).smem <= 200 * 1024;
 }
 
-cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda, int off, cudaStream_t st)
+cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda, bool balanced, int off,
+                               cudaStream_t st)
 {
     const RsPlan p = plan(g.L, b, lambda);
     RsArgs a;
@@ -514,6 +536,9 @@ cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda
     a.per_warp = p.per_warp;
     a.warps = p.warps;
     a.tile_bytes = (int)tile_bytes_of(b);
+    a.balanced = balanced ? 1 : 0;
+    const int q = (b * b / 2) / lambda;
+    a.rounds = balanced ? q / 2 : q;
     static bool attr = false;
     if (!attr) {
         const int lim = 200 * 1024;
@@ -528,7 +553,7 @@ cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda
         attr = true;
     }
     const bool ne = g.model == LAT_NE;
-    for (int launch = 0; launch < 2; ++launch) {
+    for (int launch = 0; launch < (balanced ? 4 : 2); ++launch) {
         a.launch = launch;
         if (lambda <= 32) {
             if (ne) k_rsite_warp<true><<<p.blocks, p.threads, p.smem, st>>>(a);

@@ -313,8 +313,10 @@ bool wide_supported(const Geom &g);
 // follows the first in g.tab, with no never-accept entry)
 cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st);
 // The paper's random-sub-lattice, random-site sweep (kernels_rsite.cu).
-bool rsite_params_ok(const Geom &g, int b, int lambda);
-cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda, int off, cudaStream_t st);
+// balanced: the balance-preserving variant (single-colour rounds, four launches)
+bool rsite_params_ok(const Geom &g, int b, int lambda, bool balanced);
+cudaError_t launch_sweep_rsite(const Geom &g, int8_t *scratch, int b, int lambda, bool balanced, int off,
+                               cudaStream_t st);
 bool resident_supported(const Geom &g);
 cudaError_t launch_sweep_resident(const Geom &g, int off, int n_sweeps, cudaStream_t st);
 size_t resident_smem_bytes(const Geom &g);

@@ -2,7 +2,8 @@
 algorithm) on the GPU: lattices, persistence flags, per-sweep counters and
 overlaps must equal the oracle's, integer for integer, for sub-lattice
 sizes from 8 to the whole lattice and lambda from 1 to 1024 (both the
-one-warp and the many-warp collision paths)."""
+one-warp and the many-warp collision paths), for the algorithm and for its
+balance-preserving variant."""
 import numpy as np
 import pytest
 
@@ -12,17 +13,17 @@ import paper_1209_0296_gb300 as lt
 pytestmark = pytest.mark.gpu
 
 
-def rs_pair(L, model, Tc, tile, lam, nsweeps, seed=5, chunks=None, ref=True):
+def rs_pair(L, model, Tc, tile, lam, nsweeps, seed=5, chunks=None, ref=True, balanced=False):
     J = 1.0 if model == lt.ISING else 0.0
     init = lt.INIT_RANDOM if model == lt.ISING else lt.INIT_EQUILIBRIUM
     o = oracle.Lattice(2, L, 1, model, J, 0.0, Tc, seed=seed, init=init)
     g = lt.Lattice(2, L, 1, model, J, 0.0, Tc, seed=seed, init=init)
     try:
-        g.set_dynamics(lt.DYNAMICS_RANDOM_SITE, tile, lam)
+        g.set_dynamics(lt.DYNAMICS_RANDOM_SITE_BALANCED if balanced else lt.DYNAMICS_RANDOM_SITE, tile, lam)
         if ref:
             g.set_reference()
             o.set_reference()
-        ser_o = o.rsite_sweep(nsweeps, tile, lam)
+        ser_o = o.rsite_sweep(nsweeps, tile, lam, balanced=balanced)
         for c in (chunks or [nsweeps]):
             g.sweep(c)
         spins, flags, n = g.get_state()
@@ -47,6 +48,24 @@ def rs_pair(L, model, Tc, tile, lam, nsweeps, seed=5, chunks=None, ref=True):
 @pytest.mark.parametrize("model,Tc", [(lt.NE, 0.42), (lt.ISING, 2.3)])
 def test_random_site_matches_oracle(L, tile, lam, model, Tc):
     rs_pair(L, model, Tc, tile, lam, 6, seed=L + tile + lam, chunks=[1, 5])
+
+
+@pytest.mark.parametrize("L,tile,lam", [(64, 32, 16), (64, 8, 8), (64, 8, 1), (64, 16, 4),
+                                        (128, 16, 32), (64, 32, 128), (32, 32, 4), (256, 128, 1024),
+                                        (24, 8, 2), (8, 8, 8), (40, 8, 4)])
+@pytest.mark.parametrize("model,Tc", [(lt.NE, 0.42), (lt.ISING, 2.3)])
+def test_balanced_variant_matches_oracle(L, tile, lam, model, Tc):
+    rs_pair(L, model, Tc, tile, lam, 5, seed=L + tile + lam + 1, chunks=[2, 3], balanced=True)
+
+
+def test_balanced_variant_graphs_and_rejections():
+    rs_pair(64, lt.ISING, 2.5, 16, 8, 70, chunks=[70], balanced=True, ref=False)   # a graph + direct sweeps
+    g = lt.Lattice(2, 64, 1, lt.NE, 0.0, 0.0, 0.3, seed=1, init=lt.INIT_EQUILIBRIUM)
+    for tile, lam in ((16, 64), (8, 16), (32, 256)):   # q/2 odd or q < 2
+        with pytest.raises(lt.LatticeError):
+            g.set_dynamics(lt.DYNAMICS_RANDOM_SITE_BALANCED, tile, lam)
+    g.set_dynamics(lt.DYNAMICS_RANDOM_SITE_BALANCED, 16, 32)
+    g.close()
 
 
 def test_serial_limit_whole_lattice():
