@@ -27,14 +27,15 @@ struct lattice_batch {
     std::vector<std::pair<lattice *, int64_t>> pending;
     Geom *d_geoms = nullptr;
     int geoms_cap = 0;
-    uint2 *d_items = nullptr;  // tiled items, then wide items, then generic items
+    uint2 *d_items = nullptr;  // tiled items, then wide items, then Potts items, then generic items
     int items_cap = 0;
     Ctrl **d_ctrls = nullptr;
     int ctrls_cap = 0;
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S wide
-    // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1
+    // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1,
+    // Potts colour 0 / 1
     unsigned *d_counters = nullptr;
-    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0;
+    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0, grid_potts = 0;
     int grid_wide2[2] = {0, 0};   // 2D wide, Ising / North-East
     // resident lattices
     cudaStream_t res_stream = nullptr;
@@ -51,7 +52,7 @@ namespace {
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
 constexpr int kGraphMinSteps = 128;
-constexpr int kCounters = 10;
+constexpr int kCounters = 12;
 constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
 constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
 
@@ -72,9 +73,10 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
 
 // Item counts of the current active set, in this order in d_items: tiles
 // of Ising lattices, tiles of North-East lattices, 2D wide items of Ising
-// and of North-East lattices, 3D / spin-S wide items, generic chunks.
+// and of North-East lattices, 3D / spin-S wide items, Potts items, generic
+// chunks.
 struct Shape {
-    int n_lat, n_ising, n_ne, n_w2[2], n_wide, n_gen;
+    int n_lat, n_ising, n_ne, n_w2[2], n_wide, n_potts, n_gen;
     int tab_gen;   // largest table among the generic lattices
 };
 
@@ -111,7 +113,11 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
         for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide > 0; ++colour)
             e = launch_batch_wide3(ph.geoms, wide, sh.n_wide, b->d_counters + 4 + colour, colour,
                                    std::min(b->grid_wide, sh.n_wide), st);
-        const uint2 *gen = wide + sh.n_wide;
+        const uint2 *potts = wide + sh.n_wide;
+        for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_potts > 0; ++colour)
+            e = launch_batch_potts(ph.geoms, potts, sh.n_potts, b->d_counters + 10 + colour, colour,
+                                   std::min(b->grid_potts, sh.n_potts), st);
+        const uint2 *gen = potts + sh.n_potts;
         if (e == cudaSuccess && sh.n_gen > 0)
             e = launch_batch_generic(ph.geoms, gen, sh.n_gen, b->d_counters + 2, 0, 0,
                                      std::min(b->grid_generic, sh.n_gen), sh.tab_gen, st);
@@ -225,6 +231,7 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     b->grid_tiled_ne = batch_tiled_grid(true);
     b->grid_generic = batch_generic_grid();
     b->grid_wide = batch_wide3_grid();
+    b->grid_potts = batch_potts_grid();
     b->grid_wide2[0] = batch_wide_grid(false);
     b->grid_wide2[1] = batch_wide_grid(true);
     *out = b;
@@ -292,7 +299,7 @@ int lattice_batch_run(lattice_batch_t *b)
         const int64_t steps = work[n_active - 1].second - done;
         if (steps <= 0) continue;
         const size_t g0 = all_geoms.size();
-        std::vector<uint2> tiled, tiled_ne, w2[2], wide, gen;
+        std::vector<uint2> tiled, tiled_ne, w2[2], wide, potts, gen;
         int tab_gen = 0;
         for (size_t i = 0; i < n_active; ++i) {
             lattice *lt = work[i].first;
@@ -300,9 +307,10 @@ int lattice_batch_run(lattice_batch_t *b)
             all_ctrls.push_back(lt->ctrl);
             // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
             // the tiled items when their kernel is the tiled one; 3D and
-            // spin-S Ising lattices with L % 16 == 0 take the 3D wide items;
-            // the rest (other sizes, per-bond couplings, an explicit generic
-            // choice) go to the generic chunks.  Item lattice indexes are
+            // spin-S Ising lattices with L % 16 == 0 take the 3D wide items,
+            // Potts lattices with L % 16 == 0 the Potts items; the rest
+            // (other sizes, per-site disorder, an explicit generic choice)
+            // go to the generic chunks.  Item lattice indexes are
             // local to the phase.
             const int kern = choose_kernel(lt);
             const bool generic = kern == LAT_KERNEL_GENERIC;
@@ -317,6 +325,9 @@ int lattice_batch_run(lattice_batch_t *b)
             } else if (!generic && wide3_supported(lt->geom)) {
                 const int nw = wide3_items(lt->geom);
                 for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
+            } else if (!generic && potts_supported(lt->geom)) {
+                const int np = potts_items(lt->geom);
+                for (int k = 0; k < np; ++k) potts.push_back(make_uint2((unsigned)i, (unsigned)k));
             } else {
                 const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
                 const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
@@ -326,11 +337,11 @@ int lattice_batch_run(lattice_batch_t *b)
         }
         Spec sp;
         sp.sh = Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                      (int)wide.size(), (int)gen.size(), tab_gen};
+                      (int)wide.size(), (int)potts.size(), (int)gen.size(), tab_gen};
         sp.steps = steps;
         sp.geom_off = g0;
         sp.item_off = all_items.size();
-        for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &wide, &gen})
+        for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &wide, &potts, &gen})
             all_items.insert(all_items.end(), v->begin(), v->end());
         specs.push_back(sp);
         done += steps;

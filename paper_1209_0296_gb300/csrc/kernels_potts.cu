@@ -213,7 +213,99 @@ __global__ void __launch_bounds__(kThreads, (SH == 1 && D == 3) ? 3 : 4) k_potts
     }
 }
 
+// Batched form: a persistent grid takes (lattice, item) pairs from an
+// atomic counter; an item is kItemChunks x kThreads chunks of one colour of
+// one lattice.  The descriptor and table are reloaded only when a CTA moves
+// to another lattice (items are ordered by lattice).
+constexpr int kItemChunks = 4;
+
+__global__ void __launch_bounds__(kThreads, 3) k_batch_potts(const Geom *geoms, const uint2 *items, int n_items,
+                                                            unsigned *next_item, int colour)
+{
+    __shared__ TabEntry stab[kMaxTab];
+    __shared__ long long red[kThreads / 32];
+    __shared__ Geom sg;
+    __shared__ int cur;
+    int loaded = -1;
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = cur;
+        if (it >= n_items) break;
+        const uint2 w = items[it];
+        if ((int)w.x != loaded) {
+            if (threadIdx.x < sizeof(Geom) / 4)
+                reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
+                    reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x < (unsigned)sg.tab_n) stab[threadIdx.x] = sg.tab[threadIdx.x];
+            loaded = (int)w.x;
+            __syncthreads();
+        }
+        // register copies: no aliasing with shared-memory stores
+        const ViewP g = viewp(sg);
+        Ctrl *const ctrl = sg.ctrl;
+        const int which = (sg.two_S == 1 ? 0 : 2) + (sg.dims == 3 ? 1 : 0);
+        const uint32_t rows = sg.rows;
+        const unsigned long long sweep = ctrl->sweep;
+        PhiloxPre pp;
+        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
+        const uint32_t cpr = g.half >> 3;
+        const uint64_t total = (uint64_t)rows * cpr;
+        AccP acc;
+#pragma unroll 1
+        for (int c = 0; c < kItemChunks; ++c) {
+            const uint64_t t = ((uint64_t)w.y * kItemChunks + (uint64_t)c) * kThreads + threadIdx.x;
+            if (t >= total) break;
+            const uint32_t rr = (uint32_t)(t / cpr), kk = (uint32_t)(t % cpr);
+            if (which == 0) potts_chunk<2, 2>(g, stab, colour, sweep, pp, rr, kk, acc);
+            else if (which == 1) potts_chunk<2, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
+            else if (which == 2) potts_chunk<1, 2>(g, stab, colour, sweep, pp, rr, kk, acc);
+            else potts_chunk<1, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
+        }
+        if (colour == 1) {
+            unsigned long long *slot = series_slot(ctrl, sweep);
+            long long s;
+            s = block_sum_ll((long long)acc.bond, red);
+            if (threadIdx.x == 0) add_counter(slot + 0, s);
+            s = block_sum_ll((long long)acc.zero, red);
+            if (threadIdx.x == 0) add_counter(slot + 1, s);
+            s = block_sum_ll((long long)acc.other, red);
+            if (threadIdx.x == 0) add_counter(slot + 2, s);
+            if (g.ref != nullptr) {
+                s = block_sum_ll((long long)acc.acf, red);
+                if (threadIdx.x == 0) add_counter(acf_slot(ctrl, sweep), s);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+int potts_items(const Geom &g)
+{
+    const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
+    const uint64_t per = (uint64_t)kItemChunks * kThreads;
+    return (int)((chunks + per - 1) / per);
+}
+
+int batch_potts_grid()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_potts, kThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_batch_potts(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                               int colour, int grid, cudaStream_t st)
+{
+    k_batch_potts<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    return cudaGetLastError();
+}
 
 bool potts_supported(const Geom &g)
 {

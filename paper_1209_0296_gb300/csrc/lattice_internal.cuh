@@ -332,6 +332,10 @@ bool wide3_supported(const Geom &g);
 // q-state Potts model, 8 sites per thread (kernels_potts.cu)
 bool potts_supported(const Geom &g);
 cudaError_t launch_sweep_potts(const Geom &g, int off, cudaStream_t st);
+int potts_items(const Geom &g);   // batch items of one colour of one lattice
+int batch_potts_grid();
+cudaError_t launch_batch_potts(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
+                               int colour, int grid, cudaStream_t st);
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
 int wide3_items(const Geom &g);   // batch items of one colour of one lattice
 int batch_wide3_grid();

@@ -95,6 +95,41 @@ def test_potts_batch_with_ising():
     b.close()
 
 
+def test_potts_batch_mixed_paths_and_overlaps():
+    # Potts items (L % 16 == 0), generic chunks (L = 30, and an explicit
+    # generic choice), a reference state on two of them, uneven sweep counts
+    cfg = [(2, 48, 3, 0.9, 31, 23, lt.KERNEL_AUTO, True), (2, 30, 4, 0.8, 32, 19, lt.KERNEL_AUTO, False),
+           (3, 16, 3, 1.4, 33, 27, lt.KERNEL_AUTO, True), (2, 64, 5, 0.7, 34, 21, lt.KERNEL_GENERIC, False),
+           (2, 16, 2, 1.0, 35, 40, lt.KERNEL_AUTO, False)]
+    lats, ors = [], []
+    for dims, L, q, T, seed, n, kern, ref in cfg:
+        g = lt.Lattice(dims, L, q - 1, lt.POTTS, 1.0, 0.1, T, seed=seed, init=lt.INIT_RANDOM)
+        o = oracle.Lattice(dims, L, q - 1, oracle.POTTS, 1.0, 0.1, T, seed=seed, init=oracle.INIT_RANDOM)
+        g.set_kernel(kern)
+        if ref:
+            g.set_reference()
+            o.set_reference()
+        lats.append(g)
+        ors.append(o)
+    b = lt.Batch()
+    for g, c in zip(lats, cfg):
+        b.add(g, c[5])
+    b.run()
+    b.synchronize()
+    for g, o, c in zip(lats, ors, cfg):
+        n = c[5]
+        ser_o = o.sweep(n)
+        assert np.array_equal(g.get_spins(), o.spins), c
+        ser = g.series(0, n)
+        for k in ("bond", "mag", "up"):
+            assert np.array_equal(ser[k], ser_o[k]), (c, k)
+        if c[7]:
+            assert np.array_equal(g.autocorrelation(0, n)[0], ser_o["overlap"]), c
+    b.close()
+    for g in lats:
+        g.close()
+
+
 def test_potts_labels_and_refusals():
     g = lt.Lattice(2, 16, 2, lt.POTTS, 1.0, 0.0, 1.0, seed=1, init=lt.INIT_RANDOM)
     labels = np.random.default_rng(0).integers(0, 3, 256).astype(np.int8)
