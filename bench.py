@@ -361,6 +361,10 @@ def run_profile(args):
         import math
         g = lt.Lattice(2, args.profile_L, 2, lt.POTTS, 1.0, 0.0, 1.0 / math.log(1.0 + math.sqrt(3.0)), seed=7,
                        init=lt.INIT_RANDOM)
+    elif args.profile_model == "rfim":   # random-field Ising, h = J, T = 2, eta from default_rng(6)
+        import numpy as np
+        g = lt.Lattice(2, args.profile_L, 1, lt.ISING, 1.0, 1.0, 2.0, seed=7, init=lt.INIT_RANDOM)
+        g.set_fields(np.where(np.random.default_rng(6).random(args.profile_L ** 2) < 0.5, -1, 1).astype(np.int8))
     elif args.profile_model == "ising3d":   # 3D spin-1 at T = 2 + 7 * 2/15, random start (seed 11)
         g = lt.Lattice(3, args.profile_L, 2, lt.ISING, 1.0, 0.0, 2.0 + 7 * 2.0 / 15, seed=11,
                        init=lt.INIT_RANDOM)
@@ -686,7 +690,7 @@ def main():
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
     ap.add_argument("--profile-L", type=int, default=L)
-    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d", "potts"])
+    ap.add_argument("--profile-model", default="ising", choices=["ising", "ne", "ising3d", "potts", "rfim"])
     ap.add_argument("--profile-kernel", default="auto", choices=["auto", "tiled", "wide", "generic", "resident"])
     ap.add_argument("--profile-layout", default="int8", choices=["int8", "bitpacked"])
     ap.add_argument("--profile-dynamics", default="checkerboard", choices=["checkerboard", "random-site", "random-site-balanced"])
