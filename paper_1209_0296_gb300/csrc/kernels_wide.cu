@@ -228,15 +228,16 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             for (int w = 0; w < W; ++w) dr += ((Sn[w] ^ R1[w]) & M1) + ((O[w] ^ R0[w]) & M1);
             cnt.acf += 8 * W - byte_sum(dr);
         }
-        if constexpr (kFld) {
-            // field sum over both planes' 8W sites: eta_i s_i is down when
-            // exactly one of (s_i down: bit 1, eta_i = -1: bit 6) holds
-            uint32_t C0[W], ed = 0;
-            load_words<W>(reinterpret_cast<const int8_t *>(g.cpl) + (uint64_t)y * half + 4 * W * k, C0);
+    }
+    if constexpr (kFld) {
+        // field sum over this colour's 4W sites (final after this launch:
+        // each colour adds its own sites, so no launch reads the other
+        // plane's disorder bytes); eta_i s_i is down when exactly one of
+        // (s_i down: bit 1, eta_i = -1: bit 6) holds
+        uint32_t ed = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) ed += ((Sn[w] ^ (C[w] >> 5)) & M1) + ((O[w] ^ (C0[w] >> 5)) & M1);
-            cnt.fld += 8 * W - byte_sum(ed);
-        }
+        for (int w = 0; w < W; ++w) ed += (Sn[w] ^ (C[w] >> 5)) & M1;
+        cnt.fld += 4 * W - byte_sum(ed);
     }
 }
 
@@ -330,10 +331,8 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
          t += (uint64_t)gridDim.x * blockDim.x)
         wide_chunk<kNE, false, 4, false, kCpl, kFld>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
-    if (colour == 1) {
-        flush(v, sweep, cnt, kNE, red);
-        if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);
-    }
+    if (colour == 1) flush(v, sweep, cnt, kNE, red);
+    if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
 }
 
 // Batched form: a persistent grid takes (lattice, item) pairs from an
