@@ -327,10 +327,8 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
     const SweepView v = sweep_view(g);
     // Grid-stride over chunks with one resident wave of CTAs: the counter
     // reduction (and its barrier) happens once per CTA, not once per chunk.
-    const uint64_t total = (uint64_t)g.L * cpr;
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x)
-        wide_chunk<kNE, false, 4, false, kCpl, kFld>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+    for (GridWalk w((uint32_t)g.L, cpr); w.ok(); w.next())
+        wide_chunk<kNE, false, 4, false, kCpl, kFld>(v, sthr, colour, sweep, pp, (int)w.r, (int)w.k, cnt);
     if (colour == 1) flush(v, sweep, cnt, kNE, red);
     if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
 }

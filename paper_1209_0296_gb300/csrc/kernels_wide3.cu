@@ -191,12 +191,9 @@ __global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
     const uint32_t cpr = g.half >> 3;  // 8-site chunks per plane row
-    const uint64_t total = (uint64_t)g.rows * cpr;
     const View3 v = view3(g);
     Acc3 acc;
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x)
-        wide3_chunk<SH, TS, D>(v, stab, colour, sweep, pp, (uint32_t)(t / cpr), (uint32_t)(t % cpr), acc);
+    for (GridWalk w(g.rows, cpr); w.ok(); w.next()) wide3_chunk<SH, TS, D>(v, stab, colour, sweep, pp, w.r, w.k, acc);
     if (colour == 1) {
         unsigned long long *slot = series_slot(g.ctrl, sweep);
         long long v;
