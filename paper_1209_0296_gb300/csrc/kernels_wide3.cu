@@ -248,13 +248,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_wide3(const Geom *geoms, con
         PhiloxPre pp;
         philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
         const uint32_t cpr = g.half >> 3;
-        const uint64_t total = (uint64_t)g.rows * cpr;
+        const uint32_t total = g.rows * cpr;   // < 2^28 (N < 2^32)
         Acc3 acc;
 #pragma unroll 1
         for (int c = 0; c < kItemChunks; ++c) {
-            const uint64_t t = ((uint64_t)w.y * kItemChunks + (uint64_t)c) * kThreads + threadIdx.x;
+            const uint32_t t = (w.y * (uint32_t)kItemChunks + (uint32_t)c) * kThreads + threadIdx.x;
             if (t >= total) break;
-            const uint32_t rr = (uint32_t)(t / cpr), kk = (uint32_t)(t % cpr);
+            const uint32_t rr = t / cpr, kk = t - rr * cpr;
             if (spin_half) wide3_chunk<2, 1, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
             else if (spin_one3) wide3_chunk<1, 2, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
             else wide3_chunk<1, 0, 0>(g, stab, colour, sweep, pp, rr, kk, acc);
