@@ -102,11 +102,11 @@ LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigne
     const bool p1 = ((colour + y + z) & 1) != 0;
     const uint32_t nwr = half >> 2;
     if (!p1) {  // west is j-1 of the other plane, east is j
-        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k - 1 + nwr) % nwr];
+        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k - 1 + nwr, nwr)];
         Nb[0] = make_uint2(__funnelshift_l(prev, O.x, 8), __funnelshift_l(O.x, O.y, 8));
         Nb[1] = O;
     } else {    // west is j, east is j+1
-        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k + 2) % nwr];
+        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k + 2, nwr)];
         Nb[0] = O;
         Nb[1] = make_uint2(__funnelshift_r(O.x, O.y, 8), __funnelshift_r(O.y, next, 8));
     }

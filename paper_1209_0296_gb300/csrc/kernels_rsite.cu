@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_rsite_measure(Geom g, int off)
         // colour-1 site j sits at x = 2j + ((1 + y) & 1): its row neighbours
         // are colour-0 sites j-1, j (odd x... even x) or j, j+1
         const bool right = ((1 + y) & 1) != 0;
-        const uint32_t adj = p0[r0 + (right ? (W * k + W) % nwr : (W * k + nwr - 1) % nwr)];
+        const uint32_t adj = p0[r0 + wrap_once(right ? W * k + W : W * k + nwr - 1, nwr)];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             if (!right) {   // west is j-1, east is j

@@ -98,7 +98,7 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
     uint32_t adj;
     {
         const uint32_t w = p1 ? (uint32_t)(W * k + W) : (uint32_t)(W * k - 1 + nwr);
-        adj = reinterpret_cast<const uint32_t *>(row(oc, y))[w % nwr];
+        adj = reinterpret_cast<const uint32_t *>(row(oc, y))[wrap_once(w, nwr)];
     }
     uint32_t Lf[W], R[W];
 #pragma unroll

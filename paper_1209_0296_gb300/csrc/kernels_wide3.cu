@@ -106,12 +106,12 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
     const uint32_t nwr = half >> 2;
     uint2 Lf, R;
     if (!p1) {  // west is j-1 of the other plane, east is j
-        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k - 1 + nwr) % nwr];
+        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k - 1 + nwr, nwr)];
         Lf.x = __funnelshift_l(prev, O.x, 8);
         Lf.y = __funnelshift_l(O.x, O.y, 8);
         R = O;
     } else {    // west is j, east is j+1
-        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[(2 * k + 2) % nwr];
+        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k + 2, nwr)];
         Lf = O;
         R.x = __funnelshift_r(O.x, O.y, 8);
         R.y = __funnelshift_r(O.y, next, 8);

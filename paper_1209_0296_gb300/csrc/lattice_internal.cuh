@@ -255,6 +255,9 @@ LAT_HD uint64_t planar_index(const Geom &g, int x, int y, int z)
     return (uint64_t)c * g.plane + r * g.half + (uint64_t)(x >> 1);
 }
 
+// w mod n for w < 2n (a neighbour word index one step past either row end).
+LAT_HD uint32_t wrap_once(uint32_t w, uint32_t n) { return w >= n ? w - n : w; }
+
 // Spin value <-> state index (state 0 = most negative value).
 LAT_HD int spin_of_state(int two_S, int k) { return (two_S & 1) ? 2 * k - two_S : k - (two_S >> 1); }
 LAT_HD int state_of_spin(int two_S, int s) { return (two_S & 1) ? (s + two_S) >> 1 : s + (two_S >> 1); }
