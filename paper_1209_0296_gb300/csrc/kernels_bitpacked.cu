@@ -52,7 +52,7 @@ LAT_D uint32_t spread_nibble(uint32_t x, int q) { return (((x >> (4 * q)) & 0xFu
 // bits[(sweep+1) & 1]; colour 1 then works in place there and accumulates
 // the sweep's counters.
 template <bool kNE>
-__global__ void __launch_bounds__(kThreads) k_bits_half(Geom g, int colour, int off)
+__global__ void __launch_bounds__(kThreads, 4) k_bits_half(Geom g, int colour, int off)
 {
     __shared__ uint32_t sthr[16];
     __shared__ long long red[kThreads / 32];
@@ -64,11 +64,11 @@ __global__ void __launch_bounds__(kThreads) k_bits_half(Geom g, int colour, int 
     if (colour == 1) src = dst;
     const int L = g.L;
     const uint32_t bw = g.bw;
-    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;   // L * bw < 2^26
     long long bond = 0, mag = 0, up = 0, unfl = 0, acf = 0;
-    if (t < (uint64_t)L * bw) {
+    if (t < (uint32_t)L * bw) {
         const int y = (int)(t / bw);
-        const int k = (int)(t % bw);
+        const int k = (int)(t - (uint32_t)y * bw);
         const int oc = 1 - colour;
         const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
         const int km = k == 0 ? (int)bw - 1 : k - 1, kp = k == (int)bw - 1 ? 0 : k + 1;

@@ -65,7 +65,7 @@ LAT_D void half_sweep_group(const Geom &g, const TabEntry *stab, int colour, uns
     int8_t *dst = g.s[(sweep + 1) & 1];
     if (colour == 1) src = dst;
     const bool measure = (colour == 1);
-    const uint32_t r = (uint32_t)(t / g.G), m = (uint32_t)(t % g.G);
+    const uint32_t r = (uint32_t)t / g.G, m = (uint32_t)t - r * g.G;   // rows * G < 2^31
     const int L = g.L;
     const int y = (int)(r % (uint32_t)L), z = (int)(r / (uint32_t)L);
     const int p = (colour + y + z) & 1;
