@@ -138,8 +138,6 @@ struct Ctrl {
     unsigned long long *series;      // [series_cap][4] exact counters
     unsigned long long series_base;  // global sweep index of series[0]
     unsigned long long series_cap;   // sweeps the series buffer can hold
-    unsigned int error;              // device error word (0 = none)
-    unsigned int pad;
     unsigned long long *acf;         // [series_cap] sum_i s_i(t) s_i(ref), same indexing
     unsigned long long *fld;         // [series_cap] sum_i eta_i s_i (per-site field signs), same indexing
 };

@@ -107,3 +107,17 @@ def test_invalid_and_oversized_requests():
         srv.poll(12345)
     assert e.value.code == -8
     srv.close()
+
+
+def test_drain_times_out_on_the_host_then_finishes():
+    # a bounded wait that runs out: drain returns LAT_ETIMEOUT (the request
+    # keeps running), and a later unbounded drain sees it finish
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=8, chunk_sweeps=256)
+    rid = srv.submit(dims=2, L=2048, model=lt.ISING, T_or_c=2.3, seed=3, sweeps=60000)
+    with pytest.raises(lt.LatticeError) as err:
+        srv.drain(0.001)
+    assert err.value.code == -4
+    srv.drain(0.0)
+    res = srv.poll(rid)
+    assert res is not None and res["status"] == 0 and res["sweeps_done"] == 60000
+    srv.close()
