@@ -100,6 +100,18 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         const uint32_t w = p1 ? (uint32_t)(W * k + W) : (uint32_t)(W * k - 1 + nwr);
         adj = reinterpret_cast<const uint32_t *>(row(oc, y))[wrap_once(w, nwr)];
     }
+    // Ising in the two-launch kernels: the draws do not depend on the loaded
+    // words, so they are made while the loads are in flight (a North-East
+    // item may skip them: its locked sites need none).
+    constexpr bool kEarly = !kNE && !kPre && !kInPlace;
+    U4 u[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) u[w] = U4{0, 0, 0, 0};
+    if constexpr (kEarly) {
+        const uint32_t g0 = (uint32_t)y * g.G + (uint32_t)(W * k);
+#pragma unroll
+        for (int w = 0; w < W; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)colour);
+    }
     uint32_t Lf[W], R[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -156,13 +168,10 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
     }
     // An item that needs no draw has t' = all ones at every site, so any u
     // accepts exactly as "no draw" would.
-    U4 u[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) u[w] = U4{0, 0, 0, 0};
     if constexpr (kPre) {   // draws made by the caller (same groups, same counters)
 #pragma unroll
         for (int w = 0; w < W; ++w) u[w] = upre[w];
-    } else if (need) {
+    } else if (!kEarly && need) {
         const uint32_t g0 = (uint32_t)y * g.G + (uint32_t)(W * k);
 #pragma unroll
         for (int w = 0; w < W; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)colour);
