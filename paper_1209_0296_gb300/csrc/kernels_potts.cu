@@ -98,6 +98,12 @@ LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigne
         Nb[4] = ld(oc, (uint32_t)(y + L * (z == 0 ? L - 1 : z - 1)));
         Nb[5] = ld(oc, (uint32_t)(y + L * (z == L - 1 ? 0 : z + 1)));
     }
+    // draws first: they do not depend on the loads in flight
+    const uint32_t g0 = r * g.G + ((8u * k) >> SH);   // first Philox group of the chunk
+    constexpr int kCalls = 8 >> SH;
+    U4 u[kCalls];
+#pragma unroll
+    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
     // row-shifted neighbours: x = 2j + p with p = (colour + y + z) & 1
     const bool p1 = ((colour + y + z) & 1) != 0;
     const uint32_t nwr = half >> 2;
@@ -111,11 +117,6 @@ LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigne
         Nb[1] = make_uint2(__funnelshift_r(O.x, O.y, 8), __funnelshift_r(O.y, next, 8));
     }
     // proposals (§III.A step 4 for labels: a uniform other label)
-    const uint32_t g0 = r * g.G + ((8u * k) >> SH);   // first Philox group of the chunk
-    constexpr int kCalls = 8 >> SH;
-    U4 u[kCalls];
-#pragma unroll
-    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
     uint2 Sn = make_uint2(0u, 0u);
     if constexpr (SH == 2) {
         Sn = make_uint2(S.x ^ 0x01010101u, S.y ^ 0x01010101u);   // q = 2: the other label

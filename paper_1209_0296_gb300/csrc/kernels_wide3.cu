@@ -101,6 +101,12 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
         Zd = *reinterpret_cast<const uint2 *>(row(oc, zm) + 8 * k);
         Zu = *reinterpret_cast<const uint2 *>(row(oc, zp) + 8 * k);
     }
+    // draws first: they do not depend on the loads in flight
+    const uint32_t g0 = r * g.G + ((8u * k) >> SH);  // first Philox group of the chunk
+    constexpr int kCalls = 8 >> SH;
+    U4 u[kCalls];
+#pragma unroll
+    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
     // row-shifted neighbours: x = 2j + p with p = (colour + y + z) & 1
     const bool p1 = ((colour + y + z) & 1) != 0;
     const uint32_t nwr = half >> 2;
@@ -126,11 +132,6 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
         nhi += add_bytes(Zd.y, off) + add_bytes(Zu.y, off);
     }
     const int noff = 2 * dims * smax;
-    const uint32_t g0 = r * g.G + ((8u * k) >> SH);  // first Philox group of the chunk
-    constexpr int kCalls = 8 >> SH;
-    U4 u[kCalls];
-#pragma unroll
-    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
     uint32_t out_lo = 0, out_hi = 0;
     uint2 RS = make_uint2(0u, 0u), RO = RS;   // reference words (colour 1 only)
     const bool has_ref = colour == 1 && g.ref != nullptr;
