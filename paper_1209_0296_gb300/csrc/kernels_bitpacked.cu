@@ -115,7 +115,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_bits_half(Geom g, int colour, i
                 t3 |= 0u - ((lk >> 3) & 1u);
             }
             uint32_t acc = 0xFu;
-            if ((t0 & t1 & t2 & t3) != 0xFFFFFFFFu) {
+            // Ising draws every group (a group that needs none is rare and
+            // the branch costs more than it saves); a North-East group whose
+            // sites are all locked or always-accepted skips its draw
+            if (!kNE || (t0 & t1 & t2 & t3) != 0xFFFFFFFFu) {
                 const uint32_t grp = (uint32_t)y * g.G + 8u * (uint32_t)k + (uint32_t)q;
                 const U4 u = philox_item(pp, grp, (uint32_t)colour);
                 acc = (u.x <= t0 ? 1u : 0u) | (u.y <= t1 ? 2u : 0u) | (u.z <= t2 ? 4u : 0u) |

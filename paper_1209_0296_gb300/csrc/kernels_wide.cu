@@ -310,10 +310,8 @@ LAT_D void flush_one(unsigned long long *dst, int v, int (*red)[5])
 // table (t' = thr - 1 form, all ones = always), index sd << 3 | nd as for
 // entries 0..15.
 template <bool kNE, bool kCpl, bool kFld>
-__global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
+LAT_D void wide_half_body(const Geom &g, int colour, int off, uint32_t *sthr, int (*red)[5])
 {
-    __shared__ uint32_t sthr[kFld ? 32 : 16];
-    __shared__ int red[kThreads / 32][5];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
     if constexpr (kFld) {
         if (threadIdx.x >= 16 && threadIdx.x < 32) {
@@ -340,6 +338,23 @@ __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int 
         wide_chunk<kNE, false, 4, false, kCpl, kFld>(v, sthr, colour, sweep, pp, (int)w.r, (int)w.k, cnt);
     if (colour == 1) flush(v, sweep, cnt, kNE, red);
     if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
+}
+
+template <bool kCpl, bool kFld>
+__global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
+{
+    __shared__ uint32_t sthr[kFld ? 32 : 16];
+    __shared__ int red[kThreads / 32][5];
+    wide_half_body<false, kCpl, kFld>(g, colour, off, sthr, red);
+}
+
+// North-East: bounded to three CTAs per SM (80 registers); unbounded it
+// takes 117 and only two fit.
+__global__ void __launch_bounds__(kThreads, 3) k_wide_half_ne(Geom g, int colour, int off)
+{
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kThreads / 32][5];
+    wide_half_body<true, false, false>(g, colour, off, sthr, red);
 }
 
 // Batched form: a persistent grid takes (lattice, item) pairs from an
@@ -540,8 +555,8 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
     // Ising with couplings and per-site field signs
     const int m = g.model == LAT_NE ? 1 : (g.cpl != nullptr ? (fields ? 3 : 2) : 0);
     using K = void (*)(Geom, int, int);
-    const K kern[4] = {k_wide_half<false, false, false>, k_wide_half<true, false, false>,
-                       k_wide_half<false, true, false>, k_wide_half<false, true, true>};
+    const K kern[4] = {k_wide_half<false, false>, k_wide_half_ne, k_wide_half<true, false>,
+                       k_wide_half<true, true>};
     // one wave: SMs x resident CTAs per SM (queried once per instantiation)
     static int resident[4] = {0, 0, 0, 0};
     if (resident[m] == 0) {
