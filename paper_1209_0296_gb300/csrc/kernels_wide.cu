@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wide_half_ne(Geom g, int colour
 constexpr int kItemChunks = 4;
 
 template <bool kNE>
-__global__ void __launch_bounds__(kThreads) k_batch_wide(const Geom *geoms, const uint2 *items, int n_items,
+__global__ void __launch_bounds__(kThreads, kNE ? 2 : 3) k_batch_wide(const Geom *geoms, const uint2 *items, int n_items,
                                                         unsigned *next_item, int colour)
 {
     __shared__ uint32_t sthr[16];
