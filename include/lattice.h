@@ -101,8 +101,9 @@ enum lattice_kernel {
     LAT_KERNEL_TILED = 2,   /* one launch per sweep, shared-memory tiles with halo
                                recompute; 2D spin-1/2 (Ising and North-East), L % 32 == 0 */
     LAT_KERNEL_WIDE = 3,    /* two launches per sweep, several sites per thread: 2D
-                               spin-1/2 (Ising and North-East, L % 32 == 0), or Ising
-                               in 3D / with spin S > 1/2 (L % 16 == 0) */
+                               spin-1/2 (Ising and North-East, L % 32 == 0; with
+                               coupling and field signs too), Ising in 3D / with
+                               spin S > 1/2 (L % 16 == 0), or Potts (L % 16 == 0) */
     LAT_KERNEL_RESIDENT = 4 /* one launch for many sweeps: one CTA holds the whole
                                lattice in shared memory; 2D spin-1/2 (Ising and
                                North-East), L % 32 == 0, L^2 (+ L^2/4 for North-East)
