@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int
 // CTA moves to another lattice (items are ordered by lattice).
 constexpr int kItemChunks = 4;
 
-__global__ void __launch_bounds__(kThreads) k_batch_wide3(const Geom *geoms, const uint2 *items, int n_items,
+__global__ void __launch_bounds__(kThreads, 4) k_batch_wide3(const Geom *geoms, const uint2 *items, int n_items,
                                                          unsigned *next_item, int colour)
 {
     __shared__ TabEntry stab[kMaxTab];
