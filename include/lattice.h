@@ -75,7 +75,7 @@ enum lattice_status {
 
 /* LAT_POTTS: the q-state Potts model, H = -J sum_<ij> delta(s_i, s_j) -
  * h sum_i delta(s_i, 0), with q = two_S + 1 states (2..9) stored as the
- * labels 0..q-1 (the paper's §III.C: the method suits the Potts model). */
+ * labels 0..q-1 (the remark closing the paper's §III.A: the method suits the Potts model). */
 enum lattice_model { LAT_ISING = 0, LAT_NE = 1, LAT_POTTS = 2 };
 enum lattice_init {
     LAT_INIT_COLD = 0,        /* every spin at its top value (+1 for spin-1/2) */

@@ -1,6 +1,6 @@
 // kernels_potts.cu -- two launches per sweep (one per colour, the kernel
 // boundary being the device-wide barrier of §III.A steps 6-7) for the
-// q-state Potts model (§III.C: the method carries over to Potts spins),
+// q-state Potts model (the remark closing §III.A: the method carries over to it),
 // int8 labels 0..q-1 in the checkerboard-planar layout, 2D or 3D, L a
 // multiple of 16.
 //

@@ -1,4 +1,4 @@
-"""Pins of the oracle's q-state Potts model (the paper's §III.C remark that
+"""Pins of the oracle's q-state Potts model (the remark closing the paper's §III.A that
 the method suits the Potts model; H = -J sum_<ij> delta(s_i, s_j) - h sum_i
 delta(s_i, 0), labels 0..q-1, q = two_S + 1; CPU only).
 
