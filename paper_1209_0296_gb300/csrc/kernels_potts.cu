@@ -116,7 +116,7 @@ LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigne
         Nb[0] = O;
         Nb[1] = make_uint2(__funnelshift_r(O.x, O.y, 8), __funnelshift_r(O.y, next, 8));
     }
-    // proposals (§III.A step 4 for labels: a uniform other label)
+    // proposals: a uniform other label (the spin-S proposal carried over to labels)
     uint2 Sn = make_uint2(0u, 0u);
     if constexpr (SH == 2) {
         Sn = make_uint2(S.x ^ 0x01010101u, S.y ^ 0x01010101u);   // q = 2: the other label
