@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bits_half(Geom g, int colour, i
         philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
         const char *tb = reinterpret_cast<const char *>(sthr);
         uint32_t flip = 0;
-#pragma unroll 2
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
             // byte offsets (index sd<<3 | nd, 4 bytes per entry) of the 4 sites
             const uint32_t idx = (spread_nibble(b0, q) << 2) | (spread_nibble(b1, q) << 3) |
