@@ -331,7 +331,10 @@ static int ensure_graph(lattice *lt)
 // untimed replay), so launch overheads count as they will.  The timed sweeps
 // are the caller's own sweeps: every kernel produces the same bits, so
 // tuning changes no result.  Choices are cached per (model, L) for the life
-// of the process.
+// of the process and, when LATTICE_TUNE_CACHE names a file, across
+// processes: one JSON object per line, {"model": m, "L": L, "kernel": k,
+// "tile_h": h}, read before the first lookup and appended to after each new
+// tuning.  An entry the lattice cannot run (a hand-edited file) is ignored.
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneChoice {
@@ -339,7 +342,56 @@ struct TuneChoice {
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, TuneChoice> g_tune;
+bool g_tune_file_read = false;
 constexpr int kTuneSweeps = 4;
+
+const char *tune_cache_path()
+{
+    const char *p = std::getenv("LATTICE_TUNE_CACHE");
+    return (p != nullptr && *p != '\0') ? p : nullptr;
+}
+
+// With g_tune_mu held: merge the cache file's entries (once per process).
+void read_tune_file()
+{
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *path = tune_cache_path();
+    if (path == nullptr) return;
+    FILE *f = std::fopen(path, "r");
+    if (f == nullptr) return;
+    char line[256];
+    while (std::fgets(line, sizeof line, f) != nullptr) {
+        int m = 0, L = 0, k = 0, h = 0;
+        if (std::sscanf(line, " {\"model\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d}", &m, &L, &k,
+                        &h) == 4)
+            g_tune[std::make_pair(m, L)] = TuneChoice{k, h};
+    }
+    std::fclose(f);
+}
+
+// With g_tune_mu held: append one tuned choice to the cache file.
+void append_tune_file(const std::pair<int, int> &key, const TuneChoice &c)
+{
+    const char *path = tune_cache_path();
+    if (path == nullptr) return;
+    FILE *f = std::fopen(path, "a");
+    if (f == nullptr) return;
+    std::fprintf(f, "{\"model\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d}\n", key.first, key.second,
+                 c.kernel, c.tile_h);
+    std::fclose(f);
+}
+
+// Whether a cached choice runs on this lattice.
+bool tune_choice_ok(const lattice *lt, const TuneChoice &c)
+{
+    switch (c.kernel) {
+    case LAT_KERNEL_WIDE: return wide_supported(lt->geom);
+    case LAT_KERNEL_TILED: return tiled_supported(lt->geom) && tile_shape_ok(0, c.tile_h);
+    case LAT_KERNEL_RESIDENT: return resident_supported(lt->geom);
+    default: return false;
+    }
+}
 
 // Time kTuneSweeps sweeps of the current candidate after kTuneSweeps untimed
 // ones (2 * kTuneSweeps sweeps in all, enqueued on the lattice's stream).
@@ -383,8 +435,9 @@ static int autotune(lattice *lt, int64_t &left)
     const std::pair<int, int> key(lt->P.model, lt->P.L);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
+        read_tune_file();
         auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
+        if (it != g_tune.end() && tune_choice_ok(lt, it->second)) {
             lt->tuned_kernel = it->second.kernel;
             if (lt->tile_h == 0) lt->tile_h = it->second.tile_h;
             return LAT_OK;
@@ -425,6 +478,7 @@ static int autotune(lattice *lt, int64_t &left)
     lt->graph_valid = false;
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = pick;
+    append_tune_file(key, pick);
     return LAT_OK;
 }
 
