@@ -282,7 +282,8 @@ int lattice_device_spins(lattice_t *lat, void **dev_ptr, size_t *bytes);
  * tile_h rows; 0 = default) and the sweeps per CUDA-graph replay
  * (0 = default).  LAT_ENOTSUP if the kernel does not cover the lattice.
  * With LAT_KERNEL_AUTO a 2D spin-1/2 int8 lattice is tuned by its first
- * sweep call of at least 32 sweeps: each candidate kernel runs a few of the
+ * sweep call of at least 24 sweeps (32 when the resident kernel is a
+ * candidate): each candidate kernel runs 8 of the
  * caller's sweeps (same bits whichever runs) and the fastest is kept for
  * that (model, L) for the life of the process.  If the environment variable
  * LATTICE_TUNE_CACHE names a file, the choices also persist there, one JSON
