@@ -25,8 +25,8 @@
 // assembled with masks only.  The acceptance table is held as t' = thr - 1
 // (all ones = accept without a draw), so a move is accepted iff u <= t';
 // lattices whose table has a never-accept entry (thr = 0, possible only for
-// dE/T > 22) use the generic kernel.  The Philox call is skipped when none
-// of the four sites needs a draw.
+// dE/T > 22) use the generic kernel.  For North-East the Philox call is
+// skipped when none of the sites needs a draw (locked sites need none).
 #include "lattice_internal.cuh"
 
 namespace lat {
@@ -162,10 +162,11 @@ LAT_D void do_pair(const Tile &t, const uint32_t *sthr, const PhiloxPre &pp, int
     else b.need = false;
     const bool need = active && (a.need || b.need);
     // An item that needs no draw has t' = all ones at every site, so any u
-    // accepts exactly as "no draw" would: the warp skips Philox only when no
-    // lane needs it, and otherwise every lane takes the (unused) draws.
+    // accepts exactly as "no draw" would: a North-East warp skips Philox only
+    // when no lane needs it, and otherwise every lane takes the (unused)
+    // draws; Ising always draws (an item needing none is rare).
     U4 ua = U4{0u, 0u, 0u, 0u}, ub = ua;
-    if (__any_sync(0xffffffffu, need)) {
+    if (!kNE || __any_sync(0xffffffffu, need)) {
         ua = philox_item(pp, grp_a, (uint32_t)C);
         if (two) ub = philox_item(pp, grp_b, (uint32_t)C);
     }
@@ -279,7 +280,7 @@ LAT_D void sweep_tile(const SweepView g, const uint32_t *sthr, int bx, int by, i
             const int wx = want ? -1 : nw;
             if (want) prepare<kNE, 0, 1>(t, sthr, ry, wx, ia);
             else prepare<kNE, 0, 0>(t, sthr, ry, wx, ia);
-            const U4 u = ia.need ? philox_item(pp, grp, 0u) : U4{0u, 0u, 0u, 0u};
+            const U4 u = (!kNE || ia.need) ? philox_item(pp, grp, 0u) : U4{0u, 0u, 0u, 0u};
             t.at(0, ry, wx) = finish<kNE>(ia, u, cha);
         }
     }
