@@ -340,12 +340,21 @@ LAT_D void wide_half_body(const Geom &g, int colour, int off, uint32_t *sthr, in
     if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
 }
 
-template <bool kCpl, bool kFld>
+template <bool kCpl>
 __global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
 {
-    __shared__ uint32_t sthr[kFld ? 32 : 16];
+    __shared__ uint32_t sthr[16];
     __shared__ int red[kThreads / 32][5];
-    wide_half_body<false, kCpl, kFld>(g, colour, off, sthr, red);
+    wide_half_body<false, kCpl, false>(g, colour, off, sthr, red);
+}
+
+// Couplings and field signs: bounded to three CTAs per SM (80 registers);
+// unbounded it takes 120 and only two fit.
+__global__ void __launch_bounds__(kThreads, 3) k_wide_half_fld(Geom g, int colour, int off)
+{
+    __shared__ uint32_t sthr[32];
+    __shared__ int red[kThreads / 32][5];
+    wide_half_body<false, true, true>(g, colour, off, sthr, red);
 }
 
 // North-East: bounded to three CTAs per SM (80 registers); unbounded it
@@ -555,8 +564,7 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
     // Ising with couplings and per-site field signs
     const int m = g.model == LAT_NE ? 1 : (g.cpl != nullptr ? (fields ? 3 : 2) : 0);
     using K = void (*)(Geom, int, int);
-    const K kern[4] = {k_wide_half<false, false>, k_wide_half_ne, k_wide_half<true, false>,
-                       k_wide_half<true, true>};
+    const K kern[4] = {k_wide_half<false>, k_wide_half_ne, k_wide_half<true>, k_wide_half_fld};
     // one wave: SMs x resident CTAs per SM (queried once per instantiation)
     static int resident[4] = {0, 0, 0, 0};
     if (resident[m] == 0) {
