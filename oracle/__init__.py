@@ -201,10 +201,11 @@ class Lattice:
         """Advance n sweeps; returns dict of per-sweep int64 series (bond, mag, up,
         unflipped, and "overlap" = sum_i s_i(t) s_i(0) when a reference is set)."""
         if self.ref is not None:
-            out = {k: np.zeros(n, dtype=np.int64) for k in ("bond", "mag", "up", "unflipped", "overlap")}
+            keys = ("bond", "mag", "up", "unflipped", "field")
+            out = {k: np.zeros(n, dtype=np.int64) for k in keys + ("overlap",)}
             for k in range(n):      # one sweep at a time, the overlap after each
                 one = self._sweep(1)
-                for key in ("bond", "mag", "up", "unflipped"):
+                for key in keys:
                     out[key][k] = one[key][0]
                 out["overlap"][k] = self.overlap()
             return out
