@@ -261,7 +261,7 @@ def run_gpu(args):
     prof = load_profile_numbers(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": prof.get("traffic_bytes_per_sweep"),
-                "kernel": "k_sweep_tiled<Ising>" if kname == "tiled" else "k_wide_half<Ising> x2",
+                "kernel": "k_sweep_tiled<Ising>" if kname == "tiled" else "k_wide_pipe<colour 0, colour 1>",
                 "peak_kind": peak_kind + " (copy bandwidth)",
                 "bytes_per_sweep": alg_bytes,
                 "avg_sweep_us": avg_kernel_us}

@@ -12,6 +12,12 @@
 // then updates s[(sweep+1) & 1] in place and reduces the sweep's counters.
 // Neighbour counts, thresholds and acceptance are those of the tiled kernel
 // (bytes 0x01 / 0xFF, bit-sliced adder, t' = thr - 1 table).
+//
+// Uniform Ising lattices run k_wide_pipe: each thread walks one chunk
+// column down the rows with two chunks in flight, so the Philox draws of
+// one chunk (wide multiplies) and the Metropolis step of the other (logic)
+// share each instruction block.  North-East lattices and lattices with
+// per-site disorder run k_wide_half_* (one chunk at a time, grid-stride).
 #include <algorithm>
 
 #include "lattice_internal.cuh"
@@ -340,12 +346,12 @@ LAT_D void wide_half_body(const Geom &g, int colour, int off, uint32_t *sthr, in
     if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
 }
 
-template <bool kCpl>
-__global__ void __launch_bounds__(kThreads) k_wide_half(Geom g, int colour, int off)
+// Per-bond couplings (Eq. 1, J_ij = J eps_ij), uniform field.
+__global__ void __launch_bounds__(kThreads) k_wide_half_cpl(Geom g, int colour, int off)
 {
     __shared__ uint32_t sthr[16];
     __shared__ int red[kThreads / 32][5];
-    wide_half_body<false, kCpl, false>(g, colour, off, sthr, red);
+    wide_half_body<false, true, false>(g, colour, off, sthr, red);
 }
 
 // Couplings and field signs: bounded to three CTAs per SM (80 registers);
@@ -364,6 +370,200 @@ __global__ void __launch_bounds__(kThreads, 3) k_wide_half_ne(Geom g, int colour
     __shared__ uint32_t sthr[16];
     __shared__ int red[kThreads / 32][5];
     wide_half_body<true, false, false>(g, colour, off, sthr, red);
+}
+
+// ---------------------------------------------------------------------
+// Software-pipelined two-launch Ising sweep (uniform J and h, no per-site
+// disorder).  Same chunks, draws, table and bits as wide_chunk<false>; the
+// difference is the schedule.  A chunk costs two kinds of work that load
+// different pipes: its four Philox4x32-10 calls (wide multiplies on the
+// FMA pipe) and the Metropolis step (logic on the ALU pipe).  Done one
+// after the other they keep one pipe idle while the other works, so each
+// iteration here loads and draws chunk i+1 in the same straight-line block
+// as the Metropolis step of chunk i, and the two streams interleave.
+// ---------------------------------------------------------------------
+struct WideIn {
+    uint32_t S[4], O[4], U[4], D[4];
+    uint32_t adj;
+};
+
+// What one thread needs to walk its chunk column k (16 sites) down the
+// rows of one colour: the rows it visits are y0, y0 + rs, y0 + 2 rs, ...
+// with rs * cpr threads in the grid, so the column, its row-end neighbour
+// word and its base addresses are fixed and a row costs a few 32-bit adds.
+template <int kColour>
+struct ColWalk {
+    const int8_t *pS;      // src, this colour's plane, + 16k
+    const int8_t *pO;      // src, the other plane, + 16k
+    const int8_t *pOrow;   // src, the other plane (row starts)
+    int8_t *dS;            // dst, this colour's plane, + 16k
+    int8_t *dO;            // dst, plane 1, + 16k (colour 0 copies the colour-1 sites)
+    const int8_t *r1, *r0; // reference planes 1 and 0, + 16k (or null)
+    uint32_t half, L, G, k;
+    uint32_t adjb0, adjb1; // byte offset in the row of the neighbour word past the chunk end, x parity 0 / 1
+};
+
+template <int kColour>
+LAT_D ColWalk<kColour> col_walk(const SweepView &g, const int8_t *src, int8_t *dst, uint32_t k)
+{
+    constexpr int oc = 1 - kColour;
+    ColWalk<kColour> c;
+    const uint32_t plane = (uint32_t)g.plane;   // N < 2^32, so a plane is < 2^31 bytes
+    c.pOrow = src + (size_t)oc * plane;
+    c.pS = src + (size_t)kColour * plane + 16 * k;
+    c.pO = c.pOrow + 16 * k;
+    c.dS = dst + (size_t)kColour * plane + 16 * k;
+    c.dO = dst + (size_t)plane + 16 * k;
+    c.r1 = g.ref ? g.ref + (size_t)plane + 16 * k : nullptr;
+    c.r0 = g.ref ? g.ref + 16 * k : nullptr;
+    c.half = g.half;
+    c.L = (uint32_t)g.L;
+    c.G = g.G;
+    c.k = k;
+    const uint32_t nwr = g.half >> 2;   // 4-byte words per plane row
+    c.adjb0 = 4u * wrap_once(4u * k - 1u + nwr, nwr);   // x = 2j: west word before the chunk
+    c.adjb1 = 4u * wrap_once(4u * k + 4u, nwr);         // x = 2j+1: east word after it
+    return c;
+}
+
+// Loads of the walk's chunk in plane row y.
+template <int kColour>
+LAT_D void col_load(const ColWalk<kColour> &c, uint32_t y, WideIn &in)
+{
+    const uint32_t oy = y * c.half;
+    const uint32_t oym = y == 0 ? oy + (c.L - 1) * c.half : oy - c.half;
+    const uint32_t oyp = y == c.L - 1 ? 0u : oy + c.half;
+    load_words<4>(c.pS + oy, in.S);
+    load_words<4>(c.pO + oy, in.O);
+    load_words<4>(c.pO + oym, in.U);   // north
+    load_words<4>(c.pO + oyp, in.D);   // south
+    in.adj = *reinterpret_cast<const uint32_t *>(c.pOrow + oy + (((kColour + y) & 1) ? c.adjb1 : c.adjb0));
+}
+
+// The four Philox groups of the walk's chunk in plane row y.
+template <int kColour>
+LAT_D void col_draws(const PhiloxPre &pp, const ColWalk<kColour> &c, uint32_t y, U4 (&u)[4])
+{
+    const uint32_t g0 = y * c.G + 4u * c.k;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)kColour);
+}
+
+// The Metropolis step of one loaded chunk: neighbour counts, table, accept
+// iff u <= t', write; colour 1 also counts bonds, magnetisation and up
+// sites (and the overlap with the reference when kRef).
+template <int kColour, bool kRef>
+LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y, const WideIn &in,
+                    const U4 (&u)[4], Counts &cnt)
+{
+    const uint32_t oy = y * c.half;
+    const bool p1 = ((kColour + y) & 1) != 0;
+    const char *tb = reinterpret_cast<const char *>(sthr);
+    const uint32_t M1 = 0x02020202u;
+    uint32_t Sn[4], ue = 0, dn = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        uint32_t Lf, R;
+        if (!p1) {   // x = 2j: west is j-1 of the other plane, east is j
+            Lf = __funnelshift_l(w == 0 ? in.adj : in.O[w - 1], in.O[w], 8);
+            R = in.O[w];
+        } else {     // x = 2j+1: west is j, east is j+1
+            Lf = in.O[w];
+            R = __funnelshift_r(in.O[w], w == 3 ? in.adj : in.O[w + 1], 8);
+        }
+        const uint32_t Uw = in.U[w], Dw = in.D[w];
+        const uint32_t s1 = Uw ^ Dw ^ Lf;
+        const uint32_t c1 = (Uw & Dw) | (Uw & Lf) | (Dw & Lf);
+        const uint32_t b0 = s1 ^ R;
+        const uint32_t b1 = c1 ^ (s1 & R);
+        const uint32_t b2 = c1 & s1 & R;
+        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (in.S[w] & 0x20202020u);
+        const uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
+        const uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
+        const uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
+        const uint32_t t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
+        const uint32_t acc = (u[w].x <= t0 ? 1u : 0u) | (u[w].y <= t1 ? 2u : 0u) | (u[w].z <= t2 ? 4u : 0u) |
+                             (u[w].w <= t3 ? 8u : 0u);
+        const uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu;   // 0xFE at flipped sites
+        Sn[w] = in.S[w] ^ F;
+        if constexpr (kColour == 1) {
+            ue += ((Uw ^ Sn[w]) & M1) + ((Dw ^ Sn[w]) & M1) + ((Lf ^ Sn[w]) & M1) + ((R ^ Sn[w]) & M1);
+            dn += (Sn[w] & M1) + (in.O[w] & M1);
+        }
+    }
+    store_words<4>(c.dS + oy, Sn);
+    if constexpr (kColour == 0) store_words<4>(c.dO + oy, in.O);
+    if constexpr (kColour == 1) {
+        const int d2 = byte_sum(dn);
+        cnt.bond += 64 - byte_sum(ue);
+        cnt.mag += 32 - d2;
+        cnt.up += 32 - (d2 >> 1);
+        if constexpr (kRef) {
+            uint32_t R1[4], R0[4], dr = 0;
+            load_words<4>(c.r1 + oy, R1);
+            load_words<4>(c.r0 + oy, R0);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) dr += ((Sn[w] ^ R1[w]) & M1) + ((in.O[w] ^ R0[w]) & M1);
+            cnt.acf += 32 - byte_sum(dr);
+        }
+    }
+}
+
+constexpr int kPipeMinB = 2;   // CTAs per SM (the two chunks in flight need ~100 registers)
+
+template <int kColour, bool kRef>
+__global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int off)
+{
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kThreads / 32][5];
+    if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
+    __syncthreads();
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
+    const SweepView v = sweep_view(g);
+    const int8_t *src = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *dst = (sweep & 1) ? v.s0 : v.s1;
+    if (kColour == 1) src = dst;   // colour 1 updates the new buffer in place
+    Counts cnt;
+    // thread -> (chunk column k, first row y); rs rows between visits.  The
+    // launch has at least cpr threads, and rs * cpr of them work.
+    const uint32_t cpr = g.half >> 4;
+    const uint32_t rs = (gridDim.x * blockDim.x) / cpr;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t y = gt / cpr;
+    const uint32_t k = gt - y * cpr;
+    if (y < rs && y < (uint32_t)g.L) {
+        PhiloxPre pp;
+        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+        const ColWalk<kColour> c = col_walk<kColour>(v, src, dst, k);
+        const uint32_t L = (uint32_t)g.L;
+        // Two chunks in flight, in registers A and B in turn: each block
+        // loads and draws one chunk while the Metropolis step of the other
+        // runs (no copies between the two).
+        WideIn A, B;
+        U4 uA[4], uB[4];
+        col_load<kColour>(c, y, A);
+        col_draws<kColour>(pp, c, y, uA);
+        for (;;) {
+            const uint32_t y1 = y + rs;
+            if (y1 >= L) {
+                col_step<kColour, kRef>(c, sthr, y, A, uA, cnt);
+                break;
+            }
+            col_load<kColour>(c, y1, B);
+            col_draws<kColour>(pp, c, y1, uB);
+            col_step<kColour, kRef>(c, sthr, y, A, uA, cnt);
+            const uint32_t y2 = y1 + rs;
+            if (y2 >= L) {
+                col_step<kColour, kRef>(c, sthr, y1, B, uB, cnt);
+                break;
+            }
+            col_load<kColour>(c, y2, A);
+            col_draws<kColour>(pp, c, y2, uA);
+            col_step<kColour, kRef>(c, sthr, y1, B, uB, cnt);
+            y = y2;
+        }
+    }
+    if constexpr (kColour == 1) flush(v, sweep, cnt, false, red);
 }
 
 // Batched form: a persistent grid takes (lattice, item) pairs from an
@@ -560,21 +760,39 @@ int wide_chunks(const Geom &g) { return (int)(((uint64_t)g.L * (g.half >> 4) + k
 cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st)
 {
     const Geom k = tiled_geom(g);  // compact table in t' = thr - 1 form
-    // instantiations: Ising, North-East, Ising with per-bond couplings,
-    // Ising with couplings and per-site field signs
-    const int m = g.model == LAT_NE ? 1 : (g.cpl != nullptr ? (fields ? 3 : 2) : 0);
-    using K = void (*)(Geom, int, int);
-    const K kern[4] = {k_wide_half<false>, k_wide_half_ne, k_wide_half<true>, k_wide_half_fld};
-    // one wave: SMs x resident CTAs per SM (queried once per instantiation)
-    static int resident[4] = {0, 0, 0, 0};
-    if (resident[m] == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern[m], kThreads, 0);
-        resident[m] = sms * (per > 0 ? per : 1);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // one wave: SMs x resident CTAs per SM, queried once per kernel
+    auto wave = [dev](const void *fn, int &cache) {
+        if (cache == 0) {
+            int sms = 0, per = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0);
+            cache = sms * (per > 0 ? per : 1);
+        }
+        return cache;
+    };
+    if (g.model != LAT_NE && g.cpl == nullptr) {   // uniform Ising: the software-pipelined kernels
+        static int res_pipe = 0;
+        const unsigned pb = (unsigned)std::min<long long>(
+            wide_chunks(g), wave(reinterpret_cast<const void *>(k_wide_pipe<1, true>), res_pipe));
+        if (k.ref != nullptr) {
+            k_wide_pipe<0, true><<<pb, kThreads, 0, st>>>(k, off);
+            k_wide_pipe<1, true><<<pb, kThreads, 0, st>>>(k, off);
+        } else {
+            k_wide_pipe<0, false><<<pb, kThreads, 0, st>>>(k, off);
+            k_wide_pipe<1, false><<<pb, kThreads, 0, st>>>(k, off);
+        }
+        return cudaGetLastError();
     }
-    const unsigned blocks = (unsigned)std::min<long long>(wide_chunks(g), resident[m]);
+    // North-East, Ising with per-bond couplings, Ising with couplings and
+    // per-site field signs
+    const int m = g.model == LAT_NE ? 0 : (fields ? 2 : 1);
+    using K = void (*)(Geom, int, int);
+    const K kern[3] = {k_wide_half_ne, k_wide_half_cpl, k_wide_half_fld};
+    static int resident[3] = {0, 0, 0};
+    const unsigned blocks = (unsigned)std::min<long long>(
+        wide_chunks(g), wave(reinterpret_cast<const void *>(kern[m]), resident[m]));
     for (int colour = 0; colour < 2; ++colour) {
         kern[m]<<<blocks, kThreads, 0, st>>>(k, colour, off);
         cudaError_t e = cudaGetLastError();
