@@ -393,27 +393,29 @@ struct WideIn {
 // word and its base addresses are fixed and a row costs a few 32-bit adds.
 template <int kColour>
 struct ColWalk {
-    const int8_t *pS;      // src, this colour's plane, + 16k
-    const int8_t *pO;      // src, the other plane, + 16k
-    const int8_t *pOrow;   // src, the other plane (row starts)
-    int8_t *dS;            // dst, this colour's plane, + 16k
-    int8_t *dO;            // dst, plane 1, + 16k (colour 0 copies the colour-1 sites)
+    const int8_t *pS;      // this colour's sites before the sweep, + 16k
+    const int8_t *pO;      // the other colour's current sites, + 16k
+    const int8_t *pOrow;   // the other colour's current sites (row starts)
+    int8_t *dS;            // this colour's plane in the new buffer, + 16k
     const int8_t *r1, *r0; // reference planes 1 and 0, + 16k (or null)
     uint32_t half, L, G, k;
     uint32_t adjb0, adjb1; // byte offset in the row of the neighbour word past the chunk end, x parity 0 / 1
 };
 
+// old: the buffer of the state before the sweep; nw: the new buffer.
+// Colour 0 reads both planes of old; colour 1 reads its own sites from old
+// (colour 0 did not touch them) and the new colour-0 sites from nw.  Each
+// colour writes only its own plane of nw, so no plane is copied.
 template <int kColour>
-LAT_D ColWalk<kColour> col_walk(const SweepView &g, const int8_t *src, int8_t *dst, uint32_t k)
+LAT_D ColWalk<kColour> col_walk(const SweepView &g, const int8_t *old, int8_t *nw, uint32_t k)
 {
     constexpr int oc = 1 - kColour;
     ColWalk<kColour> c;
     const uint32_t plane = (uint32_t)g.plane;   // N < 2^32, so a plane is < 2^31 bytes
-    c.pOrow = src + (size_t)oc * plane;
-    c.pS = src + (size_t)kColour * plane + 16 * k;
+    c.pOrow = (kColour == 0 ? old : nw) + (size_t)oc * plane;
+    c.pS = old + (size_t)kColour * plane + 16 * k;
     c.pO = c.pOrow + 16 * k;
-    c.dS = dst + (size_t)kColour * plane + 16 * k;
-    c.dO = dst + (size_t)plane + 16 * k;
+    c.dS = nw + (size_t)kColour * plane + 16 * k;
     c.r1 = g.ref ? g.ref + (size_t)plane + 16 * k : nullptr;
     c.r0 = g.ref ? g.ref + 16 * k : nullptr;
     c.half = g.half;
@@ -484,15 +486,20 @@ LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y,
         const uint32_t t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
         const uint32_t acc = (u[w].x <= t0 ? 1u : 0u) | (u[w].y <= t1 ? 2u : 0u) | (u[w].z <= t2 ? 4u : 0u) |
                              (u[w].w <= t3 ? 8u : 0u);
+        // (the spread multiplies run on the FMA pipe, which has room; the
+        // logic pipe is the busier one)
         const uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu;   // 0xFE at flipped sites
         Sn[w] = in.S[w] ^ F;
         if constexpr (kColour == 1) {
-            ue += ((Uw ^ Sn[w]) & M1) + ((Dw ^ Sn[w]) & M1) + ((Lf ^ Sn[w]) & M1) + ((R ^ Sn[w]) & M1);
+            // unequal bonds, 2 per pair: the adder's sum and carry words
+            // (U^D^Lf, maj(U,D,Lf)) against the new spin count the unequal
+            // bonds to U, D, Lf once and twice (every bit of a byte above
+            // bit 0 repeats the "down" flag), R counts once
+            ue += ((s1 ^ Sn[w]) & M1) + ((c1 ^ Sn[w]) & 0x04040404u) + ((R ^ Sn[w]) & M1);
             dn += (Sn[w] & M1) + (in.O[w] & M1);
         }
     }
     store_words<4>(c.dS + oy, Sn);
-    if constexpr (kColour == 0) store_words<4>(c.dO + oy, in.O);
     if constexpr (kColour == 1) {
         const int d2 = byte_sum(dn);
         cnt.bond += 64 - byte_sum(ue);
@@ -520,9 +527,8 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
     __syncthreads();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const SweepView v = sweep_view(g);
-    const int8_t *src = (sweep & 1) ? v.s1 : v.s0;
-    int8_t *dst = (sweep & 1) ? v.s0 : v.s1;
-    if (kColour == 1) src = dst;   // colour 1 updates the new buffer in place
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
     Counts cnt;
     // thread -> (chunk column k, first row y); rs rows between visits.  The
     // launch has at least cpr threads, and rs * cpr of them work.
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
     if (y < rs && y < (uint32_t)g.L) {
         PhiloxPre pp;
         philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
-        const ColWalk<kColour> c = col_walk<kColour>(v, src, dst, k);
+        const ColWalk<kColour> c = col_walk<kColour>(v, old, nw, k);
         const uint32_t L = (uint32_t)g.L;
         // Two chunks in flight, in registers A and B in turn: each block
         // loads and draws one chunk while the Metropolis step of the other
