@@ -425,8 +425,11 @@ typedef struct lattice_static_desc {
  *     the call clears what must start at zero.  Calls whose work overlaps
  *     on the GPU (for example on two streams, or from two host threads)
  *     race on the scratch: serialise them.
- *   - Waits for its own small host-to-device copies of the descriptors
- *     before queueing the sweeps; returns without waiting for the sweeps.
+ *   - The descriptors are copied from host memory on cuda_stream, and the
+ *     call then synchronises cuda_stream before it queues the sweeps: it
+ *     blocks until all work queued earlier on that stream (the previous
+ *     call's sweeps included) has finished.  It returns without waiting
+ *     for the sweeps it queues.
  * Returns LAT_EINVAL / LAT_ENOTSUP for bad or unsupported lattices. */
 int lattice_sweep_static(const lattice_static_desc_t *descs, int n_lattices, int64_t n_sweeps,
                          void *cuda_stream);

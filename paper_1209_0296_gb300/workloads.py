@@ -9,7 +9,7 @@ North-East with L log-uniform in [64, 4096] and c uniform in [0.05, 0.3];
 sweeps are log-uniform in [10^3, 10^5]; every lattice starts random
 (Ising) or at equilibrium (North-East).  numpy default_rng(99), one fixed
 draw order per request: gap, model, L, T or c, sweeps, seed.  L is rounded
-to the nearest multiple of 32 (the tiled kernel's granularity).
+to the nearest even integer (the checkerboard needs even L).
 """
 from __future__ import annotations
 
@@ -18,7 +18,7 @@ import math
 import numpy as np
 
 
-def served_mix(n=4096, seed=99, gap_ms=2.0, sweep_scale=1.0, round_to=32):
+def served_mix(n=4096, seed=99, gap_ms=2.0, sweep_scale=1.0, round_to=2):
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []

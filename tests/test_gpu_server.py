@@ -1,15 +1,18 @@
 """Serving loop: continuous batching of independent requests.
 
-Each served result must equal its lattice run alone (bit for bit), requests
-that arrive while others run must be admitted and finish before long ones
-do, and admission must respect the HBM budget and the slot limit.
+Each served result must equal its lattice run alone and the CPU oracle's
+run of the same request (bit for bit: spins and the final exact counters),
+requests that arrive while others run must be admitted and finish before
+long ones do, and admission must respect the HBM budget and the slot limit.
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_1209_0296_gb300 as lt
+from paper_1209_0296_gb300.workloads import served_mix
 
 pytestmark = pytest.mark.gpu
 
@@ -29,6 +32,30 @@ REQS = [
     dict(dims=2, L=320, two_S=1, model=lt.NE, J=0.0, h=0.0, T_or_c=0.05, seed=10,
          init=lt.INIT_EQUILIBRIUM, sweeps=129),
 ]
+
+
+def _oracle(r):
+    o = oracle.Lattice(r["dims"], r["L"], r["two_S"], r["model"], r["J"], r["h"], r["T_or_c"],
+                       seed=r["seed"], init=r["init"])
+    ser = o.sweep(r["sweeps"]) if r["sweeps"] > 0 else None
+    return o, ser
+
+
+def _check_against_oracle(r, spins, res):
+    o, ser = _oracle(r)
+    assert np.array_equal(spins, o.spins), r
+    if ser is not None:
+        # the unflipped count is kept for the North-East model only
+        keys = ("bond", "mag", "up", "unflipped") if r["model"] == lt.NE else ("bond", "mag", "up")
+        for key in keys:
+            assert res[key] == ser[key][-1], (key, r)
+    else:
+        # no sweep ran, so there are no per-sweep counters: compare the
+        # per-site observables of the initial state
+        m = o.measure()
+        N = r["L"] ** r["dims"]
+        assert res["M"] == pytest.approx(m["mag"] / N)
+        assert res["E"] == pytest.approx(float(o.energy(m["bond"], m["mag"])) / N)
 
 
 def _solo(r):
@@ -56,8 +83,28 @@ def test_served_results_equal_solo_runs():
             ser = g.series(r["sweeps"] - 1, 1)
             assert res["bond"] == ser["bond"][0] and res["mag"] == ser["mag"][0]
         assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
+        _check_against_oracle(r, spins, res)
         with pytest.raises(lt.LatticeError):
             srv.poll(rid)  # released after the first successful poll
+    srv.close()
+
+
+def test_served_mix_requests_match_the_oracle():
+    # the first requests of the served mix (L rounded to even, so sizes the
+    # fast kernels do not take are served too), sweeps scaled down so the
+    # oracle finishes in seconds; submitted back to back so they share rounds
+    reqs = [r for r in served_mix(n=40, seed=99, sweep_scale=0.01) if r["L"] ** 2 * r["sweeps"] <= 3e7]
+    assert len(reqs) >= 20 and any(r["L"] % 32 for r in reqs)
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=64, chunk_sweeps=32)
+    keys = ("dims", "L", "two_S", "model", "J", "h", "T_or_c", "seed", "init", "sweeps")
+    ids = [srv.submit(**{k: r[k] for k in keys}, keep_spins=True) for r in reqs]
+    srv.drain(300.0)
+    for rid, r in zip(ids, reqs):
+        spins = np.empty(r["L"] ** 2, dtype=np.int8)
+        res = srv.poll(rid, spins)
+        assert res is not None and res["status"] == 0, res
+        assert res["sweeps_done"] == r["sweeps"]
+        _check_against_oracle(r, spins, res)
     srv.close()
 
 

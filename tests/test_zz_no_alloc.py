@@ -46,9 +46,9 @@ def to_linear(pl, L):
     return s.reshape(-1)
 
 
-def _descs(bufs, counters, sweep0):
-    arr = (_lib.LatticeStaticDesc * len(CASES))()
-    for i, (L, J, h, T, seed) in enumerate(CASES):
+def _descs(cases, bufs, counters, sweep0):
+    arr = (_lib.LatticeStaticDesc * len(cases))()
+    for i, (L, J, h, T, seed) in enumerate(cases):
         d = arr[i]
         d.L, d.J, d.h, d.T, d.seed, d.sweep0 = L, J, h, T, seed, sweep0
         d.spins[0] = bufs[i][0].data_ptr()
@@ -57,47 +57,65 @@ def _descs(bufs, counters, sweep0):
     return arr
 
 
-def test_static_sweep_matches_allocating_entry_points_on_two_calls():
+def _two_calls_match(cases, n1=7, n2=5):
+    """Two lattice_sweep_static calls in a row against lattice_create +
+    lattice_sweep of the same lattices: spins and counters bit for bit."""
     torch = pytest.importorskip("torch")
     lib = lt.load()
     dev = torch.device("cuda", 0)
     refs = [lt.Lattice(2, L, 1, lt.ISING, J, h, T, seed=s, init=lt.INIT_RANDOM)
-            for (L, J, h, T, s) in CASES]
+            for (L, J, h, T, s) in cases]
     bufs = []
-    for g, (L, *_rest) in zip(refs, CASES):
+    for g, (L, *_rest) in zip(refs, cases):
         b = torch.empty((2, L * L), dtype=torch.int8, device=dev)
         b[0].copy_(torch.from_numpy(to_planar(g.get_spins(), L)).to(dev))
         bufs.append(b)
-    n1, n2 = 7, 5
     stream = torch.cuda.current_stream(dev).cuda_stream
-    # first call: sweeps 0..6
-    c1 = [torch.zeros(4 * n1, dtype=torch.int64, device=dev) for _ in CASES]
-    rc = lib.lattice_sweep_static(ctypes.cast(_descs(bufs, c1, 0), ctypes.c_void_p), len(CASES), n1,
+    # first call: sweeps 0 .. n1-1
+    c1 = [torch.zeros(4 * n1, dtype=torch.int64, device=dev) for _ in cases]
+    rc = lib.lattice_sweep_static(ctypes.cast(_descs(cases, bufs, c1, 0), ctypes.c_void_p), len(cases), n1,
                                   ctypes.c_void_p(stream))
     assert rc == 0, lib.lattice_strerror(rc)
     torch.cuda.synchronize(dev)
     for g in refs:
         g.sweep(n1)
-    for i, ((L, *_rest), g) in enumerate(zip(CASES, refs)):
+    for i, ((L, *_rest), g) in enumerate(zip(cases, refs)):
         ser = g.series(0, n1)
         got = c1[i].view(n1, 4).cpu().numpy()
         assert np.array_equal(got[:, 0], ser["bond"]) and np.array_equal(got[:, 1], ser["mag"])
         assert np.array_equal(got[:, 2], ser["up"])
         assert np.array_equal(to_linear(bufs[i][n1 & 1].cpu().numpy(), L), g.get_spins())
-    # second call continues the same chains: sweeps 7..11
-    c2 = [torch.full((4 * n2,), 123, dtype=torch.int64, device=dev) for _ in CASES]  # cleared by the call
-    rc = lib.lattice_sweep_static(ctypes.cast(_descs(bufs, c2, n1), ctypes.c_void_p), len(CASES), n2,
+    # second call continues the same chains: sweeps n1 .. n1+n2-1
+    c2 = [torch.full((4 * n2,), 123, dtype=torch.int64, device=dev) for _ in cases]  # cleared by the call
+    rc = lib.lattice_sweep_static(ctypes.cast(_descs(cases, bufs, c2, n1), ctypes.c_void_p), len(cases), n2,
                                   ctypes.c_void_p(stream))
     assert rc == 0, lib.lattice_strerror(rc)
     torch.cuda.synchronize(dev)
     for g in refs:
         g.sweep(n2)
-    for i, ((L, *_rest), g) in enumerate(zip(CASES, refs)):
+    for i, ((L, *_rest), g) in enumerate(zip(cases, refs)):
         ser = g.series(n1, n2)
         got = c2[i].view(n2, 4).cpu().numpy()
         assert np.array_equal(got[:, 0], ser["bond"]) and np.array_equal(got[:, 1], ser["mag"])
         assert np.array_equal(got[:, 2], ser["up"]) and np.all(got[:, 3] == 0)
         assert np.array_equal(to_linear(bufs[i][(n1 + n2) & 1].cpu().numpy(), L), g.get_spins())
+    for g in refs:
+        g.close()
+
+
+def test_static_sweep_matches_allocating_entry_points_on_two_calls():
+    _two_calls_match(CASES)
+
+
+def test_static_sweep_at_the_lattice_limit():
+    # 64 lattices (the most one call takes) of L = 32, each a single ragged tile
+    _two_calls_match([(32, 1.0, 0.0, 2.0 + 0.02 * i, 100 + i) for i in range(64)], n1=4, n2=3)
+
+
+def test_static_sweep_ragged_tiles():
+    # L = 1056: 4 full tile columns and a ragged one, 16 full tile rows and a
+    # ragged one, beside a lattice of whole tiles
+    _two_calls_match([(1056, 1.0, 0.0, 2.269185, 5), (512, 1.0, 0.1, 2.4, 6)], n1=3, n2=2)
 
 
 def test_static_sweep_rejects_sizes_beyond_its_limits():
