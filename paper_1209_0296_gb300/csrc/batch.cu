@@ -33,10 +33,12 @@ struct lattice_batch {
     int ctrls_cap = 0;
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S wide
     // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1,
-    // Potts colour 0 / 1
+    // Potts colour 0 / 1, any-L 2D Ising colour 0 / 1, any-L 2D North-East
+    // colour 0 / 1
     unsigned *d_counters = nullptr;
     int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0, grid_potts = 0;
     int grid_wide2[2] = {0, 0};   // 2D wide, Ising / North-East
+    int grid_group[2] = {0, 0};   // 2D any-L, Ising / North-East
     // resident lattices
     cudaStream_t res_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -52,7 +54,7 @@ namespace {
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
 constexpr int kGraphMinSteps = 128;
-constexpr int kCounters = 12;
+constexpr int kCounters = 16;
 constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
 constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
 
@@ -73,10 +75,10 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
 
 // Item counts of the current active set, in this order in d_items: tiles
 // of Ising lattices, tiles of North-East lattices, 2D wide items of Ising
-// and of North-East lattices, 3D / spin-S wide items, Potts items, generic
-// chunks.
+// and of North-East lattices, any-L 2D items of Ising and of North-East
+// lattices, 3D / spin-S wide items, Potts items, generic chunks.
 struct Shape {
-    int n_lat, n_ising, n_ne, n_w2[2], n_wide, n_potts, n_gen;
+    int n_lat, n_ising, n_ne, n_w2[2], n_grp[2], n_wide, n_potts, n_gen;
     int tab_gen;   // largest table among the generic lattices
 };
 
@@ -108,6 +110,12 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
                 e = launch_batch_wide(ph.geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
                                       m == 1, std::min(b->grid_wide2[m], sh.n_w2[m]), st);
             w2 += sh.n_w2[m];
+        }
+        for (int m = 0; m < 2; ++m) {   // any-L: Ising, then North-East
+            for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_grp[m] > 0; ++colour)
+                e = launch_batch_group(ph.geoms, w2, sh.n_grp[m], b->d_counters + 12 + 2 * m + colour, colour,
+                                       m == 1, std::min(b->grid_group[m], sh.n_grp[m]), st);
+            w2 += sh.n_grp[m];
         }
         const uint2 *wide = w2;
         for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide > 0; ++colour)
@@ -234,6 +242,8 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     b->grid_potts = batch_potts_grid();
     b->grid_wide2[0] = batch_wide_grid(false);
     b->grid_wide2[1] = batch_wide_grid(true);
+    b->grid_group[0] = batch_group_grid(false);
+    b->grid_group[1] = batch_group_grid(true);
     *out = b;
     return LAT_OK;
 }
@@ -299,14 +309,15 @@ int lattice_batch_run(lattice_batch_t *b)
         const int64_t steps = work[n_active - 1].second - done;
         if (steps <= 0) continue;
         const size_t g0 = all_geoms.size();
-        std::vector<uint2> tiled, tiled_ne, w2[2], wide, potts, gen;
+        std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide, potts, gen;
         int tab_gen = 0;
         for (size_t i = 0; i < n_active; ++i) {
             lattice *lt = work[i].first;
             all_geoms.push_back(tiled_geom(lt->geom));
             all_ctrls.push_back(lt->ctrl);
             // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
-            // the tiled items when their kernel is the tiled one; 3D and
+            // the tiled items when their kernel is the tiled one; other even
+            // L with uniform couplings take the any-L 2D items; 3D and
             // spin-S Ising lattices with L % 16 == 0 take the 3D wide items,
             // Potts lattices with L % 16 == 0 the Potts items; the rest
             // (other sizes, per-site disorder, an explicit generic choice)
@@ -322,6 +333,10 @@ int lattice_batch_run(lattice_batch_t *b)
                 const int nw = wide_items(lt->geom);
                 auto &dst = w2[lt->P.model == LAT_NE ? 1 : 0];
                 for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+            } else if (!generic && group_supported(lt->geom)) {
+                const int ng = group_items(lt->geom);
+                auto &dst = grp[lt->P.model == LAT_NE ? 1 : 0];
+                for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
             } else if (!generic && wide3_supported(lt->geom)) {
                 const int nw = wide3_items(lt->geom);
                 for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
@@ -337,11 +352,12 @@ int lattice_batch_run(lattice_batch_t *b)
         }
         Spec sp;
         sp.sh = Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                      (int)wide.size(), (int)potts.size(), (int)gen.size(), tab_gen};
+                      {(int)grp[0].size(), (int)grp[1].size()}, (int)wide.size(), (int)potts.size(), (int)gen.size(),
+                      tab_gen};
         sp.steps = steps;
         sp.geom_off = g0;
         sp.item_off = all_items.size();
-        for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &wide, &potts, &gen})
+        for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &grp[0], &grp[1], &wide, &potts, &gen})
             all_items.insert(all_items.end(), v->begin(), v->end());
         specs.push_back(sp);
         done += steps;

@@ -219,10 +219,12 @@ void compact_table(Geom &g, const TabEntry *host_tab)
     }
 }
 
-// LAT_KERNEL_WIDE covers three kernels: the 2D spin-1/2 one
-// (kernels_wide.cu), the 3D / spin-S Ising one (kernels_wide3.cu) and the
-// Potts one (kernels_potts.cu).
-static bool any_wide(const Geom &g) { return wide_supported(g) || wide3_supported(g) || potts_supported(g); }
+// LAT_KERNEL_WIDE covers four kernels: the 2D spin-1/2 one for L % 32 == 0
+// and its any-even-L form on single Philox groups (kernels_wide.cu), the
+// 3D / spin-S Ising one (kernels_wide3.cu) and the Potts one
+// (kernels_potts.cu).
+static bool wide2_supported(const Geom &g) { return wide_supported(g) || group_supported(g); }
+static bool any_wide(const Geom &g) { return wide2_supported(g) || wide3_supported(g) || potts_supported(g); }
 
 int choose_kernel(const lattice *lt)
 {
@@ -279,7 +281,7 @@ int enqueue_sweeps(lattice *lt, int64_t k, cudaStream_t st)
         } else if (kern == LAT_KERNEL_TILED) {
             e = launch_sweep_tiled(lt->geom, lt->tile_w, lt->tile_h, off, st);
         } else if (kern == LAT_KERNEL_WIDE) {
-            e = wide_supported(lt->geom)    ? launch_sweep_wide(lt->geom, lt->has_fields, off, st)
+            e = wide2_supported(lt->geom)   ? launch_sweep_wide(lt->geom, lt->has_fields, off, st)
                 : potts_supported(lt->geom) ? launch_sweep_potts(lt->geom, off, st)
                                             : launch_sweep_wide3(lt->geom, off, st);
         } else {
@@ -386,7 +388,7 @@ void append_tune_file(const std::pair<int, int> &key, const TuneChoice &c)
 bool tune_choice_ok(const lattice *lt, const TuneChoice &c)
 {
     switch (c.kernel) {
-    case LAT_KERNEL_WIDE: return wide_supported(lt->geom);
+    case LAT_KERNEL_WIDE: return wide2_supported(lt->geom);
     case LAT_KERNEL_TILED: return tiled_supported(lt->geom) && tile_shape_ok(0, c.tile_h);
     case LAT_KERNEL_RESIDENT: return resident_supported(lt->geom);
     default: return false;

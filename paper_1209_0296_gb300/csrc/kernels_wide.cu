@@ -572,6 +572,296 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
     if constexpr (kColour == 1) flush(v, sweep, cnt, false, red);
 }
 
+// ---------------------------------------------------------------------
+// Any even L: one Philox group (the up to four same-colour sites
+// j = 4m .. 4m+3 of a plane row) per thread and row.  A plane row holds
+// L/2 bytes, so for L % 8 != 0 rows do not start on a word boundary and the
+// last group of a row holds L/2 % 4 sites; a group's bytes are gathered
+// from the aligned words that hold them, the neighbour past the group's
+// edge (west of site 4m, or east of its last site, across the periodic
+// row end when the group is the row's last) is one byte load, and a
+// partial or misaligned group is written byte by byte (its neighbours'
+// bytes belong to other threads).  The SWAR step is the wide kernel's on
+// one word, with the bytes past the last site masked off.
+// ---------------------------------------------------------------------
+
+// The bytes p[0 .. nv) (1 <= nv <= 4) as one word, byte k = p[k], the
+// bytes from nv on unspecified.  Read from the aligned words that hold
+// them; the word after the last needed byte is not read, so every word
+// read holds an in-bounds byte (and the spin buffers are multiples of 4
+// bytes: N = L^2 with L even).
+LAT_D uint32_t load_group(const int8_t *p, uint32_t nv)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t sh = (uint32_t)(a & 3u);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(a - sh);
+    const uint32_t lo = w[0];
+    const uint32_t hi = (sh + nv > 4u) ? w[1] : 0u;
+    return __funnelshift_r(lo, hi, 8u * sh);
+}
+
+LAT_D void store_group(int8_t *p, uint32_t v, uint32_t nv)
+{
+    if (nv == 4u && (reinterpret_cast<uintptr_t>(p) & 3u) == 0u) {
+        *reinterpret_cast<uint32_t *>(p) = v;
+    } else {
+        for (uint32_t k = 0; k < nv; ++k) p[k] = (int8_t)(v >> (8u * k));
+    }
+}
+
+struct GroupIn {
+    uint32_t S, O, U, D;   // the group's sites, the other plane's same-index, north and south words
+    uint32_t nb;           // the other plane's byte past the group's edge (west of 4m, or east of the last site)
+};
+
+// One thread's column of groups (group m of every plane row it visits).
+template <int kColour>
+struct GroupWalk {
+    const int8_t *pS;      // this colour's sites before the sweep (plane base)
+    const int8_t *pO;      // the other colour's current sites (plane base)
+    int8_t *dS;            // this colour's plane in the new buffer
+    const int8_t *r1, *r0; // reference planes 1 and 0 (or null)
+    uint8_t *fc;           // persistence bytes of this colour, group m of row 0 (North-East)
+    const uint8_t *fo;     // persistence bytes of the other colour, group m of row 0
+    uint32_t half, L, G, m, j0, nv, vmask;
+    uint32_t jprev, jnext; // row index of the west neighbour of site j0 / the east neighbour of the last site
+};
+
+template <int kColour>
+LAT_D GroupWalk<kColour> group_walk(const SweepView &g, const int8_t *old, int8_t *nw, uint32_t m)
+{
+    constexpr int oc = 1 - kColour;
+    GroupWalk<kColour> c;
+    const uint32_t plane = (uint32_t)g.plane;
+    c.pS = old + (size_t)kColour * plane;
+    c.pO = (kColour == 0 ? old : nw) + (size_t)oc * plane;
+    c.dS = nw + (size_t)kColour * plane;
+    c.r1 = g.ref ? g.ref + (size_t)plane : nullptr;
+    c.r0 = g.ref;
+    c.fc = g.flags ? g.flags + (size_t)kColour * g.rows * g.G + m : nullptr;
+    c.fo = g.flags ? g.flags + (size_t)oc * g.rows * g.G + m : nullptr;
+    c.half = g.half;
+    c.L = (uint32_t)g.L;
+    c.G = g.G;
+    c.m = m;
+    c.j0 = 4u * m;
+    c.nv = min(4u, g.half - c.j0);
+    c.vmask = c.nv == 4u ? 0xFFFFFFFFu : (1u << (8u * c.nv)) - 1u;
+    c.jprev = c.j0 == 0u ? g.half - 1u : c.j0 - 1u;
+    c.jnext = c.j0 + c.nv == g.half ? 0u : c.j0 + c.nv;
+    return c;
+}
+
+template <int kColour>
+LAT_D void group_load(const GroupWalk<kColour> &c, uint32_t y, GroupIn &in)
+{
+    const uint32_t oy = y * c.half;
+    const uint32_t oym = y == 0 ? oy + (c.L - 1) * c.half : oy - c.half;
+    const uint32_t oyp = y == c.L - 1 ? 0u : oy + c.half;
+    in.S = load_group(c.pS + oy + c.j0, c.nv);
+    in.O = load_group(c.pO + oy + c.j0, c.nv);
+    in.U = load_group(c.pO + oym + c.j0, c.nv);   // north
+    in.D = load_group(c.pO + oyp + c.j0, c.nv);   // south
+    in.nb = (uint32_t)(uint8_t)c.pO[oy + (((kColour + y) & 1) ? c.jnext : c.jprev)];
+}
+
+template <int kColour>
+LAT_D U4 group_draw(const PhiloxPre &pp, const GroupWalk<kColour> &c, uint32_t y)
+{
+    return philox_item(pp, y * c.G + c.m, (uint32_t)kColour);
+}
+
+template <int kColour, bool kNE, bool kRef>
+LAT_D void group_step(const GroupWalk<kColour> &c, const uint32_t *sthr, uint32_t y, const GroupIn &in, const U4 &u,
+                      Counts &cnt)
+{
+    const uint32_t oy = y * c.half;
+    const bool p1 = ((kColour + y) & 1) != 0;
+    const char *tb = reinterpret_cast<const char *>(sthr);
+    const uint32_t M1 = 0x02020202u;
+    uint32_t Lf, R;
+    if (!p1) {   // x = 2j: west is j-1 of the other plane (nb for site j0), east is j
+        Lf = (in.O << 8) | in.nb;
+        R = in.O;
+    } else {     // x = 2j+1: west is j, east is j+1 (nb for the last site)
+        Lf = in.O;
+        R = ((in.O >> 8) & (c.vmask >> 8)) | (in.nb << (8u * (c.nv - 1u)));
+    }
+    const uint32_t s1 = in.U ^ in.D ^ Lf;
+    const uint32_t c1 = (in.U & in.D) | (in.U & Lf) | (in.D & Lf);
+    const uint32_t b0 = s1 ^ R;
+    const uint32_t b1 = c1 ^ (s1 & R);
+    const uint32_t b2 = c1 & s1 & R;
+    const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (in.S & 0x20202020u);
+    uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
+    uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
+    uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
+    uint32_t t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
+    uint32_t locked = 0;
+    if constexpr (kNE) {   // §III.B: north (U) and east (R) must be up
+        locked = in.U | R;
+        t0 |= prmt_sign(locked, 0x8888u);
+        t1 |= prmt_sign(locked, 0x9999u);
+        t2 |= prmt_sign(locked, 0xAAAAu);
+        t3 |= prmt_sign(locked, 0xBBBBu);
+    }
+    const uint32_t acc = (u.x <= t0 ? 1u : 0u) | (u.y <= t1 ? 2u : 0u) | (u.z <= t2 ? 4u : 0u) | (u.w <= t3 ? 8u : 0u);
+    uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu & c.vmask;   // 0xFE at flipped sites
+    if constexpr (kNE) F &= ~locked;
+    const uint32_t Sn = in.S ^ F;
+    store_group(c.dS + oy + c.j0, Sn, c.nv);
+    uint32_t fl = 0;
+    if constexpr (kNE) {
+        const uint32_t chg = (((F >> 1) & 0x01010101u) * 0x01020408u) >> 24 & 0xFu;
+        uint8_t *fp = c.fc + (size_t)y * c.G;
+        fl = (uint32_t)*fp | chg;
+        *fp = (uint8_t)fl;
+    }
+    if constexpr (kColour == 1) {
+        const uint32_t ue = (((s1 ^ Sn) & M1) + ((c1 ^ Sn) & 0x04040404u) + ((R ^ Sn) & M1)) & c.vmask;
+        const uint32_t dn = ((Sn & M1) + (in.O & M1)) & c.vmask;
+        const int d2 = byte_sum(dn);
+        const int nv = (int)c.nv;
+        cnt.bond += 4 * nv - byte_sum(ue);
+        cnt.mag += 2 * nv - d2;
+        cnt.up += 2 * nv - (d2 >> 1);
+        if constexpr (kNE) cnt.unfl += 2 * nv - __popc(fl) - __popc((uint32_t)c.fo[(size_t)y * c.G]);
+        if constexpr (kRef) {
+            const uint32_t R1 = load_group(c.r1 + oy + c.j0, c.nv), R0 = load_group(c.r0 + oy + c.j0, c.nv);
+            const uint32_t dr = (((Sn ^ R1) & M1) + ((in.O ^ R0) & M1)) & c.vmask;
+            cnt.acf += 2 * nv - byte_sum(dr);
+        }
+    }
+}
+
+template <int kColour, bool kNE, bool kRef>
+__global__ void __launch_bounds__(kThreads, 3) k_group_pipe(Geom g, int off)
+{
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kThreads / 32][5];
+    if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
+    __syncthreads();
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
+    const SweepView v = sweep_view(g);
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
+    Counts cnt;
+    // thread -> (group m, first row y); rs rows between visits (the launch
+    // has at least G threads, rs * G of them work)
+    const uint32_t G = g.G;
+    const uint32_t rs = (gridDim.x * blockDim.x) / G;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t y = gt / G;
+    const uint32_t m = gt - y * G;
+    if (y < rs && y < (uint32_t)g.L) {
+        PhiloxPre pp;
+        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+        const GroupWalk<kColour> c = group_walk<kColour>(v, old, nw, m);
+        const uint32_t L = (uint32_t)g.L;
+        // two groups in flight (A and B in turn), as in k_wide_pipe
+        GroupIn A, B;
+        U4 uA, uB;
+        group_load<kColour>(c, y, A);
+        uA = group_draw<kColour>(pp, c, y);
+        for (;;) {
+            const uint32_t y1 = y + rs;
+            if (y1 >= L) {
+                group_step<kColour, kNE, kRef>(c, sthr, y, A, uA, cnt);
+                break;
+            }
+            group_load<kColour>(c, y1, B);
+            uB = group_draw<kColour>(pp, c, y1);
+            group_step<kColour, kNE, kRef>(c, sthr, y, A, uA, cnt);
+            const uint32_t y2 = y1 + rs;
+            if (y2 >= L) {
+                group_step<kColour, kNE, kRef>(c, sthr, y1, B, uB, cnt);
+                break;
+            }
+            group_load<kColour>(c, y2, A);
+            uA = group_draw<kColour>(pp, c, y2);
+            group_step<kColour, kNE, kRef>(c, sthr, y1, B, uB, cnt);
+            y = y2;
+        }
+    }
+    if constexpr (kColour == 1) flush(v, sweep, cnt, kNE, red);
+}
+
+// Batched form of the any-L kernel: items are (lattice, band of rows) of
+// one colour; the CTA's threads take the band's groups in row-major order.
+constexpr uint32_t kGroupItemGroups = 2048;   // about 8 groups per thread per item
+
+LAT_HD uint32_t group_band_rows(uint32_t G) { return G >= kGroupItemGroups ? 1u : kGroupItemGroups / G; }
+
+template <int kColour, bool kNE>
+LAT_D void batch_group_item(const SweepView &v, const uint32_t *sthr, uint32_t band, Counts &cnt)
+{
+    const unsigned long long sweep = v.ctrl->sweep;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), v.key0, v.key1);
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
+    const uint32_t G = v.G, L = (uint32_t)v.L;
+    const uint32_t br = group_band_rows(G);
+    const uint32_t y0 = band * br;
+    const uint32_t y1 = min(L, y0 + br);
+    const uint32_t total = (y1 - y0) * G;
+    // walk t = tid, tid + 256, ... over the band as (row, group), without a
+    // division per step
+    uint32_t t = threadIdx.x;
+    uint32_t r = t / G, m = t - r * G;
+    const uint32_t sr = kThreads / G, sm = kThreads - sr * G;
+    for (; t < total; t += kThreads) {
+        const GroupWalk<kColour> c = group_walk<kColour>(v, old, nw, m);
+        GroupIn in;
+        group_load<kColour>(c, y0 + r, in);
+        const U4 u = group_draw<kColour>(pp, c, y0 + r);
+        if (v.ref != nullptr) group_step<kColour, kNE, true>(c, sthr, y0 + r, in, u, cnt);
+        else group_step<kColour, kNE, false>(c, sthr, y0 + r, in, u, cnt);
+        r += sr;
+        m += sm;
+        if (m >= G) {
+            m -= G;
+            ++r;
+        }
+    }
+}
+
+template <bool kNE>
+__global__ void __launch_bounds__(kThreads, 3) k_batch_group(const Geom *geoms, const uint2 *items, int n_items,
+                                                           unsigned *next_item, int colour)
+{
+    __shared__ uint32_t sthr[16];
+    __shared__ int red[kThreads / 32][5];
+    __shared__ Geom sg;
+    __shared__ int cur;
+    int loaded = -1;
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = cur;
+        if (it >= n_items) break;
+        const uint2 w = items[it];
+        if ((int)w.x != loaded) {
+            if (threadIdx.x < sizeof(Geom) / 4)
+                reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
+                    reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
+            __syncthreads();
+            if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
+            loaded = (int)w.x;
+            __syncthreads();
+        }
+        const SweepView v = sweep_view(sg);
+        Counts cnt;
+        if (colour == 0) {
+            batch_group_item<0, kNE>(v, sthr, w.y, cnt);
+        } else {
+            batch_group_item<1, kNE>(v, sthr, w.y, cnt);
+            flush(v, v.ctrl->sweep, cnt, kNE, red);   // ends with __syncthreads()
+        }
+        __syncthreads();
+    }
+}
+
 // Batched form: a persistent grid takes (lattice, item) pairs from an
 // atomic counter; an item is kItemChunks x kThreads chunks of one colour of
 // one lattice.  The descriptor and table are reloaded only when a CTA moves
@@ -763,6 +1053,42 @@ bool wide_supported(const Geom &g)
 
 int wide_chunks(const Geom &g) { return (int)(((uint64_t)g.L * (g.half >> 4) + kThreads - 1) / kThreads); }
 
+bool group_supported(const Geom &g)
+{
+    if (!(g.dims == 2 && g.two_S == 1 && g.bits[0] == nullptr && g.cpl == nullptr && (g.L % 2) == 0)) return false;
+    if (g.model == LAT_POTTS) return false;
+    for (int k = 0; k < 16; ++k) {
+        if ((k & 7) > 4) continue;
+        if (!((g.always16 >> k) & 1u) && g.thr16[k] == 0u) return false;
+    }
+    return true;
+}
+
+int group_items(const Geom &g)
+{
+    const uint32_t br = group_band_rows(g.G);
+    return (int)(((uint32_t)g.L + br - 1) / br);
+}
+
+int batch_group_grid(bool ne)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ne) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_group<true>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_group<false>, kThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_batch_group(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
+                               bool ne, int grid, cudaStream_t st)
+{
+    if (ne) k_batch_group<true><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    else k_batch_group<false><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st)
 {
     const Geom k = tiled_geom(g);  // compact table in t' = thr - 1 form
@@ -778,6 +1104,22 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
         }
         return cache;
     };
+    if (!wide_supported(g)) {   // L % 32 != 0: the any-L group kernels
+        static int res_group = 0;
+        const uint64_t groups = (uint64_t)g.L * g.G;
+        const unsigned gb = (unsigned)std::min<long long>(
+            (long long)((groups + kThreads - 1) / kThreads),
+            wave(reinterpret_cast<const void *>(k_group_pipe<1, true, true>), res_group));
+        using KG = void (*)(Geom, int);
+        const bool ne = g.model == LAT_NE, ref = k.ref != nullptr;
+        const KG c0 = ne ? (ref ? k_group_pipe<0, true, true> : k_group_pipe<0, true, false>)
+                         : (ref ? k_group_pipe<0, false, true> : k_group_pipe<0, false, false>);
+        const KG c1 = ne ? (ref ? k_group_pipe<1, true, true> : k_group_pipe<1, true, false>)
+                         : (ref ? k_group_pipe<1, false, true> : k_group_pipe<1, false, false>);
+        c0<<<gb, kThreads, 0, st>>>(k, off);
+        c1<<<gb, kThreads, 0, st>>>(k, off);
+        return cudaGetLastError();
+    }
     if (g.model != LAT_NE && g.cpl == nullptr) {   // uniform Ising: the software-pipelined kernels
         static int res_pipe = 0;
         const unsigned pb = (unsigned)std::min<long long>(

@@ -373,6 +373,14 @@ int batch_wide3_grid();
 cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
                                int colour, int grid, cudaStream_t st);
 int wide_chunks(const Geom &g);
+// 2D spin-1/2 Ising / North-East with uniform couplings at any even L (the
+// wide kernel's sweep on single Philox groups; launch_sweep_wide takes these
+// lattices when L % 32 != 0), and its batched form
+bool group_supported(const Geom &g);
+int group_items(const Geom &g);   // batch items of one colour of one lattice
+int batch_group_grid(bool ne);
+cudaError_t launch_batch_group(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
+                               bool ne, int grid, cudaStream_t st);
 // batched engine
 Geom tiled_geom(const Geom &g);
 int tiles_of(const Geom &g, int tile_h);
