@@ -272,13 +272,22 @@ def run_gpu(args):
                      "traffic": bprof.get("traffic_bytes_per_sweep"), "kernel": "k_bits_half<Ising> x2",
                      "bytes_per_sweep": bbytes, "avg_sweep_us": avg_bits_us,
                      "updates_per_ns": L * L / (avg_bits_us * 1e3)}
-    if prof.get("warp_inst_per_sweep"):
-        sm_clk = (clk.summary().get("sm_mhz") or 2070.0) * 1e6
-        inst_rate = prof["warp_inst_per_sweep"] / (avg_kernel_us * 1e-6)
-        issue_peak = 152 * 4 * sm_clk
-        roofline["issue"] = {"bound": "alu", "achieved": inst_rate / 1e12, "peak": issue_peak / 1e12,
-                             "unit": "Twarp-inst/s", "frac": inst_rate / issue_peak,
-                             "inst_per_site": prof["warp_inst_per_sweep"] * 32 / (L * L)}
+    sm_clk = (clk.summary().get("sm_mhz") or 2070.0) * 1e6
+    issue_peak = 152 * 4 * sm_clk   # warp instructions per second: 152 SMs x 4 schedulers x clock
+
+    def issue(pr, us):
+        # instruction-issue roofline from the committed ncu count of the same kernel
+        if not pr.get("warp_inst_per_sweep"):
+            return None
+        rate = pr["warp_inst_per_sweep"] / (us * 1e-6)
+        return {"bound": "alu", "achieved": rate / 1e12, "peak": issue_peak / 1e12, "unit": "Twarp-inst/s",
+                "frac": rate / issue_peak, "inst_per_site": pr["warp_inst_per_sweep"] * 32 / (L * L),
+                "peak_kind": "152 SMs x 4 schedulers x 1 warp-instruction per cycle at the sampled SM clock"}
+
+    roofline["issue"] = issue(prof, avg_kernel_us)
+    roofline_bits["issue"] = issue(bprof, avg_bits_us)
+    if not args.no_other:
+        roofline["hbm_sized"] = hbm_sized_run(dev, hbm)
 
     # ---- end to end through the C ABI with pinned host buffers ----------
     e2e = None
@@ -333,6 +342,12 @@ def run_gpu(args):
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MiB write outside the timed events)"},
                 "hbm_roofline_pct": 100.0 * roofline["frac"],
+                "rows": {"int8": {"updates_per_ns": len(TEMPS) * S * L * L * args.steps / (ms_int8 * 1e6),
+                                  "hbm_frac": roofline["frac"],
+                                  "issue_frac": (roofline["issue"] or {}).get("frac")},
+                         "bitpacked": {"updates_per_ns": len(TEMPS) * S * L * L * args.steps / (ms_bits * 1e6),
+                                       "hbm_frac": roofline_bits["frac"],
+                                       "issue_frac": (roofline_bits["issue"] or {}).get("frac")}},
                 "roofline": roofline, "roofline_bitpacked": roofline_bits,
                 "gpu_launches": launches, "sweep_launches": sweep_launches,
                 "clocks": clk.summary()}
@@ -471,11 +486,12 @@ def served_bench(n_req=256, sweep_scale=0.01, load=None):
                                   init=r["init"], sweeps=r["sweeps"]))
         srv.drain(600.0)
         res = [srv.poll(i) for i in ids]
+        st = srv.stats()
         srv.close()
         lat = np.array([q["t_done"] - q["t_submit"] for q in res])
         span = max(q["t_done"] for q in res) - min(q["t_submit"] for q in res)
         ok = all(q["status"] == 0 for q in res)
-        return lat, span, ok
+        return lat, span, ok, st["busy_s"] / max(st["wall_s"] - t0, 1e-9)
 
     def run_plain(reqs):
         t0 = time.perf_counter()
@@ -495,8 +511,8 @@ def served_bench(n_req=256, sweep_scale=0.01, load=None):
 
     out = {"workload": "first %d requests of the served mix (default_rng(99)), sweeps x%g, gaps x%g"
                        % (n_req, sweep_scale, sweep_scale), "offered_updates": upd}
-    lat, span, ok = run_served(base)
-    out["served"] = dict(pct(lat), throughput=upd / span / 1e9, all_ok=ok)
+    lat, span, ok, busy = run_served(base)
+    out["served"] = dict(pct(lat), throughput=upd / span / 1e9, all_ok=ok, gpu_busy_frac=busy)
     plat, pspan = run_plain(base)
     out["plain"] = dict(pct(plat), throughput=upd / pspan / 1e9)
     arrival_span = base[-1]["arrival"]
@@ -504,8 +520,8 @@ def served_bench(n_req=256, sweep_scale=0.01, load=None):
     # the same requests at an offered load of about 0.7 of the served throughput
     scale = (upd / (0.7 * out["served"]["throughput"] * 1e9)) / arrival_span
     slow = [dict(r, arrival=r["arrival"] * scale) for r in base]
-    lat2, span2, ok2 = run_served(slow)
-    out["served_load_0.7"] = dict(pct(lat2), throughput=upd / span2 / 1e9, all_ok=ok2)
+    lat2, span2, ok2, busy2 = run_served(slow)
+    out["served_load_0.7"] = dict(pct(lat2), throughput=upd / span2 / 1e9, all_ok=ok2, gpu_busy_frac=busy2)
     plat2, pspan2 = run_plain(slow)
     out["plain_load_0.7"] = dict(pct(plat2), throughput=upd / pspan2 / 1e9)
     out["unit"] = "updates/ns"
@@ -636,14 +652,26 @@ def other_configs(dev):
                                 "kernel": names.get(g.get_kernel()["kernel"], "?")}
     g.close()
 
-    # one 2D Ising lattice far larger than L2: L = 32768 (1 GiB per buffer)
-    g = lt.Lattice(2, 32768, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=7, init=lt.INIT_RANDOM, stream=stream)
-    n = 10
+    return out
+
+
+def hbm_sized_run(dev, hbm, L5=32768, n=100):
+    """The int8 sweep on one 2D Ising lattice far larger than L2 (L = 32768:
+    1 GiB per buffer, random start, T = 2.269185), n timed sweeps: the kernel
+    against HBM rather than L2."""
+    import torch
+    import paper_1209_0296_gb300 as lt
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    g = lt.Lattice(2, L5, 1, lt.ISING, 1.0, 0.0, 2.269185, seed=7, init=lt.INIT_RANDOM, stream=stream)
     t = _timed_sweeps(torch, stream, [g], n, flush)
-    N5 = 32768 * 32768
-    out["L32768_int8"] = {"updates_per_ns": N5 * n / t / 1e9, "alg_GBps": 2.0 * N5 * n / t / 1e9,
-                          "hbm_frac": 2.0 * N5 * n / t / 1e9 / hbm, "sweeps": n,
-                          "kernel": names.get(g.get_kernel()["kernel"], "?")}
+    N5 = L5 * L5
+    ach = 2.0 * N5 * n / t / 1e9
+    out = {"workload": "2D Ising spin-1/2, L=%d, T=2.269185, random start (seed 7), int8" % L5,
+           "sweeps": n, "updates_per_ns": N5 * n / t / 1e9, "achieved": ach, "peak": hbm, "unit": "GB/s",
+           "frac": ach / hbm, "bytes_per_sweep": 2.0 * N5, "avg_sweep_us": t / n * 1e6,
+           "kernel": {lt.KERNEL_WIDE: "k_wide_pipe<colour 0, colour 1>", lt.KERNEL_TILED: "k_sweep_tiled<Ising>"}.get(
+               g.get_kernel()["kernel"], "?")}
     g.close()
     return out
 

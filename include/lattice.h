@@ -245,8 +245,11 @@ int lattice_clear_reference(lattice_t *lat);
 /* Copy the overlaps of sweeps [first, first+count) (global sweep indexes as in
  * lattice_series; first >= the reference's ref_sweep) to overlap[] and, if phi
  * is not NULL, Phi = (overlap/N - m^2) / (1 - m^2) to phi[] (|m| < 1 required,
- * LAT_EINVAL otherwise).  NULL arrays are skipped.  LAT_ENOENT if no reference
- * is set, LAT_ERANGE if the range is not recorded. */
+ * LAT_EINVAL otherwise).  m = NaN asks for the model's own polarisation: for
+ * the North-East model at concentration c, m = <s_i> = 2c - 1 (§III.B,
+ * Eq. 4); a lattice without one gives LAT_EINVAL when phi is requested.
+ * NULL arrays are skipped.  LAT_ENOENT if no reference is set, LAT_ERANGE
+ * if the range is not recorded. */
 int lattice_autocorrelation(lattice_t *lat, int64_t first, int64_t count, double m,
                             int64_t *overlap, double *phi);
 
@@ -354,16 +357,21 @@ typedef struct lattice_result {
     double t_submit, t_admit, t_done;  /* seconds on the server's clock */
 } lattice_result_t;
 
-/* A server owns one CUDA stream (on the device current at creation) and
- * one scheduler thread.  Requests wait in arrival order and are admitted
- * while their device footprint fits in hbm_budget_bytes and fewer than
- * max_slots lattices are resident.  Each scheduling round advances every
- * resident lattice by up to chunk_sweeps sweeps through the batched engine
- * (so work of requests that arrived at different times shares launches),
- * then retires finished lattices (freeing their memory) and admits waiting
- * requests.  Every result is bit-identical to running its lattice alone.
- * This is continuous batching: admission happens between rounds, never
- * by stopping resident work. */
+/* A server owns two CUDA streams (on the device current at creation: one
+ * for the batched rounds, one for creating, reading back and freeing
+ * lattices) and one scheduler thread.  Requests wait in arrival order and
+ * are admitted while their device footprint fits in hbm_budget_bytes and
+ * fewer than max_slots lattices are resident.  Each scheduling round
+ * advances every resident lattice by up to chunk_sweeps sweeps through the
+ * batched engine (so work of requests that arrived at different times
+ * shares launches).  Rounds are pipelined: the next round is queued while
+ * the current one runs, and admission, lattice creation and the retirement
+ * of finished lattices (read-back, freeing their memory) happen meanwhile.
+ * Every result is bit-identical to running its lattice alone.  This is
+ * continuous batching: admission happens between rounds, never by stopping
+ * resident work.  A request whose lattice cannot be created or queued
+ * (e.g. LAT_ENOMEM) ends with that status alone; a failed launch ends the
+ * requests of its round with LAT_ECUDA. */
 int lattice_server_create(lattice_server_t **out, size_t hbm_budget_bytes, int max_slots,
                           int chunk_sweeps);
 /* Non-blocking; *id identifies the request. LAT_EINVAL for a bad request,
@@ -379,6 +387,11 @@ int lattice_server_poll(lattice_server_t *s, uint64_t id, lattice_result_t *res,
 int lattice_server_drain(lattice_server_t *s, double timeout_s);
 /* Seconds on the server's clock (same clock as lattice_result times). */
 double lattice_server_clock(lattice_server_t *s);
+/* Device time of the rounds run so far (*busy_s, from CUDA events around
+ * each round's device work), the server's clock (*wall_s) and the number of
+ * rounds; busy / wall is the fraction of time the GPU worked for the server.
+ * NULL outputs are skipped. */
+int lattice_server_stats(lattice_server_t *s, double *busy_s, double *wall_s, int64_t *rounds);
 void lattice_server_destroy(lattice_server_t *s);
 
 /* ------------------------------------------------------------------ */

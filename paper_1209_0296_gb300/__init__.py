@@ -8,6 +8,7 @@ or an integer ``cudaStream_t``).
 from __future__ import annotations
 
 import ctypes
+import math
 
 import numpy as np
 
@@ -129,12 +130,11 @@ class Lattice:
         lattice in c-mode; Phi omitted when m is unknown)."""
         if count is None:
             count = self.sweeps() - first
-        if m is None and self.model == NE and self.J == 0.0 and self.h == 0.0:
-            m = 2.0 * self.T_or_c - 1.0
         ov = np.zeros(count, dtype=np.int64)
-        phi = np.zeros(count, dtype=np.float64) if m is not None else None
+        own = m is None and self.model == NE and self.J == 0.0 and self.h == 0.0
+        phi = np.zeros(count, dtype=np.float64) if (m is not None or own) else None
         check(self._lib.lattice_autocorrelation(self._h, int(first), int(count),
-                                                0.0 if m is None else float(m), _ptr(ov), _ptr(phi)),
+                                                math.nan if m is None else float(m), _ptr(ov), _ptr(phi)),
               "lattice_autocorrelation")
         return (ov, phi) if phi is not None else (ov, None)
 
@@ -313,6 +313,13 @@ class Server:
 
     def clock(self) -> float:
         return self._lib.lattice_server_clock(self._h)
+
+    def stats(self):
+        """Device time of the rounds so far, the server's clock, rounds run."""
+        busy, wall, rounds = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        check(self._lib.lattice_server_stats(self._h, ctypes.byref(busy), ctypes.byref(wall),
+                                             ctypes.byref(rounds)), "lattice_server_stats")
+        return dict(busy_s=busy.value, wall_s=wall.value, rounds=rounds.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -76,6 +76,7 @@ SIGNATURES = {
     "lattice_server_poll": (c_int, [c_void_p, c_uint64, ctypes.POINTER(LatticeResult), c_void_p]),
     "lattice_server_drain": (c_int, [c_void_p, c_double]),
     "lattice_server_clock": (c_double, [c_void_p]),
+    "lattice_server_stats": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "lattice_server_destroy": (None, [c_void_p]),
     "lattice_sweep_static": (c_int, [c_void_p, c_int, c_int64, c_void_p]),
     "lattice_strerror": (ctypes.c_char_p, [c_int]),

@@ -13,6 +13,7 @@
 // table and sweep counter, so its result is bit-identical to running it
 // alone.
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <new>
 #include <vector>
@@ -21,16 +22,43 @@
 
 using namespace lat;
 
-struct lattice_batch {
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    std::vector<std::pair<lattice *, int64_t>> pending;
+// Device arrays of one run (descriptors, work items, control pointers, the
+// resident lattices' descriptors and sweep counts) with their pinned host
+// staging.  Runs take the slots in turn and a slot is reused only after the
+// run that last used it has finished (its event), so a run's uploads never
+// wait for the work queued before it: the host can queue run k+1 while run k
+// executes.
+struct BatchSlot {
     Geom *d_geoms = nullptr;
     int geoms_cap = 0;
     uint2 *d_items = nullptr;  // tiled items, then wide items, then Potts items, then generic items
     int items_cap = 0;
     Ctrl **d_ctrls = nullptr;
     int ctrls_cap = 0;
+    Geom *d_res_geoms = nullptr;
+    int res_geoms_cap = 0;
+    long long *d_res_n = nullptr;
+    int res_n_cap = 0;
+    char *h_pin = nullptr;     // pinned staging of the uploads
+    size_t h_cap = 0;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+constexpr int kBatchSlots = 3;
+
+struct lattice_batch {
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<std::pair<lattice *, int64_t>> pending;
+    BatchSlot slots[kBatchSlots];
+    int next_slot = 0;
+    // The caller orders every other use of the lattices against this batch's
+    // stream itself (the server): no per-lattice stream synchronisation
+    // before a run and no per-lattice stream waits after it.
+    bool caller_orders = false;
+    // Recorded on the batch stream right before a run's first device work
+    // (after its host preparation), when set: the server's busy-time clock.
+    cudaEvent_t start_event = nullptr;
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S wide
     // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1,
     // Potts colour 0 / 1, any-L 2D Ising colour 0 / 1, any-L 2D North-East
@@ -43,10 +71,7 @@ struct lattice_batch {
     cudaStream_t res_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_done = nullptr;   // end of a run: each lattice's stream waits on it
-    Geom *d_res_geoms = nullptr;
-    int res_geoms_cap = 0;
-    long long *d_res_n = nullptr;
-    int res_n_cap = 0;
+    std::vector<cudaEvent_t> ev_streams;   // one per distinct lattice stream of a run
 };
 
 namespace {
@@ -70,6 +95,47 @@ int grow(T **p, int &cap, int need, cudaStream_t st)
     dev_free(*p, st);
     *p = (T *)q;
     cap = c;
+    return LAT_OK;
+}
+
+// Copy n elements of host data into the slot's pinned staging at byte
+// offset `at` (rounded up to 16) and queue their upload to dst; returns the
+// next free offset.
+template <typename T>
+size_t stage(BatchSlot &sl, size_t at, T *dst, const T *src, size_t n, cudaStream_t st, cudaError_t &e)
+{
+    at = (at + 15) & ~(size_t)15;
+    if (e != cudaSuccess || n == 0) return at;
+    memcpy(sl.h_pin + at, src, n * sizeof(T));
+    e = cudaMemcpyAsync(dst, sl.h_pin + at, n * sizeof(T), cudaMemcpyHostToDevice, st);
+    return at + n * sizeof(T);
+}
+
+int ensure_pinned(BatchSlot &sl, size_t bytes)
+{
+    if (bytes <= sl.h_cap) return LAT_OK;
+    size_t c = sl.h_cap ? sl.h_cap : 64 * 1024;
+    while (c < bytes) c *= 2;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocHost(&p, c);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LAT_ENOMEM : cuda_fail(e, "batch staging");
+    if (sl.h_pin) cudaFreeHost(sl.h_pin);   // the slot's last run has finished
+    sl.h_pin = (char *)p;
+    sl.h_cap = c;
+    return LAT_OK;
+}
+
+// Take the next slot, once the run that used it last has finished.
+int take_slot(lattice_batch *b, BatchSlot **out)
+{
+    BatchSlot &sl = b->slots[b->next_slot];
+    b->next_slot = (b->next_slot + 1) % kBatchSlots;
+    cudaError_t e = cudaSuccess;
+    if (sl.done == nullptr) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    else if (sl.used) e = cudaEventSynchronize(sl.done);
+    if (e != cudaSuccess) return cuda_fail(e, "batch slot");
+    sl.used = false;
+    *out = &sl;
     return LAT_OK;
 }
 
@@ -182,7 +248,7 @@ bool runs_resident(const lattice *lt)
 
 // Launch the resident lattices on the side stream (after the work already
 // on the batch stream) and record the join event.
-int run_resident(lattice_batch *b, const std::vector<std::pair<lattice *, int64_t>> &res)
+int run_resident(lattice_batch *b, BatchSlot &sl, const std::vector<std::pair<lattice *, int64_t>> &res)
 {
     const int n = (int)res.size();
     std::vector<Geom> geoms((size_t)n);
@@ -195,24 +261,21 @@ int run_resident(lattice_batch *b, const std::vector<std::pair<lattice *, int64_
         smem = std::max(smem, resident_smem_bytes(res[(size_t)i].first->geom));
         most = std::max(most, counts[(size_t)i]);
     }
-    int rc = grow(&b->d_res_geoms, b->res_geoms_cap, n, b->stream);
-    if (rc == LAT_OK) rc = grow(&b->d_res_n, b->res_n_cap, n, b->stream);
+    int rc = grow(&sl.d_res_geoms, sl.res_geoms_cap, n, b->stream);
+    if (rc == LAT_OK) rc = grow(&sl.d_res_n, sl.res_n_cap, n, b->stream);
+    if (rc == LAT_OK) rc = ensure_pinned(sl, (size_t)n * (sizeof(Geom) + sizeof(long long)) + 64);
     if (rc != LAT_OK) return rc;
     cudaError_t e = cudaSuccess;
     if (b->res_stream == nullptr) e = cudaStreamCreateWithFlags(&b->res_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && b->ev_fork == nullptr) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess && b->ev_join == nullptr) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_res_geoms, geoms.data(), (size_t)n * sizeof(Geom), cudaMemcpyHostToDevice,
-                            b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_res_n, counts.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice,
-                            b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host vectors go out of scope
+    size_t at = 0;
+    at = stage(sl, at, sl.d_res_geoms, geoms.data(), (size_t)n, b->stream, e);
+    at = stage(sl, at, sl.d_res_n, counts.data(), (size_t)n, b->stream, e);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->res_stream, b->ev_fork, 0);
     for (long long done = 0; done < most && e == cudaSuccess; done += kResidentChunk)
-        e = launch_batch_resident(b->d_res_geoms, b->d_res_n, n, done, kResidentChunk, smem, b->res_stream);
+        e = launch_batch_resident(sl.d_res_geoms, sl.d_res_n, n, done, kResidentChunk, smem, b->res_stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->res_stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch resident launch");
     return LAT_OK;
@@ -268,24 +331,43 @@ int lattice_batch_run(lattice_batch_t *b)
     std::vector<std::pair<lattice *, int64_t>> work;
     work.swap(b->pending);
     if (work.empty()) return LAT_OK;
-    // Lattices must have no work in flight on their own streams (each
-    // distinct stream is synchronised once: lattices often share one).
-    std::vector<cudaStream_t> synced;
+    // Counter space for every sweep of the run (queued on each lattice's own
+    // stream), then the batch stream waits for the work queued so far on
+    // each distinct lattice stream (lattices often share one): an event
+    // wait, so the host does not block.
+    std::vector<cudaStream_t> streams;
     for (auto &pr : work) {
-        cudaStream_t ls = pr.first->stream;
-        if (std::find(synced.begin(), synced.end(), ls) == synced.end()) {
-            cudaError_t e = cudaStreamSynchronize(ls);
-            if (e != cudaSuccess) return cuda_fail(e, "batch sync");
-            synced.push_back(ls);
-        }
         int rc = ensure_series(pr.first, (unsigned long long)(pr.first->sweeps + pr.second));
         if (rc != LAT_OK) return rc;
+        cudaStream_t ls = pr.first->stream;
+        if (ls != b->stream && std::find(streams.begin(), streams.end(), ls) == streams.end()) streams.push_back(ls);
     }
+    while (b->ev_streams.size() < streams.size()) {
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "batch event");
+        b->ev_streams.push_back(ev);
+    }
+    for (size_t i = 0; i < streams.size(); ++i) {
+        cudaError_t e = cudaEventRecord(b->ev_streams[i], streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_streams[i], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "batch order");
+    }
+    BatchSlot *slp = nullptr;
+    int rc0 = take_slot(b, &slp);
+    if (rc0 != LAT_OK) return rc0;
+    BatchSlot &sl = *slp;
+    bool started = false;
+    auto mark_start = [&]() {
+        if (!started && b->start_event != nullptr) cudaEventRecord(b->start_event, b->stream);
+        started = true;
+    };
     // Small lattices: resident CTAs on the side stream.
     std::vector<std::pair<lattice *, int64_t>> res, rest;
     for (auto &pr : work) (runs_resident(pr.first) ? res : rest).push_back(pr);
     if (!res.empty()) {
-        int rc = run_resident(b, res);
+        mark_start();
+        int rc = run_resident(b, sl, res);
         if (rc != LAT_OK) return rc;
     }
     for (auto &pr : res) pr.first->sweeps += pr.second;
@@ -363,41 +445,75 @@ int lattice_batch_run(lattice_batch_t *b)
         done += steps;
     }
     if (!specs.empty()) {
-        int rc = grow(&b->d_geoms, b->geoms_cap, (int)all_geoms.size(), b->stream);
-        if (rc == LAT_OK) rc = grow(&b->d_items, b->items_cap, (int)all_items.size(), b->stream);
-        if (rc == LAT_OK) rc = grow(&b->d_ctrls, b->ctrls_cap, (int)all_ctrls.size(), b->stream);
+        int rc = grow(&sl.d_geoms, sl.geoms_cap, (int)all_geoms.size(), b->stream);
+        if (rc == LAT_OK) rc = grow(&sl.d_items, sl.items_cap, (int)all_items.size(), b->stream);
+        if (rc == LAT_OK) rc = grow(&sl.d_ctrls, sl.ctrls_cap, (int)all_ctrls.size(), b->stream);
+        const size_t need = all_geoms.size() * sizeof(Geom) + all_items.size() * sizeof(uint2) +
+                            all_ctrls.size() * sizeof(Ctrl *) + 64;
+        // the resident lattices' uploads sit at the front of the staging
+        const size_t res_bytes = res.empty() ? 0 : ((res.size() * (sizeof(Geom) + sizeof(long long)) + 64 + 15) & ~(size_t)15);
+        if (rc == LAT_OK && res.empty()) rc = ensure_pinned(sl, need);
+        if (rc == LAT_OK && !res.empty() && sl.h_cap < res_bytes + need) {
+            // growing would free staging that this run's resident uploads
+            // still read: wait for them first
+            cudaError_t e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "batch staging");
+            rc = ensure_pinned(sl, res_bytes + need);
+        }
         if (rc != LAT_OK) return rc;
-        cudaError_t e = cudaMemcpyAsync(b->d_geoms, all_geoms.data(), all_geoms.size() * sizeof(Geom),
-                                        cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_items, all_items.data(), all_items.size() * sizeof(uint2),
-                                cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_ctrls, all_ctrls.data(), all_ctrls.size() * sizeof(Ctrl *),
-                                cudaMemcpyHostToDevice, b->stream);
-        // The host vectors go out of scope: make the copies complete first.
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        mark_start();
+        cudaError_t e = cudaSuccess;
+        size_t at = res_bytes;
+        at = stage(sl, at, sl.d_geoms, all_geoms.data(), all_geoms.size(), b->stream, e);
+        at = stage(sl, at, sl.d_items, all_items.data(), all_items.size(), b->stream, e);
+        at = stage(sl, at, sl.d_ctrls, all_ctrls.data(), all_ctrls.size(), b->stream, e);
         if (e != cudaSuccess) return cuda_fail(e, "batch upload");
         for (const Spec &sp : specs) {
-            const Phase ph{sp.sh, sp.steps, b->d_geoms + sp.geom_off, b->d_items + sp.item_off,
-                           b->d_ctrls + sp.geom_off};
+            const Phase ph{sp.sh, sp.steps, sl.d_geoms + sp.geom_off, sl.d_items + sp.item_off,
+                           sl.d_ctrls + sp.geom_off};
             rc = run_steps(b, ph);
             if (rc != LAT_OK) return rc;
         }
     }
     for (auto &pr : work) pr.first->sweeps += pr.second;
+    mark_start();
     cudaError_t e = cudaSuccess;
     if (!res.empty()) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
     // Order later work on each lattice's own stream after the batch.
     if (e == cudaSuccess && b->ev_done == nullptr) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, b->stream);
-    for (auto *list : {&work, &res})
-        for (auto &pr : *list)
-            if (e == cudaSuccess && pr.first->stream != b->stream)
-                e = cudaStreamWaitEvent(pr.first->stream, b->ev_done, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, b->stream);   // the slot is free again after this
+    if (e == cudaSuccess) sl.used = true;
+    if (!b->caller_orders) {
+        streams.clear();
+        for (auto *list : {&work, &res})
+            for (auto &pr : *list) {
+                cudaStream_t ls = pr.first->stream;
+                if (ls != b->stream && std::find(streams.begin(), streams.end(), ls) == streams.end())
+                    streams.push_back(ls);
+            }
+        for (cudaStream_t ls : streams)
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ls, b->ev_done, 0);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "batch join");
     return LAT_OK;
 }
+
+}  // extern "C"
+
+// The server orders every other use of its lattices against the batch
+// stream itself (internal, not part of the C ABI).
+void batch_set_caller_orders(lattice_batch_t *b, bool on)
+{
+    if (b) b->caller_orders = on;
+}
+
+void batch_set_start_event(lattice_batch_t *b, cudaEvent_t ev)
+{
+    if (b) b->start_event = ev;
+}
+
+extern "C" {
 
 int lattice_batch_synchronize(lattice_batch_t *b)
 {
@@ -412,13 +528,20 @@ void lattice_batch_destroy(lattice_batch_t *b)
 {
     if (b == nullptr) return;
     cudaStreamSynchronize(b->stream);
-    dev_free(b->d_geoms, b->stream);
-    dev_free(b->d_items, b->stream);
-    dev_free(b->d_ctrls, b->stream);
-    dev_free(b->d_counters, b->stream);
     if (b->res_stream) cudaStreamSynchronize(b->res_stream);
-    dev_free(b->d_res_geoms, b->stream);
-    dev_free(b->d_res_n, b->stream);
+    for (BatchSlot &sl : b->slots) {
+        dev_free(sl.d_geoms, b->stream);
+        dev_free(sl.d_items, b->stream);
+        dev_free(sl.d_ctrls, b->stream);
+        dev_free(sl.d_res_geoms, b->stream);
+        dev_free(sl.d_res_n, b->stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    cudaStreamSynchronize(b->stream);
+    for (BatchSlot &sl : b->slots)
+        if (sl.h_pin) cudaFreeHost(sl.h_pin);
+    for (cudaEvent_t ev : b->ev_streams) cudaEventDestroy(ev);
+    dev_free(b->d_counters, b->stream);
     if (b->res_stream) cudaStreamDestroy(b->res_stream);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);

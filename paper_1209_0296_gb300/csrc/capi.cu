@@ -966,6 +966,12 @@ int lattice_autocorrelation(lattice_t *lt, int64_t first, int64_t count, double 
 {
     if (lt == nullptr || first < 0 || count < 0) return LAT_EINVAL;
     if (lt->ref_sweep < 0) return LAT_ENOENT;
+    if (std::isnan(m)) {
+        // the model's own polarisation: m = <s_i> = 2c - 1 for the North-East
+        // model at concentration c (§III.B, Eq. 4); other lattices have none
+        if (lt->P.model == LAT_NE && lt->P.cmode) m = 2.0 * lt->P.c - 1.0;
+        else if (phi != nullptr) return LAT_EINVAL;
+    }
     if (phi != nullptr && !(std::fabs(m) < 1.0)) return LAT_EINVAL;
     if (first < lt->series_first || first < lt->ref_sweep || first + count > lt->sweeps) return LAT_ERANGE;
     if (count == 0) return LAT_OK;

@@ -168,3 +168,68 @@ def test_drain_times_out_on_the_host_then_finishes():
     res = srv.poll(rid)
     assert res is not None and res["status"] == 0 and res["sweeps_done"] == 60000
     srv.close()
+
+
+def test_a_failed_request_ends_alone():
+    # An allocation failure injected on the host hits one request's lattice
+    # creation: that request ends with LAT_ENOMEM while a long request that
+    # was already running and one submitted after it finish, bit-exact.
+    lib = lt.load()
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=16, chunk_sweeps=32)
+    long_req = dict(dims=2, L=1024, two_S=1, model=lt.ISING, J=1.0, h=0.0, T_or_c=2.3, seed=3,
+                    init=lt.INIT_RANDOM, sweeps=3000)
+    wid = srv.submit(**long_req)
+    t0 = time.time()
+    while srv.stats()["rounds"] < 4 and time.time() - t0 < 60:   # its upload slots are all in use by now
+        time.sleep(0.005)
+    lib.lattice_test_fail_alloc(1)            # the next device allocation fails
+    bad = srv.submit(dims=2, L=96, model=lt.ISING, T_or_c=2.5, seed=4, sweeps=50)
+    late = dict(dims=2, L=50, two_S=1, model=lt.NE, J=0.0, h=0.0, T_or_c=0.3, seed=5,
+                init=lt.INIT_EQUILIBRIUM, sweeps=80)
+    res_bad = None
+    try:
+        t0 = time.time()
+        while res_bad is None and time.time() - t0 < 60:
+            res_bad = srv.poll(bad)
+            time.sleep(0.002)
+    finally:
+        lib.lattice_test_fail_alloc(0)
+    assert res_bad is not None and res_bad["status"] == -2 and res_bad["sweeps_done"] == 0
+    assert srv.poll(wid) is None              # the long request is still running
+    lid = srv.submit(**late, keep_spins=True)
+    srv.drain(300.0)
+    N = late["L"] ** 2
+    spins = np.empty(N, dtype=np.int8)
+    res_late = srv.poll(lid, spins)
+    res_long = srv.poll(wid)
+    assert res_late["status"] == 0 and res_long["status"] == 0
+    assert res_long["sweeps_done"] == 3000
+    _check_against_oracle(late, spins, res_late)
+    srv.close()
+
+
+def test_failed_request_status_is_reported():
+    lib = lt.load()
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=4, chunk_sweeps=16)
+    lib.lattice_test_fail_alloc(1)
+    try:
+        rid = srv.submit(dims=2, L=64, model=lt.ISING, T_or_c=2.5, seed=4, sweeps=10)
+        srv.drain(60.0)
+    finally:
+        lib.lattice_test_fail_alloc(0)
+    res = srv.poll(rid)
+    assert res["status"] == -2 and res["sweeps_done"] == 0   # LAT_ENOMEM
+    ok = srv.submit(dims=2, L=64, model=lt.ISING, T_or_c=2.5, seed=4, sweeps=10)
+    srv.drain(60.0)
+    assert srv.poll(ok)["status"] == 0
+    srv.close()
+
+
+def test_busy_time_is_reported():
+    srv = lt.Server(hbm_budget_bytes=1 << 30, max_slots=16, chunk_sweeps=64)
+    for s in range(6):
+        srv.submit(dims=2, L=512, model=lt.ISING, T_or_c=2.3, seed=s, sweeps=400)
+    srv.drain(120.0)
+    st = srv.stats()
+    assert st["rounds"] >= 7 and 0.0 < st["busy_s"] <= st["wall_s"]
+    srv.close()
