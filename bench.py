@@ -463,67 +463,80 @@ def batched_bench(n_lat=64, sweeps=200):
             "speedup": t_plain / t_batch, "bit_exact_vs_plain": exact}
 
 
-def served_bench(n_req=256, sweep_scale=0.01, load=None):
+def _run_served(lt, reqs, chunk=64):
+    """Serve the requests (arrival times in seconds from the start) through
+    the continuous-batching server: per-request latencies (completion -
+    arrival), the span from the first arrival to the last completion, all
+    statuses OK, and the fraction of the wall time the GPU ran rounds."""
+    srv = lt.Server(hbm_budget_bytes=32 << 30, max_slots=1024, chunk_sweeps=chunk)
+    t0 = srv.clock()
+    ids = []
+    for r in reqs:
+        while srv.clock() - t0 < r["arrival"]:
+            pass
+        ids.append(srv.submit(dims=r["dims"], L=r["L"], two_S=r["two_S"], model=r["model"],
+                              J=r["J"], h=r["h"], T_or_c=r["T_or_c"], seed=r["seed"],
+                              init=r["init"], sweeps=r["sweeps"]))
+    srv.drain(0.0)
+    res = [srv.poll(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([q["t_done"] - q["t_submit"] for q in res])
+    span = max(q["t_done"] for q in res) - min(q["t_submit"] for q in res)
+    ok = all(q["status"] == 0 for q in res)
+    return lat, span, ok, st["busy_s"] / max(st["wall_s"] - t0, 1e-9)
+
+
+def _run_plain(lt, reqs):
+    """The same requests one after another, each lattice with its own
+    launches (the plain arm): latencies and span."""
+    t0 = time.perf_counter()
+    lat = []
+    for r in reqs:
+        while time.perf_counter() - t0 < r["arrival"]:
+            pass
+        g = _lat_of(lt, r)
+        g.sweep(r["sweeps"])
+        g.synchronize()
+        lat.append(time.perf_counter() - t0 - r["arrival"])
+        g.close()
+    return np.array(lat), time.perf_counter() - t0
+
+
+def _pct(a):
+    return {"p50_ms": float(np.percentile(a, 50) * 1e3), "p99_ms": float(np.percentile(a, 99) * 1e3)}
+
+
+def served_bench(n_req=256, sweep_scale=0.01, arms=("served", "plain", "served_load_0.7", "plain_load_0.7")):
     """Requests of the served mix arriving as a Poisson process: served by
     the continuous-batching server, and (plain) one after another with one
     lattice's own launches each.  Latency = completion - arrival."""
-    import torch
     import paper_1209_0296_gb300 as lt
     from paper_1209_0296_gb300.workloads import served_mix, offered_updates
     base = served_mix(n=n_req, seed=99, gap_ms=2.0 * sweep_scale, sweep_scale=sweep_scale)
     upd = offered_updates(base)
     _warm_tuner(lt, base)
-
-    def run_served(reqs):
-        srv = lt.Server(hbm_budget_bytes=32 << 30, max_slots=1024, chunk_sweeps=64)
-        t0 = srv.clock()
-        ids = []
-        for r in reqs:
-            while srv.clock() - t0 < r["arrival"]:
-                pass
-            ids.append(srv.submit(dims=r["dims"], L=r["L"], two_S=r["two_S"], model=r["model"],
-                                  J=r["J"], h=r["h"], T_or_c=r["T_or_c"], seed=r["seed"],
-                                  init=r["init"], sweeps=r["sweeps"]))
-        srv.drain(600.0)
-        res = [srv.poll(i) for i in ids]
-        st = srv.stats()
-        srv.close()
-        lat = np.array([q["t_done"] - q["t_submit"] for q in res])
-        span = max(q["t_done"] for q in res) - min(q["t_submit"] for q in res)
-        ok = all(q["status"] == 0 for q in res)
-        return lat, span, ok, st["busy_s"] / max(st["wall_s"] - t0, 1e-9)
-
-    def run_plain(reqs):
-        t0 = time.perf_counter()
-        lat = []
-        for r in reqs:
-            while time.perf_counter() - t0 < r["arrival"]:
-                pass
-            g = _lat_of(lt, r)
-            g.sweep(r["sweeps"])
-            g.synchronize()
-            lat.append(time.perf_counter() - t0 - r["arrival"])
-            g.close()
-        return np.array(lat), time.perf_counter() - t0
-
-    def pct(a):
-        return {"p50_ms": float(np.percentile(a, 50) * 1e3), "p99_ms": float(np.percentile(a, 99) * 1e3)}
-
-    out = {"workload": "first %d requests of the served mix (default_rng(99)), sweeps x%g, gaps x%g"
-                       % (n_req, sweep_scale, sweep_scale), "offered_updates": upd}
-    lat, span, ok, busy = run_served(base)
-    out["served"] = dict(pct(lat), throughput=upd / span / 1e9, all_ok=ok, gpu_busy_frac=busy)
-    plat, pspan = run_plain(base)
-    out["plain"] = dict(pct(plat), throughput=upd / pspan / 1e9)
+    scaled = "first %d requests" % n_req if n_req < 4096 else "all 4096 requests"
+    out = {"workload": "%s of the served mix (default_rng(99)), sweeps x%g, gaps x%g"
+                       % (scaled, sweep_scale, sweep_scale), "offered_updates": upd,
+           "reduced": n_req < 4096 or sweep_scale != 1.0}
+    lat, span, ok, busy = _run_served(lt, base)
+    out["served"] = dict(_pct(lat), throughput=upd / span / 1e9, all_ok=ok, gpu_busy_frac=busy, span_s=span)
+    if "plain" in arms:
+        plat, pspan = _run_plain(lt, base)
+        out["plain"] = dict(_pct(plat), throughput=upd / pspan / 1e9, span_s=pspan)
     arrival_span = base[-1]["arrival"]
     out["offered_load"] = upd / arrival_span / 1e9 / out["served"]["throughput"]
     # the same requests at an offered load of about 0.7 of the served throughput
     scale = (upd / (0.7 * out["served"]["throughput"] * 1e9)) / arrival_span
     slow = [dict(r, arrival=r["arrival"] * scale) for r in base]
-    lat2, span2, ok2, busy2 = run_served(slow)
-    out["served_load_0.7"] = dict(pct(lat2), throughput=upd / span2 / 1e9, all_ok=ok2, gpu_busy_frac=busy2)
-    plat2, pspan2 = run_plain(slow)
-    out["plain_load_0.7"] = dict(pct(plat2), throughput=upd / pspan2 / 1e9)
+    if "served_load_0.7" in arms:
+        lat2, span2, ok2, busy2 = _run_served(lt, slow)
+        out["served_load_0.7"] = dict(_pct(lat2), throughput=upd / span2 / 1e9, all_ok=ok2,
+                                      gpu_busy_frac=busy2, span_s=span2)
+    if "plain_load_0.7" in arms:
+        plat2, pspan2 = _run_plain(lt, slow)
+        out["plain_load_0.7"] = dict(_pct(plat2), throughput=upd / pspan2 / 1e9, span_s=pspan2)
     out["unit"] = "updates/ns"
     return out
 
@@ -715,6 +728,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--no-other", action="store_true", help="skip the timings of the other named workloads")
+    ap.add_argument("--served-full", default="", metavar="ARMS",
+                    help="no headline: serve the whole served-mix workload (all 4096 requests, unscaled sweeps "
+                         "and gaps) through the arms named, comma-separated from served, plain, "
+                         "served_load_0.7, plain_load_0.7; prints one JSON line")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="no timing: run N sweeps of the T=2.0 lattice (a short run for ncu)")
     ap.add_argument("--profile-L", type=int, default=L)
@@ -727,6 +744,16 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+        return
+    if args.served_full:
+        import torch
+        torch.cuda.set_device(0)
+        t0 = time.perf_counter()
+        with Clocks(0) as clk:
+            out = served_bench(n_req=4096, sweep_scale=1.0, arms=tuple(args.served_full.split(",")))
+        out["wall_s"] = time.perf_counter() - t0
+        out["clocks"] = clk.summary()
+        print(json.dumps(out), flush=True)
         return
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

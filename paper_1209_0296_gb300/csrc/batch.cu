@@ -65,8 +65,7 @@ struct lattice_batch {
     // colour 0 / 1
     unsigned *d_counters = nullptr;
     int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0, grid_potts = 0;
-    int grid_wide2[2] = {0, 0};   // 2D wide, Ising / North-East
-    int grid_group[2] = {0, 0};   // 2D any-L, Ising / North-East
+    int grid_any[2] = {0, 0};     // 2D any-L, Ising / North-East
     // resident lattices
     cudaStream_t res_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -171,16 +170,16 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
             e = launch_batch_tiled(ph.geoms, ph.items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
                                    std::min(b->grid_tiled_ne, sh.n_ne), true, st);
         const uint2 *w2 = ph.items + sh.n_ising + sh.n_ne;
-        for (int m = 0; m < 2; ++m) {   // Ising, then North-East: colour 0, then colour 1
+        for (int m = 0; m < 2; ++m) {   // L % 32 == 0: Ising, then North-East: colour 0, then colour 1
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_w2[m] > 0; ++colour)
-                e = launch_batch_wide(ph.geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
-                                      m == 1, std::min(b->grid_wide2[m], sh.n_w2[m]), st);
+                e = launch_batch_any(ph.geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
+                                     m == 1, true, std::min(b->grid_any[m], sh.n_w2[m]), st);
             w2 += sh.n_w2[m];
         }
-        for (int m = 0; m < 2; ++m) {   // any-L: Ising, then North-East
+        for (int m = 0; m < 2; ++m) {   // other even L: Ising, then North-East
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_grp[m] > 0; ++colour)
-                e = launch_batch_group(ph.geoms, w2, sh.n_grp[m], b->d_counters + 12 + 2 * m + colour, colour,
-                                       m == 1, std::min(b->grid_group[m], sh.n_grp[m]), st);
+                e = launch_batch_any(ph.geoms, w2, sh.n_grp[m], b->d_counters + 12 + 2 * m + colour, colour,
+                                     m == 1, false, std::min(b->grid_any[m], sh.n_grp[m]), st);
             w2 += sh.n_grp[m];
         }
         const uint2 *wide = w2;
@@ -303,10 +302,8 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     b->grid_generic = batch_generic_grid();
     b->grid_wide = batch_wide3_grid();
     b->grid_potts = batch_potts_grid();
-    b->grid_wide2[0] = batch_wide_grid(false);
-    b->grid_wide2[1] = batch_wide_grid(true);
-    b->grid_group[0] = batch_group_grid(false);
-    b->grid_group[1] = batch_group_grid(true);
+    b->grid_any[0] = batch_any_grid(false);
+    b->grid_any[1] = batch_any_grid(true);
     *out = b;
     return LAT_OK;
 }
@@ -411,13 +408,9 @@ int lattice_batch_run(lattice_batch_t *b)
                 const int nt = tiles_of(lt->geom, 0);
                 auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
                 for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else if (!generic && wide_supported(lt->geom) && lt->geom.cpl == nullptr) {
-                const int nw = wide_items(lt->geom);
-                auto &dst = w2[lt->P.model == LAT_NE ? 1 : 0];
-                for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else if (!generic && group_supported(lt->geom)) {
-                const int ng = group_items(lt->geom);
-                auto &dst = grp[lt->P.model == LAT_NE ? 1 : 0];
+            } else if (!generic && any_supported(lt->geom)) {
+                const int ng = any_items(lt->geom);
+                auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[lt->P.model == LAT_NE ? 1 : 0];
                 for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
             } else if (!generic && wide3_supported(lt->geom)) {
                 const int nw = wide3_items(lt->geom);

@@ -220,10 +220,10 @@ void compact_table(Geom &g, const TabEntry *host_tab)
 }
 
 // LAT_KERNEL_WIDE covers four kernels: the 2D spin-1/2 one for L % 32 == 0
-// and its any-even-L form on single Philox groups (kernels_wide.cu), the
+// and its any-even-L form (kernels_wide.cu), the
 // 3D / spin-S Ising one (kernels_wide3.cu) and the Potts one
 // (kernels_potts.cu).
-static bool wide2_supported(const Geom &g) { return wide_supported(g) || group_supported(g); }
+static bool wide2_supported(const Geom &g) { return wide_supported(g) || any_supported(g); }
 static bool any_wide(const Geom &g) { return wide2_supported(g) || wide3_supported(g) || potts_supported(g); }
 
 int choose_kernel(const lattice *lt)

@@ -573,169 +573,385 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
 }
 
 // ---------------------------------------------------------------------
-// Any even L: one Philox group (the up to four same-colour sites
-// j = 4m .. 4m+3 of a plane row) per thread and row.  A plane row holds
-// L/2 bytes, so for L % 8 != 0 rows do not start on a word boundary and the
-// last group of a row holds L/2 % 4 sites; a group's bytes are gathered
-// from the aligned words that hold them, the neighbour past the group's
-// edge (west of site 4m, or east of its last site, across the periodic
-// row end when the group is the row's last) is one byte load, and a
-// partial or misaligned group is written byte by byte (its neighbours'
-// bytes belong to other threads).  The SWAR step is the wide kernel's on
-// one word, with the bytes past the last site masked off.
+// North-East model (§III.B), the same column walk with the loads of the
+// next chunk in flight, and draws compacted across the warp.  A site moves
+// only if its north and east neighbours are up, and then, in c-mode with
+// c < 1/2, an up site turns down without a draw; so only a few percent of
+// the Philox groups need a draw.  Each lane marks the groups of its chunk
+// that do; the warp lists them (ballot and prefix count), every lane makes
+// the Philox calls of list entries lane, lane + 32, ... and the draws go
+// back to their owners through shared memory.  A warp then makes
+// ceil(needed / 32) calls per lane instead of 4.  Same groups, counters and
+// bits as the other kernels.
 // ---------------------------------------------------------------------
+constexpr int kNeSlots = 4 * 32;   // list entries per warp (4 groups per lane)
 
-// The bytes p[0 .. nv) (1 <= nv <= 4) as one word, byte k = p[k], the
-// bytes from nv on unspecified.  Read from the aligned words that hold
-// them; the word after the last needed byte is not read, so every word
-// read holds an in-bounds byte (and the spin buffers are multiples of 4
-// bytes: N = L^2 with L even).
-LAT_D uint32_t load_group(const int8_t *p, uint32_t nv)
+template <int kColour, bool kRef>
+LAT_D void ne_col_step(bool act, const ColWalk<kColour> &c, const uint8_t *fl_c, const uint8_t *fl_o,
+                       const uint32_t *sthr, uint32_t y, const WideIn &in, const PhiloxPre &pp,
+                       uint32_t *gtab, uint4 *dq, Counts &cnt)
 {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const uint32_t sh = (uint32_t)(a & 3u);
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(a - sh);
-    const uint32_t lo = w[0];
-    const uint32_t hi = (sh + nv > 4u) ? w[1] : 0u;
-    return __funnelshift_r(lo, hi, 8u * sh);
-}
-
-LAT_D void store_group(int8_t *p, uint32_t v, uint32_t nv)
-{
-    if (nv == 4u && (reinterpret_cast<uintptr_t>(p) & 3u) == 0u) {
-        *reinterpret_cast<uint32_t *>(p) = v;
-    } else {
-        for (uint32_t k = 0; k < nv; ++k) p[k] = (int8_t)(v >> (8u * k));
+    const uint32_t oy = y * c.half;
+    const bool p1 = ((kColour + y) & 1) != 0;
+    const char *tb = reinterpret_cast<const char *>(sthr);
+    const uint32_t M1 = 0x02020202u;
+    const int lane = threadIdx.x & 31;
+    uint32_t Lf[4], R[4], t[4][4], locked[4], s1[4], c1[4];
+    unsigned need = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (!p1) {
+            Lf[w] = __funnelshift_l(w == 0 ? in.adj : in.O[w - 1], in.O[w], 8);
+            R[w] = in.O[w];
+        } else {
+            Lf[w] = in.O[w];
+            R[w] = __funnelshift_r(in.O[w], w == 3 ? in.adj : in.O[w + 1], 8);
+        }
+        const uint32_t Uw = in.U[w], Dw = in.D[w];
+        s1[w] = Uw ^ Dw ^ Lf[w];
+        c1[w] = (Uw & Dw) | (Uw & Lf[w]) | (Dw & Lf[w]);
+        const uint32_t b0 = s1[w] ^ R[w];
+        const uint32_t b1 = c1[w] ^ (s1[w] & R[w]);
+        const uint32_t b2 = c1[w] & s1[w] & R[w];
+        // §III.B: north (U) and east (R) must be up.  A locked site (either
+        // down: bit 6 of U | R set) indexes entries 16..31 of the table, all
+        // t' = all ones, so it needs no draw; its flip is masked off below.
+        locked[w] = Uw | R[w];
+        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
+                             (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u);
+        t[w][0] = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
+        t[w][1] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
+        t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
+        t[w][3] = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
+        if (act && (t[w][0] & t[w][1] & t[w][2] & t[w][3]) != 0xFFFFFFFFu) need |= 1u << w;
+    }
+    // the warp's list of groups that need a draw: group w of every lane, then w+1
+    unsigned bal[4], base[4], total = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        bal[w] = __ballot_sync(0xffffffffu, (need >> w) & 1u);
+        base[w] = total;
+        total += __popc(bal[w]);
+    }
+    U4 u[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) u[w] = U4{0u, 0u, 0u, 0u};   // t' all ones: any draw accepts
+    if (total > 0) {   // warp-uniform
+        const unsigned lt_mask = (1u << lane) - 1u;
+        const uint32_t g0 = y * c.G + 4u * c.k;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if ((need >> w) & 1u) gtab[base[w] + __popc(bal[w] & lt_mask)] = g0 + (uint32_t)w;
+        __syncwarp();
+        for (unsigned j = (unsigned)lane; j < total; j += 32) {
+            const U4 d = philox_item(pp, gtab[j], (uint32_t)kColour);
+            dq[j] = make_uint4(d.x, d.y, d.z, d.w);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if ((need >> w) & 1u) {
+                const uint4 q = dq[base[w] + __popc(bal[w] & lt_mask)];
+                u[w] = U4{q.x, q.y, q.z, q.w};
+            }
+        __syncwarp();   // the next chunk's list may overwrite these entries
+    }
+    if (!act) return;
+    uint32_t Sn[4], ue = 0, dn = 0, chg = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t acc = (u[w].x <= t[w][0] ? 1u : 0u) | (u[w].y <= t[w][1] ? 2u : 0u) |
+                             (u[w].z <= t[w][2] ? 4u : 0u) | (u[w].w <= t[w][3] ? 8u : 0u);
+        const uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu & ~locked[w];
+        chg |= ((((F >> 1) & 0x01010101u) * 0x01020408u) >> 24 & 0xFu) << (8 * w);
+        Sn[w] = in.S[w] ^ F;
+        if constexpr (kColour == 1) {
+            ue += ((s1[w] ^ Sn[w]) & M1) + ((c1[w] ^ Sn[w]) & 0x04040404u) + ((R[w] ^ Sn[w]) & M1);
+            dn += (Sn[w] & M1) + (in.O[w] & M1);
+        }
+    }
+    store_words<4>(c.dS + oy, Sn);
+    // persistence bytes of the chunk's four groups (bit q = site 4m+q)
+    uint32_t *fp = reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(fl_c) + (size_t)y * c.G);
+    const uint32_t f = *fp | chg;
+    *fp = f;
+    if constexpr (kColour == 1) {
+        const uint32_t fo = *reinterpret_cast<const uint32_t *>(fl_o + (size_t)y * c.G);
+        const int d2 = byte_sum(dn);
+        cnt.bond += 64 - byte_sum(ue);
+        cnt.mag += 32 - d2;
+        cnt.up += 32 - (d2 >> 1);
+        cnt.unfl += 32 - __popc(f) - __popc(fo);
+        if constexpr (kRef) {
+            uint32_t R1[4], R0[4], dr = 0;
+            load_words<4>(c.r1 + oy, R1);
+            load_words<4>(c.r0 + oy, R0);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) dr += ((Sn[w] ^ R1[w]) & M1) + ((in.O[w] ^ R0[w]) & M1);
+            cnt.acf += 32 - byte_sum(dr);
+        }
     }
 }
 
-struct GroupIn {
-    uint32_t S, O, U, D;   // the group's sites, the other plane's same-index, north and south words
-    uint32_t nb;           // the other plane's byte past the group's edge (west of 4m, or east of the last site)
+template <int kColour, bool kRef>
+__global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe_ne(Geom g, int off)
+{
+    __shared__ uint32_t sthr[32];   // entries 16..31: locked sites, always accepted (then masked)
+    __shared__ int red[kThreads / 32][5];
+    __shared__ uint32_t gtab[kThreads / 32][kNeSlots];
+    __shared__ uint4 dq[kThreads / 32][kNeSlots];
+    if (threadIdx.x < 32) sthr[threadIdx.x] = threadIdx.x < 16 ? g.thr16[threadIdx.x] : 0xFFFFFFFFu;
+    __syncthreads();
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
+    const SweepView v = sweep_view(g);
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
+    Counts cnt;
+    const uint32_t cpr = g.half >> 4;
+    const uint32_t rs = (gridDim.x * blockDim.x) / cpr;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t L = (uint32_t)g.L;
+    uint32_t y = gt / cpr;
+    const uint32_t k = gt - y * cpr;
+    bool act = y < rs && y < L;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+    const ColWalk<kColour> c = col_walk<kColour>(v, old, nw, act ? k : 0u);
+    const uint8_t *fl_c = g.flags + (size_t)kColour * g.rows * g.G + 4u * k;
+    const uint8_t *fl_o = g.flags + (size_t)(1 - kColour) * g.rows * g.G + 4u * k;
+    const int warp = threadIdx.x >> 5;
+    // Two chunks in flight (A and B in turn).  The warp's lanes stay in step
+    // (the draw list is made by the whole warp), so a lane that has run out
+    // of rows takes part with nothing to update.
+    WideIn A, B;
+    if (act) col_load<kColour>(c, y, A);
+    for (;;) {
+        if (!__any_sync(0xffffffffu, act)) break;
+        const uint32_t y1 = y + rs;
+        const bool act1 = act && y1 < L;
+        if (act1) col_load<kColour>(c, y1, B);
+        ne_col_step<kColour, kRef>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab[warp], dq[warp], cnt);
+        if (!__any_sync(0xffffffffu, act1)) break;
+        const uint32_t y2 = y1 + rs;
+        const bool act2 = act1 && y2 < L;
+        if (act2) col_load<kColour>(c, y2, A);
+        ne_col_step<kColour, kRef>(act1, c, fl_c, fl_o, sthr, y1, B, pp, gtab[warp], dq[warp], cnt);
+        y = y2;
+        act = act2;
+    }
+    if constexpr (kColour == 1) flush(v, sweep, cnt, true, red);
+}
+
+// ---------------------------------------------------------------------
+// Any even L, 16 sites per lane: the wide kernel's chunk of four Philox
+// groups on rows at any byte alignment.  A chunk's 16 bytes are gathered
+// from the aligned words that hold them; the last chunk of a row holds
+// L/2 % 16 sites (its bytes past the row are masked, its neighbour past the
+// row end is the row's first byte); stores write whole aligned words inside
+// the chunk and single bytes at its two ends, so no byte of another lane's
+// chunk is touched.  Column walk with two chunks in flight as in
+// k_wide_pipe (Ising: the next chunk's draws too) and, for the North-East
+// model, the warp-compacted draws of k_wide_pipe_ne.
+// ---------------------------------------------------------------------
+
+// Bytes p[0 .. nv) (1 <= nv <= 16) as four words, byte b = p[b], the bytes
+// from nv on unspecified; an aligned word that holds none of them is not
+// read (the spin buffers are multiples of 4 bytes, so every word read is in
+// bounds).  kAligned: p is 16-byte aligned and nv = 16 (every chunk of a
+// lattice with L % 32 == 0), one 16-byte load.
+template <bool kAligned = false>
+LAT_D void load16_any(const int8_t *p, uint32_t nv, uint32_t (&v)[4])
+{
+    if constexpr (kAligned) {
+        load_words<4>(p, v);
+        return;
+    }
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t sh = (uint32_t)(a & 3u);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(a - sh);
+    uint32_t x[5];
+    x[0] = w[0];
+#pragma unroll
+    for (int i = 1; i < 5; ++i) x[i] = (4u * (uint32_t)i < nv + sh) ? w[i] : 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __funnelshift_r(x[i], x[i + 1], 8u * sh);
+}
+
+// Write bytes [0, nv) of v to p (any alignment) and no other byte: whole
+// aligned words where the chunk covers them, single bytes at its ends.
+template <bool kAligned = false>
+LAT_D void store16_any(int8_t *p, uint32_t nv, const uint32_t (&v)[4])
+{
+    if constexpr (kAligned) {
+        store_words<4>(p, v);
+        return;
+    }
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t sh = (uint32_t)(a & 3u);
+    uint32_t *w = reinterpret_cast<uint32_t *>(a - sh);
+    uint32_t o[5];   // o[i]: the chunk's bytes that fall in aligned word i
+    o[0] = __funnelshift_l(0u, v[0], 8u * sh);
+#pragma unroll
+    for (int i = 1; i < 4; ++i) o[i] = __funnelshift_l(v[i - 1], v[i], 8u * sh);
+    o[4] = __funnelshift_l(v[3], 0u, 8u * sh);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int lo = i == 0 ? (int)sh : 0;
+        const int hi = min(4, (int)(nv + sh) - 4 * i);
+        if (hi <= lo) continue;
+        if (lo == 0 && hi == 4) {
+            w[i] = o[i];
+        } else {
+            int8_t *pb = reinterpret_cast<int8_t *>(w + i);
+            for (int j = lo; j < hi; ++j) pb[j] = (int8_t)(o[i] >> (8 * j));
+        }
+    }
+}
+
+struct AnyIn {
+    uint32_t S[4], O[4], U[4], D[4];
+    uint32_t nb;   // the other plane's byte past the chunk's edge (west of j0, or east of its last site)
 };
 
-// One thread's column of groups (group m of every plane row it visits).
+// One thread's column of chunks (chunk k of every plane row it visits).
 template <int kColour>
-struct GroupWalk {
-    const int8_t *pS;      // this colour's sites before the sweep (plane base)
-    const int8_t *pO;      // the other colour's current sites (plane base)
-    int8_t *dS;            // this colour's plane in the new buffer
-    const int8_t *r1, *r0; // reference planes 1 and 0 (or null)
-    uint8_t *fc;           // persistence bytes of this colour, group m of row 0 (North-East)
-    const uint8_t *fo;     // persistence bytes of the other colour, group m of row 0
-    uint32_t half, L, G, m, j0, nv, vmask;
-    uint32_t jprev, jnext; // row index of the west neighbour of site j0 / the east neighbour of the last site
+struct AnyWalk {
+    const int8_t *pS, *pO;   // planes: this colour's old sites, the other colour's current sites
+    int8_t *dS;              // this colour's plane in the new buffer
+    const int8_t *r1, *r0;   // reference planes 1 and 0 (or null)
+    uint32_t half, L, G, k, j0, nv;
+    uint32_t vm[4];          // valid-byte masks of the chunk's words
+    uint32_t jprev, jnext;   // row index of the west neighbour of j0 / the east neighbour of the last site
 };
 
 template <int kColour>
-LAT_D GroupWalk<kColour> group_walk(const SweepView &g, const int8_t *old, int8_t *nw, uint32_t m)
+LAT_D AnyWalk<kColour> any_walk(const SweepView &g, const int8_t *old, int8_t *nw, uint32_t k)
 {
     constexpr int oc = 1 - kColour;
-    GroupWalk<kColour> c;
+    AnyWalk<kColour> c;
     const uint32_t plane = (uint32_t)g.plane;
     c.pS = old + (size_t)kColour * plane;
     c.pO = (kColour == 0 ? old : nw) + (size_t)oc * plane;
     c.dS = nw + (size_t)kColour * plane;
     c.r1 = g.ref ? g.ref + (size_t)plane : nullptr;
     c.r0 = g.ref;
-    c.fc = g.flags ? g.flags + (size_t)kColour * g.rows * g.G + m : nullptr;
-    c.fo = g.flags ? g.flags + (size_t)oc * g.rows * g.G + m : nullptr;
     c.half = g.half;
     c.L = (uint32_t)g.L;
     c.G = g.G;
-    c.m = m;
-    c.j0 = 4u * m;
-    c.nv = min(4u, g.half - c.j0);
-    c.vmask = c.nv == 4u ? 0xFFFFFFFFu : (1u << (8u * c.nv)) - 1u;
+    c.k = k;
+    c.j0 = 16u * k;
+    c.nv = min(16u, g.half - c.j0);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int n = (int)c.nv - 4 * w;
+        c.vm[w] = n >= 4 ? 0xFFFFFFFFu : (n <= 0 ? 0u : (1u << (8 * n)) - 1u);
+    }
     c.jprev = c.j0 == 0u ? g.half - 1u : c.j0 - 1u;
     c.jnext = c.j0 + c.nv == g.half ? 0u : c.j0 + c.nv;
     return c;
 }
 
-template <int kColour>
-LAT_D void group_load(const GroupWalk<kColour> &c, uint32_t y, GroupIn &in)
+template <int kColour, bool kAligned = false>
+LAT_D void any_load(const AnyWalk<kColour> &c, uint32_t y, AnyIn &in)
 {
     const uint32_t oy = y * c.half;
     const uint32_t oym = y == 0 ? oy + (c.L - 1) * c.half : oy - c.half;
     const uint32_t oyp = y == c.L - 1 ? 0u : oy + c.half;
-    in.S = load_group(c.pS + oy + c.j0, c.nv);
-    in.O = load_group(c.pO + oy + c.j0, c.nv);
-    in.U = load_group(c.pO + oym + c.j0, c.nv);   // north
-    in.D = load_group(c.pO + oyp + c.j0, c.nv);   // south
+    load16_any<kAligned>(c.pS + oy + c.j0, c.nv, in.S);
+    load16_any<kAligned>(c.pO + oy + c.j0, c.nv, in.O);
+    load16_any<kAligned>(c.pO + oym + c.j0, c.nv, in.U);   // north
+    load16_any<kAligned>(c.pO + oyp + c.j0, c.nv, in.D);   // south
     in.nb = (uint32_t)(uint8_t)c.pO[oy + (((kColour + y) & 1) ? c.jnext : c.jprev)];
 }
 
 template <int kColour>
-LAT_D U4 group_draw(const PhiloxPre &pp, const GroupWalk<kColour> &c, uint32_t y)
+LAT_D void any_draws(const PhiloxPre &pp, const AnyWalk<kColour> &c, uint32_t y, U4 (&u)[4])
 {
-    return philox_item(pp, y * c.G + c.m, (uint32_t)kColour);
+    const uint32_t g0 = y * c.G + 4u * c.k;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)kColour);
 }
 
-template <int kColour, bool kNE, bool kRef>
-LAT_D void group_step(const GroupWalk<kColour> &c, const uint32_t *sthr, uint32_t y, const GroupIn &in, const U4 &u,
-                      Counts &cnt)
+// West (Lf) and east (R) neighbour words of the chunk's sites.
+template <int kColour>
+LAT_D void any_sides(const AnyWalk<kColour> &c, uint32_t y, const AnyIn &in, uint32_t (&Lf)[4], uint32_t (&R)[4])
+{
+    if (((kColour + y) & 1) == 0) {   // x = 2j: west is j-1 (nb for j0), east is j
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            Lf[w] = __funnelshift_l(w == 0 ? (in.nb << 24) : in.O[w - 1], in.O[w], 8);
+            R[w] = in.O[w];
+        }
+    } else {                          // x = 2j+1: west is j, east is j+1 (nb for the last site)
+        // a partial chunk's last site: its east neighbour nb goes to byte nv
+        // of the sequence (a mask that is zero in every other word)
+        uint32_t Oe[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t d = c.nv - 4u * (uint32_t)w;
+            const uint32_t m = d < 4u ? (0xFFu << (8u * d)) : 0u;
+            Oe[w] = (in.O[w] & ~m) | ((in.nb << (8u * (d & 3u))) & m);
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            Lf[w] = in.O[w];
+            R[w] = __funnelshift_r(Oe[w], w == 3 ? in.nb : Oe[w + 1], 8);
+        }
+    }
+}
+
+template <int kColour, bool kRef, bool kAligned = false>
+LAT_D void any_step(const AnyWalk<kColour> &c, const uint32_t *sthr, uint32_t y, const AnyIn &in, const U4 (&u)[4],
+                    Counts &cnt)
 {
     const uint32_t oy = y * c.half;
-    const bool p1 = ((kColour + y) & 1) != 0;
     const char *tb = reinterpret_cast<const char *>(sthr);
     const uint32_t M1 = 0x02020202u;
-    uint32_t Lf, R;
-    if (!p1) {   // x = 2j: west is j-1 of the other plane (nb for site j0), east is j
-        Lf = (in.O << 8) | in.nb;
-        R = in.O;
-    } else {     // x = 2j+1: west is j, east is j+1 (nb for the last site)
-        Lf = in.O;
-        R = ((in.O >> 8) & (c.vmask >> 8)) | (in.nb << (8u * (c.nv - 1u)));
+    uint32_t Lf[4], R[4];
+    any_sides<kColour>(c, y, in, Lf, R);
+    uint32_t Sn[4], ue = 0, dn = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t Uw = in.U[w], Dw = in.D[w];
+        const uint32_t s1 = Uw ^ Dw ^ Lf[w];
+        const uint32_t c1 = (Uw & Dw) | (Uw & Lf[w]) | (Dw & Lf[w]);
+        const uint32_t b0 = s1 ^ R[w];
+        const uint32_t b1 = c1 ^ (s1 & R[w]);
+        const uint32_t b2 = c1 & s1 & R[w];
+        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (in.S[w] & 0x20202020u);
+        const uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
+        const uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
+        const uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
+        const uint32_t t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
+        const uint32_t acc = (u[w].x <= t0 ? 1u : 0u) | (u[w].y <= t1 ? 2u : 0u) | (u[w].z <= t2 ? 4u : 0u) |
+                             (u[w].w <= t3 ? 8u : 0u);
+        const uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu & c.vm[w];
+        Sn[w] = in.S[w] ^ F;
+        if constexpr (kColour == 1) {
+            ue += (((s1 ^ Sn[w]) & M1) + ((c1 ^ Sn[w]) & 0x04040404u) + ((R[w] ^ Sn[w]) & M1)) & c.vm[w];
+            dn += ((Sn[w] & M1) + (in.O[w] & M1)) & c.vm[w];
+        }
     }
-    const uint32_t s1 = in.U ^ in.D ^ Lf;
-    const uint32_t c1 = (in.U & in.D) | (in.U & Lf) | (in.D & Lf);
-    const uint32_t b0 = s1 ^ R;
-    const uint32_t b1 = c1 ^ (s1 & R);
-    const uint32_t b2 = c1 & s1 & R;
-    const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (in.S & 0x20202020u);
-    uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
-    uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
-    uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
-    uint32_t t3 = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
-    uint32_t locked = 0;
-    if constexpr (kNE) {   // §III.B: north (U) and east (R) must be up
-        locked = in.U | R;
-        t0 |= prmt_sign(locked, 0x8888u);
-        t1 |= prmt_sign(locked, 0x9999u);
-        t2 |= prmt_sign(locked, 0xAAAAu);
-        t3 |= prmt_sign(locked, 0xBBBBu);
-    }
-    const uint32_t acc = (u.x <= t0 ? 1u : 0u) | (u.y <= t1 ? 2u : 0u) | (u.z <= t2 ? 4u : 0u) | (u.w <= t3 ? 8u : 0u);
-    uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu & c.vmask;   // 0xFE at flipped sites
-    if constexpr (kNE) F &= ~locked;
-    const uint32_t Sn = in.S ^ F;
-    store_group(c.dS + oy + c.j0, Sn, c.nv);
-    uint32_t fl = 0;
-    if constexpr (kNE) {
-        const uint32_t chg = (((F >> 1) & 0x01010101u) * 0x01020408u) >> 24 & 0xFu;
-        uint8_t *fp = c.fc + (size_t)y * c.G;
-        fl = (uint32_t)*fp | chg;
-        *fp = (uint8_t)fl;
-    }
+    store16_any<kAligned>(c.dS + oy + c.j0, c.nv, Sn);
     if constexpr (kColour == 1) {
-        const uint32_t ue = (((s1 ^ Sn) & M1) + ((c1 ^ Sn) & 0x04040404u) + ((R ^ Sn) & M1)) & c.vmask;
-        const uint32_t dn = ((Sn & M1) + (in.O & M1)) & c.vmask;
-        const int d2 = byte_sum(dn);
         const int nv = (int)c.nv;
+        const int d2 = byte_sum(dn);
         cnt.bond += 4 * nv - byte_sum(ue);
         cnt.mag += 2 * nv - d2;
         cnt.up += 2 * nv - (d2 >> 1);
-        if constexpr (kNE) cnt.unfl += 2 * nv - __popc(fl) - __popc((uint32_t)c.fo[(size_t)y * c.G]);
         if constexpr (kRef) {
-            const uint32_t R1 = load_group(c.r1 + oy + c.j0, c.nv), R0 = load_group(c.r0 + oy + c.j0, c.nv);
-            const uint32_t dr = (((Sn ^ R1) & M1) + ((in.O ^ R0) & M1)) & c.vmask;
+            uint32_t R1[4], R0[4], dr = 0;
+            load16_any<kAligned>(c.r1 + oy + c.j0, c.nv, R1);
+            load16_any<kAligned>(c.r0 + oy + c.j0, c.nv, R0);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) dr += (((Sn[w] ^ R1[w]) & M1) + ((in.O[w] ^ R0[w]) & M1)) & c.vm[w];
             cnt.acf += 2 * nv - byte_sum(dr);
         }
     }
 }
 
-template <int kColour, bool kNE, bool kRef>
-__global__ void __launch_bounds__(kThreads, 3) k_group_pipe(Geom g, int off)
+template <int kColour, bool kRef>
+__global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe(Geom g, int off)
 {
     __shared__ uint32_t sthr[16];
     __shared__ int red[kThreads / 32][5];
@@ -746,95 +962,312 @@ __global__ void __launch_bounds__(kThreads, 3) k_group_pipe(Geom g, int off)
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
     int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
     Counts cnt;
-    // thread -> (group m, first row y); rs rows between visits (the launch
-    // has at least G threads, rs * G of them work)
-    const uint32_t G = g.G;
-    const uint32_t rs = (gridDim.x * blockDim.x) / G;
+    const uint32_t cpr = (g.half + 15u) >> 4;   // chunks per plane row, the last partial
+    const uint32_t rs = (gridDim.x * blockDim.x) / cpr;
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t y = gt / G;
-    const uint32_t m = gt - y * G;
+    uint32_t y = gt / cpr;
+    const uint32_t k = gt - y * cpr;
     if (y < rs && y < (uint32_t)g.L) {
         PhiloxPre pp;
         philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
-        const GroupWalk<kColour> c = group_walk<kColour>(v, old, nw, m);
+        const AnyWalk<kColour> c = any_walk<kColour>(v, old, nw, k);
         const uint32_t L = (uint32_t)g.L;
-        // two groups in flight (A and B in turn), as in k_wide_pipe
-        GroupIn A, B;
-        U4 uA, uB;
-        group_load<kColour>(c, y, A);
-        uA = group_draw<kColour>(pp, c, y);
+        AnyIn A, B;
+        U4 uA[4], uB[4];
+        any_load<kColour>(c, y, A);
+        any_draws<kColour>(pp, c, y, uA);
         for (;;) {
             const uint32_t y1 = y + rs;
             if (y1 >= L) {
-                group_step<kColour, kNE, kRef>(c, sthr, y, A, uA, cnt);
+                any_step<kColour, kRef>(c, sthr, y, A, uA, cnt);
                 break;
             }
-            group_load<kColour>(c, y1, B);
-            uB = group_draw<kColour>(pp, c, y1);
-            group_step<kColour, kNE, kRef>(c, sthr, y, A, uA, cnt);
+            any_load<kColour>(c, y1, B);
+            any_draws<kColour>(pp, c, y1, uB);
+            any_step<kColour, kRef>(c, sthr, y, A, uA, cnt);
             const uint32_t y2 = y1 + rs;
             if (y2 >= L) {
-                group_step<kColour, kNE, kRef>(c, sthr, y1, B, uB, cnt);
+                any_step<kColour, kRef>(c, sthr, y1, B, uB, cnt);
                 break;
             }
-            group_load<kColour>(c, y2, A);
-            uA = group_draw<kColour>(pp, c, y2);
-            group_step<kColour, kNE, kRef>(c, sthr, y1, B, uB, cnt);
+            any_load<kColour>(c, y2, A);
+            any_draws<kColour>(pp, c, y2, uA);
+            any_step<kColour, kRef>(c, sthr, y1, B, uB, cnt);
             y = y2;
         }
     }
-    if constexpr (kColour == 1) flush(v, sweep, cnt, kNE, red);
+    if constexpr (kColour == 1) flush(v, sweep, cnt, false, red);
 }
 
-// Batched form of the any-L kernel: items are (lattice, band of rows) of
-// one colour; the CTA's threads take the band's groups in row-major order.
-constexpr uint32_t kGroupItemGroups = 2048;   // about 8 groups per thread per item
+// North-East at any even L: the step of ne_col_step with any-alignment
+// loads and stores, per-byte persistence updates (the groups of a row need
+// not start on a word), and the warp-compacted draws.
+template <int kColour, bool kRef, bool kAligned = false>
+LAT_D void any_ne_step(bool act, const AnyWalk<kColour> &c, uint8_t *fl_c, const uint8_t *fl_o,
+                       const uint32_t *sthr, uint32_t y, const AnyIn &in, const PhiloxPre &pp, uint32_t *gtab,
+                       uint4 *dq, Counts &cnt)
+{
+    const uint32_t oy = y * c.half;
+    const char *tb = reinterpret_cast<const char *>(sthr);
+    const uint32_t M1 = 0x02020202u;
+    const int lane = threadIdx.x & 31;
+    uint32_t Lf[4], R[4], t[4][4], locked[4], s1[4], c1[4];
+    any_sides<kColour>(c, y, in, Lf, R);
+    unsigned need = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t Uw = in.U[w], Dw = in.D[w];
+        s1[w] = Uw ^ Dw ^ Lf[w];
+        c1[w] = (Uw & Dw) | (Uw & Lf[w]) | (Dw & Lf[w]);
+        const uint32_t b0 = s1[w] ^ R[w];
+        const uint32_t b1 = c1[w] ^ (s1[w] & R[w]);
+        const uint32_t b2 = c1[w] & s1[w] & R[w];
+        // §III.B: a locked site (north or east down) indexes the all-accept
+        // entries 16..31; so do the bytes past the row (masked below)
+        locked[w] = Uw | R[w] | ~c.vm[w];
+        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
+                             (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u);
+        t[w][0] = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
+        t[w][1] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
+        t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
+        t[w][3] = *reinterpret_cast<const uint32_t *>(tb + (idx >> 24));
+        if (act && (t[w][0] & t[w][1] & t[w][2] & t[w][3]) != 0xFFFFFFFFu) need |= 1u << w;
+    }
+    unsigned bal[4], base[4], total = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        bal[w] = __ballot_sync(0xffffffffu, (need >> w) & 1u);
+        base[w] = total;
+        total += __popc(bal[w]);
+    }
+    U4 u[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) u[w] = U4{0u, 0u, 0u, 0u};
+    if (total > 0) {
+        const unsigned lt_mask = (1u << lane) - 1u;
+        const uint32_t g0 = y * c.G + 4u * c.k;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if ((need >> w) & 1u) gtab[base[w] + __popc(bal[w] & lt_mask)] = g0 + (uint32_t)w;
+        __syncwarp();
+        for (unsigned j = (unsigned)lane; j < total; j += 32) {
+            const U4 d = philox_item(pp, gtab[j], (uint32_t)kColour);
+            dq[j] = make_uint4(d.x, d.y, d.z, d.w);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if ((need >> w) & 1u) {
+                const uint4 q = dq[base[w] + __popc(bal[w] & lt_mask)];
+                u[w] = U4{q.x, q.y, q.z, q.w};
+            }
+        __syncwarp();
+    }
+    if (!act) return;
+    uint32_t Sn[4], ue = 0, dn = 0, chg = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t acc = (u[w].x <= t[w][0] ? 1u : 0u) | (u[w].y <= t[w][1] ? 2u : 0u) |
+                             (u[w].z <= t[w][2] ? 4u : 0u) | (u[w].w <= t[w][3] ? 8u : 0u);
+        const uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu & ~locked[w];
+        chg |= ((((F >> 1) & 0x01010101u) * 0x01020408u) >> 24 & 0xFu) << (8 * w);
+        Sn[w] = in.S[w] ^ F;
+        if constexpr (kColour == 1) {
+            ue += (((s1[w] ^ Sn[w]) & M1) + ((c1[w] ^ Sn[w]) & 0x04040404u) + ((R[w] ^ Sn[w]) & M1)) & c.vm[w];
+            dn += ((Sn[w] & M1) + (in.O[w] & M1)) & c.vm[w];
+        }
+    }
+    store16_any<kAligned>(c.dS + oy + c.j0, c.nv, Sn);
+    // persistence bytes of the chunk's groups that exist (4k + w < G)
+    uint8_t *fp = fl_c + (size_t)y * c.G;
+    const uint8_t *fop = fl_o + (size_t)y * c.G;
+    const uint32_t ng = min(4u, c.G - 4u * c.k);
+    int fpop = 0, fopop = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+        if ((uint32_t)w < ng) {
+            const uint32_t f = (uint32_t)fp[w] | ((chg >> (8 * w)) & 0xFu);
+            fp[w] = (uint8_t)f;
+            fpop += __popc(f);
+            if constexpr (kColour == 1) fopop += __popc((uint32_t)fop[w]);
+        }
+    if constexpr (kColour == 1) {
+        const int nv = (int)c.nv;
+        const int d2 = byte_sum(dn);
+        cnt.bond += 4 * nv - byte_sum(ue);
+        cnt.mag += 2 * nv - d2;
+        cnt.up += 2 * nv - (d2 >> 1);
+        cnt.unfl += 2 * nv - fpop - fopop;
+        if constexpr (kRef) {
+            uint32_t R1[4], R0[4], dr = 0;
+            load16_any<kAligned>(c.r1 + oy + c.j0, c.nv, R1);
+            load16_any<kAligned>(c.r0 + oy + c.j0, c.nv, R0);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) dr += (((Sn[w] ^ R1[w]) & M1) + ((in.O[w] ^ R0[w]) & M1)) & c.vm[w];
+            cnt.acf += 2 * nv - byte_sum(dr);
+        }
+    }
+}
 
-LAT_HD uint32_t group_band_rows(uint32_t G) { return G >= kGroupItemGroups ? 1u : kGroupItemGroups / G; }
+template <int kColour, bool kRef>
+__global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe_ne(Geom g, int off)
+{
+    __shared__ uint32_t sthr[32];   // entries 16..31: locked sites, always accepted (then masked)
+    __shared__ int red[kThreads / 32][5];
+    __shared__ uint32_t gtab[kThreads / 32][kNeSlots];
+    __shared__ uint4 dq[kThreads / 32][kNeSlots];
+    if (threadIdx.x < 32) sthr[threadIdx.x] = threadIdx.x < 16 ? g.thr16[threadIdx.x] : 0xFFFFFFFFu;
+    __syncthreads();
+    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
+    const SweepView v = sweep_view(g);
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
+    Counts cnt;
+    const uint32_t cpr = (g.half + 15u) >> 4;
+    const uint32_t rs = (gridDim.x * blockDim.x) / cpr;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t L = (uint32_t)g.L;
+    uint32_t y = gt / cpr;
+    const uint32_t k = gt - y * cpr;
+    bool act = y < rs && y < L;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
+    const AnyWalk<kColour> c = any_walk<kColour>(v, old, nw, act ? k : 0u);
+    uint8_t *fl_c = g.flags + (size_t)kColour * g.rows * g.G + 4u * c.k;
+    const uint8_t *fl_o = g.flags + (size_t)(1 - kColour) * g.rows * g.G + 4u * c.k;
+    const int warp = threadIdx.x >> 5;
+    AnyIn A, B;
+    if (act) any_load<kColour>(c, y, A);
+    for (;;) {
+        if (!__any_sync(0xffffffffu, act)) break;
+        const uint32_t y1 = y + rs;
+        const bool act1 = act && y1 < L;
+        if (act1) any_load<kColour>(c, y1, B);
+        any_ne_step<kColour, kRef>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab[warp], dq[warp], cnt);
+        if (!__any_sync(0xffffffffu, act1)) break;
+        const uint32_t y2 = y1 + rs;
+        const bool act2 = act1 && y2 < L;
+        if (act2) any_load<kColour>(c, y2, A);
+        any_ne_step<kColour, kRef>(act1, c, fl_c, fl_o, sthr, y1, B, pp, gtab[warp], dq[warp], cnt);
+        y = y2;
+        act = act2;
+    }
+    if constexpr (kColour == 1) flush(v, sweep, cnt, true, red);
+}
 
-template <int kColour, bool kNE>
-LAT_D void batch_group_item(const SweepView &v, const uint32_t *sthr, uint32_t band, Counts &cnt)
+// Batched form of the any-L kernels: a persistent grid takes (lattice,
+// item) pairs from an atomic counter.  An item is a band of rows and, in
+// rows of more than 256 chunks, a segment of 256 chunk columns; a thread
+// walks one chunk column down the band with two chunks in flight, as the
+// solo kernels do.
+struct AnyItemShape {
+    uint32_t cpr, nseg, rsb, br;   // chunks per row, column segments, rows per pass, rows per band
+};
+
+// Rows a thread visits per item: 8 on large lattices (few items, long
+// pipelines), 2 on small ones (enough items to spread a batch of small
+// lattices over the SMs).
+LAT_HD AnyItemShape any_item_shape(uint32_t half)
+{
+    AnyItemShape sh;
+    sh.cpr = (half + 15u) >> 4;
+    sh.nseg = (sh.cpr + kThreads - 1u) / kThreads;
+    sh.rsb = sh.cpr <= (uint32_t)kThreads ? (uint32_t)kThreads / sh.cpr : 1u;
+    sh.br = (half >= 512u ? 8u : 2u) * sh.rsb;
+    return sh;
+}
+
+template <int kColour, bool kNE, bool kAligned>
+LAT_D void batch_any_item(const SweepView &v, const uint32_t *sthr, uint32_t item, uint32_t *gtab, uint4 *dq,
+                          Counts &cnt)
 {
     const unsigned long long sweep = v.ctrl->sweep;
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), v.key0, v.key1);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
     int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
-    const uint32_t G = v.G, L = (uint32_t)v.L;
-    const uint32_t br = group_band_rows(G);
-    const uint32_t y0 = band * br;
-    const uint32_t y1 = min(L, y0 + br);
-    const uint32_t total = (y1 - y0) * G;
-    // walk t = tid, tid + 256, ... over the band as (row, group), without a
-    // division per step
-    uint32_t t = threadIdx.x;
-    uint32_t r = t / G, m = t - r * G;
-    const uint32_t sr = kThreads / G, sm = kThreads - sr * G;
-    for (; t < total; t += kThreads) {
-        const GroupWalk<kColour> c = group_walk<kColour>(v, old, nw, m);
-        GroupIn in;
-        group_load<kColour>(c, y0 + r, in);
-        const U4 u = group_draw<kColour>(pp, c, y0 + r);
-        if (v.ref != nullptr) group_step<kColour, kNE, true>(c, sthr, y0 + r, in, u, cnt);
-        else group_step<kColour, kNE, false>(c, sthr, y0 + r, in, u, cnt);
-        r += sr;
-        m += sm;
-        if (m >= G) {
-            m -= G;
-            ++r;
+    const AnyItemShape sh = any_item_shape(v.half);
+    const uint32_t L = (uint32_t)v.L;
+    const uint32_t band = item / sh.nseg, seg = item - band * sh.nseg;
+    const uint32_t y0 = band * sh.br, y1 = min(L, y0 + sh.br);
+    uint32_t k, r0;
+    if (sh.cpr <= (uint32_t)kThreads) {
+        k = threadIdx.x % sh.cpr;
+        r0 = threadIdx.x / sh.cpr;
+    } else {
+        k = seg * kThreads + threadIdx.x;
+        r0 = 0;
+    }
+    const bool mine = k < sh.cpr && r0 < sh.rsb;
+    uint32_t y = y0 + r0;
+    const AnyWalk<kColour> c = any_walk<kColour>(v, old, nw, mine ? k : 0u);
+    if constexpr (!kNE) {
+        if (!(mine && y < y1)) return;
+        AnyIn A, B;
+        U4 uA[4], uB[4];
+        any_load<kColour, kAligned>(c, y, A);
+        any_draws<kColour>(pp, c, y, uA);
+        for (;;) {
+            const uint32_t ya = y + sh.rsb;
+            if (ya >= y1) {
+                if (v.ref) any_step<kColour, true, kAligned>(c, sthr, y, A, uA, cnt);
+                else any_step<kColour, false, kAligned>(c, sthr, y, A, uA, cnt);
+                break;
+            }
+            any_load<kColour, kAligned>(c, ya, B);
+            any_draws<kColour>(pp, c, ya, uB);
+            if (v.ref) any_step<kColour, true, kAligned>(c, sthr, y, A, uA, cnt);
+            else any_step<kColour, false, kAligned>(c, sthr, y, A, uA, cnt);
+            const uint32_t yb = ya + sh.rsb;
+            if (yb >= y1) {
+                if (v.ref) any_step<kColour, true, kAligned>(c, sthr, ya, B, uB, cnt);
+                else any_step<kColour, false, kAligned>(c, sthr, ya, B, uB, cnt);
+                break;
+            }
+            any_load<kColour, kAligned>(c, yb, A);
+            any_draws<kColour>(pp, c, yb, uA);
+            if (v.ref) any_step<kColour, true, kAligned>(c, sthr, ya, B, uB, cnt);
+            else any_step<kColour, false, kAligned>(c, sthr, ya, B, uB, cnt);
+            y = yb;
+        }
+    } else {
+        // the warp's lanes stay in step (warp-compacted draws)
+        uint8_t *fl_c = v.flags + (size_t)kColour * v.rows * v.G + 4u * c.k;
+        const uint8_t *fl_o = v.flags + (size_t)(1 - kColour) * v.rows * v.G + 4u * c.k;
+        bool act = mine && y < y1;
+        AnyIn A, B;   // two chunks in flight
+        if (act) any_load<kColour, kAligned>(c, y, A);
+        for (;;) {
+            if (!__any_sync(0xffffffffu, act)) break;
+            const uint32_t ya = y + sh.rsb;
+            const bool act1 = act && ya < y1;
+            if (act1) any_load<kColour, kAligned>(c, ya, B);
+            if (v.ref) any_ne_step<kColour, true, kAligned>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab, dq, cnt);
+            else any_ne_step<kColour, false, kAligned>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab, dq, cnt);
+            if (!__any_sync(0xffffffffu, act1)) break;
+            const uint32_t yb = ya + sh.rsb;
+            const bool act2 = act1 && yb < y1;
+            if (act2) any_load<kColour, kAligned>(c, yb, A);
+            if (v.ref) any_ne_step<kColour, true, kAligned>(act1, c, fl_c, fl_o, sthr, ya, B, pp, gtab, dq, cnt);
+            else any_ne_step<kColour, false, kAligned>(act1, c, fl_c, fl_o, sthr, ya, B, pp, gtab, dq, cnt);
+            y = yb;
+            act = act2;
         }
     }
 }
 
-template <bool kNE>
-__global__ void __launch_bounds__(kThreads, 3) k_batch_group(const Geom *geoms, const uint2 *items, int n_items,
-                                                           unsigned *next_item, int colour)
+template <bool kNE, bool kAligned, int kColour>
+__global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *geoms, const uint2 *items, int n_items,
+                                                                  unsigned *next_item)
 {
-    __shared__ uint32_t sthr[16];
+    __shared__ uint32_t sthr[32];   // entries 16..31: locked North-East sites
     __shared__ int red[kThreads / 32][5];
+    __shared__ uint32_t gtab[kNE ? kThreads / 32 : 1][kNeSlots];
+    __shared__ uint4 dq[kNE ? kThreads / 32 : 1][kNeSlots];
     __shared__ Geom sg;
     __shared__ int cur;
     int loaded = -1;
+    const int warp = kNE ? (int)(threadIdx.x >> 5) : 0;
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
         __syncthreads();
@@ -846,67 +1279,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_batch_group(const Geom *geoms, 
                 reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
                     reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
             __syncthreads();
-            if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
+            if (threadIdx.x < 32) sthr[threadIdx.x] = threadIdx.x < 16 ? sg.thr16[threadIdx.x] : 0xFFFFFFFFu;
             loaded = (int)w.x;
             __syncthreads();
         }
         const SweepView v = sweep_view(sg);
         Counts cnt;
-        if (colour == 0) {
-            batch_group_item<0, kNE>(v, sthr, w.y, cnt);
-        } else {
-            batch_group_item<1, kNE>(v, sthr, w.y, cnt);
-            flush(v, v.ctrl->sweep, cnt, kNE, red);   // ends with __syncthreads()
-        }
-        __syncthreads();
-    }
-}
-
-// Batched form: a persistent grid takes (lattice, item) pairs from an
-// atomic counter; an item is kItemChunks x kThreads chunks of one colour of
-// one lattice.  The descriptor and table are reloaded only when a CTA moves
-// to another lattice (items are ordered by lattice); the sweep works on a
-// register copy of the descriptor.
-constexpr int kItemChunks = 4;
-
-template <bool kNE>
-__global__ void __launch_bounds__(kThreads, kNE ? 2 : 3) k_batch_wide(const Geom *geoms, const uint2 *items, int n_items,
-                                                        unsigned *next_item, int colour)
-{
-    __shared__ uint32_t sthr[16];
-    __shared__ int red[kThreads / 32][5];
-    __shared__ Geom sg;
-    __shared__ int cur;
-    int loaded = -1;
-    for (;;) {
-        if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
-        __syncthreads();
-        const int it = cur;
-        if (it >= n_items) break;
-        const uint2 w = items[it];
-        if ((int)w.x != loaded) {
-            if (threadIdx.x < sizeof(Geom) / 4)
-                reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
-                    reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
-            __syncthreads();
-            if (threadIdx.x < 16) sthr[threadIdx.x] = sg.thr16[threadIdx.x];
-            loaded = (int)w.x;
-            __syncthreads();
-        }
-        const SweepView v = sweep_view(sg);
-        const unsigned long long sweep = v.ctrl->sweep;
-        PhiloxPre pp;
-        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), v.key0, v.key1);
-        const uint32_t cpr = v.half >> 4;
-        const uint32_t total = (uint32_t)v.L * cpr;
-        Counts cnt;
-#pragma unroll 1
-        for (int c = 0; c < kItemChunks; ++c) {
-            const uint32_t t = (w.y * (uint32_t)kItemChunks + (uint32_t)c) * kThreads + threadIdx.x;
-            if (t >= total) break;
-            wide_chunk<kNE>(v, sthr, colour, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
-        }
-        if (colour == 1) flush(v, sweep, cnt, kNE, red);   // ends with __syncthreads()
+        batch_any_item<kColour, kNE, kAligned>(v, sthr, w.y, gtab[warp], dq[warp], cnt);
+        if constexpr (kColour == 1) flush(v, v.ctrl->sweep, cnt, kNE, red);   // ends with __syncthreads()
         __syncthreads();
     }
 }
@@ -1053,7 +1433,7 @@ bool wide_supported(const Geom &g)
 
 int wide_chunks(const Geom &g) { return (int)(((uint64_t)g.L * (g.half >> 4) + kThreads - 1) / kThreads); }
 
-bool group_supported(const Geom &g)
+bool any_supported(const Geom &g)
 {
     if (!(g.dims == 2 && g.two_S == 1 && g.bits[0] == nullptr && g.cpl == nullptr && (g.L % 2) == 0)) return false;
     if (g.model == LAT_POTTS) return false;
@@ -1064,28 +1444,33 @@ bool group_supported(const Geom &g)
     return true;
 }
 
-int group_items(const Geom &g)
+int any_items(const Geom &g)
 {
-    const uint32_t br = group_band_rows(g.G);
-    return (int)(((uint32_t)g.L + br - 1) / br);
+    const AnyItemShape sh = any_item_shape(g.half);
+    return (int)((((uint32_t)g.L + sh.br - 1u) / sh.br) * sh.nseg);
 }
 
-int batch_group_grid(bool ne)
+int batch_any_grid(bool ne)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (ne) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_group<true>, kThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_group<false>, kThreads, 0);
+    if (ne) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_any<true, false, 1>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_any<false, false, 1>, kThreads, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
 
-cudaError_t launch_batch_group(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                               bool ne, int grid, cudaStream_t st)
+cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
+                             bool ne, bool aligned, int grid, cudaStream_t st)
 {
-    if (ne) k_batch_group<true><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
-    else k_batch_group<false><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    using K = void (*)(const Geom *, const uint2 *, int, unsigned *);
+    static const K kern[2][2][2] = {
+        {{k_batch_any<false, false, 0>, k_batch_any<false, false, 1>},
+         {k_batch_any<false, true, 0>, k_batch_any<false, true, 1>}},
+        {{k_batch_any<true, false, 0>, k_batch_any<true, false, 1>},
+         {k_batch_any<true, true, 0>, k_batch_any<true, true, 1>}}};
+    kern[ne ? 1 : 0][aligned ? 1 : 0][colour ? 1 : 0]<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item);
     return cudaGetLastError();
 }
 
@@ -1104,20 +1489,33 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
         }
         return cache;
     };
-    if (!wide_supported(g)) {   // L % 32 != 0: the any-L group kernels
-        static int res_group = 0;
-        const uint64_t groups = (uint64_t)g.L * g.G;
+    if (!wide_supported(g)) {   // L % 32 != 0: the any-L kernels, 16 sites per lane
+        static int res_any = 0;
+        const uint64_t chunks = (uint64_t)g.L * ((g.half + 15u) >> 4);
         const unsigned gb = (unsigned)std::min<long long>(
-            (long long)((groups + kThreads - 1) / kThreads),
-            wave(reinterpret_cast<const void *>(k_group_pipe<1, true, true>), res_group));
+            (long long)((chunks + kThreads - 1) / kThreads),
+            wave(reinterpret_cast<const void *>(k_any_pipe_ne<1, true>), res_any));
         using KG = void (*)(Geom, int);
         const bool ne = g.model == LAT_NE, ref = k.ref != nullptr;
-        const KG c0 = ne ? (ref ? k_group_pipe<0, true, true> : k_group_pipe<0, true, false>)
-                         : (ref ? k_group_pipe<0, false, true> : k_group_pipe<0, false, false>);
-        const KG c1 = ne ? (ref ? k_group_pipe<1, true, true> : k_group_pipe<1, true, false>)
-                         : (ref ? k_group_pipe<1, false, true> : k_group_pipe<1, false, false>);
+        const KG c0 = ne ? (ref ? k_any_pipe_ne<0, true> : k_any_pipe_ne<0, false>)
+                         : (ref ? k_any_pipe<0, true> : k_any_pipe<0, false>);
+        const KG c1 = ne ? (ref ? k_any_pipe_ne<1, true> : k_any_pipe_ne<1, false>)
+                         : (ref ? k_any_pipe<1, true> : k_any_pipe<1, false>);
         c0<<<gb, kThreads, 0, st>>>(k, off);
         c1<<<gb, kThreads, 0, st>>>(k, off);
+        return cudaGetLastError();
+    }
+    if (g.model == LAT_NE && g.cpl == nullptr) {   // North-East: pipelined, draws compacted per warp
+        static int res_ne = 0;
+        const unsigned pb = (unsigned)std::min<long long>(
+            wide_chunks(g), wave(reinterpret_cast<const void *>(k_wide_pipe_ne<1, true>), res_ne));
+        if (k.ref != nullptr) {
+            k_wide_pipe_ne<0, true><<<pb, kThreads, 0, st>>>(k, off);
+            k_wide_pipe_ne<1, true><<<pb, kThreads, 0, st>>>(k, off);
+        } else {
+            k_wide_pipe_ne<0, false><<<pb, kThreads, 0, st>>>(k, off);
+            k_wide_pipe_ne<1, false><<<pb, kThreads, 0, st>>>(k, off);
+        }
         return cudaGetLastError();
     }
     if (g.model != LAT_NE && g.cpl == nullptr) {   // uniform Ising: the software-pipelined kernels
@@ -1201,30 +1599,5 @@ size_t resident_smem_bytes(const Geom &g) { return resident_bytes(g); }
 
 namespace lat {
 
-int wide_items(const Geom &g)
-{
-    const uint64_t chunks = (uint64_t)g.L * (g.half >> 4);
-    const uint64_t per = (uint64_t)kItemChunks * kThreads;
-    return (int)((chunks + per - 1) / per);
-}
-
-int batch_wide_grid(bool ne)
-{
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (ne) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide<true>, kThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide<false>, kThreads, 0);
-    if (per < 1) per = 1;
-    return sms * per;
-}
-
-cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                              bool ne, int grid, cudaStream_t st)
-{
-    if (ne) k_batch_wide<true><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
-    else k_batch_wide<false><<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
-    return cudaGetLastError();
-}
 
 }  // namespace lat

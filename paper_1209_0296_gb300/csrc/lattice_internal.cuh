@@ -354,11 +354,6 @@ size_t resident_smem_bytes(const Geom &g);
 // geoms: compact-table descriptors (tiled_geom); n[i]: sweeps for lattice i
 cudaError_t launch_batch_resident(const Geom *geoms, const long long *n, int n_lat, long long done, int chunk,
                                   size_t smem, cudaStream_t st);
-// Batched 2D spin-1/2 wide sweep (geoms: compact-table descriptors).
-int wide_items(const Geom &g);
-int batch_wide_grid(bool ne);
-cudaError_t launch_batch_wide(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                              bool ne, int grid, cudaStream_t st);
 bool wide3_supported(const Geom &g);
 // q-state Potts model, 8 sites per thread (kernels_potts.cu)
 bool potts_supported(const Geom &g);
@@ -374,13 +369,14 @@ cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_item
                                int colour, int grid, cudaStream_t st);
 int wide_chunks(const Geom &g);
 // 2D spin-1/2 Ising / North-East with uniform couplings at any even L (the
-// wide kernel's sweep on single Philox groups; launch_sweep_wide takes these
-// lattices when L % 32 != 0), and its batched form
-bool group_supported(const Geom &g);
-int group_items(const Geom &g);   // batch items of one colour of one lattice
-int batch_group_grid(bool ne);
-cudaError_t launch_batch_group(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                               bool ne, int grid, cudaStream_t st);
+// wide kernel's sweep on rows at any byte alignment; launch_sweep_wide takes
+// these lattices when L % 32 != 0), and its batched form
+bool any_supported(const Geom &g);
+int any_items(const Geom &g);   // batch items of one colour of one lattice
+int batch_any_grid(bool ne);
+// aligned: every lattice of the items has L % 32 == 0 (16-byte aligned rows)
+cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
+                             bool ne, bool aligned, int grid, cudaStream_t st);
 // batched engine
 Geom tiled_geom(const Geom &g);
 int tiles_of(const Geom &g, int tile_h);
