@@ -284,13 +284,21 @@ int lattice_device_spins(lattice_t *lat, void **dev_ptr, size_t *bytes);
 /* Pick the kernel (enum lattice_kernel), the tile shape (tile_w columns x
  * tile_h rows; 0 = default) and the sweeps per CUDA-graph replay
  * (0 = default).  LAT_ENOTSUP if the kernel does not cover the lattice.
- * With LAT_KERNEL_AUTO a 2D spin-1/2 int8 lattice is tuned by its first
- * sweep call of at least 24 sweeps (32 when the resident kernel is a
- * candidate): each candidate kernel runs 8 of the
- * caller's sweeps (same bits whichever runs) and the fastest is kept for
- * that (model, L) for the life of the process.  If the environment variable
- * LATTICE_TUNE_CACHE names a file, the choices also persist there, one JSON
- * object per line: {"model": m, "L": L, "kernel": k, "tile_h": h}. */
+ * With LAT_KERNEL_AUTO an int8 lattice with uniform couplings is tuned by
+ * its first long enough sweep call, on the caller's own sweeps (same bits
+ * whichever kernel or graph size runs them):
+ *   - the kernel, when there is a choice (2D spin-1/2 with L % 32 == 0:
+ *     wide, tiled at two tile heights, resident when it fits one CTA), 8
+ *     sweeps per candidate, which needs a call of at least 8 sweeps per
+ *     candidate;
+ *   - then the sweeps per CUDA-graph replay (a size set here is kept): half,
+ *     one, two and four times the default size, each timed on one replay
+ *     after an untimed one, as far as the call's remaining sweeps reach.
+ * The choice is kept for that (model, dims, two_S, L) for the life of the
+ * process.  If the environment variable LATTICE_TUNE_CACHE names a file,
+ * the choices also persist there, one JSON object per line:
+ * {"model": m, "dims": d, "two_S": s, "L": L, "kernel": k, "tile_h": h,
+ *  "graph": g} (g = 0: the default size). */
 int lattice_set_kernel(lattice_t *lat, int kernel, int tile_w, int tile_h,
                        int sweeps_per_graph);
 
@@ -322,8 +330,9 @@ void lattice_destroy(lattice_t *lat);
 /* Results are bit-exact with running each lattice alone.               */
 /* ------------------------------------------------------------------ */
 
-/* A batch runs on its own stream (NULL = default stream); lattices added
- * to it must not have other work in flight. */
+/* A batch runs on its own stream (NULL = default stream).  Work already
+ * queued on a lattice's own stream is ordered before the batch's (an event
+ * wait: the host does not block). */
 int lattice_batch_create(lattice_batch_t **out, void *cuda_stream);
 /* Schedule n more sweeps of lat in the next lattice_batch_run. */
 int lattice_batch_add(lattice_batch_t *b, lattice_t *lat, int64_t n);
@@ -335,6 +344,16 @@ int lattice_batch_add(lattice_batch_t *b, lattice_t *lat, int64_t n);
  * their sweeps, concurrently with the others. */
 int lattice_batch_run(lattice_batch_t *b);
 int lattice_batch_synchronize(lattice_batch_t *b);
+/* The batch engine's two tunables as its last run used them: the rows a
+ * thread visits per 2D item (*rows_per_item; 0 = the size-based default,
+ * 8 rows on lattices with L >= 1024 and 2 below) and the steps per captured
+ * CUDA graph (*steps_per_graph).  A run whose first phase (all its
+ * lattices) has at least 192 steps tunes both once per composition of
+ * lattices (models, dimensions, spins, sizes and kernels), timing
+ * candidates on its own steps (same bits whichever runs) and synchronising
+ * the host meanwhile; shorter runs use the tuned values of their
+ * composition, or the defaults.  NULL outputs are skipped. */
+int lattice_batch_tuning(lattice_batch_t *b, int *rows_per_item, int *steps_per_graph);
 void lattice_batch_destroy(lattice_batch_t *b);
 
 /* ------------------------------------------------------------------ */

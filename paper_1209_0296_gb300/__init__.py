@@ -264,6 +264,12 @@ class Batch:
         check(self._lib.lattice_batch_run(self._h), "lattice_batch_run")
         self._keep = []
 
+    def tuning(self):
+        """Rows per 2D item (0 = size-based default) and steps per graph of the last run."""
+        r, g = ctypes.c_int(), ctypes.c_int()
+        check(self._lib.lattice_batch_tuning(self._h, ctypes.byref(r), ctypes.byref(g)), "lattice_batch_tuning")
+        return dict(rows_per_item=r.value, steps_per_graph=g.value)
+
     def synchronize(self):
         check(self._lib.lattice_batch_synchronize(self._h), "lattice_batch_synchronize")
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "lattice_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_void_p]),
     "lattice_batch_add": (c_int, [c_void_p, c_void_p, c_int64]),
     "lattice_batch_run": (c_int, [c_void_p]),
+    "lattice_batch_tuning": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "lattice_batch_synchronize": (c_int, [c_void_p]),
     "lattice_batch_destroy": (None, [c_void_p]),
     "lattice_server_create": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int]),

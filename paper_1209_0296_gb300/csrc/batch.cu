@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -59,6 +60,9 @@ struct lattice_batch {
     // Recorded on the batch stream right before a run's first device work
     // (after its host preparation), when set: the server's busy-time clock.
     cudaEvent_t start_event = nullptr;
+    // The rows per any-L item and steps per graph of the last run (0 rows:
+    // the size-based default), as tuned or defaulted.
+    int last_passes = 0, last_gsteps = 0;
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S wide
     // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1,
     // Potts colour 0 / 1, any-L 2D Ising colour 0 / 1, any-L 2D North-East
@@ -155,6 +159,14 @@ struct Phase {
     const Geom *geoms;
     const uint2 *items;
     Ctrl *const *ctrls;
+    int passes;   // rows a thread visits per any-L item (0: the size-based default)
+    int gsteps;   // steps per captured graph
+};
+
+// The batch tuner's choice for one composition of lattices: rows per
+// any-L item and steps per captured graph.
+struct BatchTune {
+    int passes, gsteps;
 };
 
 // Queue `steps` sweep steps of one phase.
@@ -173,13 +185,13 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
         for (int m = 0; m < 2; ++m) {   // L % 32 == 0: Ising, then North-East: colour 0, then colour 1
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_w2[m] > 0; ++colour)
                 e = launch_batch_any(ph.geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
-                                     m == 1, true, std::min(b->grid_any[m], sh.n_w2[m]), st);
+                                     m == 1, true, ph.passes, std::min(b->grid_any[m], sh.n_w2[m]), st);
             w2 += sh.n_w2[m];
         }
         for (int m = 0; m < 2; ++m) {   // other even L: Ising, then North-East
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_grp[m] > 0; ++colour)
                 e = launch_batch_any(ph.geoms, w2, sh.n_grp[m], b->d_counters + 12 + 2 * m + colour, colour,
-                                     m == 1, false, std::min(b->grid_any[m], sh.n_grp[m]), st);
+                                     m == 1, false, ph.passes, std::min(b->grid_any[m], sh.n_grp[m]), st);
             w2 += sh.n_grp[m];
         }
         const uint2 *wide = w2;
@@ -203,33 +215,42 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
     return LAT_OK;
 }
 
+// Capture `steps` steps of a phase in a CUDA graph on the capture stream.
+int capture_steps(lattice_batch *b, const Phase &ph, int steps, cudaGraphExec_t *exec)
+{
+    if (b->cap_stream == nullptr) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "batch capture stream");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "batch begin capture");
+    int rc = enqueue_steps(b, ph, steps, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rc != LAT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+    return LAT_OK;
+}
+
 int run_steps(lattice_batch *b, const Phase &ph)
 {
     int64_t left = ph.steps;
     // A graph pays for its capture and instantiation (milliseconds) only
     // over many replays; short runs (a serving round) launch directly,
     // which the host enqueues faster than the device drains them.
-    if (left >= kGraphMinSteps) {
-        if (b->cap_stream == nullptr) {
-            cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_fail(e, "batch capture stream");
-        }
-        cudaGraph_t graph = nullptr;
+    if (left >= std::max<int64_t>(kGraphMinSteps, ph.gsteps)) {
         cudaGraphExec_t exec = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "batch begin capture");
-        int rc = enqueue_steps(b, ph, kGraphSteps, b->cap_stream);
-        e = cudaStreamEndCapture(b->cap_stream, &graph);
-        if (rc != LAT_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "batch graph");
-        while (left >= kGraphSteps && e == cudaSuccess) {
+        int rc = capture_steps(b, ph, ph.gsteps, &exec);
+        if (rc != LAT_OK) return rc;
+        cudaError_t e = cudaSuccess;
+        while (left >= ph.gsteps && e == cudaSuccess) {
             e = cudaGraphLaunch(exec, b->stream);
-            left -= kGraphSteps;
+            left -= ph.gsteps;
         }
         cudaGraphExecDestroy(exec);  // safe: destruction waits for no launch; launches stay valid
         if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
@@ -278,6 +299,162 @@ int run_resident(lattice_batch *b, BatchSlot &sl, const std::vector<std::pair<la
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->res_stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch resident launch");
     return LAT_OK;
+}
+
+// The work lists of one phase (the first n_active lattices of `work`),
+// appended to geoms / ctrls / items; returns its item counts.
+Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t n_active, int passes,
+                  std::vector<Geom> &geoms, std::vector<Ctrl *> &ctrls, std::vector<uint2> &items)
+{
+    std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide, potts, gen;
+    int tab_gen = 0;
+    for (size_t i = 0; i < n_active; ++i) {
+        lattice *lt = work[i].first;
+        geoms.push_back(tiled_geom(lt->geom));
+        ctrls.push_back(lt->ctrl);
+        // 2D spin-1/2 lattices take the tiled items when their kernel is the
+        // tiled one, else the any-L items (16-byte aligned rows when
+        // L % 32 == 0); 3D and spin-S Ising lattices with L % 16 == 0 take
+        // the 3D wide items, Potts lattices with L % 16 == 0 the Potts items;
+        // the rest (other sizes, per-site disorder, an explicit generic
+        // choice) go to the generic chunks.  Item lattice indexes are local
+        // to the phase.
+        const int kern = choose_kernel(lt);
+        const bool generic = kern == LAT_KERNEL_GENERIC;
+        if (!generic && tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) {
+            const int nt = tiles_of(lt->geom, 0);
+            auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
+            for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+        } else if (!generic && any_supported(lt->geom)) {
+            const int ng = any_items(lt->geom, passes);
+            auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[lt->P.model == LAT_NE ? 1 : 0];
+            for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
+        } else if (!generic && wide3_supported(lt->geom)) {
+            const int nw = wide3_items(lt->geom);
+            for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
+        } else if (!generic && potts_supported(lt->geom)) {
+            const int np = potts_items(lt->geom);
+            for (int k = 0; k < np; ++k) potts.push_back(make_uint2((unsigned)i, (unsigned)k));
+        } else {
+            const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
+            const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
+            for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
+            tab_gen = std::max(tab_gen, lt->geom.tab_n);
+        }
+    }
+    for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &grp[0], &grp[1], &wide, &potts, &gen})
+        items.insert(items.end(), v->begin(), v->end());
+    return Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
+                 {(int)grp[0].size(), (int)grp[1].size()}, (int)wide.size(), (int)potts.size(), (int)gen.size(),
+                 tab_gen};
+}
+
+// Upload a run's work lists into the slot's device arrays through its
+// pinned staging, after the first res_bytes of staging (the resident
+// lattices' uploads of the same run).
+int upload_lists(lattice_batch *b, BatchSlot &sl, size_t res_bytes, const std::vector<Geom> &geoms,
+                 const std::vector<uint2> &items, const std::vector<Ctrl *> &ctrls)
+{
+    int rc = grow(&sl.d_geoms, sl.geoms_cap, (int)geoms.size(), b->stream);
+    if (rc == LAT_OK) rc = grow(&sl.d_items, sl.items_cap, (int)items.size(), b->stream);
+    if (rc == LAT_OK) rc = grow(&sl.d_ctrls, sl.ctrls_cap, (int)ctrls.size(), b->stream);
+    const size_t need = geoms.size() * sizeof(Geom) + items.size() * sizeof(uint2) + ctrls.size() * sizeof(Ctrl *) + 64;
+    if (rc == LAT_OK && sl.h_cap < res_bytes + need) {
+        // growing frees staging that earlier uploads of this run may still
+        // read: wait for them first
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch staging");
+        rc = ensure_pinned(sl, res_bytes + need);
+    }
+    if (rc != LAT_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    size_t at = res_bytes;
+    at = stage(sl, at, sl.d_geoms, geoms.data(), geoms.size(), b->stream, e);
+    at = stage(sl, at, sl.d_items, items.data(), items.size(), b->stream, e);
+    at = stage(sl, at, sl.d_ctrls, ctrls.data(), ctrls.size(), b->stream, e);
+    if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+    return LAT_OK;
+}
+
+// Batch tuner: per composition of lattices (models, dimensions, spins,
+// sizes and kernels of the lattices of a run's first phase), the rows per
+// any-L item and the steps per captured graph, chosen by timing candidates
+// on the run's own steps (one graph replay each after an untimed one; every
+// candidate computes the same bits).  A run tunes only when its first phase
+// has at least kBatchTuneMin steps (tuning synchronises the host, so short
+// runs such as server rounds keep the defaults).  Choices last for the
+// life of the process.
+constexpr int64_t kBatchTuneMin = 192;
+constexpr BatchTune kBatchCand[] = {{2, 8}, {2, 32}, {8, 8}, {8, 32}};   // 160 steps in all
+std::mutex g_btune_mu;
+std::map<uint64_t, BatchTune> g_btune;
+
+uint64_t composition_key(const std::vector<std::pair<lattice *, int64_t>> &work)
+{
+    std::vector<uint64_t> v;
+    v.reserve(work.size());
+    for (auto &pr : work) {
+        const lattice *lt = pr.first;
+        v.push_back(((uint64_t)lt->P.model << 56) ^ ((uint64_t)lt->P.dims << 52) ^ ((uint64_t)lt->P.two_S << 44) ^
+                    ((uint64_t)choose_kernel(lt) << 40) ^ ((uint64_t)(lt->geom.cpl != nullptr) << 39) ^
+                    (uint64_t)lt->P.L);
+    }
+    std::sort(v.begin(), v.end());
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over the sorted shape words
+    for (uint64_t x : v)
+        for (int k = 0; k < 8; ++k) {
+            h ^= (x >> (8 * k)) & 0xFFu;
+            h *= 1099511628211ull;
+        }
+    return h;
+}
+
+// Time the candidates on the first phase (all lattices of `work`); returns
+// the steps run (every lattice advanced by them) and the pick.
+int tune_batch(lattice_batch *b, BatchSlot &sl, size_t res_bytes, const std::vector<std::pair<lattice *, int64_t>> &work,
+               int64_t &steps_run, BatchTune &pick)
+{
+    steps_run = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return cuda_fail(cudaGetLastError(), "batch tune");
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_fail(cudaGetLastError(), "batch tune");
+    }
+    float best = 1e30f;
+    int rc = LAT_OK;
+    for (const BatchTune &c : kBatchCand) {
+        std::vector<Geom> geoms;
+        std::vector<Ctrl *> ctrls;
+        std::vector<uint2> items;
+        const Shape sh = build_phase(work, work.size(), c.passes, geoms, ctrls, items);
+        rc = upload_lists(b, sl, res_bytes, geoms, items, ctrls);
+        if (rc != LAT_OK) break;
+        const Phase ph{sh, 2 * (int64_t)c.gsteps, sl.d_geoms, sl.d_items, sl.d_ctrls, c.passes, c.gsteps};
+        cudaGraphExec_t exec = nullptr;
+        rc = capture_steps(b, ph, c.gsteps, &exec);
+        if (rc != LAT_OK) break;
+        cudaError_t e = cudaGraphLaunch(exec, b->stream);   // untimed
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], b->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);   // the next candidate reuses the arrays
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "batch tune");
+            break;
+        }
+        steps_run += 2 * c.gsteps;
+        if (ms / c.gsteps < best) {
+            best = ms / c.gsteps;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    return rc;
 }
 
 }  // namespace
@@ -374,6 +551,36 @@ int lattice_batch_run(lattice_batch_t *b)
     // built first and uploaded together, so the phases are queued back to
     // back with no host synchronisation between them.
     std::sort(work.begin(), work.end(), [](const auto &a, const auto &c) { return a.second > c.second; });
+    // the resident lattices' uploads sit at the front of the staging
+    const size_t res_bytes =
+        res.empty() ? 0 : ((res.size() * (sizeof(Geom) + sizeof(long long)) + 64 + 15) & ~(size_t)15);
+    BatchTune tune{0, kGraphSteps};
+    if (!work.empty()) {
+        const uint64_t key = composition_key(work);
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> g(g_btune_mu);
+            auto it = g_btune.find(key);
+            if (it != g_btune.end()) {
+                tune = it->second;
+                found = true;
+            }
+        }
+        if (!found && work.back().second >= kBatchTuneMin) {
+            mark_start();
+            int64_t steps_run = 0;
+            int rc = tune_batch(b, sl, res_bytes, work, steps_run, tune);
+            if (rc != LAT_OK) return rc;
+            for (auto &pr : work) {   // the tuning steps were real steps of every lattice
+                pr.second -= steps_run;
+                pr.first->sweeps += steps_run;
+            }
+            std::lock_guard<std::mutex> g(g_btune_mu);
+            g_btune[key] = tune;
+        }
+        b->last_passes = tune.passes;
+        b->last_gsteps = tune.gsteps;
+    }
     std::vector<Geom> all_geoms;
     std::vector<Ctrl *> all_ctrls;
     std::vector<uint2> all_items;
@@ -387,83 +594,21 @@ int lattice_batch_run(lattice_batch_t *b)
     for (size_t n_active = work.size(); n_active > 0; --n_active) {
         const int64_t steps = work[n_active - 1].second - done;
         if (steps <= 0) continue;
-        const size_t g0 = all_geoms.size();
-        std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide, potts, gen;
-        int tab_gen = 0;
-        for (size_t i = 0; i < n_active; ++i) {
-            lattice *lt = work[i].first;
-            all_geoms.push_back(tiled_geom(lt->geom));
-            all_ctrls.push_back(lt->ctrl);
-            // 2D spin-1/2 lattices (L % 32 == 0) take the 2D wide items, or
-            // the tiled items when their kernel is the tiled one; other even
-            // L with uniform couplings take the any-L 2D items; 3D and
-            // spin-S Ising lattices with L % 16 == 0 take the 3D wide items,
-            // Potts lattices with L % 16 == 0 the Potts items; the rest
-            // (other sizes, per-site disorder, an explicit generic choice)
-            // go to the generic chunks.  Item lattice indexes are
-            // local to the phase.
-            const int kern = choose_kernel(lt);
-            const bool generic = kern == LAT_KERNEL_GENERIC;
-            if (!generic && tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) {
-                const int nt = tiles_of(lt->geom, 0);
-                auto &dst = (lt->P.model == LAT_NE) ? tiled_ne : tiled;
-                for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else if (!generic && any_supported(lt->geom)) {
-                const int ng = any_items(lt->geom);
-                auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[lt->P.model == LAT_NE ? 1 : 0];
-                for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else if (!generic && wide3_supported(lt->geom)) {
-                const int nw = wide3_items(lt->geom);
-                for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else if (!generic && potts_supported(lt->geom)) {
-                const int np = potts_items(lt->geom);
-                for (int k = 0; k < np; ++k) potts.push_back(make_uint2((unsigned)i, (unsigned)k));
-            } else {
-                const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
-                const unsigned nc = (unsigned)((groups + kChunk - 1) / kChunk);
-                for (unsigned k = 0; k < nc; ++k) gen.push_back(make_uint2((unsigned)i, k));
-                tab_gen = std::max(tab_gen, lt->geom.tab_n);
-            }
-        }
         Spec sp;
-        sp.sh = Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                      {(int)grp[0].size(), (int)grp[1].size()}, (int)wide.size(), (int)potts.size(), (int)gen.size(),
-                      tab_gen};
-        sp.steps = steps;
-        sp.geom_off = g0;
+        sp.geom_off = all_geoms.size();
         sp.item_off = all_items.size();
-        for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &grp[0], &grp[1], &wide, &potts, &gen})
-            all_items.insert(all_items.end(), v->begin(), v->end());
+        sp.sh = build_phase(work, n_active, tune.passes, all_geoms, all_ctrls, all_items);
+        sp.steps = steps;
         specs.push_back(sp);
         done += steps;
     }
     if (!specs.empty()) {
-        int rc = grow(&sl.d_geoms, sl.geoms_cap, (int)all_geoms.size(), b->stream);
-        if (rc == LAT_OK) rc = grow(&sl.d_items, sl.items_cap, (int)all_items.size(), b->stream);
-        if (rc == LAT_OK) rc = grow(&sl.d_ctrls, sl.ctrls_cap, (int)all_ctrls.size(), b->stream);
-        const size_t need = all_geoms.size() * sizeof(Geom) + all_items.size() * sizeof(uint2) +
-                            all_ctrls.size() * sizeof(Ctrl *) + 64;
-        // the resident lattices' uploads sit at the front of the staging
-        const size_t res_bytes = res.empty() ? 0 : ((res.size() * (sizeof(Geom) + sizeof(long long)) + 64 + 15) & ~(size_t)15);
-        if (rc == LAT_OK && res.empty()) rc = ensure_pinned(sl, need);
-        if (rc == LAT_OK && !res.empty() && sl.h_cap < res_bytes + need) {
-            // growing would free staging that this run's resident uploads
-            // still read: wait for them first
-            cudaError_t e = cudaStreamSynchronize(b->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "batch staging");
-            rc = ensure_pinned(sl, res_bytes + need);
-        }
+        int rc = upload_lists(b, sl, res_bytes, all_geoms, all_items, all_ctrls);
         if (rc != LAT_OK) return rc;
         mark_start();
-        cudaError_t e = cudaSuccess;
-        size_t at = res_bytes;
-        at = stage(sl, at, sl.d_geoms, all_geoms.data(), all_geoms.size(), b->stream, e);
-        at = stage(sl, at, sl.d_items, all_items.data(), all_items.size(), b->stream, e);
-        at = stage(sl, at, sl.d_ctrls, all_ctrls.data(), all_ctrls.size(), b->stream, e);
-        if (e != cudaSuccess) return cuda_fail(e, "batch upload");
         for (const Spec &sp : specs) {
             const Phase ph{sp.sh, sp.steps, sl.d_geoms + sp.geom_off, sl.d_items + sp.item_off,
-                           sl.d_ctrls + sp.geom_off};
+                           sl.d_ctrls + sp.geom_off, tune.passes, tune.gsteps};
             rc = run_steps(b, ph);
             if (rc != LAT_OK) return rc;
         }
@@ -507,6 +652,14 @@ void batch_set_start_event(lattice_batch_t *b, cudaEvent_t ev)
 }
 
 extern "C" {
+
+int lattice_batch_tuning(lattice_batch_t *b, int *rows_per_item, int *steps_per_graph)
+{
+    if (b == nullptr) return LAT_EINVAL;
+    if (rows_per_item) *rows_per_item = b->last_passes;
+    if (steps_per_graph) *steps_per_graph = b->last_gsteps;
+    return LAT_OK;
+}
 
 int lattice_batch_synchronize(lattice_batch_t *b)
 {

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <string>
@@ -324,28 +325,38 @@ static int ensure_graph(lattice *lt)
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner for LAT_KERNEL_AUTO on 2D spin-1/2 lattices: the first sweep call
-// with enough sweeps times a few of them with each candidate (the wide
-// two-launch kernel, the tiled one-launch kernel at two tile heights and,
-// when the lattice fits one CTA, the resident kernel) and keeps the fastest.
+// Autotuner for LAT_KERNEL_AUTO: the first sweep call with enough sweeps
+// times candidates on the caller's own sweeps and keeps the fastest.
+//  1. The kernel, when the lattice has more than one candidate (2D spin-1/2
+//     with L % 32 == 0: the wide two-launch kernel, the tiled one-launch
+//     kernel at two tile heights and, when the lattice fits one CTA, the
+//     resident kernel).
+//  2. The sweeps per CUDA-graph replay, for every lattice the sweep loop
+//     runs through graphs (any dims, spin and model): half, one, two and
+//     four times the default size, as far as the call's sweeps reach.
 // Each candidate is timed the way the sweep loop will run it: the resident
-// kernel as one launch, the others as a replayed CUDA graph (after one
-// untimed replay), so launch overheads count as they will.  The timed sweeps
-// are the caller's own sweeps: every kernel produces the same bits, so
-// tuning changes no result.  Choices are cached per (model, L) for the life
-// of the process and, when LATTICE_TUNE_CACHE names a file, across
-// processes: one JSON object per line, {"model": m, "L": L, "kernel": k,
-// "tile_h": h}, read before the first lookup and appended to after each new
-// tuning.  An entry the lattice cannot run (a hand-edited file) is ignored.
+// kernel as one launch, the others as a replayed CUDA graph after one
+// untimed replay, so launch overheads count as they will.  Every kernel and
+// graph size produces the same bits, so tuning changes no result.  Choices
+// are cached per (model, dims, 2S, L) for the life of the process and, when
+// LATTICE_TUNE_CACHE names a file, across processes: one JSON object per
+// line, {"model": m, "dims": d, "two_S": s, "L": L, "kernel": k,
+// "tile_h": h, "graph": g}, read before the first lookup and appended to
+// after each new tuning (a line of the older form {"model", "L", "kernel",
+// "tile_h"} reads as a 2D spin-1/2 lattice with the default graph size).
+// An entry the lattice cannot run (a hand-edited file) is ignored.
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneChoice {
-    int kernel, tile_h;
+    int kernel, tile_h, graph;   // graph: sweeps per replay, 0 = the default
 };
+using TuneKey = std::tuple<int, int, int, int>;   // model, dims, two_S, L
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, TuneChoice> g_tune;
+std::map<TuneKey, TuneChoice> g_tune;
 bool g_tune_file_read = false;
 constexpr int kTuneSweeps = 4;
+
+TuneKey tune_key(const lattice *lt) { return TuneKey(lt->P.model, lt->P.dims, lt->P.two_S, lt->P.L); }
 
 const char *tune_cache_path()
 {
@@ -362,42 +373,52 @@ void read_tune_file()
     if (path == nullptr) return;
     FILE *f = std::fopen(path, "r");
     if (f == nullptr) return;
-    char line[256];
+    char line[512];
     while (std::fgets(line, sizeof line, f) != nullptr) {
-        int m = 0, L = 0, k = 0, h = 0;
-        if (std::sscanf(line, " {\"model\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d}", &m, &L, &k,
-                        &h) == 4)
-            g_tune[std::make_pair(m, L)] = TuneChoice{k, h};
+        int m = 0, d = 0, s2 = 0, L = 0, k = 0, h = 0, gs = 0;
+        if (std::sscanf(line,
+                        " {\"model\": %d, \"dims\": %d, \"two_S\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d, "
+                        "\"graph\": %d}",
+                        &m, &d, &s2, &L, &k, &h, &gs) == 7)
+            g_tune[TuneKey(m, d, s2, L)] = TuneChoice{k, h, gs};
+        else if (std::sscanf(line, " {\"model\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d}", &m, &L, &k, &h) ==
+                 4)
+            g_tune[TuneKey(m, 2, 1, L)] = TuneChoice{k, h, 0};
     }
     std::fclose(f);
 }
 
 // With g_tune_mu held: append one tuned choice to the cache file.
-void append_tune_file(const std::pair<int, int> &key, const TuneChoice &c)
+void append_tune_file(const TuneKey &key, const TuneChoice &c)
 {
     const char *path = tune_cache_path();
     if (path == nullptr) return;
     FILE *f = std::fopen(path, "a");
     if (f == nullptr) return;
-    std::fprintf(f, "{\"model\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d}\n", key.first, key.second,
-                 c.kernel, c.tile_h);
+    std::fprintf(f,
+                 "{\"model\": %d, \"dims\": %d, \"two_S\": %d, \"L\": %d, \"kernel\": %d, \"tile_h\": %d, "
+                 "\"graph\": %d}\n",
+                 std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key), c.kernel, c.tile_h, c.graph);
     std::fclose(f);
 }
 
-// Whether a cached choice runs on this lattice.
+// Whether a choice runs on this lattice.
 bool tune_choice_ok(const lattice *lt, const TuneChoice &c)
 {
+    if (c.graph < 0 || c.graph > 4096) return false;
     switch (c.kernel) {
-    case LAT_KERNEL_WIDE: return wide2_supported(lt->geom);
+    case LAT_KERNEL_WIDE: return any_wide(lt->geom);
     case LAT_KERNEL_TILED: return tiled_supported(lt->geom) && tile_shape_ok(0, c.tile_h);
     case LAT_KERNEL_RESIDENT: return resident_supported(lt->geom);
+    case LAT_KERNEL_GENERIC: return true;
     default: return false;
     }
 }
 
-// Time kTuneSweeps sweeps of the current candidate after kTuneSweeps untimed
-// ones (2 * kTuneSweeps sweeps in all, enqueued on the lattice's stream).
-int time_candidate(lattice *lt, cudaEvent_t ev0, cudaEvent_t ev1, float &ms)
+// Time one replay of a graph of n sweeps after one untimed replay (the
+// resident kernel: two launches of n sweeps, the second timed); 2n sweeps
+// are enqueued on the lattice's stream.
+int time_candidate(lattice *lt, int n, cudaEvent_t ev0, cudaEvent_t ev1, float &ms)
 {
     cudaGraphExec_t exec = nullptr;
     int rc = LAT_OK;
@@ -409,7 +430,7 @@ int time_candidate(lattice *lt, cudaEvent_t ev0, cudaEvent_t ev1, float &ms)
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(lt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return LAT_ECUDA;
-        rc = enqueue_sweeps(lt, kTuneSweeps, lt->cap_stream);
+        rc = enqueue_sweeps(lt, n, lt->cap_stream);
         const cudaError_t e = cudaStreamEndCapture(lt->cap_stream, &graph);
         if (rc == LAT_OK && e != cudaSuccess) rc = LAT_ECUDA;
         if (rc == LAT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = LAT_ECUDA;
@@ -420,7 +441,7 @@ int time_candidate(lattice *lt, cudaEvent_t ev0, cudaEvent_t ev1, float &ms)
         if (rep == 1 && cudaEventRecord(ev0, lt->stream) != cudaSuccess) rc = LAT_ECUDA;
         if (rc == LAT_OK) {
             if (graphed) rc = cudaGraphLaunch(exec, lt->stream) == cudaSuccess ? LAT_OK : LAT_ECUDA;
-            else rc = enqueue_sweeps(lt, kTuneSweeps, lt->stream);
+            else rc = enqueue_sweeps(lt, n, lt->stream);
         }
     }
     if (rc == LAT_OK && cudaEventRecord(ev1, lt->stream) != cudaSuccess) rc = LAT_ECUDA;
@@ -430,54 +451,96 @@ int time_candidate(lattice *lt, cudaEvent_t ev0, cudaEvent_t ev1, float &ms)
     if (rc == LAT_ECUDA) return cuda_fail(cudaGetLastError(), "autotune");
     return rc;
 }
+
+// Apply a choice to the lattice (the user's own tile or graph size wins).
+void apply_choice(lattice *lt, const TuneChoice &c)
+{
+    lt->tuned_kernel = c.kernel;
+    if (lt->tile_h == 0) lt->tile_h = c.tile_h;
+    if (!lt->graph_pinned && c.graph > 0) lt->graph_sweeps = c.graph;
+    lt->graph_valid = false;
+}
 }  // namespace
 
 static int autotune(lattice *lt, int64_t &left)
 {
-    const std::pair<int, int> key(lt->P.model, lt->P.L);
+    const TuneKey key = tune_key(lt);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         read_tune_file();
         auto it = g_tune.find(key);
         if (it != g_tune.end() && tune_choice_ok(lt, it->second)) {
-            lt->tuned_kernel = it->second.kernel;
-            if (lt->tile_h == 0) lt->tile_h = it->second.tile_h;
+            apply_choice(lt, it->second);
             return LAT_OK;
         }
     }
-    const TuneChoice all[] = {{LAT_KERNEL_WIDE, 0}, {LAT_KERNEL_TILED, 64}, {LAT_KERNEL_TILED, 32},
-                              {LAT_KERNEL_RESIDENT, 0}};
-    const int n_c = resident_supported(lt->geom) ? 4 : 3;
-    if (left < (int64_t)(n_c * 2 * kTuneSweeps)) return LAT_OK;  // too short to tune now
+    // kernel candidates
+    std::vector<TuneChoice> cand;
+    const bool d2 = lt->P.dims == 2 && lt->P.two_S == 1 && lt->P.model != LAT_POTTS;
+    if (any_wide(lt->geom)) cand.push_back(TuneChoice{LAT_KERNEL_WIDE, 0, 0});
+    if (d2 && tiled_supported(lt->geom)) {
+        cand.push_back(TuneChoice{LAT_KERNEL_TILED, 64, 0});
+        cand.push_back(TuneChoice{LAT_KERNEL_TILED, 32, 0});
+    }
+    if (d2 && resident_supported(lt->geom)) cand.push_back(TuneChoice{LAT_KERNEL_RESIDENT, 0, 0});
+    if (cand.empty()) cand.push_back(TuneChoice{LAT_KERNEL_GENERIC, 0, 0});
+    const int n_c = (int)cand.size();
+    const int g0 = default_graph_sweeps(lt->P);
+    // too short to tune now (a later, longer call tunes): the kernel when
+    // there is a choice, else at least the smallest graph size
+    if (n_c > 1 && left < (int64_t)(n_c * 2 * kTuneSweeps)) return LAT_OK;
+    if (n_c == 1 && (lt->graph_pinned || cand[0].kernel == LAT_KERNEL_RESIDENT || left < 2 * (int64_t)std::max(2, g0 / 2)))
+        return LAT_OK;
     cudaEvent_t ev[2];
     if (cudaEventCreate(&ev[0]) != cudaSuccess) return LAT_OK;
     if (cudaEventCreate(&ev[1]) != cudaSuccess) {
         cudaEventDestroy(ev[0]);
         return LAT_OK;
     }
-    float best = 1e30f;
-    TuneChoice pick = all[0];
     const int keep_tile = lt->tile_h;
+    const int keep_graph = lt->graph_sweeps;
+    TuneChoice pick = cand[0];
     int rc = LAT_OK;
-    for (int c = 0; c < n_c && rc == LAT_OK; ++c) {
-        lt->tuned_kernel = all[c].kernel;
-        lt->tile_h = all[c].tile_h;
-        float ms = 0.f;
-        rc = time_candidate(lt, ev[0], ev[1], ms);
-        if (rc != LAT_OK) break;
-        lt->sweeps += 2 * kTuneSweeps;
-        left -= 2 * kTuneSweeps;
-        if (ms < best) {
-            best = ms;
-            pick = all[c];
+    if (n_c > 1) {
+        float best = 1e30f;
+        for (int c = 0; c < n_c && rc == LAT_OK; ++c) {
+            lt->tuned_kernel = cand[(size_t)c].kernel;
+            lt->tile_h = cand[(size_t)c].tile_h;
+            float ms = 0.f;
+            rc = time_candidate(lt, kTuneSweeps, ev[0], ev[1], ms);
+            if (rc != LAT_OK) break;
+            lt->sweeps += 2 * kTuneSweeps;
+            left -= 2 * kTuneSweeps;
+            if (ms < best) {
+                best = ms;
+                pick = cand[(size_t)c];
+            }
+        }
+    }
+    lt->tuned_kernel = pick.kernel;
+    lt->tile_h = keep_tile ? keep_tile : pick.tile_h;
+    // sweeps per graph replay (graph-launched kernels, size not set by the user)
+    if (rc == LAT_OK && pick.kernel != LAT_KERNEL_RESIDENT && !lt->graph_pinned) {
+        float best = 1e30f;
+        for (int f : {1, 2, 4, 8}) {   // g0 / 2, g0, 2 g0, 4 g0
+            const int gs = std::max(2, g0 * f / 2);
+            if (left < 2 * (int64_t)gs) break;
+            float ms = 0.f;
+            rc = time_candidate(lt, gs, ev[0], ev[1], ms);
+            if (rc != LAT_OK) break;
+            lt->sweeps += 2 * gs;
+            left -= 2 * gs;
+            if (ms / gs < best) {
+                best = ms / gs;
+                pick.graph = gs;
+            }
         }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
+    lt->graph_sweeps = keep_graph;
     if (rc != LAT_OK) return rc;
-    lt->tuned_kernel = pick.kernel;
-    lt->tile_h = keep_tile ? keep_tile : pick.tile_h;
-    lt->graph_valid = false;
+    apply_choice(lt, pick);
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = pick;
     append_tune_file(key, pick);
@@ -492,8 +555,7 @@ int sweep_impl(lattice *lt, int64_t n)
     if (rc != LAT_OK) return rc;
     int64_t left = n;
     if (lt->kernel == LAT_KERNEL_AUTO && lt->tuned_kernel == 0 && lt->P.layout == LAT_INT8 &&
-        lt->dynamics == LAT_DYNAMICS_CHECKERBOARD && lt->geom.cpl == nullptr && wide_supported(lt->geom) &&
-        tiled_supported(lt->geom)) {
+        lt->dynamics == LAT_DYNAMICS_CHECKERBOARD && lt->geom.cpl == nullptr) {
         const int64_t before = lt->sweeps;
         rc = autotune(lt, left);
         if (rc != LAT_OK) return rc;
@@ -1191,6 +1253,7 @@ int lattice_set_kernel(lattice_t *lt, int kernel, int tile_w, int tile_h, int sw
     lt->tile_w = tile_w;
     lt->tile_h = tile_h;
     lt->graph_sweeps = sweeps_per_graph ? sweeps_per_graph : default_graph_sweeps(lt->P);
+    lt->graph_pinned = sweeps_per_graph != 0;
     lt->graph_valid = false;
     return LAT_OK;
 }

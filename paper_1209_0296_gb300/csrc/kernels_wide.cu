@@ -1164,29 +1164,31 @@ struct AnyItemShape {
     uint32_t cpr, nseg, rsb, br;   // chunks per row, column segments, rows per pass, rows per band
 };
 
-// Rows a thread visits per item: 8 on large lattices (few items, long
-// pipelines), 2 on small ones (enough items to spread a batch of small
-// lattices over the SMs).
-LAT_HD AnyItemShape any_item_shape(uint32_t half)
+// Rows a thread visits per item (passes): given by the batch (its tuner),
+// or 0 for the default: 8 on large lattices (few items, long pipelines), 2
+// on small ones (enough items to spread a batch of small lattices over the
+// SMs).
+LAT_HD AnyItemShape any_item_shape(uint32_t half, uint32_t passes)
 {
     AnyItemShape sh;
     sh.cpr = (half + 15u) >> 4;
     sh.nseg = (sh.cpr + kThreads - 1u) / kThreads;
     sh.rsb = sh.cpr <= (uint32_t)kThreads ? (uint32_t)kThreads / sh.cpr : 1u;
-    sh.br = (half >= 512u ? 8u : 2u) * sh.rsb;
+    if (passes == 0u) passes = half >= 512u ? 8u : 2u;
+    sh.br = passes * sh.rsb;
     return sh;
 }
 
 template <int kColour, bool kNE, bool kAligned>
-LAT_D void batch_any_item(const SweepView &v, const uint32_t *sthr, uint32_t item, uint32_t *gtab, uint4 *dq,
-                          Counts &cnt)
+LAT_D void batch_any_item(const SweepView &v, const uint32_t *sthr, uint32_t item, uint32_t passes, uint32_t *gtab,
+                          uint4 *dq, Counts &cnt)
 {
     const unsigned long long sweep = v.ctrl->sweep;
     PhiloxPre pp;
     philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), v.key0, v.key1);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
     int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
-    const AnyItemShape sh = any_item_shape(v.half);
+    const AnyItemShape sh = any_item_shape(v.half, passes);
     const uint32_t L = (uint32_t)v.L;
     const uint32_t band = item / sh.nseg, seg = item - band * sh.nseg;
     const uint32_t y0 = band * sh.br, y1 = min(L, y0 + sh.br);
@@ -1258,7 +1260,7 @@ LAT_D void batch_any_item(const SweepView &v, const uint32_t *sthr, uint32_t ite
 
 template <bool kNE, bool kAligned, int kColour>
 __global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *geoms, const uint2 *items, int n_items,
-                                                                  unsigned *next_item)
+                                                                  unsigned *next_item, uint32_t passes)
 {
     __shared__ uint32_t sthr[32];   // entries 16..31: locked North-East sites
     __shared__ int red[kThreads / 32][5];
@@ -1285,7 +1287,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *g
         }
         const SweepView v = sweep_view(sg);
         Counts cnt;
-        batch_any_item<kColour, kNE, kAligned>(v, sthr, w.y, gtab[warp], dq[warp], cnt);
+        batch_any_item<kColour, kNE, kAligned>(v, sthr, w.y, passes, gtab[warp], dq[warp], cnt);
         if constexpr (kColour == 1) flush(v, v.ctrl->sweep, cnt, kNE, red);   // ends with __syncthreads()
         __syncthreads();
     }
@@ -1444,9 +1446,9 @@ bool any_supported(const Geom &g)
     return true;
 }
 
-int any_items(const Geom &g)
+int any_items(const Geom &g, int passes)
 {
-    const AnyItemShape sh = any_item_shape(g.half);
+    const AnyItemShape sh = any_item_shape(g.half, (uint32_t)passes);
     return (int)((((uint32_t)g.L + sh.br - 1u) / sh.br) * sh.nseg);
 }
 
@@ -1462,15 +1464,16 @@ int batch_any_grid(bool ne)
 }
 
 cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                             bool ne, bool aligned, int grid, cudaStream_t st)
+                             bool ne, bool aligned, int passes, int grid, cudaStream_t st)
 {
-    using K = void (*)(const Geom *, const uint2 *, int, unsigned *);
+    using K = void (*)(const Geom *, const uint2 *, int, unsigned *, uint32_t);
     static const K kern[2][2][2] = {
         {{k_batch_any<false, false, 0>, k_batch_any<false, false, 1>},
          {k_batch_any<false, true, 0>, k_batch_any<false, true, 1>}},
         {{k_batch_any<true, false, 0>, k_batch_any<true, false, 1>},
          {k_batch_any<true, true, 0>, k_batch_any<true, true, 1>}}};
-    kern[ne ? 1 : 0][aligned ? 1 : 0][colour ? 1 : 0]<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item);
+    kern[ne ? 1 : 0][aligned ? 1 : 0][colour ? 1 : 0]<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item,
+                                                                                 (uint32_t)passes);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,7 @@ struct lattice {
     int64_t series_first = 0;  // first sweep index recorded in the series buffer
     int kernel = 0, tile_w = 0, tile_h = 0, graph_sweeps = 0;
     int tuned_kernel = 0;      // autotuner's choice for LAT_KERNEL_AUTO (0 = not tuned)
+    bool graph_pinned = false; // sweeps per graph set by lattice_set_kernel (the tuner keeps it)
     cudaGraphExec_t graph_exec = nullptr;
     bool graph_valid = false;
 };

@@ -372,11 +372,13 @@ int wide_chunks(const Geom &g);
 // wide kernel's sweep on rows at any byte alignment; launch_sweep_wide takes
 // these lattices when L % 32 != 0), and its batched form
 bool any_supported(const Geom &g);
-int any_items(const Geom &g);   // batch items of one colour of one lattice
+// batch items of one colour of one lattice; passes: rows a thread visits
+// per item (0: the size-based default)
+int any_items(const Geom &g, int passes);
 int batch_any_grid(bool ne);
 // aligned: every lattice of the items has L % 32 == 0 (16-byte aligned rows)
 cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                             bool ne, bool aligned, int grid, cudaStream_t st);
+                             bool ne, bool aligned, int passes, int grid, cudaStream_t st);
 // batched engine
 Geom tiled_geom(const Geom &g);
 int tiles_of(const Geom &g, int tile_h);

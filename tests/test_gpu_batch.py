@@ -170,3 +170,37 @@ def test_explicit_resident_in_batch_and_stream_order():
         o.sweep(c[-1] + 3)
         assert np.array_equal(g.get_spins(), o.spins), c
     b.close()
+
+
+def test_batch_tuner_changes_no_bits():
+    # A run long enough to tune (its first phase has >= 192 steps): the
+    # batch times its candidates (rows per item, steps per graph) on the
+    # run's own steps; every lattice must still end bit for bit where its
+    # solo run ends, and the tuned values are reported.
+    mix = [(2, 1000, 1, lt.NE, 0.0, 0.0, 0.3, 41, lt.INIT_EQUILIBRIUM),
+           (2, 1024, 1, lt.ISING, 1.0, 0.0, 2.3, 42, lt.INIT_RANDOM),
+           (2, 202, 1, lt.ISING, 1.0, 0.1, 2.0, 43, lt.INIT_RANDOM),
+           (3, 32, 2, lt.ISING, 1.0, 0.0, 3.0, 44, lt.INIT_RANDOM),
+           (2, 512, 2, lt.POTTS, 1.0, 0.0, 1.0, 45, lt.INIT_RANDOM)]
+    n = 300
+    lats = [lt.Lattice(*c[:7], seed=c[7], init=c[8]) for c in mix]
+    b = lt.Batch()
+    for g in lats:
+        b.add(g, n)
+    b.run()
+    b.synchronize()
+    tun = b.tuning()
+    assert tun["steps_per_graph"] in (8, 32) and tun["rows_per_item"] in (2, 8)
+    for g, c in zip(lats, mix):
+        solo = lt.Lattice(*c[:7], seed=c[7], init=c[8])
+        solo.sweep(n)
+        assert g.sweeps() == n
+        assert np.array_equal(g.get_spins(), solo.get_spins()), c
+        assert np.array_equal(g.series(0, n)["bond"], solo.series(0, n)["bond"]), c
+    # a second run of the same composition takes the tuned values without tuning
+    for g in lats:
+        b.add(g, 20)
+    b.run()
+    b.synchronize()
+    assert b.tuning() == tun
+    b.close()

@@ -58,3 +58,43 @@ def test_unusable_entry_is_ignored(tmp_path):
     k = _run(1024, cache)
     assert k["kernel"] != 4
     assert len(cache.read_text().splitlines()) == 2   # tuned afresh and appended
+
+
+PROBE3 = r"""
+import json, sys
+import numpy as np
+import paper_1209_0296_gb300 as lt
+dims, L, two_S, model = (int(x) for x in sys.argv[1:5])
+args = (dims, L, two_S, model, 1.0, 0.0, 2.7) if model != lt.NE else (dims, L, two_S, model, 0.0, 0.0, 0.3)
+init = lt.INIT_EQUILIBRIUM if model == lt.NE else lt.INIT_RANDOM
+g = lt.Lattice(*args, seed=5, init=init)
+g.sweep(300)                      # tuned on these sweeps
+ref = lt.Lattice(*args, seed=5, init=init)
+ref.set_kernel(lt.KERNEL_WIDE, 0, 0, 3)   # fixed kernel, graph size 3 (pinned: never tuned)
+ref.sweep(300)
+k = g.get_kernel()
+same = bool(np.array_equal(g.get_spins(), ref.get_spins())) and bool(
+    np.array_equal(g.series(0, 300)["bond"], ref.series(0, 300)["bond"]))
+print(json.dumps({"kernel": k["kernel"], "graph": k["sweeps_per_graph"], "same": same,
+                  "ref_graph": ref.get_kernel()["sweeps_per_graph"]}))
+"""
+
+
+@pytest.mark.parametrize("dims,L,two_S,model", [(2, 4096, 1, 0), (2, 1000, 1, 1), (3, 64, 2, 0), (2, 256, 2, 2)])
+def test_graph_size_is_tuned_and_changes_no_bits(tmp_path, dims, L, two_S, model):
+    # the tuner picks the sweeps per graph replay for every model and
+    # dimension (3D spin-1, Potts and North-East at L % 32 != 0 included),
+    # records it, and the tuned lattice ends bit for bit where a lattice
+    # with a fixed kernel and graph size ends
+    cache = tmp_path / "tune.jsonl"
+    env = dict(os.environ, LATTICE_TUNE_CACHE=str(cache), PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", PROBE3, str(dims), str(L), str(two_S), str(model)], env=env,
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["same"] and r["ref_graph"] == 3
+    lines = [json.loads(x) for x in cache.read_text().splitlines()]
+    assert len(lines) == 1
+    e = lines[0]
+    assert (e["model"], e["dims"], e["two_S"], e["L"]) == (model, dims, two_S, L)
+    assert e["graph"] > 0 and e["graph"] == r["graph"]
