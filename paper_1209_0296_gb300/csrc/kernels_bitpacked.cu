@@ -12,7 +12,6 @@ namespace lat {
 namespace {
 
 constexpr int kThreads = 256;
-static_assert(kThreads == 256, "the spread tables are filled one entry per thread");
 
 // planar int8 -> bits: word k of plane c row y holds sites j = 32k .. 32k+31.
 __global__ void k_pack(Geom g, const int8_t *planar, uint32_t *bits)
@@ -43,36 +42,21 @@ __global__ void k_unpack(Geom g, const uint32_t *bits, int8_t *planar)
 }
 
 
+// Bits 4q..4q+3 of x spread to bit 0 of bytes 0..3.
+LAT_D uint32_t spread_nibble(uint32_t x, int q) { return (((x >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u; }
+
 // One colour of one sweep on the bit-packed planes (L % 64 == 0).  Thread =
 // one 32-bit word of the colour-c plane of row y: 32 same-colour sites = 8
 // Philox groups.  Colour 0 reads bits[sweep & 1] and writes the new colour-0
 // word and a copy of the colour-1 word at the same index into
 // bits[(sweep+1) & 1]; colour 1 then works in place there and accumulates
 // the sweep's counters.
-// Per-site table offsets from bit planes, two planes at a time: for an
-// 8-bit v = a | b << 4 (a, b: the bits of 4 consecutive sites in two planes),
-// spread[0][v] has in byte i the bits a_i << 2 | b_i << 3 and spread[1][v]
-// a_i << 4 | b_i << 5 -- so the byte offsets (sd << 3 | nd) * 4 of four
-// sites into the acceptance table are spread[0][b0 | b1 << 4] |
-// spread[1][b2 | sd << 4].
-LAT_D uint32_t spread_pair(uint32_t v, int lo)
-{
-    uint32_t w = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        w |= ((((v >> i) & 1u) << lo) | (((v >> (4 + i)) & 1u) << (lo + 1))) << (8 * i);
-    return w;
-}
-
 template <bool kNE>
 __global__ void __launch_bounds__(kThreads, 4) k_bits_half(Geom g, int colour, int off)
 {
     __shared__ uint32_t sthr[16];
-    __shared__ uint32_t spread[2][256];
     __shared__ long long red[kThreads / 32];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
-    spread[0][threadIdx.x] = spread_pair(threadIdx.x, 2);   // kThreads == 256
-    spread[1][threadIdx.x] = spread_pair(threadIdx.x, 4);
     __syncthreads();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const uint32_t *src = g.bits[sweep & 1];
@@ -116,9 +100,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bits_half(Geom g, int colour, i
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             // byte offsets (index sd<<3 | nd, 4 bytes per entry) of the 4 sites
-            const uint32_t v01 = ((b0 >> (4 * q)) & 0xFu) | (((b1 >> (4 * q)) & 0xFu) << 4);
-            const uint32_t v23 = ((b2 >> (4 * q)) & 0xFu) | (((Sd >> (4 * q)) & 0xFu) << 4);
-            const uint32_t idx = spread[0][v01] | spread[1][v23];
+            const uint32_t idx = (spread_nibble(b0, q) << 2) | (spread_nibble(b1, q) << 3) |
+                                 (spread_nibble(b2, q) << 4) | (spread_nibble(Sd, q) << 5);
             uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
             uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
             uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
