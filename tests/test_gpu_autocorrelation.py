@@ -165,3 +165,24 @@ def test_full_size_north_east_L8192_reference():
     # North-East L = 8192, c = 0.3, equilibrium start (seed 21): overlap of
     # the first two sweeps with the initial state
     pair(2, 8192, 1, lt.NE, 0.0, 0.0, 0.3, 21, lt.INIT_EQUILIBRIUM, 0, 2)
+
+
+def test_default_polarisation_is_the_models_own():
+    # m = NaN (the binding's m=None) asks the library for the North-East
+    # model's own polarisation, <s_i> = 2c - 1 (Eq. 4): the same Phi as an
+    # explicit m; a lattice without one refuses Phi but still gives overlaps
+    c = 0.3
+    g = lt.Lattice(2, 64, 1, lt.NE, 0.0, 0.0, c, seed=21, init=lt.INIT_EQUILIBRIUM)
+    g.set_reference()
+    g.sweep(12)
+    ov_d, phi_d = g.autocorrelation(0, 12)
+    ov_e, phi_e = g.autocorrelation(0, 12, m=2 * c - 1)
+    assert np.array_equal(ov_d, ov_e)
+    assert np.allclose(phi_d, phi_e, rtol=0, atol=1e-15)
+    g.close()
+    h = lt.Lattice(2, 64, 1, lt.ISING, 1.0, 0.0, 2.5, seed=3, init=lt.INIT_RANDOM)
+    h.set_reference()
+    h.sweep(5)
+    ov, phi = h.autocorrelation(0, 5)
+    assert phi is None and ov.shape == (5,)
+    h.close()
