@@ -269,7 +269,7 @@ def run_gpu(args):
     bbytes = 0.25 * L * L  # one bit read + one bit written per site per sweep
     bach = bbytes / (avg_bits_us * 1e-6) / 1e9
     roofline_bits = {"bound": "hbm", "achieved": bach, "peak": hbm, "unit": "GB/s", "frac": bach / hbm,
-                     "traffic": bprof.get("traffic_bytes_per_sweep"), "kernel": "k_bits_half<Ising> x2",
+                     "traffic": bprof.get("traffic_bytes_per_sweep"), "kernel": "k_bits_pipe<colour 0, colour 1>",
                      "bytes_per_sweep": bbytes, "avg_sweep_us": avg_bits_us,
                      "updates_per_ns": L * L / (avg_bits_us * 1e3)}
     sm_clk = (clk.summary().get("sm_mhz") or 2070.0) * 1e6
