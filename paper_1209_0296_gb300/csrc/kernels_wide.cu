@@ -7,17 +7,18 @@
 // 16-byte load = four Philox groups), so the loads, index arithmetic and
 // Philox set-up are shared by 16 sites.  The colour-c sites only read the
 // other plane, so the colour-c pass never reads a byte another thread
-// writes: colour 0 reads buffer s[sweep & 1] and writes the new colour-0
-// sites plus a copy of the colour-1 sites into s[(sweep+1) & 1]; colour 1
-// then updates s[(sweep+1) & 1] in place and reduces the sweep's counters.
-// Neighbour counts, thresholds and acceptance are those of the tiled kernel
-// (bytes 0x01 / 0xFF, bit-sliced adder, t' = thr - 1 table).
+// writes.  Neighbour counts, thresholds and acceptance are those of the
+// tiled kernel (bytes 0x01 / 0xFF, bit-sliced adder, t' = thr - 1 table).
 //
-// Uniform Ising lattices run k_wide_pipe: each thread walks one chunk
-// column down the rows with two chunks in flight, so the Philox draws of
-// one chunk (wide multiplies) and the Metropolis step of the other (logic)
-// share each instruction block.  North-East lattices and lattices with
-// per-site disorder run k_wide_half_* (one chunk at a time, grid-stride).
+// The solo kernels (k_wide_pipe for Ising, uniform or with per-bond and
+// per-site disorder; k_wide_pipe_ne for the North-East model; k_any_pipe*
+// for any even L) walk one chunk column per thread down the rows with two
+// chunks in flight, so the Philox draws of one chunk (wide multiplies) and
+// the Metropolis step of the other (logic) share each instruction block.
+// They read s[sweep & 1] and write s[(sweep+1) & 1] without copying a
+// plane: colour 1 takes the new colour-0 sites from the new buffer.  The
+// resident kernels (wide_chunk, in place) keep the whole lattice in one
+// CTA's shared memory.
 #include <algorithm>
 
 #include "lattice_internal.cuh"
@@ -312,70 +313,11 @@ LAT_D void flush_one(unsigned long long *dst, int v, int (*red)[5])
     __syncthreads();
 }
 
-// kFld: 32-entry table, entries 16..31 built from the -h half of the full
-// table (t' = thr - 1 form, all ones = always), index sd << 3 | nd as for
-// entries 0..15.
-template <bool kNE, bool kCpl, bool kFld>
-LAT_D void wide_half_body(const Geom &g, int colour, int off, uint32_t *sthr, int (*red)[5])
-{
-    if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
-    if constexpr (kFld) {
-        if (threadIdx.x >= 16 && threadIdx.x < 32) {
-            const int k = threadIdx.x - 16, nd = k & 7;
-            uint32_t t = 0u;
-            if (nd <= 4) {
-                const int ds = (k >> 3) ? 2 : -2, n = 4 - 2 * nd;
-                const TabEntry e = g.tab[(2 * g.dsmax + 1) * g.nn + (ds + g.dsmax) * g.nn + (n + g.nmax)];
-                t = e.always ? 0xFFFFFFFFu : e.thr - 1u;
-            }
-            sthr[threadIdx.x] = t;
-        }
-    }
-    __syncthreads();
-    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
-    PhiloxPre pp;
-    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
-    const uint32_t cpr = g.half >> 4;  // 16-site chunks per plane row
-    Counts cnt;
-    const SweepView v = sweep_view(g);
-    // Grid-stride over chunks with one resident wave of CTAs: the counter
-    // reduction (and its barrier) happens once per CTA, not once per chunk.
-    for (GridWalk w((uint32_t)g.L, cpr); w.ok(); w.next())
-        wide_chunk<kNE, false, 4, false, kCpl, kFld>(v, sthr, colour, sweep, pp, (int)w.r, (int)w.k, cnt);
-    if (colour == 1) flush(v, sweep, cnt, kNE, red);
-    if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
-}
-
-// Per-bond couplings (Eq. 1, J_ij = J eps_ij), uniform field.
-__global__ void __launch_bounds__(kThreads) k_wide_half_cpl(Geom g, int colour, int off)
-{
-    __shared__ uint32_t sthr[16];
-    __shared__ int red[kThreads / 32][5];
-    wide_half_body<false, true, false>(g, colour, off, sthr, red);
-}
-
-// Couplings and field signs: bounded to three CTAs per SM (80 registers);
-// unbounded it takes 120 and only two fit.
-__global__ void __launch_bounds__(kThreads, 3) k_wide_half_fld(Geom g, int colour, int off)
-{
-    __shared__ uint32_t sthr[32];
-    __shared__ int red[kThreads / 32][5];
-    wide_half_body<false, true, true>(g, colour, off, sthr, red);
-}
-
-// North-East: bounded to three CTAs per SM (80 registers); unbounded it
-// takes 117 and only two fit.
-__global__ void __launch_bounds__(kThreads, 3) k_wide_half_ne(Geom g, int colour, int off)
-{
-    __shared__ uint32_t sthr[16];
-    __shared__ int red[kThreads / 32][5];
-    wide_half_body<true, false, false>(g, colour, off, sthr, red);
-}
-
 // ---------------------------------------------------------------------
-// Software-pipelined two-launch Ising sweep (uniform J and h, no per-site
-// disorder).  Same chunks, draws, table and bits as wide_chunk<false>; the
-// difference is the schedule.  A chunk costs two kinds of work that load
+// Software-pipelined two-launch Ising sweep, uniform or with per-bond
+// coupling signs (kCpl) and per-site field signs (kFld).  Same chunks,
+// draws, table and bits as wide_chunk<false>; the difference is the
+// schedule.  A chunk costs two kinds of work that load
 // different pipes: its four Philox4x32-10 calls (wide multiplies on the
 // FMA pipe) and the Metropolis step (logic on the ALU pipe).  Done one
 // after the other they keep one pipe idle while the other works, so each
@@ -385,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_wide_half_ne(Geom g, int colour
 struct WideIn {
     uint32_t S[4], O[4], U[4], D[4];
     uint32_t adj;
+    uint32_t C[4];   // disorder bytes of the chunk's sites (kCpl only)
 };
 
 // What one thread needs to walk its chunk column k (16 sites) down the
@@ -398,6 +341,7 @@ struct ColWalk {
     const int8_t *pOrow;   // the other colour's current sites (row starts)
     int8_t *dS;            // this colour's plane in the new buffer, + 16k
     const int8_t *r1, *r0; // reference planes 1 and 0, + 16k (or null)
+    const int8_t *pC;      // this colour's disorder bytes, + 16k (or null)
     uint32_t half, L, G, k;
     uint32_t adjb0, adjb1; // byte offset in the row of the neighbour word past the chunk end, x parity 0 / 1
 };
@@ -418,6 +362,7 @@ LAT_D ColWalk<kColour> col_walk(const SweepView &g, const int8_t *old, int8_t *n
     c.dS = nw + (size_t)kColour * plane + 16 * k;
     c.r1 = g.ref ? g.ref + (size_t)plane + 16 * k : nullptr;
     c.r0 = g.ref ? g.ref + 16 * k : nullptr;
+    c.pC = g.cpl ? reinterpret_cast<const int8_t *>(g.cpl) + (size_t)kColour * plane + 16 * k : nullptr;
     c.half = g.half;
     c.L = (uint32_t)g.L;
     c.G = g.G;
@@ -428,8 +373,8 @@ LAT_D ColWalk<kColour> col_walk(const SweepView &g, const int8_t *old, int8_t *n
     return c;
 }
 
-// Loads of the walk's chunk in plane row y.
-template <int kColour>
+// Loads of the walk's chunk in plane row y (and its disorder bytes when kCpl).
+template <int kColour, bool kCpl = false>
 LAT_D void col_load(const ColWalk<kColour> &c, uint32_t y, WideIn &in)
 {
     const uint32_t oy = y * c.half;
@@ -440,6 +385,7 @@ LAT_D void col_load(const ColWalk<kColour> &c, uint32_t y, WideIn &in)
     load_words<4>(c.pO + oym, in.U);   // north
     load_words<4>(c.pO + oyp, in.D);   // south
     in.adj = *reinterpret_cast<const uint32_t *>(c.pOrow + oy + (((kColour + y) & 1) ? c.adjb1 : c.adjb0));
+    if constexpr (kCpl) load_words<4>(c.pC + oy, in.C);
 }
 
 // The four Philox groups of the walk's chunk in plane row y.
@@ -453,8 +399,9 @@ LAT_D void col_draws(const PhiloxPre &pp, const ColWalk<kColour> &c, uint32_t y,
 
 // The Metropolis step of one loaded chunk: neighbour counts, table, accept
 // iff u <= t', write; colour 1 also counts bonds, magnetisation and up
-// sites (and the overlap with the reference when kRef).
-template <int kColour, bool kRef>
+// sites (and the overlap with the reference when kRef); with kFld each
+// colour adds the field sum of its own sites.
+template <int kColour, bool kRef, bool kCpl = false, bool kFld = false>
 LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y, const WideIn &in,
                     const U4 (&u)[4], Counts &cnt)
 {
@@ -462,7 +409,7 @@ LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y,
     const bool p1 = ((kColour + y) & 1) != 0;
     const char *tb = reinterpret_cast<const char *>(sthr);
     const uint32_t M1 = 0x02020202u;
-    uint32_t Sn[4], ue = 0, dn = 0;
+    uint32_t Sn[4], ue = 0, dn = 0, ed = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         uint32_t Lf, R;
@@ -473,13 +420,24 @@ LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y,
             Lf = in.O[w];
             R = __funnelshift_r(in.O[w], w == 3 ? in.adj : in.O[w + 1], 8);
         }
-        const uint32_t Uw = in.U[w], Dw = in.D[w];
+        uint32_t Uw = in.U[w], Dw = in.D[w];
+        if constexpr (kCpl) {
+            // Eq. 1 couplings: a negative bond enters as a flipped neighbour
+            // (XOR 0xFE turns +1 into -1 and back); bits 0-3 of a disorder
+            // byte are the west, east, north and south bonds
+            const uint32_t Cw = in.C[w];
+            Lf ^= (Cw & 0x01010101u) * 0xFEu;
+            R ^= ((Cw >> 1) & 0x01010101u) * 0xFEu;
+            Uw ^= ((Cw >> 2) & 0x01010101u) * 0xFEu;
+            Dw ^= ((Cw >> 3) & 0x01010101u) * 0xFEu;
+        }
         const uint32_t s1 = Uw ^ Dw ^ Lf;
         const uint32_t c1 = (Uw & Dw) | (Uw & Lf) | (Dw & Lf);
         const uint32_t b0 = s1 ^ R;
         const uint32_t b1 = c1 ^ (s1 & R);
         const uint32_t b2 = c1 & s1 & R;
-        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (in.S[w] & 0x20202020u);
+        uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (in.S[w] & 0x20202020u);
+        if constexpr (kFld) idx |= in.C[w] & 0x40404040u;   // eta_i = -1: the -h entries 16..31
         const uint32_t t0 = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
         const uint32_t t1 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
         const uint32_t t2 = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
@@ -490,6 +448,8 @@ LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y,
         // logic pipe is the busier one)
         const uint32_t F = ((acc * 0x00204081u) & 0x01010101u) * 0xFEu;   // 0xFE at flipped sites
         Sn[w] = in.S[w] ^ F;
+        // eta_i s_i is down when exactly one of (s_i down: bit 1, eta_i = -1: bit 6) holds
+        if constexpr (kFld) ed += (Sn[w] ^ (in.C[w] >> 5)) & M1;
         if constexpr (kColour == 1) {
             // unequal bonds, 2 per pair: the adder's sum and carry words
             // (U^D^Lf, maj(U,D,Lf)) against the new spin count the unequal
@@ -514,16 +474,32 @@ LAT_D void col_step(const ColWalk<kColour> &c, const uint32_t *sthr, uint32_t y,
             cnt.acf += 32 - byte_sum(dr);
         }
     }
+    if constexpr (kFld) cnt.fld += 16 - byte_sum(ed);
 }
 
 constexpr int kPipeMinB = 2;   // CTAs per SM (the two chunks in flight need ~100 registers)
 
-template <int kColour, bool kRef>
+// kFld: a 32-entry table, entries 16..31 built from the -h half of the full
+// table (t' = thr - 1 form, all ones = always), index sd << 3 | nd as for
+// entries 0..15.
+template <int kColour, bool kRef, bool kCpl = false, bool kFld = false>
 __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int off)
 {
-    __shared__ uint32_t sthr[16];
+    __shared__ uint32_t sthr[kFld ? 32 : 16];
     __shared__ int red[kThreads / 32][5];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
+    if constexpr (kFld) {
+        if (threadIdx.x >= 16 && threadIdx.x < 32) {
+            const int e = threadIdx.x - 16, nd = e & 7;
+            uint32_t t = 0u;
+            if (nd <= 4) {
+                const int ds = (e >> 3) ? 2 : -2, n = 4 - 2 * nd;
+                const TabEntry te = g.tab[(2 * g.dsmax + 1) * g.nn + (ds + g.dsmax) * g.nn + (n + g.nmax)];
+                t = te.always ? 0xFFFFFFFFu : te.thr - 1u;
+            }
+            sthr[threadIdx.x] = t;
+        }
+    }
     __syncthreads();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const SweepView v = sweep_view(g);
@@ -547,29 +523,30 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
         // runs (no copies between the two).
         WideIn A, B;
         U4 uA[4], uB[4];
-        col_load<kColour>(c, y, A);
+        col_load<kColour, kCpl>(c, y, A);
         col_draws<kColour>(pp, c, y, uA);
         for (;;) {
             const uint32_t y1 = y + rs;
             if (y1 >= L) {
-                col_step<kColour, kRef>(c, sthr, y, A, uA, cnt);
+                col_step<kColour, kRef, kCpl, kFld>(c, sthr, y, A, uA, cnt);
                 break;
             }
-            col_load<kColour>(c, y1, B);
+            col_load<kColour, kCpl>(c, y1, B);
             col_draws<kColour>(pp, c, y1, uB);
-            col_step<kColour, kRef>(c, sthr, y, A, uA, cnt);
+            col_step<kColour, kRef, kCpl, kFld>(c, sthr, y, A, uA, cnt);
             const uint32_t y2 = y1 + rs;
             if (y2 >= L) {
-                col_step<kColour, kRef>(c, sthr, y1, B, uB, cnt);
+                col_step<kColour, kRef, kCpl, kFld>(c, sthr, y1, B, uB, cnt);
                 break;
             }
-            col_load<kColour>(c, y2, A);
+            col_load<kColour, kCpl>(c, y2, A);
             col_draws<kColour>(pp, c, y2, uA);
-            col_step<kColour, kRef>(c, sthr, y1, B, uB, cnt);
+            col_step<kColour, kRef, kCpl, kFld>(c, sthr, y1, B, uB, cnt);
             y = y2;
         }
     }
     if constexpr (kColour == 1) flush(v, sweep, cnt, false, red);
+    if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
 }
 
 // ---------------------------------------------------------------------
@@ -1521,29 +1498,22 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
         }
         return cudaGetLastError();
     }
-    if (g.model != LAT_NE && g.cpl == nullptr) {   // uniform Ising: the software-pipelined kernels
-        static int res_pipe = 0;
-        const unsigned pb = (unsigned)std::min<long long>(
-            wide_chunks(g), wave(reinterpret_cast<const void *>(k_wide_pipe<1, true>), res_pipe));
-        if (k.ref != nullptr) {
-            k_wide_pipe<0, true><<<pb, kThreads, 0, st>>>(k, off);
-            k_wide_pipe<1, true><<<pb, kThreads, 0, st>>>(k, off);
-        } else {
-            k_wide_pipe<0, false><<<pb, kThreads, 0, st>>>(k, off);
-            k_wide_pipe<1, false><<<pb, kThreads, 0, st>>>(k, off);
-        }
-        return cudaGetLastError();
-    }
-    // North-East, Ising with per-bond couplings, Ising with couplings and
-    // per-site field signs
-    const int m = g.model == LAT_NE ? 0 : (fields ? 2 : 1);
-    using K = void (*)(Geom, int, int);
-    const K kern[3] = {k_wide_half_ne, k_wide_half_cpl, k_wide_half_fld};
-    static int resident[3] = {0, 0, 0};
-    const unsigned blocks = (unsigned)std::min<long long>(
-        wide_chunks(g), wave(reinterpret_cast<const void *>(kern[m]), resident[m]));
+    // Ising, uniform or with per-bond couplings (and per-site field signs):
+    // the software-pipelined kernels
+    using KP = void (*)(Geom, int);
+    static const KP pipe[3][2][2] = {
+        {{k_wide_pipe<0, false>, k_wide_pipe<1, false>}, {k_wide_pipe<0, true>, k_wide_pipe<1, true>}},
+        {{k_wide_pipe<0, false, true, false>, k_wide_pipe<1, false, true, false>},
+         {k_wide_pipe<0, true, true, false>, k_wide_pipe<1, true, true, false>}},
+        {{k_wide_pipe<0, false, true, true>, k_wide_pipe<1, false, true, true>},
+         {k_wide_pipe<0, true, true, true>, k_wide_pipe<1, true, true, true>}}};
+    static int res_pipe[3] = {0, 0, 0};
+    const int m = g.cpl == nullptr ? 0 : (fields ? 2 : 1);
+    const int ref = k.ref != nullptr ? 1 : 0;
+    const unsigned pb = (unsigned)std::min<long long>(
+        wide_chunks(g), wave(reinterpret_cast<const void *>(pipe[m][1][1]), res_pipe[m]));
     for (int colour = 0; colour < 2; ++colour) {
-        kern[m]<<<blocks, kThreads, 0, st>>>(k, colour, off);
+        pipe[m][ref][colour]<<<pb, kThreads, 0, st>>>(k, off);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

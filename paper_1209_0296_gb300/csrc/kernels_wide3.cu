@@ -11,10 +11,11 @@
 // with plain adds (at most 6 * 2 * 8 = 96 per byte, no carries).  The
 // proposal, dE index, table lookup and acceptance follow the generic
 // kernel site by site; draws come from the same Philox groups (4 sites per
-// call for spin-1/2, 2 for spin-S).  Colour 0 reads s[sweep & 1] and writes
-// the new colour-0 sites and a copy of the colour-1 sites into
-// s[(sweep+1) & 1]; colour 1 then updates that buffer in place and reduces
-// the sweep's counters.
+// call for spin-1/2, 2 for spin-S).  The solo kernel reads s[sweep & 1]
+// and writes s[(sweep+1) & 1] without copying a plane (colour 1 takes the
+// new colour-0 sites from the new buffer); the batched kernel copies the
+// colour-1 plane at colour 0 and updates it in place.  Colour 1 reduces the
+// sweep's counters.
 #include <algorithm>
 
 #include "lattice_internal.cuh"
@@ -179,36 +180,6 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
     *reinterpret_cast<uint2 *>(dst + (uint64_t)colour * g.plane + (uint64_t)r * half + 8 * k) =
         make_uint2(out_lo, out_hi);
     if (colour == 0) *reinterpret_cast<uint2 *>(dst + g.plane + (uint64_t)r * half + 8 * k) = O;
-}
-
-template <int SH, int TS, int D>
-__global__ void __launch_bounds__(kThreads) k_wide3_half(Geom g, int colour, int off)
-{
-    __shared__ TabEntry stab[kMaxTab];
-    __shared__ long long red[kThreads / 32];
-    for (int i = threadIdx.x; i < g.tab_n; i += blockDim.x) stab[i] = g.tab[i];
-    __syncthreads();
-    const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
-    PhiloxPre pp;
-    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
-    const uint32_t cpr = g.half >> 3;  // 8-site chunks per plane row
-    const View3 v = view3(g);
-    Acc3 acc;
-    for (GridWalk w(g.rows, cpr); w.ok(); w.next()) wide3_chunk<SH, TS, D>(v, stab, colour, sweep, pp, w.r, w.k, acc);
-    if (colour == 1) {
-        unsigned long long *slot = series_slot(g.ctrl, sweep);
-        long long v;
-        v = block_sum_ll((long long)acc.bond, red);
-        if (threadIdx.x == 0) add_counter(slot + 0, v);
-        v = block_sum_ll((long long)acc.mag, red);
-        if (threadIdx.x == 0) add_counter(slot + 1, v);
-        v = block_sum_ll((long long)acc.up, red);
-        if (threadIdx.x == 0) add_counter(slot + 2, v);
-        if (g.ref != nullptr) {
-            v = block_sum_ll((long long)acc.acf, red);
-            if (threadIdx.x == 0) add_counter(acf_slot(g.ctrl, sweep), v);
-        }
-    }
 }
 
 // ---------------------------------------------------------------------

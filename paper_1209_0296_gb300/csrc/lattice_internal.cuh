@@ -284,36 +284,6 @@ LAT_D void add_counter(unsigned long long *slot, long long v)
 {
     if (v != 0) atomicAdd(slot, (unsigned long long)v);
 }
-
-// Grid-stride walk of one thread over the (row, chunk) pairs of a rows x
-// cpr grid (rows * cpr < 2^31), in the order t = row * cpr + chunk: the
-// first pair costs one division, each further step adds the quotient and
-// remainder of the grid size instead of dividing again.
-struct GridWalk {
-    uint32_t t, total, stride, cpr, r, k, sr, sk;
-    LAT_D GridWalk(uint32_t rows, uint32_t cpr_)
-    {
-        cpr = cpr_;
-        total = rows * cpr;
-        stride = gridDim.x * blockDim.x;
-        t = blockIdx.x * blockDim.x + threadIdx.x;
-        r = t / cpr;
-        k = t - r * cpr;
-        sr = stride / cpr;
-        sk = stride - sr * cpr;
-    }
-    LAT_D bool ok() const { return t < total; }
-    LAT_D void next()
-    {
-        t += stride;
-        r += sr;
-        k += sk;
-        if (k >= cpr) {
-            k -= cpr;
-            ++r;
-        }
-    }
-};
 #endif
 
 }  // namespace lat

@@ -96,6 +96,40 @@ def test_full_size_L4096():
     fld_pair(2, 4096, 1, 1.0, 1.0, 1.5, 7, 2, bonds=True)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("fields", [False, True])
+def test_column_walk_with_reference_L2048(fields):
+    # L = 2048: each thread of the one-wave grid walks its chunk column over
+    # several rows (some threads one more than others), so the two-chunk
+    # pipeline runs its steady state and both exits; couplings always, the
+    # field signs when asked, the overlap with the start recorded
+    L, N, n = 2048, 2048 * 2048, 3
+    eps, eta = _signs(2 * N, 31), _signs(N, 32)
+    o = oracle.Lattice(2, L, 1, oracle.ISING, 1.0, 0.7, 1.8, seed=33, init=oracle.INIT_RANDOM)
+    g = lt.Lattice(2, L, 1, lt.ISING, 1.0, 0.7, 1.8, seed=33, init=lt.INIT_RANDOM)
+    try:
+        o.set_couplings(eps)
+        g.set_couplings(eps)
+        if fields:
+            o.set_fields(eta)
+            g.set_fields(eta)
+        o.set_reference()
+        g.set_reference()
+        ser_o = o.sweep(n)
+        g.sweep(1)
+        g.sweep(n - 1)
+        assert g.get_kernel()["kernel"] == lt.KERNEL_WIDE
+        assert np.array_equal(g.get_spins(), o.spins)
+        ser = g.series(0, n)
+        for k in ("bond", "mag", "up"):
+            assert np.array_equal(ser[k], ser_o[k]), k
+        assert np.array_equal(g.autocorrelation(0, n)[0], ser_o["overlap"])
+        if fields:
+            assert np.array_equal(g.field_series(0, n), ser_o["field"])
+    finally:
+        g.close()
+
+
 def test_batch_with_field_lattices():
     cfgs = [(2, 128, 1, 1.0, 0.7, 1.5, 81, False), (2, 96, 1, 1.0, 0.4, 2.0, 82, True),
             (3, 16, 1, 1.0, 1.2, 2.0, 83, False), (2, 50, 1, 1.0, 0.5, 2.2, 84, True),

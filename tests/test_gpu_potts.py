@@ -66,6 +66,16 @@ def test_potts_full_size_L4096_q3():
     potts_pair(2, 4096, 3, 1.0, 0.0, 1 / math.log(1 + math.sqrt(3)), 7, 2)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("dims,L,q,ref", [(2, 2560, 2, False), (2, 2560, 4, True), (3, 160, 2, True),
+                                          (3, 160, 3, False)])
+def test_potts_column_walk_several_rows_per_thread(dims, L, q, ref):
+    # at these sizes the one-wave grid walks each chunk column over several
+    # plane rows (some threads one more than others), so the two-chunk
+    # pipeline runs its steady state and both of its exits
+    potts_pair(dims, L, q, 1.0, 0.1, 0.9 if dims == 2 else 1.6, 17 + q, 3, chunks=[1, 2], ref=ref)
+
+
 @pytest.mark.parametrize("init", [lt.INIT_COLD, lt.INIT_RANDOM])
 def test_potts_critical_q3(init):
     import math
