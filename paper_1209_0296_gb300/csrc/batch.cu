@@ -60,15 +60,16 @@ struct lattice_batch {
     // Recorded on the batch stream right before a run's first device work
     // (after its host preparation), when set: the server's busy-time clock.
     cudaEvent_t start_event = nullptr;
-    // The rows per any-L item and steps per graph of the last run (0 rows:
-    // the size-based default), as tuned or defaulted.
+    // The rows per pipelined item (2D any-L, 3D / spin-S) and steps per
+    // graph of the last run (0 rows: the size-based default), as tuned or
+    // defaulted.
     int last_passes = 0, last_gsteps = 0;
-    // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S wide
-    // colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide colour 0 / 1,
-    // Potts colour 0 / 1, any-L 2D Ising colour 0 / 1, any-L 2D North-East
-    // colour 0 / 1
+    // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S
+    // per site colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide
+    // colour 0 / 1, Potts colour 0 / 1, any-L 2D Ising colour 0 / 1, any-L 2D
+    // North-East colour 0 / 1, 3D/spin-S byte-parallel colour 0 / 1
     unsigned *d_counters = nullptr;
-    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide = 0, grid_potts = 0;
+    int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide[2] = {0, 0}, grid_potts = 0;
     int grid_any[2] = {0, 0};     // 2D any-L, Ising / North-East
     // resident lattices
     cudaStream_t res_stream = nullptr;
@@ -82,7 +83,7 @@ namespace {
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
 constexpr int kGraphMinSteps = 128;
-constexpr int kCounters = 16;
+constexpr int kCounters = 18;
 constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
 constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
 
@@ -147,7 +148,7 @@ int take_slot(lattice_batch *b, BatchSlot **out)
 // and of North-East lattices, any-L 2D items of Ising and of North-East
 // lattices, 3D / spin-S wide items, Potts items, generic chunks.
 struct Shape {
-    int n_lat, n_ising, n_ne, n_w2[2], n_grp[2], n_wide, n_potts, n_gen;
+    int n_lat, n_ising, n_ne, n_w2[2], n_grp[2], n_wide[2], n_potts, n_gen;
     int tab_gen;   // largest table among the generic lattices
 };
 
@@ -159,12 +160,12 @@ struct Phase {
     const Geom *geoms;
     const uint2 *items;
     Ctrl *const *ctrls;
-    int passes;   // rows a thread visits per any-L item (0: the size-based default)
+    int passes;   // rows a thread visits per any-L or 3D / spin-S item (0: the size-based default)
     int gsteps;   // steps per captured graph
 };
 
 // The batch tuner's choice for one composition of lattices: rows per
-// any-L item and steps per captured graph.
+// pipelined item (2D any-L, 3D / spin-S) and steps per captured graph.
 struct BatchTune {
     int passes, gsteps;
 };
@@ -195,10 +196,14 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
             w2 += sh.n_grp[m];
         }
         const uint2 *wide = w2;
-        for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide > 0; ++colour)
-            e = launch_batch_wide3(ph.geoms, wide, sh.n_wide, b->d_counters + 4 + colour, colour,
-                                   std::min(b->grid_wide, sh.n_wide), st);
-        const uint2 *potts = wide + sh.n_wide;
+        for (int m = 0; m < 2; ++m) {   // 3D / spin-S: per site, then byte-parallel
+            static const int kCtr[2] = {4, 16};
+            for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide[m] > 0; ++colour)
+                e = launch_batch_wide3(ph.geoms, wide, sh.n_wide[m], b->d_counters + kCtr[m] + colour, colour,
+                                       m == 1, ph.passes, std::min(b->grid_wide[m], sh.n_wide[m]), st);
+            wide += sh.n_wide[m];
+        }
+        const uint2 *potts = wide;
         for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_potts > 0; ++colour)
             e = launch_batch_potts(ph.geoms, potts, sh.n_potts, b->d_counters + 10 + colour, colour,
                                    std::min(b->grid_potts, sh.n_potts), st);
@@ -306,7 +311,7 @@ int run_resident(lattice_batch *b, BatchSlot &sl, const std::vector<std::pair<la
 Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t n_active, int passes,
                   std::vector<Geom> &geoms, std::vector<Ctrl *> &ctrls, std::vector<uint2> &items)
 {
-    std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide, potts, gen;
+    std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide[2], potts, gen;
     int tab_gen = 0;
     for (size_t i = 0; i < n_active; ++i) {
         lattice *lt = work[i].first;
@@ -330,8 +335,9 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
             auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[lt->P.model == LAT_NE ? 1 : 0];
             for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && wide3_supported(lt->geom)) {
-            const int nw = wide3_items(lt->geom);
-            for (int k = 0; k < nw; ++k) wide.push_back(make_uint2((unsigned)i, (unsigned)k));
+            const int nw = wide3_items(lt->geom, passes);
+            auto &dst = wide[wide3_swar(lt->geom) ? 1 : 0];
+            for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && potts_supported(lt->geom)) {
             const int np = potts_items(lt->geom);
             for (int k = 0; k < np; ++k) potts.push_back(make_uint2((unsigned)i, (unsigned)k));
@@ -342,10 +348,11 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
             tab_gen = std::max(tab_gen, lt->geom.tab_n);
         }
     }
-    for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &grp[0], &grp[1], &wide, &potts, &gen})
+    for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &grp[0], &grp[1], &wide[0], &wide[1], &potts, &gen})
         items.insert(items.end(), v->begin(), v->end());
     return Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                 {(int)grp[0].size(), (int)grp[1].size()}, (int)wide.size(), (int)potts.size(), (int)gen.size(),
+                 {(int)grp[0].size(), (int)grp[1].size()}, {(int)wide[0].size(), (int)wide[1].size()},
+                 (int)potts.size(), (int)gen.size(),
                  tab_gen};
 }
 
@@ -378,7 +385,7 @@ int upload_lists(lattice_batch *b, BatchSlot &sl, size_t res_bytes, const std::v
 
 // Batch tuner: per composition of lattices (models, dimensions, spins,
 // sizes and kernels of the lattices of a run's first phase), the rows per
-// any-L item and the steps per captured graph, chosen by timing candidates
+// pipelined item and the steps per captured graph, chosen by timing candidates
 // on the run's own steps (one graph replay each after an untimed one; every
 // candidate computes the same bits).  A run tunes only when its first phase
 // has at least kBatchTuneMin steps (tuning synchronises the host, so short
@@ -477,7 +484,8 @@ int lattice_batch_create(lattice_batch_t **out, void *cuda_stream)
     b->grid_tiled_ising = batch_tiled_grid(false);
     b->grid_tiled_ne = batch_tiled_grid(true);
     b->grid_generic = batch_generic_grid();
-    b->grid_wide = batch_wide3_grid();
+    b->grid_wide[0] = batch_wide3_grid(false);
+    b->grid_wide[1] = batch_wide3_grid(true);
     b->grid_potts = batch_potts_grid();
     b->grid_any[0] = batch_any_grid(false);
     b->grid_any[1] = batch_any_grid(true);

@@ -208,6 +208,18 @@ void compact_table(Geom &g, const TabEntry *host_tab)
 {
     g.always16 = 0;
     for (int k = 0; k < 16; ++k) g.thr16[k] = 0;
+    // the rows a spin-1/2 (ds = +-2) or spin-1 (ds = +-1, +-2) move reaches
+    g.tab_strict = 0;
+    if (g.two_S <= 2 && g.dsmax == 2) {
+        g.tab_strict = 1;
+        for (int ds = -2; ds <= 2; ++ds) {
+            if (ds == 0 || (g.two_S == 1 && (ds & 1))) continue;
+            for (int n = 0; n < g.nn; ++n) {
+                const TabEntry e = host_tab[(ds + g.dsmax) * g.nn + n];
+                if (!e.always && e.thr == 0u) g.tab_strict = 0;
+            }
+        }
+    }
     if (g.dims != 2 || g.two_S != 1) return;
     for (int k = 0; k < 16; ++k) {
         const int sd = k >> 3, nd = k & 7;

@@ -11,11 +11,11 @@
 // with plain adds (at most 6 * 2 * 8 = 96 per byte, no carries).  The
 // proposal, dE index, table lookup and acceptance follow the generic
 // kernel site by site; draws come from the same Philox groups (4 sites per
-// call for spin-1/2, 2 for spin-S).  The solo kernel reads s[sweep & 1]
-// and writes s[(sweep+1) & 1] without copying a plane (colour 1 takes the
-// new colour-0 sites from the new buffer); the batched kernel copies the
-// colour-1 plane at colour 0 and updates it in place.  Colour 1 reduces the
-// sweep's counters.
+// call for spin-1/2, 2 for spin-S).  The kernels (solo and batched) read
+// s[sweep & 1] and write s[(sweep+1) & 1] without copying a plane (colour 1
+// takes the new colour-0 sites from the new buffer).  Colour 1 reduces the
+// sweep's counters.  Spin-1/2 and spin-1 lattices whose tables hold no
+// never-accept entry take a byte-parallel step (four sites per word).
 #include <algorithm>
 
 #include "lattice_internal.cuh"
@@ -69,119 +69,6 @@ LAT_D View3 view3(const Geom &g)
     return v;
 }
 
-// Colour `colour` of the 8-site chunk k of plane row r = y + L*z.  TS and
-// D fix two_S and dims at compile time (0: read them from g), which turns
-// the spin/state maps, the proposal and the table index into constants.
-template <int SH, int TS, int D>
-LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigned long long sweep,
-                       const PhiloxPre &pp, uint32_t r, uint32_t k, Acc3 &acc)
-{
-    const int two_S = TS ? TS : g.two_S;
-    const int dims = D ? D : g.dims;
-    const int dsmax = TS ? 2 * max_spin(TS) : g.dsmax;
-    const int nmax = (TS && D) ? 2 * D * max_spin(TS) : g.nmax;
-    const int nn = (TS && D) ? 2 * nmax + 1 : g.nn;
-    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
-    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
-    if (colour == 1) src = dst;
-    const int L = g.L;
-    const uint32_t half = g.half;
-    const int oc = 1 - colour;
-    const int y = (int)(r % (uint32_t)L), z = (int)(r / (uint32_t)L);
-    auto row = [&](int c, uint32_t rr) { return src + (uint64_t)c * g.plane + (uint64_t)rr * half; };
-    const uint32_t ym = (uint32_t)((y == 0 ? L - 1 : y - 1) + L * z);
-    const uint32_t yp = (uint32_t)((y == L - 1 ? 0 : y + 1) + L * z);
-    const uint2 S = *reinterpret_cast<const uint2 *>(row(colour, r) + 8 * k);
-    const uint2 O = *reinterpret_cast<const uint2 *>(row(oc, r) + 8 * k);
-    const uint2 Yn = *reinterpret_cast<const uint2 *>(row(oc, ym) + 8 * k);
-    const uint2 Ys = *reinterpret_cast<const uint2 *>(row(oc, yp) + 8 * k);
-    uint2 Zd = make_uint2(0u, 0u), Zu = make_uint2(0u, 0u);
-    if (dims == 3) {
-        const uint32_t zm = (uint32_t)(y + L * (z == 0 ? L - 1 : z - 1));
-        const uint32_t zp = (uint32_t)(y + L * (z == L - 1 ? 0 : z + 1));
-        Zd = *reinterpret_cast<const uint2 *>(row(oc, zm) + 8 * k);
-        Zu = *reinterpret_cast<const uint2 *>(row(oc, zp) + 8 * k);
-    }
-    // draws first: they do not depend on the loads in flight
-    const uint32_t g0 = r * g.G + ((8u * k) >> SH);  // first Philox group of the chunk
-    constexpr int kCalls = 8 >> SH;
-    U4 u[kCalls];
-#pragma unroll
-    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
-    // row-shifted neighbours: x = 2j + p with p = (colour + y + z) & 1
-    const bool p1 = ((colour + y + z) & 1) != 0;
-    const uint32_t nwr = half >> 2;
-    uint2 Lf, R;
-    if (!p1) {  // west is j-1 of the other plane, east is j
-        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k - 1 + nwr, nwr)];
-        Lf.x = __funnelshift_l(prev, O.x, 8);
-        Lf.y = __funnelshift_l(O.x, O.y, 8);
-        R = O;
-    } else {    // west is j, east is j+1
-        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k + 2, nwr)];
-        Lf = O;
-        R.x = __funnelshift_r(O.x, O.y, 8);
-        R.y = __funnelshift_r(O.y, next, 8);
-    }
-    // neighbour sums offset by 2*dims*smax, byte-wise
-    const int smax = max_spin(two_S);
-    const uint32_t off = 0x01010101u * (uint32_t)smax;
-    uint32_t nlo = add_bytes(Lf.x, off) + add_bytes(R.x, off) + add_bytes(Yn.x, off) + add_bytes(Ys.x, off);
-    uint32_t nhi = add_bytes(Lf.y, off) + add_bytes(R.y, off) + add_bytes(Yn.y, off) + add_bytes(Ys.y, off);
-    if (dims == 3) {
-        nlo += add_bytes(Zd.x, off) + add_bytes(Zu.x, off);
-        nhi += add_bytes(Zd.y, off) + add_bytes(Zu.y, off);
-    }
-    const int noff = 2 * dims * smax;
-    uint32_t out_lo = 0, out_hi = 0;
-    uint2 RS = make_uint2(0u, 0u), RO = RS;   // reference words (colour 1 only)
-    const bool has_ref = colour == 1 && g.ref != nullptr;
-    if (has_ref) {
-        RS = *reinterpret_cast<const uint2 *>(g.ref + g.plane + (uint64_t)r * half + 8 * k);
-        RO = *reinterpret_cast<const uint2 *>(g.ref + (uint64_t)r * half + 8 * k);
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t sw = q < 4 ? S.x : S.y, nw = q < 4 ? nlo : nhi, ow = q < 4 ? O.x : O.y;
-        const int sh8 = 8 * (q & 3);
-        const int s_old = (int)(int8_t)(sw >> sh8);
-        const int n = (int)((nw >> sh8) & 0xFFu) - noff;
-        int s_new;
-        uint32_t u_acc;
-        if (SH == 2) {
-            s_new = -s_old;   // spin-1/2: the flip
-            u_acc = word_of(u[q >> 2], q & 3);
-        } else {
-            const int w = 2 * (q & 1);
-            u_acc = word_of(u[q >> 1], w);
-            const uint32_t u_prop = word_of(u[q >> 1], w + 1);
-            const int k_old = state_of_spin(two_S, s_old);
-            int k_new = k_old + 1 + (int)(((uint64_t)u_prop * (uint64_t)two_S) >> 32);
-            if (k_new > two_S) k_new -= two_S + 1;
-            s_new = spin_of_state(two_S, k_new);
-        }
-        const TabEntry e = stab[(s_new - s_old + dsmax) * nn + (n + nmax)];
-        const int s_fin = (e.always || u_acc < e.thr) ? s_new : s_old;
-        const uint32_t b = ((uint32_t)s_fin & 0xFFu) << sh8;
-        if (q < 4) out_lo |= b;
-        else out_hi |= b;
-        if (colour == 1) {
-            const int so = (int)(int8_t)(ow >> sh8);
-            acc.bond += s_fin * n;
-            acc.mag += s_fin + so;
-            acc.up += (s_fin > 0) + (so > 0);
-            if (has_ref) {
-                const int rs = (int)(int8_t)((q < 4 ? RS.x : RS.y) >> sh8);
-                const int ro = (int)(int8_t)((q < 4 ? RO.x : RO.y) >> sh8);
-                acc.acf += s_fin * rs + so * ro;
-            }
-        }
-    }
-    *reinterpret_cast<uint2 *>(dst + (uint64_t)colour * g.plane + (uint64_t)r * half + 8 * k) =
-        make_uint2(out_lo, out_hi);
-    if (colour == 0) *reinterpret_cast<uint2 *>(dst + g.plane + (uint64_t)r * half + 8 * k) = O;
-}
-
 // ---------------------------------------------------------------------
 // Software-pipelined solo form: each thread walks one 8-site chunk column
 // down the plane rows r = y + L*z (rs rows apart) with two chunks in
@@ -190,42 +77,60 @@ LAT_D void wide3_chunk(const View3 &g, const TabEntry *stab, int colour, unsigne
 // the ALU pipe).  Colour 0 reads both planes of the old buffer and writes
 // plane 0 of the new one; colour 1 reads its own old sites from the old
 // buffer and the new colour-0 sites from the new one, and writes plane 1:
-// no plane is copied.  Same chunks, draws and bits as wide3_chunk.
+// no plane is copied.  Same chunks and draws as the generic kernel.
 // ---------------------------------------------------------------------
 struct W3In {
     uint2 S, O, Yn, Ys, Zd, Zu;
     uint32_t nb;   // the other plane's word past the chunk (west word for x = 2j, east word for x = 2j+1)
+    uint32_t o;    // byte offset of the chunk in its plane: r * half + 8k
 };
 
-template <int D>
-struct W3Walk {
-    const int8_t *pS, *pO;   // this colour's old sites, the other colour's current sites (plane bases)
-    int8_t *dS;              // this colour's plane in the new buffer
-    const int8_t *r1, *r0;   // reference planes 1 and 0 (or null)
-    uint32_t half, L, G, k, nwr;
-    uint32_t wprev, wnext;   // word index in the row of the west word (p = 0) / east word (p = 1)
+// Per-thread constants of the column walk: byte offsets within a plane
+// (N < 2^32, so a plane is below 2^31 bytes and 32-bit offsets suffice).
+struct W3Geo {
+    uint32_t half, L, k8;
+    uint32_t wrap_y;   // (L - 1) * half: from row y = 0 to y = L - 1
+    uint32_t step_z;   // L * half: one z layer
+    uint32_t wrap_z;   // (L - 1) * L * half: from z = 0 to z = L - 1
+    uint32_t wp4, wn4; // byte offsets in a row of the west word (x = 2j) / east word (x = 2j + 1)
 };
+
+LAT_D W3Geo w3_geo(uint32_t half, uint32_t L, uint32_t k, uint32_t wprev, uint32_t wnext)
+{
+    W3Geo c;
+    c.half = half;
+    c.L = L;
+    c.k8 = 8u * k;
+    c.wrap_y = (L - 1u) * half;
+    c.step_z = L * half;
+    c.wrap_z = (L - 1u) * L * half;
+    c.wp4 = 4u * wprev;
+    c.wn4 = 4u * wnext;
+    return c;
+}
 
 template <int kColour>
-LAT_D void w3_load(const View3 &g, const int8_t *pS, const int8_t *pO, uint32_t half, uint32_t L, int dims,
-                   uint32_t r, uint32_t y, uint32_t z, uint32_t k, uint32_t wprev, uint32_t wnext, W3In &in)
+LAT_D void w3_load(const W3Geo &c, const int8_t *pS, const int8_t *pO, int dims, uint32_t r, uint32_t y, uint32_t z,
+                   W3In &in)
 {
-    const uint32_t ym = (y == 0 ? L - 1 : y - 1) + L * z;
-    const uint32_t yp = (y == L - 1 ? 0 : y + 1) + L * z;
-    in.S = *reinterpret_cast<const uint2 *>(pS + (size_t)r * half + 8 * k);
-    in.O = *reinterpret_cast<const uint2 *>(pO + (size_t)r * half + 8 * k);
-    in.Yn = *reinterpret_cast<const uint2 *>(pO + (size_t)ym * half + 8 * k);
-    in.Ys = *reinterpret_cast<const uint2 *>(pO + (size_t)yp * half + 8 * k);
+    const uint32_t row = r * c.half, o = row + c.k8;
+    const uint32_t oym = y == 0 ? o + c.wrap_y : o - c.half;
+    const uint32_t oyp = y == c.L - 1u ? o - c.wrap_y : o + c.half;
+    in.o = o;
+    in.S = *reinterpret_cast<const uint2 *>(pS + o);
+    in.O = *reinterpret_cast<const uint2 *>(pO + o);
+    in.Yn = *reinterpret_cast<const uint2 *>(pO + oym);
+    in.Ys = *reinterpret_cast<const uint2 *>(pO + oyp);
     in.Zd = make_uint2(0u, 0u);
     in.Zu = make_uint2(0u, 0u);
     if (dims == 3) {
-        const uint32_t zm = y + L * (z == 0 ? L - 1 : z - 1);
-        const uint32_t zp = y + L * (z == L - 1 ? 0 : z + 1);
-        in.Zd = *reinterpret_cast<const uint2 *>(pO + (size_t)zm * half + 8 * k);
-        in.Zu = *reinterpret_cast<const uint2 *>(pO + (size_t)zp * half + 8 * k);
+        const uint32_t ozm = z == 0 ? o + c.wrap_z : o - c.step_z;
+        const uint32_t ozp = z == c.L - 1u ? o - c.wrap_z : o + c.step_z;
+        in.Zd = *reinterpret_cast<const uint2 *>(pO + ozm);
+        in.Zu = *reinterpret_cast<const uint2 *>(pO + ozp);
     }
     const bool p1 = ((kColour + y + z) & 1) != 0;
-    in.nb = reinterpret_cast<const uint32_t *>(pO + (size_t)r * half)[p1 ? wnext : wprev];
+    in.nb = *reinterpret_cast<const uint32_t *>(pO + row + (p1 ? c.wn4 : c.wp4));
 }
 
 template <int SH, int TS, int D, int kColour, bool kRef>
@@ -237,7 +142,6 @@ LAT_D void w3_step(const View3 &g, const TabEntry *stab, int8_t *dS, const int8_
     const int dsmax = TS ? 2 * max_spin(TS) : g.dsmax;
     const int nmax = (TS && D) ? 2 * D * max_spin(TS) : g.nmax;
     const int nn = (TS && D) ? 2 * nmax + 1 : g.nn;
-    const uint32_t half = g.half;
     const bool p1 = ((kColour + y + z) & 1) != 0;
     uint2 Lf, R;
     if (!p1) {   // west is j-1 of the other plane, east is j
@@ -261,8 +165,8 @@ LAT_D void w3_step(const View3 &g, const TabEntry *stab, int8_t *dS, const int8_
     uint32_t out_lo = 0, out_hi = 0;
     uint2 RS = make_uint2(0u, 0u), RO = RS;
     if constexpr (kColour == 1 && kRef) {
-        RS = *reinterpret_cast<const uint2 *>(r1 + (size_t)r * half + 8 * k);
-        RO = *reinterpret_cast<const uint2 *>(r0 + (size_t)r * half + 8 * k);
+        RS = *reinterpret_cast<const uint2 *>(r1 + in.o);
+        RO = *reinterpret_cast<const uint2 *>(r0 + in.o);
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -301,15 +205,158 @@ LAT_D void w3_step(const View3 &g, const TabEntry *stab, int8_t *dS, const int8_
             }
         }
     }
-    *reinterpret_cast<uint2 *>(dS + (size_t)r * half + 8 * k) = make_uint2(out_lo, out_hi);
+    *reinterpret_cast<uint2 *>(dS + in.o) = make_uint2(out_lo, out_hi);
+}
+
+// ---------------------------------------------------------------------
+// Byte-parallel step for spin-1/2 and spin-1 (TS = 1, 2): the proposal,
+// the table index, the acceptance mask and the counters are formed for the
+// four sites of a word at once; per site remain one byte extract, one
+// table lookup and one compare.  Spins are bytes s in {-1, 0, 1} (0xFF,
+// 0x00, 0x01); k = s + 1 is the state in {0, 1, 2} (spin-1/2: {0, 2}).
+// The table is the compact form t'[r * nn + n + nmax] = (always ? ~0 :
+// thr - 1), accept iff u <= t', with row r = 0, 1, 2, 3 for ds = s' - s =
+// -2, -1, +1, +2; it needs a table without never-accept entries.
+// ---------------------------------------------------------------------
+
+// k = s + 1 byte-wise: the word add carries out of each 0xFF byte, and that
+// carry is taken back from the byte above (the top byte's leaves the word).
+LAT_D uint32_t plus_one_bytes(uint32_t v) { return v + 0x01010101u - ((v << 1) & 0x01010100u); }
+
+// s = k - 1 byte-wise for k in {0, 1, 2}: the word subtract borrows from the
+// byte above each zero byte, and that borrow is given back.
+LAT_D uint32_t minus_one_bytes(uint32_t k)
+{
+    return k - 0x01010101u + ((~(k | (k >> 1)) & 0x01010101u) << 8);
+}
+
+LAT_D uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Byte q = bit 31 of word q: a selector nibble with bit 3 set copies the
+// sign of the chosen byte (byte 3 of a word) over the whole target byte.
+LAT_D uint32_t top_bits(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t u3)
+{
+    const uint32_t t01 = prmt(u0, u1, 0x00FBu), t23 = prmt(u2, u3, 0x00FBu);
+    return prmt(t01, t23, 0x5410u) & 0x01010101u;
+}
+
+// 0xFF in each byte whose bit 7 is set, else 0x00.
+LAT_D uint32_t sign_bytes(uint32_t x) { return prmt(x, 0u, 0xBA98u); }
+
+constexpr int kSwarTab = 4 * 13;   // rows x nn, nn <= 13 (3D, nmax = 6)
+
+// Rows of the compact table: ds = -2, -1, +1, +2.
+LAT_HD int swar_ds(int row) { return row < 2 ? row - 2 : row - 1; }
+
+template <int TS, int D, int kColour, bool kRef>
+LAT_D void w3s_word(uint32_t S, uint32_t O, uint32_t nsum, uint32_t bits, const uint32_t *acc_u,
+                    const char *tb, uint32_t &Sfin, Acc3 &acc, uint32_t R1, uint32_t R0)
+{
+    constexpr uint32_t ones = 0x01010101u;
+    constexpr uint32_t nn4 = 4u * (2u * 2u * D + 1u);
+    const uint32_t Ko = plus_one_bytes(S);
+    uint32_t Kn;
+    if constexpr (TS == 1) {
+        Kn = 0x02020202u - Ko;                       // the flip: k' = 2 - k
+    } else {
+        Kn = Ko + ones + bits;                       // k + 1 + [u_prop >= 2^31], in [1, 4]
+        Kn -= sign_bytes(Kn + 0x7D7D7D7Du) & 0x03030303u;   // wrap modulo 3 (bit 7 set iff k' >= 3)
+    }
+    const uint32_t X = Kn + 0x02020202u - Ko;        // ds + 2 in {0, 1, 3, 4}
+    const uint32_t row = X - (((X + ones) >> 2) & ones);
+    const uint32_t idx4 = row * nn4 + (nsum << 2);   // byte offsets, at most 204
+    uint32_t am = 0;   // bit 7 of byte q: site q accepted
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t t = *reinterpret_cast<const uint32_t *>(tb + ((idx4 >> (8 * q)) & 0xFFu));
+        am |= (acc_u[q] <= t ? 0x80u : 0u) << (8 * q);
+    }
+    const uint32_t m = sign_bytes(am);
+    if constexpr (TS == 1) {
+        Sfin = S ^ (m & 0xFEFEFEFEu);
+    } else {
+        Sfin = minus_one_bytes(Ko ^ ((Ko ^ Kn) & m));
+    }
+    if constexpr (kColour == 1) {
+        // bond: sum s (n_sum - 2D), n_sum = n + 2D; up: (sum s + #nonzero) / 2
+        const int ss = __dp4a((int)Sfin, (int)ones, 0), so = __dp4a((int)O, (int)ones, 0);
+        acc.bond += __dp4a((int)Sfin, (int)nsum, 0) - 2 * D * ss;
+        acc.mag += ss + so;
+        const int nz = TS == 1 ? 8 : __popc(Sfin & ones) + __popc(O & ones);
+        acc.up += (ss + so + nz) >> 1;
+        if constexpr (kRef) acc.acf += __dp4a((int)Sfin, (int)R1, __dp4a((int)O, (int)R0, 0));
+    }
 }
 
 template <int SH, int TS, int D, int kColour, bool kRef>
+LAT_D void w3s_step(const View3 &g, const uint32_t *st4, int8_t *dS, const int8_t *r1, const int8_t *r0,
+                    uint32_t r, uint32_t y, uint32_t z, uint32_t k, const W3In &in, const U4 (&u)[8 >> SH],
+                    Acc3 &acc)
+{
+    const bool p1 = ((kColour + y + z) & 1) != 0;
+    uint2 Lf, R;
+    if (!p1) {   // west is j-1 of the other plane, east is j
+        Lf.x = __funnelshift_l(in.nb, in.O.x, 8);
+        Lf.y = __funnelshift_l(in.O.x, in.O.y, 8);
+        R = in.O;
+    } else {     // west is j, east is j+1
+        Lf = in.O;
+        R.x = __funnelshift_r(in.O.x, in.O.y, 8);
+        R.y = __funnelshift_r(in.O.y, in.nb, 8);
+    }
+    // n + nmax = sum of the neighbours' k (each s + 1), at most 12 per byte
+    uint32_t nlo = plus_one_bytes(Lf.x) + plus_one_bytes(R.x) + plus_one_bytes(in.Yn.x) + plus_one_bytes(in.Ys.x);
+    uint32_t nhi = plus_one_bytes(Lf.y) + plus_one_bytes(R.y) + plus_one_bytes(in.Yn.y) + plus_one_bytes(in.Ys.y);
+    if constexpr (D == 3) {
+        nlo += plus_one_bytes(in.Zd.x) + plus_one_bytes(in.Zu.x);
+        nhi += plus_one_bytes(in.Zd.y) + plus_one_bytes(in.Zu.y);
+    }
+    uint32_t ua_lo[4], ua_hi[4], b_lo = 0, b_hi = 0;
+    if constexpr (TS == 1) {   // 4 sites per call: word q of call 0 (lo) and 1 (hi)
+        ua_lo[0] = u[0].x, ua_lo[1] = u[0].y, ua_lo[2] = u[0].z, ua_lo[3] = u[0].w;
+        ua_hi[0] = u[1].x, ua_hi[1] = u[1].y, ua_hi[2] = u[1].z, ua_hi[3] = u[1].w;
+    } else {                   // 2 sites per call: acceptance words 0, 2, proposal words 1, 3
+        ua_lo[0] = u[0].x, ua_lo[1] = u[0].z, ua_lo[2] = u[1].x, ua_lo[3] = u[1].z;
+        ua_hi[0] = u[2].x, ua_hi[1] = u[2].z, ua_hi[2] = u[3].x, ua_hi[3] = u[3].z;
+        b_lo = top_bits(u[0].y, u[0].w, u[1].y, u[1].w);
+        b_hi = top_bits(u[2].y, u[2].w, u[3].y, u[3].w);
+    }
+    uint32_t R1lo = 0, R1hi = 0, R0lo = 0, R0hi = 0;
+    if constexpr (kColour == 1 && kRef) {
+        const uint2 RS = *reinterpret_cast<const uint2 *>(r1 + in.o);
+        const uint2 RO = *reinterpret_cast<const uint2 *>(r0 + in.o);
+        R1lo = RS.x, R1hi = RS.y, R0lo = RO.x, R0hi = RO.y;
+    }
+    const char *tb = reinterpret_cast<const char *>(st4);
+    uint2 out;
+    w3s_word<TS, D, kColour, kRef>(in.S.x, in.O.x, nlo, b_lo, ua_lo, tb, out.x, acc, R1lo, R0lo);
+    w3s_word<TS, D, kColour, kRef>(in.S.y, in.O.y, nhi, b_hi, ua_hi, tb, out.y, acc, R1hi, R0hi);
+    *reinterpret_cast<uint2 *>(dS + in.o) = out;
+}
+
+// kSwar: the byte-parallel step (TS = 1, 2 with a table free of
+// never-accept entries), else the per-site one.
+template <int SH, int TS, int D, int kColour, bool kRef, bool kSwar = false>
 __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
 {
-    __shared__ TabEntry stab[kMaxTab];
+    __shared__ TabEntry stab[kSwar ? 1 : kMaxTab];
+    __shared__ uint32_t st4[kSwar ? kSwarTab : 1];
     __shared__ long long red[kThreads / 32];
-    for (int i = threadIdx.x; i < g.tab_n; i += blockDim.x) stab[i] = g.tab[i];
+    if constexpr (kSwar) {
+        const int nn = g.nn;
+        for (int i = threadIdx.x; i < 4 * nn; i += blockDim.x) {
+            const int row = i / nn, col = i - row * nn;
+            const TabEntry e = g.tab[(swar_ds(row) + g.dsmax) * nn + col];
+            st4[i] = e.always ? 0xFFFFFFFFu : e.thr - 1u;
+        }
+    } else {
+        for (int i = threadIdx.x; i < g.tab_n; i += blockDim.x) stab[i] = g.tab[i];
+    }
     __syncthreads();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const View3 v = view3(g);
@@ -332,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
         PhiloxPre pp;
         philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), g.key0, g.key1);
         const uint32_t nwr = v.half >> 2;
-        const uint32_t wprev = wrap_once(2 * k - 1 + nwr, nwr), wnext = wrap_once(2 * k + 2, nwr);
+        const W3Geo geo = w3_geo(v.half, L, k, wrap_once(2 * k - 1 + nwr, nwr), wrap_once(2 * k + 2, nwr));
         // (y, z) of row r, stepped by rs rows without a division
         uint32_t y = r % L, z = r / L;
         const uint32_t dy = rs % L, dz = rs / L;
@@ -350,31 +397,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
 #pragma unroll
             for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)kColour);
         };
+        auto step = [&](uint32_t rr, uint32_t yy, uint32_t zz, const W3In &in, const U4 (&u)[kCalls]) {
+            if constexpr (kSwar) w3s_step<SH, TS, D, kColour, kRef>(v, st4, dS, r1, r0, rr, yy, zz, k, in, u, acc);
+            else w3_step<SH, TS, D, kColour, kRef>(v, stab, dS, r1, r0, rr, yy, zz, k, in, u, acc);
+        };
         W3In A, B;
         U4 uA[kCalls], uB[kCalls];
-        w3_load<kColour>(v, pS, pO, v.half, L, dims, r, y, z, k, wprev, wnext, A);
+        w3_load<kColour>(geo, pS, pO, dims, r, y, z, A);
         draws(r, uA);
         for (;;) {
             const uint32_t r1_ = r + rs;
             uint32_t y1 = y, z1 = z;
             step_row(y1, z1);
             if (r1_ >= rows) {
-                w3_step<SH, TS, D, kColour, kRef>(v, stab, dS, r1, r0, r, y, z, k, A, uA, acc);
+                step(r, y, z, A, uA);
                 break;
             }
-            w3_load<kColour>(v, pS, pO, v.half, L, dims, r1_, y1, z1, k, wprev, wnext, B);
+            w3_load<kColour>(geo, pS, pO, dims, r1_, y1, z1, B);
             draws(r1_, uB);
-            w3_step<SH, TS, D, kColour, kRef>(v, stab, dS, r1, r0, r, y, z, k, A, uA, acc);
+            step(r, y, z, A, uA);
             const uint32_t r2 = r1_ + rs;
             uint32_t y2 = y1, z2 = z1;
             step_row(y2, z2);
             if (r2 >= rows) {
-                w3_step<SH, TS, D, kColour, kRef>(v, stab, dS, r1, r0, r1_, y1, z1, k, B, uB, acc);
+                step(r1_, y1, z1, B, uB);
                 break;
             }
-            w3_load<kColour>(v, pS, pO, v.half, L, dims, r2, y2, z2, k, wprev, wnext, A);
+            w3_load<kColour>(geo, pS, pO, dims, r2, y2, z2, A);
             draws(r2, uA);
-            w3_step<SH, TS, D, kColour, kRef>(v, stab, dS, r1, r0, r1_, y1, z1, k, B, uB, acc);
+            step(r1_, y1, z1, B, uB);
             r = r2;
             y = y2;
             z = z2;
@@ -396,16 +447,122 @@ __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
     }
 }
 
+// ---------------------------------------------------------------------
 // Batched form: a persistent grid takes (lattice, item) pairs from an
-// atomic counter; an item is kItemChunks x kThreads chunks of one colour of
-// one lattice.  The lattice's descriptor and table are reloaded only when a
-// CTA moves to another lattice (items are ordered by lattice).
-constexpr int kItemChunks = 4;
+// atomic counter.  An item is a band of plane rows x a segment of up to
+// kThreads chunk columns of one colour of one lattice; each thread walks
+// its column down the band (rsb rows apart) with two chunks in flight, as
+// the solo kernel does, and the same no-copy convention.  The lattice's
+// descriptor and table are reloaded only when a CTA moves to another
+// lattice (items are ordered by lattice).  kSwar: the list of lattices that
+// take the byte-parallel step (spin-1/2 and spin-1 with strict tables).
+// ---------------------------------------------------------------------
+struct W3ItemShape {
+    uint32_t cpr, nseg, rsb, br;   // chunks per row, column segments, rows per pass, rows per band
+};
 
-__global__ void __launch_bounds__(kThreads, 4) k_batch_wide3(const Geom *geoms, const uint2 *items, int n_items,
-                                                         unsigned *next_item, int colour)
+// passes: rows a thread visits per item, given by the batch (its tuner), or
+// 0 for the default: 8 on large lattices (long pipelines, few items), 2 on
+// small ones (enough items to spread a batch of small lattices).
+LAT_HD W3ItemShape w3_item_shape(uint32_t half, uint32_t rows, uint32_t passes)
 {
-    __shared__ TabEntry stab[kMaxTab];
+    W3ItemShape sh;
+    sh.cpr = half >> 3;
+    sh.nseg = (sh.cpr + kThreads - 1u) / kThreads;
+    sh.rsb = sh.cpr <= (uint32_t)kThreads ? (uint32_t)kThreads / sh.cpr : 1u;
+    if (passes == 0u) passes = (uint64_t)rows * sh.cpr >= 65536u ? 8u : 2u;
+    sh.br = passes * sh.rsb;
+    return sh;
+}
+
+template <int SH, int TS, int D, int kColour, bool kRef, bool kSwar>
+LAT_D void batch_w3_item(const View3 &v, uint32_t key0, uint32_t key1, unsigned long long sweep,
+                         const TabEntry *stab, const uint32_t *st4, uint32_t item, uint32_t passes, Acc3 &acc)
+{
+    const W3ItemShape sh = w3_item_shape(v.half, v.rows, passes);
+    const uint32_t L = (uint32_t)v.L;
+    const int dims = D ? D : v.dims;
+    const uint32_t band = item / sh.nseg, seg = item - band * sh.nseg;
+    const uint32_t r_end = min(v.rows, band * sh.br + sh.br);
+    uint32_t k, r;
+    if (sh.cpr <= (uint32_t)kThreads) {
+        k = threadIdx.x % sh.cpr;
+        r = band * sh.br + threadIdx.x / sh.cpr;
+        if (threadIdx.x / sh.cpr >= sh.rsb) return;
+    } else {
+        k = seg * kThreads + threadIdx.x;
+        r = band * sh.br;
+        if (k >= sh.cpr) return;
+    }
+    if (r >= r_end) return;
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
+    const uint32_t plane = (uint32_t)v.plane;
+    const int8_t *pS = old + (size_t)kColour * plane;
+    const int8_t *pO = (kColour == 0 ? old : nw) + (size_t)(1 - kColour) * plane;
+    int8_t *dS = nw + (size_t)kColour * plane;
+    const int8_t *r1 = v.ref ? v.ref + plane : nullptr, *r0 = v.ref;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), key0, key1);
+    const uint32_t nwr = v.half >> 2;
+    const W3Geo geo = w3_geo(v.half, L, k, wrap_once(2 * k - 1 + nwr, nwr), wrap_once(2 * k + 2, nwr));
+    uint32_t y = r % L, z = r / L;
+    const uint32_t dy = sh.rsb % L, dz = sh.rsb / L;
+    auto step_row = [&](uint32_t &yy, uint32_t &zz) {
+        yy += dy;
+        zz += dz;
+        if (yy >= L) {
+            yy -= L;
+            ++zz;
+        }
+    };
+    constexpr int kCalls = 8 >> SH;
+    auto draws = [&](uint32_t rr, U4 (&u)[kCalls]) {
+        const uint32_t g0 = rr * v.G + ((8u * k) >> SH);
+#pragma unroll
+        for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)kColour);
+    };
+    auto step = [&](uint32_t rr, uint32_t yy, uint32_t zz, const W3In &in, const U4 (&u)[kCalls]) {
+        if constexpr (kSwar) w3s_step<SH, TS, D, kColour, kRef>(v, st4, dS, r1, r0, rr, yy, zz, k, in, u, acc);
+        else w3_step<SH, TS, D, kColour, kRef>(v, stab, dS, r1, r0, rr, yy, zz, k, in, u, acc);
+    };
+    W3In A, B;
+    U4 uA[kCalls], uB[kCalls];
+    w3_load<kColour>(geo, pS, pO, dims, r, y, z, A);
+    draws(r, uA);
+    for (;;) {
+        const uint32_t ra = r + sh.rsb;
+        uint32_t ya = y, za = z;
+        step_row(ya, za);
+        if (ra >= r_end) {
+            step(r, y, z, A, uA);
+            break;
+        }
+        w3_load<kColour>(geo, pS, pO, dims, ra, ya, za, B);
+        draws(ra, uB);
+        step(r, y, z, A, uA);
+        const uint32_t rb = ra + sh.rsb;
+        uint32_t yb = ya, zb = za;
+        step_row(yb, zb);
+        if (rb >= r_end) {
+            step(ra, ya, za, B, uB);
+            break;
+        }
+        w3_load<kColour>(geo, pS, pO, dims, rb, yb, zb, A);
+        draws(rb, uA);
+        step(ra, ya, za, B, uB);
+        r = rb;
+        y = yb;
+        z = zb;
+    }
+}
+
+template <int kColour, bool kSwar>
+__global__ void __launch_bounds__(kThreads, 2) k_batch_wide3(const Geom *geoms, const uint2 *items, int n_items,
+                                                         unsigned *next_item, uint32_t passes)
+{
+    __shared__ TabEntry stab[kSwar ? 1 : kMaxTab];
+    __shared__ uint32_t st4[kSwar ? kSwarTab : 1];
     __shared__ long long red[kThreads / 32];
     __shared__ Geom sg;
     __shared__ int cur;
@@ -421,42 +578,59 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_wide3(const Geom *geoms, 
                 reinterpret_cast<uint32_t *>(&sg)[threadIdx.x] =
                     reinterpret_cast<const uint32_t *>(&geoms[w.x])[threadIdx.x];
             __syncthreads();
-            for (int i = threadIdx.x; i < sg.tab_n; i += blockDim.x) stab[i] = sg.tab[i];
+            if constexpr (kSwar) {
+                const int nn = sg.nn;
+                for (int i = threadIdx.x; i < 4 * nn; i += blockDim.x) {
+                    const int row = i / nn, col = i - row * nn;
+                    const TabEntry e = sg.tab[(swar_ds(row) + sg.dsmax) * nn + col];
+                    st4[i] = e.always ? 0xFFFFFFFFu : e.thr - 1u;
+                }
+            } else {
+                for (int i = threadIdx.x; i < sg.tab_n; i += blockDim.x) stab[i] = sg.tab[i];
+            }
             loaded = (int)w.x;
             __syncthreads();
         }
         // register copies: no aliasing with shared-memory stores
-        const View3 g = view3(sg);
+        const View3 v = view3(sg);
         Ctrl *const ctrl = sg.ctrl;
-        const bool spin_half = sg.sh == 2;   // wide3 takes 2D spin-1/2 never, so this is 3D
-        const bool spin_one3 = sg.two_S == 2 && sg.dims == 3;
+        const uint32_t key0 = sg.key0, key1 = sg.key1;
         const unsigned long long sweep = ctrl->sweep;
-        PhiloxPre pp;
-        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
-        const uint32_t cpr = g.half >> 3;
-        const uint32_t total = g.rows * cpr;   // < 2^28 (N < 2^32)
+        const bool ref = v.ref != nullptr;
         Acc3 acc;
-#pragma unroll 1
-        for (int c = 0; c < kItemChunks; ++c) {
-            const uint32_t t = (w.y * (uint32_t)kItemChunks + (uint32_t)c) * kThreads + threadIdx.x;
-            if (t >= total) break;
-            const uint32_t rr = t / cpr, kk = t - rr * cpr;
-            if (spin_half) wide3_chunk<2, 1, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
-            else if (spin_one3) wide3_chunk<1, 2, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
-            else wide3_chunk<1, 0, 0>(g, stab, colour, sweep, pp, rr, kk, acc);
+        if constexpr (kSwar) {   // 3D spin-1/2, 3D spin-1, 2D spin-1
+            const int which = v.two_S == 1 ? 0 : (v.dims == 3 ? 1 : 2);
+            if (which == 0) {
+                if (ref) batch_w3_item<2, 1, 3, kColour, true, true>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+                else batch_w3_item<2, 1, 3, kColour, false, true>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+            } else if (which == 1) {
+                if (ref) batch_w3_item<1, 2, 3, kColour, true, true>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+                else batch_w3_item<1, 2, 3, kColour, false, true>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+            } else {
+                if (ref) batch_w3_item<1, 2, 2, kColour, true, true>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+                else batch_w3_item<1, 2, 2, kColour, false, true>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+            }
+        } else {                 // per site: 3D spin-1/2 (4 sites per call), any other spin
+            if (v.two_S == 1) {
+                if (ref) batch_w3_item<2, 1, 3, kColour, true, false>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+                else batch_w3_item<2, 1, 3, kColour, false, false>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+            } else {
+                if (ref) batch_w3_item<1, 0, 0, kColour, true, false>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+                else batch_w3_item<1, 0, 0, kColour, false, false>(v, key0, key1, sweep, stab, st4, w.y, passes, acc);
+            }
         }
-        if (colour == 1) {
+        if constexpr (kColour == 1) {
             unsigned long long *slot = series_slot(ctrl, sweep);
-            long long v;
-            v = block_sum_ll((long long)acc.bond, red);
-            if (threadIdx.x == 0) add_counter(slot + 0, v);
-            v = block_sum_ll((long long)acc.mag, red);
-            if (threadIdx.x == 0) add_counter(slot + 1, v);
-            v = block_sum_ll((long long)acc.up, red);
-            if (threadIdx.x == 0) add_counter(slot + 2, v);
-            if (g.ref != nullptr) {
-                v = block_sum_ll((long long)acc.acf, red);
-                if (threadIdx.x == 0) add_counter(acf_slot(ctrl, sweep), v);
+            long long t;
+            t = block_sum_ll((long long)acc.bond, red);
+            if (threadIdx.x == 0) add_counter(slot + 0, t);
+            t = block_sum_ll((long long)acc.mag, red);
+            if (threadIdx.x == 0) add_counter(slot + 1, t);
+            t = block_sum_ll((long long)acc.up, red);
+            if (threadIdx.x == 0) add_counter(slot + 2, t);
+            if (ref) {
+                t = block_sum_ll((long long)acc.acf, red);
+                if (threadIdx.x == 0) add_counter(acf_slot(ctrl, sweep), t);
             }
         }
         __syncthreads();
@@ -465,27 +639,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_wide3(const Geom *geoms, 
 
 }  // namespace
 
-int wide3_items(const Geom &g)
+bool wide3_swar(const Geom &g)
 {
-    const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
-    const uint64_t per = (uint64_t)kItemChunks * kThreads;
-    return (int)((chunks + per - 1) / per);
+    return g.tab_strict && (g.two_S == 1 || g.two_S == 2) && (g.dims == 3 || g.two_S == 2);
 }
 
-int batch_wide3_grid()
+int wide3_items(const Geom &g, int passes)
+{
+    const W3ItemShape sh = w3_item_shape(g.half, g.rows, (uint32_t)passes);
+    return (int)(((g.rows + sh.br - 1u) / sh.br) * sh.nseg);
+}
+
+int batch_wide3_grid(bool swar)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide3, kThreads, 0);
+    if (swar) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide3<1, true>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_wide3<1, false>, kThreads, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
 
 cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                               int colour, int grid, cudaStream_t st)
+                               int colour, bool swar, int passes, int grid, cudaStream_t st)
 {
-    k_batch_wide3<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
+    using K = void (*)(const Geom *, const uint2 *, int, unsigned *, uint32_t);
+    static const K kern[2][2] = {{k_batch_wide3<0, false>, k_batch_wide3<1, false>},
+                                 {k_batch_wide3<0, true>, k_batch_wide3<1, true>}};
+    kern[swar ? 1 : 0][colour ? 1 : 0]<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item,
+                                                                 (uint32_t)passes);
     return cudaGetLastError();
 }
 
@@ -497,12 +680,14 @@ bool wide3_supported(const Geom &g)
 
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st)
 {
-    // instantiations: 3D spin-1/2, 3D spin-1, 2D spin-1, any other spin-S;
-    // each colour, with and without a reference state
-    const int which = g.two_S == 1 ? 0 : (g.two_S == 2 ? (g.dims == 3 ? 1 : 2) : 3);
+    // instantiations: 3D spin-1/2, 3D spin-1, 2D spin-1 (each byte-parallel
+    // when the table has no never-accept entry, else per site), any other
+    // spin-S; each colour, with and without a reference state
+    const int base = g.two_S == 1 ? 0 : (g.two_S == 2 ? (g.dims == 3 ? 1 : 2) : 3);
+    const int which = base < 3 && g.tab_strict ? base + 4 : base;
     const int ref = g.ref != nullptr ? 1 : 0;
     using K = void (*)(Geom, int);
-    static const K kern[4][2][2] = {
+    static const K kern[7][2][2] = {
         {{k_wide3_pipe<2, 1, 3, 0, false>, k_wide3_pipe<2, 1, 3, 1, false>},
          {k_wide3_pipe<2, 1, 3, 0, true>, k_wide3_pipe<2, 1, 3, 1, true>}},
         {{k_wide3_pipe<1, 2, 3, 0, false>, k_wide3_pipe<1, 2, 3, 1, false>},
@@ -510,8 +695,14 @@ cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st)
         {{k_wide3_pipe<1, 2, 2, 0, false>, k_wide3_pipe<1, 2, 2, 1, false>},
          {k_wide3_pipe<1, 2, 2, 0, true>, k_wide3_pipe<1, 2, 2, 1, true>}},
         {{k_wide3_pipe<1, 0, 0, 0, false>, k_wide3_pipe<1, 0, 0, 1, false>},
-         {k_wide3_pipe<1, 0, 0, 0, true>, k_wide3_pipe<1, 0, 0, 1, true>}}};
-    static int resident[4] = {0, 0, 0, 0};
+         {k_wide3_pipe<1, 0, 0, 0, true>, k_wide3_pipe<1, 0, 0, 1, true>}},
+        {{k_wide3_pipe<2, 1, 3, 0, false, true>, k_wide3_pipe<2, 1, 3, 1, false, true>},
+         {k_wide3_pipe<2, 1, 3, 0, true, true>, k_wide3_pipe<2, 1, 3, 1, true, true>}},
+        {{k_wide3_pipe<1, 2, 3, 0, false, true>, k_wide3_pipe<1, 2, 3, 1, false, true>},
+         {k_wide3_pipe<1, 2, 3, 0, true, true>, k_wide3_pipe<1, 2, 3, 1, true, true>}},
+        {{k_wide3_pipe<1, 2, 2, 0, false, true>, k_wide3_pipe<1, 2, 2, 1, false, true>},
+         {k_wide3_pipe<1, 2, 2, 0, true, true>, k_wide3_pipe<1, 2, 2, 1, true, true>}}};
+    static int resident[7] = {0, 0, 0, 0, 0, 0, 0};
     if (resident[which] == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);

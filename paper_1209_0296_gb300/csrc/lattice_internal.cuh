@@ -209,6 +209,10 @@ struct Geom {
     // kernels): index (self down) << 3 | (# down neighbours).
     uint32_t thr16[16];
     uint32_t always16;
+    // 1 when no entry that a spin-1/2 or spin-1 move can reach is
+    // never-accept (not always and thr = 0), so the table converts to the
+    // t' = thr - 1 form of the byte-parallel 3D / spin-1 kernels.
+    uint32_t tab_strict;
 };
 
 // The fields of a Geom that the 2D spin-1/2 sweep kernels read, small
@@ -333,10 +337,14 @@ int batch_potts_grid();
 cudaError_t launch_batch_potts(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
                                int colour, int grid, cudaStream_t st);
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
-int wide3_items(const Geom &g);   // batch items of one colour of one lattice
-int batch_wide3_grid();
+// the byte-parallel step applies (spin-1/2 or spin-1, strict table)
+bool wide3_swar(const Geom &g);
+// batch items of one colour of one lattice; passes: rows a thread visits
+// per item (0: the size-based default)
+int wide3_items(const Geom &g, int passes);
+int batch_wide3_grid(bool swar);
 cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                               int colour, int grid, cudaStream_t st);
+                               int colour, bool swar, int passes, int grid, cudaStream_t st);
 int wide_chunks(const Geom &g);
 // 2D spin-1/2 Ising / North-East with uniform couplings at any even L (the
 // wide kernel's sweep on rows at any byte alignment; launch_sweep_wide takes

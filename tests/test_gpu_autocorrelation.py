@@ -137,6 +137,10 @@ def test_batched_lattices_with_references():
             (2, 64, 1, lt.NE, 0.0, 0.0, 0.25, 62, lt.INIT_EQUILIBRIUM),   # resident CTA
             (3, 16, 2, lt.ISING, 1.0, 0.0, 3.3, 63, lt.INIT_RANDOM),      # wide 3D items
             (3, 6, 1, lt.ISING, 1.0, 0.0, 4.0, 64, lt.INIT_RANDOM),       # generic chunks
+            (3, 32, 1, lt.ISING, 1.0, 0.0, 4.3, 66, lt.INIT_RANDOM),      # byte-parallel 3D spin-1/2
+            (2, 48, 2, lt.ISING, 1.0, 0.1, 1.8, 67, lt.INIT_RANDOM),      # byte-parallel 2D spin-1
+            (3, 16, 3, lt.ISING, 1.0, 0.0, 8.0, 68, lt.INIT_RANDOM),      # per-site 3D items
+            (3, 16, 2, lt.ISING, 1.0, 0.0, 0.25, 69, lt.INIT_RANDOM),     # per site: never-accept entries
             (2, 64, 1, lt.ISING, 1.0, 0.0, 2.3, 65, lt.INIT_RANDOM)]      # no reference
     lats = [lt.Lattice(*c[:7], seed=c[7], init=c[8]) for c in cfgs]
     ors = [oracle.Lattice(*c[:7], seed=c[7], init=c[8]) for c in cfgs]

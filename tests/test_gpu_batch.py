@@ -29,6 +29,14 @@ MIX = [
     (3, 32, 1, lt.ISING, 1.0, 0.05, 4.2, 32, lt.INIT_COLD, 35),
     (2, 48, 3, lt.ISING, 0.9, -0.2, 5.0, 33, lt.INIT_RANDOM, 66),
     (3, 16, 7, lt.ISING, 1.0, 0.0, 30.0, 34, lt.INIT_RANDOM, 12),
+    # 3D / spin-S items: byte-parallel (2D spin-1; bands with a partial last
+    # one), and per site where the table has never-accept entries
+    (2, 64, 2, lt.ISING, 1.0, 0.1, 1.8, 35, lt.INIT_RANDOM, 20),
+    (3, 16, 2, lt.ISING, 1.0, 0.0, 0.25, 36, lt.INIT_RANDOM, 15),
+    (3, 16, 1, lt.ISING, 1.0, 0.0, 0.2, 37, lt.INIT_RANDOM, 15),
+    (3, 48, 2, lt.ISING, 1.0, 0.0, 3.0, 38, lt.INIT_RANDOM, 7),
+    (2, 1024, 2, lt.ISING, 1.0, 0.0, 1.7, 39, lt.INIT_RANDOM, 3),
+    (3, 96, 1, lt.ISING, 1.0, 0.0, 4.5, 40, lt.INIT_RANDOM, 3),
 ]
 
 

@@ -201,6 +201,44 @@ def test_allocation_failure_is_reported():
 
 # ---- full sizes, in the launch configuration the benchmark times ----------
 
+@pytest.mark.parametrize("dims,L,two_S,T,J,h", [(3, 32, 1, 0.2, 1.0, 0.0), (3, 32, 2, 0.25, 1.0, 0.1),
+                                                  (2, 64, 2, 0.25, 1.0, 0.0), (3, 16, 2, 0.25, -1.0, 0.0)])
+def test_wide_three_d_never_accept_tables(dims, L, two_S, T, J, h):
+    # So cold that some moves have p < 2^-32 (thr = 0): the byte-parallel
+    # spin-1/2 / spin-1 step, whose t' = thr - 1 table cannot hold such an
+    # entry, must give way to the per-site step, still bit-exact
+    run_pair(dims, L, two_S, lt.ISING, J, h, T, 29 + L, lt.INIT_RANDOM, 12, kernel=lt.KERNEL_WIDE)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dims,L,two_S,T,J,h,ref", [(3, 160, 1, 4.0, 1.0, 0.2, True),
+                                                    (3, 160, 2, 3.0, 1.0, -0.1, False),
+                                                    (2, 2048, 2, 1.7, 1.0, 0.1, True),
+                                                    (3, 160, 2, 2.0, -1.0, 0.3, True)])
+def test_wide_three_d_column_walk_several_rows(dims, L, two_S, T, J, h, ref):
+    # sizes at which each thread of the one-wave grid walks its chunk column
+    # over several rows (some one more than others): the two-chunk pipeline's
+    # steady state and both exits, with and without the overlap counter
+    o = oracle.Lattice(dims, L, two_S, lt.ISING, J, h, T, seed=41, init=oracle.INIT_RANDOM)
+    g = lt.Lattice(dims, L, two_S, lt.ISING, J, h, T, seed=41, init=lt.INIT_RANDOM)
+    try:
+        g.set_kernel(lt.KERNEL_WIDE)
+        if ref:
+            o.set_reference()
+            g.set_reference()
+        ser_o = o.sweep(3)
+        g.sweep(1)
+        g.sweep(2)
+        assert np.array_equal(g.get_spins(), o.spins)
+        ser = g.series(0, 3)
+        for k in ("bond", "mag", "up"):
+            assert np.array_equal(ser[k], ser_o[k]), k
+        if ref:
+            assert np.array_equal(g.autocorrelation(0, 3)[0], ser_o["overlap"])
+    finally:
+        g.close()
+
+
 @pytest.mark.parametrize("kernel", [lt.KERNEL_TILED, lt.KERNEL_WIDE])
 def test_full_size_2d_L4096_random(kernel):
     # 2D Ising spin-1/2, L=4096, T=2.0, random +-1 start (seed 7).
