@@ -345,10 +345,11 @@ int lattice_batch_add(lattice_batch_t *b, lattice_t *lat, int64_t n);
 int lattice_batch_run(lattice_batch_t *b);
 int lattice_batch_synchronize(lattice_batch_t *b);
 /* The batch engine's two tunables as its last run used them: the rows a
- * thread visits per item of the pipelined 2D spin-1/2 and 3D / spin-S
- * kernels (*rows_per_item; 0 = the size-based default: 8 rows on 2D
- * lattices with L >= 1024 and on 3D / spin-S lattices of at least 2^19
- * sites, 2 below) and the steps per captured
+ * thread visits per item of the pipelined 2D spin-1/2 kernel
+ * (*rows_per_item; 0 = the size-based default, 8 rows on lattices with
+ * L >= 1024 and 2 below; the 3D / spin-S items size themselves to the
+ * phase's 3D work, 2 to 32 rows, at least 4 items per CTA) and the steps
+ * per captured
  * CUDA graph (*steps_per_graph).  A run whose first phase (all its
  * lattices) has at least 192 steps tunes both once per composition of
  * lattices (models, dimensions, spins, sizes and kernels), timing

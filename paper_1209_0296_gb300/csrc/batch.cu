@@ -60,9 +60,8 @@ struct lattice_batch {
     // Recorded on the batch stream right before a run's first device work
     // (after its host preparation), when set: the server's busy-time clock.
     cudaEvent_t start_event = nullptr;
-    // The rows per pipelined item (2D any-L, 3D / spin-S) and steps per
-    // graph of the last run (0 rows: the size-based default), as tuned or
-    // defaulted.
+    // The rows per any-L item and steps per graph of the last run (0 rows:
+    // the size-based default), as tuned or defaulted.
     int last_passes = 0, last_gsteps = 0;
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S
     // per site colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide
@@ -149,6 +148,7 @@ int take_slot(lattice_batch *b, BatchSlot **out)
 // lattices, 3D / spin-S wide items, Potts items, generic chunks.
 struct Shape {
     int n_lat, n_ising, n_ne, n_w2[2], n_grp[2], n_wide[2], n_potts, n_gen;
+    int passes3;   // rows a thread visits per 3D / spin-S item
     int tab_gen;   // largest table among the generic lattices
 };
 
@@ -160,12 +160,12 @@ struct Phase {
     const Geom *geoms;
     const uint2 *items;
     Ctrl *const *ctrls;
-    int passes;   // rows a thread visits per any-L or 3D / spin-S item (0: the size-based default)
+    int passes;   // rows a thread visits per any-L item (0: the size-based default)
     int gsteps;   // steps per captured graph
 };
 
 // The batch tuner's choice for one composition of lattices: rows per
-// pipelined item (2D any-L, 3D / spin-S) and steps per captured graph.
+// any-L item and steps per captured graph.
 struct BatchTune {
     int passes, gsteps;
 };
@@ -200,7 +200,7 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
             static const int kCtr[2] = {4, 16};
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_wide[m] > 0; ++colour)
                 e = launch_batch_wide3(ph.geoms, wide, sh.n_wide[m], b->d_counters + kCtr[m] + colour, colour,
-                                       m == 1, ph.passes, std::min(b->grid_wide[m], sh.n_wide[m]), st);
+                                       m == 1, sh.passes3, std::min(b->grid_wide[m], sh.n_wide[m]), st);
             wide += sh.n_wide[m];
         }
         const uint2 *potts = wide;
@@ -313,6 +313,18 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
 {
     std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide[2], potts, gen;
     int tab_gen = 0;
+    // 3D / spin-S items: the rows per item follow the phase's whole 3D work
+    // (a few items per CTA), not the 2D tunable
+    uint64_t chunk_rows3 = 0;
+    for (size_t i = 0; i < n_active; ++i) {
+        const lattice *lt = work[i].first;
+        const int kern = choose_kernel(lt);
+        const bool generic = kern == LAT_KERNEL_GENERIC;
+        if (!generic && !(tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) && !any_supported(lt->geom) &&
+            wide3_supported(lt->geom))
+            chunk_rows3 += (uint64_t)lt->geom.rows * (lt->geom.half >> 3);
+    }
+    const int passes3 = wide3_batch_passes(chunk_rows3);
     for (size_t i = 0; i < n_active; ++i) {
         lattice *lt = work[i].first;
         geoms.push_back(tiled_geom(lt->geom));
@@ -335,7 +347,7 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
             auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[lt->P.model == LAT_NE ? 1 : 0];
             for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && wide3_supported(lt->geom)) {
-            const int nw = wide3_items(lt->geom, passes);
+            const int nw = wide3_items(lt->geom, passes3);
             auto &dst = wide[wide3_swar(lt->geom) ? 1 : 0];
             for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && potts_supported(lt->geom)) {
@@ -352,7 +364,7 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
         items.insert(items.end(), v->begin(), v->end());
     return Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
                  {(int)grp[0].size(), (int)grp[1].size()}, {(int)wide[0].size(), (int)wide[1].size()},
-                 (int)potts.size(), (int)gen.size(),
+                 (int)potts.size(), (int)gen.size(), passes3,
                  tab_gen};
 }
 
@@ -385,7 +397,7 @@ int upload_lists(lattice_batch *b, BatchSlot &sl, size_t res_bytes, const std::v
 
 // Batch tuner: per composition of lattices (models, dimensions, spins,
 // sizes and kernels of the lattices of a run's first phase), the rows per
-// pipelined item and the steps per captured graph, chosen by timing candidates
+// any-L item and the steps per captured graph, chosen by timing candidates
 // on the run's own steps (one graph replay each after an untimed one; every
 // candidate computes the same bits).  A run tunes only when its first phase
 // has at least kBatchTuneMin steps (tuning synchronises the host, so short

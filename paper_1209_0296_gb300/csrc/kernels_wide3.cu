@@ -644,6 +644,20 @@ bool wide3_swar(const Geom &g)
     return g.tab_strict && (g.two_S == 1 || g.two_S == 2) && (g.dims == 3 || g.two_S == 2);
 }
 
+// Rows per thread for the 3D / spin-S items of a batch phase whose lattices
+// hold chunk_rows (row, chunk column) pairs in all: at least 4 items per CTA
+// of one wave (2 CTAs on 152 SMs), 2 to 32 rows.  Long items pay their
+// set-up (Philox keys, counter reduction) once per many chunks; enough
+// items keep the SMs level.  (16 lattices of 256^3: 32 rows, 476 upd/ns,
+// against 432 at 8 rows and 464 at 16.)
+int wide3_batch_passes(uint64_t chunk_rows)
+{
+    const uint64_t per = chunk_rows / ((uint64_t)kThreads * 4u * 2u * 152u);
+    int p = 2;
+    while (p < 32 && (uint64_t)(2 * p) <= per) p *= 2;
+    return p;
+}
+
 int wide3_items(const Geom &g, int passes)
 {
     const W3ItemShape sh = w3_item_shape(g.half, g.rows, (uint32_t)passes);

@@ -342,6 +342,8 @@ bool wide3_swar(const Geom &g);
 // batch items of one colour of one lattice; passes: rows a thread visits
 // per item (0: the size-based default)
 int wide3_items(const Geom &g, int passes);
+// rows per thread of the 3D / spin-S items of a phase with chunk_rows (row, chunk) pairs
+int wide3_batch_passes(uint64_t chunk_rows);
 int batch_wide3_grid(bool swar);
 cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
                                int colour, bool swar, int passes, int grid, cudaStream_t st);
