@@ -247,6 +247,8 @@ cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st)
     }
     const uint64_t words = (uint64_t)g.L * g.bw;
     const unsigned blocks = (unsigned)std::min<uint64_t>((words + kThreads - 1) / kThreads, (uint64_t)w);
+    // plain launches: early-scheduled dependents (programmatic dependent
+    // launch, as the int8 kernels use) measured 2% slower here
     c0<<<blocks, kThreads, 0, st>>>(k, off);
     c1<<<blocks, kThreads, 0, st>>>(k, off);
     return cudaGetLastError();

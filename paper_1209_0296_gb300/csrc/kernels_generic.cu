@@ -261,9 +261,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_half_sweep(const Geom *geoms
 __global__ void k_batch_advance(Ctrl *const *ctrls, int n, unsigned *counters, int n_counters,
                                 unsigned long long k)
 {
+    dep_wait();   // the step's sweep kernels are done with the counters and sweep numbers
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) ctrls[i]->sweep += k;
     if (i < n_counters) counters[i] = 0u;
+    dep_launch();
 }
 
 // Counters of a configuration from their definitions (before the first
@@ -424,8 +426,8 @@ cudaError_t launch_batch_advance(Ctrl *const *ctrls, int n, unsigned *counters, 
                                  unsigned long long k, cudaStream_t st)
 {
     const int m = n > n_counters ? n : n_counters;
-    k_batch_advance<<<(m + kThreads - 1) / kThreads, kThreads, 0, st>>>(ctrls, n, counters, n_counters, k);
-    return cudaGetLastError();
+    return launch_pdl(k_batch_advance, (unsigned)((m + kThreads - 1) / kThreads), kThreads, st, ctrls, n, counters,
+                      n_counters, k);
 }
 
 cudaError_t launch_measure(const Geom &g, const int8_t *spins, unsigned long long *out5, cudaStream_t st)

@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_potts_pipe(Geom g, int off)
     __shared__ long long red[kThreads / 32];
     if (threadIdx.x < (unsigned)g.tab_n) stab[threadIdx.x] = g.tab[threadIdx.x];
     __syncthreads();
+    dep_wait();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const ViewP v = viewp(g);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_potts_pipe(Geom g, int off)
             z = z2;
         }
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if constexpr (kColour == 1) {
         unsigned long long *slot = series_slot(g.ctrl, sweep);
         long long s;
@@ -501,8 +503,7 @@ cudaError_t launch_sweep_potts(const Geom &g, int off, cudaStream_t st)
     const unsigned blocks = (unsigned)std::min<uint64_t>((chunks + kThreads - 1) / kThreads,
                                                         (uint64_t)resident[which]);
     for (int colour = 0; colour < 2; ++colour) {
-        kern[which][ref][colour]<<<blocks, kThreads, 0, st>>>(g, off);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(kern[which][ref][colour], blocks, kThreads, st, g, off);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

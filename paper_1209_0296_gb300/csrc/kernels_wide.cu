@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
         }
     }
     __syncthreads();
+    dep_wait();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const SweepView v = sweep_view(g);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
@@ -545,6 +546,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
             y = y2;
         }
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if constexpr (kColour == 1) flush(v, sweep, cnt, false, red);
     if constexpr (kFld) flush_one(fld_slot(g.ctrl, sweep), cnt.fld, red);   // both colours
 }
@@ -679,6 +681,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe_ne(Geom g, in
     __shared__ uint4 dq[kThreads / 32][kNeSlots];
     if (threadIdx.x < 32) sthr[threadIdx.x] = threadIdx.x < 16 ? g.thr16[threadIdx.x] : 0xFFFFFFFFu;
     __syncthreads();
+    dep_wait();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const SweepView v = sweep_view(g);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
@@ -716,6 +719,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe_ne(Geom g, in
         y = y2;
         act = act2;
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if constexpr (kColour == 1) flush(v, sweep, cnt, true, red);
 }
 
@@ -934,6 +938,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe(Geom g, int of
     __shared__ int red[kThreads / 32][5];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
     __syncthreads();
+    dep_wait();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const SweepView v = sweep_view(g);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
@@ -973,6 +978,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe(Geom g, int of
             y = y2;
         }
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if constexpr (kColour == 1) flush(v, sweep, cnt, false, red);
 }
 
@@ -1095,6 +1101,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe_ne(Geom g, int
     __shared__ uint4 dq[kThreads / 32][kNeSlots];
     if (threadIdx.x < 32) sthr[threadIdx.x] = threadIdx.x < 16 ? g.thr16[threadIdx.x] : 0xFFFFFFFFu;
     __syncthreads();
+    dep_wait();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const SweepView v = sweep_view(g);
     const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
@@ -1129,6 +1136,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe_ne(Geom g, int
         y = y2;
         act = act2;
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if constexpr (kColour == 1) flush(v, sweep, cnt, true, red);
 }
 
@@ -1247,6 +1255,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *g
     __shared__ int cur;
     int loaded = -1;
     const int warp = kNE ? (int)(threadIdx.x >> 5) : 0;
+    dep_wait();   // the work counter, sweep numbers and spins of the step before
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
         __syncthreads();
@@ -1268,6 +1277,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *g
         if constexpr (kColour == 1) flush(v, v.ctrl->sweep, cnt, kNE, red);   // ends with __syncthreads()
         __syncthreads();
     }
+    dep_launch();   // no items left: the next kernel may be scheduled
 }
 
 // Resident form for lattices that fit in one CTA's shared memory (§III.A
@@ -1449,9 +1459,8 @@ cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items,
          {k_batch_any<false, true, 0>, k_batch_any<false, true, 1>}},
         {{k_batch_any<true, false, 0>, k_batch_any<true, false, 1>},
          {k_batch_any<true, true, 0>, k_batch_any<true, true, 1>}}};
-    kern[ne ? 1 : 0][aligned ? 1 : 0][colour ? 1 : 0]<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item,
-                                                                                 (uint32_t)passes);
-    return cudaGetLastError();
+    return launch_pdl(kern[ne ? 1 : 0][aligned ? 1 : 0][colour ? 1 : 0], (unsigned)grid, kThreads, st, geoms, items,
+                      n_items, next_item, (uint32_t)passes);
 }
 
 cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st)
@@ -1481,21 +1490,24 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
                          : (ref ? k_any_pipe<0, true> : k_any_pipe<0, false>);
         const KG c1 = ne ? (ref ? k_any_pipe_ne<1, true> : k_any_pipe_ne<1, false>)
                          : (ref ? k_any_pipe<1, true> : k_any_pipe<1, false>);
-        c0<<<gb, kThreads, 0, st>>>(k, off);
-        c1<<<gb, kThreads, 0, st>>>(k, off);
-        return cudaGetLastError();
+        if (ne) {   // plain launches: early-scheduled dependents measured 2% slower here
+            c0<<<gb, kThreads, 0, st>>>(k, off);
+            c1<<<gb, kThreads, 0, st>>>(k, off);
+            return cudaGetLastError();
+        }
+        cudaError_t e = launch_pdl(c0, gb, kThreads, st, k, off);
+        return e == cudaSuccess ? launch_pdl(c1, gb, kThreads, st, k, off) : e;
     }
     if (g.model == LAT_NE && g.cpl == nullptr) {   // North-East: pipelined, draws compacted per warp
         static int res_ne = 0;
         const unsigned pb = (unsigned)std::min<long long>(
             wide_chunks(g), wave(reinterpret_cast<const void *>(k_wide_pipe_ne<1, true>), res_ne));
-        if (k.ref != nullptr) {
-            k_wide_pipe_ne<0, true><<<pb, kThreads, 0, st>>>(k, off);
-            k_wide_pipe_ne<1, true><<<pb, kThreads, 0, st>>>(k, off);
-        } else {
-            k_wide_pipe_ne<0, false><<<pb, kThreads, 0, st>>>(k, off);
-            k_wide_pipe_ne<1, false><<<pb, kThreads, 0, st>>>(k, off);
-        }
+        // plain launches: early-scheduled dependents measured no faster here
+        using KG = void (*)(Geom, int);
+        const KG c0 = k.ref != nullptr ? k_wide_pipe_ne<0, true> : k_wide_pipe_ne<0, false>;
+        const KG c1 = k.ref != nullptr ? k_wide_pipe_ne<1, true> : k_wide_pipe_ne<1, false>;
+        c0<<<pb, kThreads, 0, st>>>(k, off);
+        c1<<<pb, kThreads, 0, st>>>(k, off);
         return cudaGetLastError();
     }
     // Ising, uniform or with per-bond couplings (and per-site field signs):
@@ -1513,8 +1525,7 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
     const unsigned pb = (unsigned)std::min<long long>(
         wide_chunks(g), wave(reinterpret_cast<const void *>(pipe[m][1][1]), res_pipe[m]));
     for (int colour = 0; colour < 2; ++colour) {
-        pipe[m][ref][colour]<<<pb, kThreads, 0, st>>>(k, off);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(pipe[m][ref][colour], pb, kThreads, st, k, off);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -358,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
         for (int i = threadIdx.x; i < g.tab_n; i += blockDim.x) stab[i] = g.tab[i];
     }
     __syncthreads();
+    dep_wait();
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const View3 v = view3(g);
     const int dims = D ? D : v.dims;
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
             z = z2;
         }
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if constexpr (kColour == 1) {
         unsigned long long *slot = series_slot(g.ctrl, sweep);
         long long t;
@@ -567,6 +569,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_wide3(const Geom *geoms, 
     __shared__ Geom sg;
     __shared__ int cur;
     int loaded = -1;
+    dep_wait();   // the work counter, sweep numbers and spins of the step before
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
         __syncthreads();
@@ -635,6 +638,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_wide3(const Geom *geoms, 
         }
         __syncthreads();
     }
+    dep_launch();   // no items left: the next kernel may be scheduled
 }
 
 }  // namespace
@@ -681,9 +685,8 @@ cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_item
     using K = void (*)(const Geom *, const uint2 *, int, unsigned *, uint32_t);
     static const K kern[2][2] = {{k_batch_wide3<0, false>, k_batch_wide3<1, false>},
                                  {k_batch_wide3<0, true>, k_batch_wide3<1, true>}};
-    kern[swar ? 1 : 0][colour ? 1 : 0]<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item,
-                                                                 (uint32_t)passes);
-    return cudaGetLastError();
+    return launch_pdl(kern[swar ? 1 : 0][colour ? 1 : 0], (unsigned)grid, kThreads, st, geoms, items, n_items,
+                      next_item, (uint32_t)passes);
 }
 
 bool wide3_supported(const Geom &g)
@@ -728,8 +731,7 @@ cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st)
     const unsigned blocks = (unsigned)std::min<uint64_t>((chunks + kThreads - 1) / kThreads,
                                                         (uint64_t)resident[which]);
     for (int colour = 0; colour < 2; ++colour) {
-        kern[which][ref][colour]<<<blocks, kThreads, 0, st>>>(g, off);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(kern[which][ref][colour], blocks, kThreads, st, g, off);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

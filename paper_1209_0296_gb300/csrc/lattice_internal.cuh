@@ -143,6 +143,37 @@ struct Ctrl {
 };
 
 #if defined(__CUDACC__)
+// Programmatic dependent launch.  The sweep kernels are launched so that the
+// next kernel on the stream may be scheduled while this one drains.  Each
+// calls dep_wait() before it touches anything an earlier kernel writes (the
+// sweep counter, spins, flags, counters), and dep_launch() only when its own
+// main work is done, so the successor's CTAs (which then sit in dep_wait())
+// are placed on SMs no earlier than every CTA of this grid has run: when
+// other streams' kernels share the GPU and not all of this grid fits at
+// once, an earlier trigger could let waiting successor CTAs take the slots
+// this grid's remaining CTAs need.  Launched without the attribute (or with
+// no kernel before it), dep_wait() returns at once.
+LAT_D void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+LAT_D void dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch kern<<<grid, block, 0, st>>>(args...) with programmatic stream
+// serialisation (the kernel must call dep_wait() as above).
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kern)(P...), unsigned grid, unsigned block, cudaStream_t st, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<P>(args)...);
+}
+
 // Counter slot of global sweep `sweep` (4 x int64: bond, mag, up, unflipped).
 LAT_D unsigned long long *series_slot(const Ctrl *c, unsigned long long sweep)
 {
