@@ -148,7 +148,7 @@ int take_slot(lattice_batch *b, BatchSlot **out)
 // lattices, 3D / spin-S wide items, Potts items, generic chunks.
 struct Shape {
     int n_lat, n_ising, n_ne, n_w2[2], n_grp[2], n_wide[2], n_potts, n_gen;
-    int passes3;   // rows a thread visits per 3D / spin-S item
+    int passes3, passes_p;   // rows a thread visits per 3D / spin-S item and per Potts item
     int tab_gen;   // largest table among the generic lattices
 };
 
@@ -205,7 +205,7 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
         }
         const uint2 *potts = wide;
         for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_potts > 0; ++colour)
-            e = launch_batch_potts(ph.geoms, potts, sh.n_potts, b->d_counters + 10 + colour, colour,
+            e = launch_batch_potts(ph.geoms, potts, sh.n_potts, b->d_counters + 10 + colour, colour, sh.passes_p,
                                    std::min(b->grid_potts, sh.n_potts), st);
         const uint2 *gen = potts + sh.n_potts;
         if (e == cudaSuccess && sh.n_gen > 0)
@@ -313,18 +313,19 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
 {
     std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide[2], potts, gen;
     int tab_gen = 0;
-    // 3D / spin-S items: the rows per item follow the phase's whole 3D work
-    // (a few items per CTA), not the 2D tunable
-    uint64_t chunk_rows3 = 0;
+    // 3D / spin-S and Potts items: the rows per item follow the phase's whole
+    // work of that kind (a few items per CTA), not the 2D tunable
+    uint64_t chunk_rows3 = 0, chunk_rows_p = 0;
     for (size_t i = 0; i < n_active; ++i) {
         const lattice *lt = work[i].first;
         const int kern = choose_kernel(lt);
         const bool generic = kern == LAT_KERNEL_GENERIC;
-        if (!generic && !(tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) && !any_supported(lt->geom) &&
-            wide3_supported(lt->geom))
-            chunk_rows3 += (uint64_t)lt->geom.rows * (lt->geom.half >> 3);
+        if (generic || (tiled_supported(lt->geom) && kern == LAT_KERNEL_TILED) || any_supported(lt->geom)) continue;
+        const uint64_t cr = (uint64_t)lt->geom.rows * (lt->geom.half >> 3);
+        if (wide3_supported(lt->geom)) chunk_rows3 += cr;
+        else if (potts_supported(lt->geom)) chunk_rows_p += cr;
     }
-    const int passes3 = wide3_batch_passes(chunk_rows3);
+    const int passes3 = batch_item_passes(chunk_rows3), passes_p = batch_item_passes(chunk_rows_p);
     for (size_t i = 0; i < n_active; ++i) {
         lattice *lt = work[i].first;
         geoms.push_back(tiled_geom(lt->geom));
@@ -351,7 +352,7 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
             auto &dst = wide[wide3_swar(lt->geom) ? 1 : 0];
             for (int k = 0; k < nw; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && potts_supported(lt->geom)) {
-            const int np = potts_items(lt->geom);
+            const int np = potts_items(lt->geom, passes_p);
             for (int k = 0; k < np; ++k) potts.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else {
             const uint64_t groups = (uint64_t)lt->geom.rows * lt->geom.G;
@@ -364,7 +365,7 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
         items.insert(items.end(), v->begin(), v->end());
     return Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
                  {(int)grp[0].size(), (int)grp[1].size()}, {(int)wide[0].size(), (int)wide[1].size()},
-                 (int)potts.size(), (int)gen.size(), passes3,
+                 (int)potts.size(), (int)gen.size(), passes3, passes_p,
                  tab_gen};
 }
 

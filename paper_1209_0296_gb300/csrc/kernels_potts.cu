@@ -11,12 +11,12 @@
 // 8 sites at once with byte-wise adds (every byte stays below 64, so no
 // carry crosses a byte).  Per site remain the proposal, one table lookup
 // and the acceptance compare.  Draws come from the same Philox groups as
-// the generic kernel (4 sites per call for q = 2, 2 for q >= 3).  The solo
-// kernel reads s[sweep & 1] and writes s[(sweep+1) & 1] without copying a
-// plane (colour 1 takes the new colour-0 labels from the new buffer); the
-// batched kernel copies the colour-1 plane at colour 0 and updates it in
-// place.  Colour 1 reduces the sweep's counters (equal-neighbour bonds,
-// sites in state 0, the others, and the overlap with a reference state).
+// the generic kernel (4 sites per call for q = 2, 2 for q >= 3).  The
+// kernels (solo and batched) read s[sweep & 1] and write s[(sweep+1) & 1]
+// without copying a plane (colour 1 takes the new colour-0 labels from the
+// new buffer).  Colour 1 reduces the sweep's counters (equal-neighbour
+// bonds, sites in state 0, the others, and the overlap with a reference
+// state).
 #include <algorithm>
 
 #include "lattice_internal.cuh"
@@ -74,111 +74,6 @@ LAT_D ViewP viewp(const Geom &g)
     return v;
 }
 
-// Colour `colour` of the 8-site chunk k of plane row r = y + L*z.  SH:
-// log2(sites per Philox call), 2 for q = 2 and 1 otherwise; D: dimension.
-template <int SH, int D>
-LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigned long long sweep,
-                       const PhiloxPre &pp, uint32_t r, uint32_t k, AccP &acc)
-{
-    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
-    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
-    if (colour == 1) src = dst;
-    const int L = g.L;
-    const uint32_t half = g.half;
-    const int oc = 1 - colour;
-    const int y = (int)(r % (uint32_t)L), z = (int)(r / (uint32_t)L);
-    auto row = [&](int c, uint32_t rr) { return src + (uint64_t)c * g.plane + (uint64_t)rr * half; };
-    auto ld = [&](int c, uint32_t rr) { return *reinterpret_cast<const uint2 *>(row(c, rr) + 8 * k); };
-    const uint2 S = ld(colour, r);
-    const uint2 O = ld(oc, r);
-    // neighbours: west, east, north, south (and z-1, z+1 in 3D)
-    uint2 Nb[2 * D];
-    Nb[2] = ld(oc, (uint32_t)((y == 0 ? L - 1 : y - 1) + L * z));
-    Nb[3] = ld(oc, (uint32_t)((y == L - 1 ? 0 : y + 1) + L * z));
-    if constexpr (D == 3) {
-        Nb[4] = ld(oc, (uint32_t)(y + L * (z == 0 ? L - 1 : z - 1)));
-        Nb[5] = ld(oc, (uint32_t)(y + L * (z == L - 1 ? 0 : z + 1)));
-    }
-    // draws first: they do not depend on the loads in flight
-    const uint32_t g0 = r * g.G + ((8u * k) >> SH);   // first Philox group of the chunk
-    constexpr int kCalls = 8 >> SH;
-    U4 u[kCalls];
-#pragma unroll
-    for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)colour);
-    // row-shifted neighbours: x = 2j + p with p = (colour + y + z) & 1
-    const bool p1 = ((colour + y + z) & 1) != 0;
-    const uint32_t nwr = half >> 2;
-    if (!p1) {  // west is j-1 of the other plane, east is j
-        const uint32_t prev = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k - 1 + nwr, nwr)];
-        Nb[0] = make_uint2(__funnelshift_l(prev, O.x, 8), __funnelshift_l(O.x, O.y, 8));
-        Nb[1] = O;
-    } else {    // west is j, east is j+1
-        const uint32_t next = reinterpret_cast<const uint32_t *>(row(oc, r))[wrap_once(2 * k + 2, nwr)];
-        Nb[0] = O;
-        Nb[1] = make_uint2(__funnelshift_r(O.x, O.y, 8), __funnelshift_r(O.y, next, 8));
-    }
-    // proposals: a uniform other label (the spin-S proposal carried over to labels)
-    uint2 Sn = make_uint2(0u, 0u);
-    if constexpr (SH == 2) {
-        Sn = make_uint2(S.x ^ 0x01010101u, S.y ^ 0x01010101u);   // q = 2: the other label
-    } else {
-        const uint32_t q1 = (uint32_t)g.two_S;   // q - 1
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t sw = q < 4 ? S.x : S.y;
-            const int sh8 = 8 * (q & 3);
-            const uint32_t k_old = (sw >> sh8) & 0xFFu;
-            const uint32_t u_prop = word_of(u[q >> 1], 2 * (q & 1) + 1);
-            uint32_t k_new = k_old + 1u + (uint32_t)(((uint64_t)u_prop * (uint64_t)q1) >> 32);
-            if (k_new > q1) k_new -= q1 + 1u;
-            if (q < 4) Sn.x |= k_new << sh8;
-            else Sn.y |= k_new << sh8;
-        }
-    }
-    // byte-wise table index: (df + 1) * nn + (dn + nmax), with
-    // dn = #equal(new) - #equal(old) and df = [new = 0] - [old = 0]
-    const uint32_t ones = 0x01010101u;
-    uint32_t c_old_lo = 0, c_old_hi = 0, c_new_lo = 0, c_new_hi = 0;
-#pragma unroll
-    for (int d = 0; d < 2 * D; ++d) {
-        c_old_lo += eq_bytes(Nb[d].x, S.x);
-        c_old_hi += eq_bytes(Nb[d].y, S.y);
-        c_new_lo += eq_bytes(Nb[d].x, Sn.x);
-        c_new_hi += eq_bytes(Nb[d].y, Sn.y);
-    }
-    const uint32_t nn = (uint32_t)g.nn, nmax = (uint32_t)g.nmax;
-    const uint32_t idx_lo = (eq_bytes(Sn.x, 0u) + ones - eq_bytes(S.x, 0u)) * nn + (c_new_lo + nmax * ones - c_old_lo);
-    const uint32_t idx_hi = (eq_bytes(Sn.y, 0u) + ones - eq_bytes(S.y, 0u)) * nn + (c_new_hi + nmax * ones - c_old_hi);
-    uint32_t am = 0;   // bit q: site q accepted
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t iw = q < 4 ? idx_lo : idx_hi;
-        const TabEntry e = stab[(iw >> (8 * (q & 3))) & 0xFFu];
-        const uint32_t u_acc = SH == 2 ? word_of(u[q >> 2], q & 3) : word_of(u[q >> 1], 2 * (q & 1));
-        if (e.always || u_acc < e.thr) am |= 1u << q;
-    }
-    const uint32_t m_lo = spread4(am & 0xFu), m_hi = spread4(am >> 4);
-    const uint2 Sf = make_uint2(S.x ^ ((S.x ^ Sn.x) & m_lo), S.y ^ ((S.y ^ Sn.y) & m_hi));
-    *reinterpret_cast<uint2 *>(dst + (uint64_t)colour * g.plane + (uint64_t)r * half + 8 * k) = Sf;
-    if (colour == 0) *reinterpret_cast<uint2 *>(dst + g.plane + (uint64_t)r * half + 8 * k) = O;
-    if (colour == 1) {
-        // every bond has exactly one colour-1 end
-        uint32_t eq = 0;
-#pragma unroll
-        for (int d = 0; d < 2 * D; ++d) eq += eq_bytes(Nb[d].x, Sf.x) + eq_bytes(Nb[d].y, Sf.y);
-        acc.bond += byte_sum(eq);
-        const int z0 = byte_sum(eq_bytes(Sf.x, 0u) + eq_bytes(Sf.y, 0u) + eq_bytes(O.x, 0u) + eq_bytes(O.y, 0u));
-        acc.zero += z0;
-        acc.other += 16 - z0;
-        if (g.ref != nullptr) {
-            const uint2 R1 = *reinterpret_cast<const uint2 *>(g.ref + g.plane + (uint64_t)r * half + 8 * k);
-            const uint2 R0 = *reinterpret_cast<const uint2 *>(g.ref + (uint64_t)r * half + 8 * k);
-            acc.acf += byte_sum(eq_bytes(Sf.x, R1.x) + eq_bytes(Sf.y, R1.y) + eq_bytes(O.x, R0.x) +
-                                eq_bytes(O.y, R0.y));
-        }
-    }
-}
-
 // ---------------------------------------------------------------------
 // Software-pipelined solo form: each thread walks one 8-site chunk column
 // down the plane rows r = y + L*z (rs rows apart) with two chunks in
@@ -186,7 +81,7 @@ LAT_D void potts_chunk(const ViewP &g, const TabEntry *stab, int colour, unsigne
 // this chunk's step.  Colour 0 reads both planes of the old buffer and
 // writes plane 0 of the new one; colour 1 reads its own old labels from the
 // old buffer and the new colour-0 labels from the new one and writes plane
-// 1: no plane is copied.  Same chunks, draws and bits as potts_chunk.
+// 1: no plane is copied.  Same chunks and draws as the generic kernel.
 // ---------------------------------------------------------------------
 template <int D>
 struct PIn {
@@ -376,19 +271,98 @@ __global__ void __launch_bounds__(kThreads, 2) k_potts_pipe(Geom g, int off)
 }
 
 // Batched form: a persistent grid takes (lattice, item) pairs from an
-// atomic counter; an item is kItemChunks x kThreads chunks of one colour of
-// one lattice.  The descriptor and table are reloaded only when a CTA moves
-// to another lattice (items are ordered by lattice).
-constexpr int kItemChunks = 4;
+// atomic counter; an item is a band of plane rows x a segment of chunk
+// columns of one colour of one lattice (col_item_shape), each thread walking
+// its column down the band with two chunks in flight and the same no-copy
+// convention as the solo kernel.  The descriptor and table are reloaded only
+// when a CTA moves to another lattice (items are ordered by lattice).
+template <int SH, int D, int kColour, bool kRef>
+LAT_D void batch_potts_item(const ViewP &v, uint32_t rows, uint32_t key0, uint32_t key1, unsigned long long sweep,
+                            const TabEntry *stab, uint32_t item, uint32_t passes, AccP &acc)
+{
+    const ColItemShape sh = col_item_shape(v.half, rows, passes);
+    const uint32_t L = (uint32_t)v.L;
+    const uint32_t band = item / sh.nseg, seg = item - band * sh.nseg;
+    const uint32_t r_end = min(rows, band * sh.br + sh.br);
+    uint32_t k, r;
+    if (sh.cpr <= (uint32_t)kThreads) {
+        k = threadIdx.x % sh.cpr;
+        r = band * sh.br + threadIdx.x / sh.cpr;
+        if (threadIdx.x / sh.cpr >= sh.rsb) return;
+    } else {
+        k = seg * kThreads + threadIdx.x;
+        r = band * sh.br;
+        if (k >= sh.cpr) return;
+    }
+    if (r >= r_end) return;
+    const int8_t *old = (sweep & 1) ? v.s1 : v.s0;
+    int8_t *nw = (sweep & 1) ? v.s0 : v.s1;
+    const uint32_t plane = (uint32_t)v.plane;
+    const int8_t *pS = old + (size_t)kColour * plane;
+    const int8_t *pO = (kColour == 0 ? old : nw) + (size_t)(1 - kColour) * plane;
+    int8_t *dS = nw + (size_t)kColour * plane;
+    const int8_t *r1 = v.ref ? v.ref + plane : nullptr, *r0 = v.ref;
+    PhiloxPre pp;
+    philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), key0, key1);
+    const uint32_t nwr = v.half >> 2;
+    const uint32_t wprev = wrap_once(2 * k - 1 + nwr, nwr), wnext = wrap_once(2 * k + 2, nwr);
+    uint32_t y = r % L, z = r / L;
+    const uint32_t dy = sh.rsb % L, dz = sh.rsb / L;
+    auto step_row = [&](uint32_t &yy, uint32_t &zz) {
+        yy += dy;
+        zz += dz;
+        if (yy >= L) {
+            yy -= L;
+            ++zz;
+        }
+    };
+    constexpr int kCalls = 8 >> SH;
+    auto draws = [&](uint32_t rr, U4 (&u)[kCalls]) {
+        const uint32_t g0 = rr * v.G + ((8u * k) >> SH);
+#pragma unroll
+        for (int c = 0; c < kCalls; ++c) u[c] = philox_item(pp, g0 + (uint32_t)c, (uint32_t)kColour);
+    };
+    PIn<D> A, B;
+    U4 uA[kCalls], uB[kCalls];
+    potts_load<D, kColour>(pS, pO, v.half, L, r, y, z, k, wprev, wnext, A);
+    draws(r, uA);
+    for (;;) {
+        const uint32_t ra = r + sh.rsb;
+        uint32_t ya = y, za = z;
+        step_row(ya, za);
+        if (ra >= r_end) {
+            potts_step<SH, D, kColour, kRef>(v, stab, dS, r1, r0, r, y, z, k, A, uA, acc);
+            break;
+        }
+        potts_load<D, kColour>(pS, pO, v.half, L, ra, ya, za, k, wprev, wnext, B);
+        draws(ra, uB);
+        potts_step<SH, D, kColour, kRef>(v, stab, dS, r1, r0, r, y, z, k, A, uA, acc);
+        const uint32_t rb = ra + sh.rsb;
+        uint32_t yb = ya, zb = za;
+        step_row(yb, zb);
+        if (rb >= r_end) {
+            potts_step<SH, D, kColour, kRef>(v, stab, dS, r1, r0, ra, ya, za, k, B, uB, acc);
+            break;
+        }
+        potts_load<D, kColour>(pS, pO, v.half, L, rb, yb, zb, k, wprev, wnext, A);
+        draws(rb, uA);
+        potts_step<SH, D, kColour, kRef>(v, stab, dS, r1, r0, ra, ya, za, k, B, uB, acc);
+        r = rb;
+        y = yb;
+        z = zb;
+    }
+}
 
-__global__ void __launch_bounds__(kThreads, 3) k_batch_potts(const Geom *geoms, const uint2 *items, int n_items,
-                                                            unsigned *next_item, int colour)
+template <int kColour>
+__global__ void __launch_bounds__(kThreads, 2) k_batch_potts(const Geom *geoms, const uint2 *items, int n_items,
+                                                            unsigned *next_item, uint32_t passes)
 {
     __shared__ TabEntry stab[kMaxTab];
     __shared__ long long red[kThreads / 32];
     __shared__ Geom sg;
     __shared__ int cur;
     int loaded = -1;
+    dep_wait();   // the work counter, sweep numbers and labels of the step before
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(next_item, 1u);
         __syncthreads();
@@ -405,27 +379,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_batch_potts(const Geom *geoms, 
             __syncthreads();
         }
         // register copies: no aliasing with shared-memory stores
-        const ViewP g = viewp(sg);
+        const ViewP v = viewp(sg);
         Ctrl *const ctrl = sg.ctrl;
+        const uint32_t rows = sg.rows, key0 = sg.key0, key1 = sg.key1;
         const int which = (sg.two_S == 1 ? 0 : 2) + (sg.dims == 3 ? 1 : 0);
-        const uint32_t rows = sg.rows;
         const unsigned long long sweep = ctrl->sweep;
-        PhiloxPre pp;
-        philox_prepare(pp, (uint32_t)sweep, (uint32_t)(sweep >> 32), sg.key0, sg.key1);
-        const uint32_t cpr = g.half >> 3;
-        const uint64_t total = (uint64_t)rows * cpr;
+        const bool ref = v.ref != nullptr;
         AccP acc;
-#pragma unroll 1
-        for (int c = 0; c < kItemChunks; ++c) {
-            const uint64_t t = ((uint64_t)w.y * kItemChunks + (uint64_t)c) * kThreads + threadIdx.x;
-            if (t >= total) break;
-            const uint32_t rr = (uint32_t)(t / cpr), kk = (uint32_t)(t % cpr);
-            if (which == 0) potts_chunk<2, 2>(g, stab, colour, sweep, pp, rr, kk, acc);
-            else if (which == 1) potts_chunk<2, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
-            else if (which == 2) potts_chunk<1, 2>(g, stab, colour, sweep, pp, rr, kk, acc);
-            else potts_chunk<1, 3>(g, stab, colour, sweep, pp, rr, kk, acc);
+        switch (which) {
+        case 0:
+            if (ref) batch_potts_item<2, 2, kColour, true>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            else batch_potts_item<2, 2, kColour, false>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            break;
+        case 1:
+            if (ref) batch_potts_item<2, 3, kColour, true>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            else batch_potts_item<2, 3, kColour, false>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            break;
+        case 2:
+            if (ref) batch_potts_item<1, 2, kColour, true>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            else batch_potts_item<1, 2, kColour, false>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            break;
+        default:
+            if (ref) batch_potts_item<1, 3, kColour, true>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
+            else batch_potts_item<1, 3, kColour, false>(v, rows, key0, key1, sweep, stab, w.y, passes, acc);
         }
-        if (colour == 1) {
+        if constexpr (kColour == 1) {
             unsigned long long *slot = series_slot(ctrl, sweep);
             long long s;
             s = block_sum_ll((long long)acc.bond, red);
@@ -434,22 +412,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_batch_potts(const Geom *geoms, 
             if (threadIdx.x == 0) add_counter(slot + 1, s);
             s = block_sum_ll((long long)acc.other, red);
             if (threadIdx.x == 0) add_counter(slot + 2, s);
-            if (g.ref != nullptr) {
+            if (ref) {
                 s = block_sum_ll((long long)acc.acf, red);
                 if (threadIdx.x == 0) add_counter(acf_slot(ctrl, sweep), s);
             }
         }
         __syncthreads();
     }
+    dep_launch();   // no items left: the next kernel may be scheduled
 }
 
 }  // namespace
 
-int potts_items(const Geom &g)
+int potts_items(const Geom &g, int passes)
 {
-    const uint64_t chunks = (uint64_t)g.rows * (g.half >> 3);
-    const uint64_t per = (uint64_t)kItemChunks * kThreads;
-    return (int)((chunks + per - 1) / per);
+    const ColItemShape sh = col_item_shape(g.half, g.rows, (uint32_t)passes);
+    return (int)(((g.rows + sh.br - 1u) / sh.br) * sh.nseg);
 }
 
 int batch_potts_grid()
@@ -457,16 +435,17 @@ int batch_potts_grid()
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_potts, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_potts<1>, kThreads, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
 
 cudaError_t launch_batch_potts(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                               int colour, int grid, cudaStream_t st)
+                               int colour, int passes, int grid, cudaStream_t st)
 {
-    k_batch_potts<<<grid, kThreads, 0, st>>>(geoms, items, n_items, next_item, colour);
-    return cudaGetLastError();
+    using K = void (*)(const Geom *, const uint2 *, int, unsigned *, uint32_t);
+    const K kern = colour ? k_batch_potts<1> : k_batch_potts<0>;
+    return launch_pdl(kern, (unsigned)grid, kThreads, st, geoms, items, n_items, next_item, (uint32_t)passes);
 }
 
 bool potts_supported(const Geom &g)

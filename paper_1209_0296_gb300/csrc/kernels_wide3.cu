@@ -459,29 +459,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_wide3_pipe(Geom g, int off)
 // lattice (items are ordered by lattice).  kSwar: the list of lattices that
 // take the byte-parallel step (spin-1/2 and spin-1 with strict tables).
 // ---------------------------------------------------------------------
-struct W3ItemShape {
-    uint32_t cpr, nseg, rsb, br;   // chunks per row, column segments, rows per pass, rows per band
-};
-
-// passes: rows a thread visits per item, given by the batch (its tuner), or
-// 0 for the default: 8 on large lattices (long pipelines, few items), 2 on
-// small ones (enough items to spread a batch of small lattices).
-LAT_HD W3ItemShape w3_item_shape(uint32_t half, uint32_t rows, uint32_t passes)
-{
-    W3ItemShape sh;
-    sh.cpr = half >> 3;
-    sh.nseg = (sh.cpr + kThreads - 1u) / kThreads;
-    sh.rsb = sh.cpr <= (uint32_t)kThreads ? (uint32_t)kThreads / sh.cpr : 1u;
-    if (passes == 0u) passes = (uint64_t)rows * sh.cpr >= 65536u ? 8u : 2u;
-    sh.br = passes * sh.rsb;
-    return sh;
-}
-
 template <int SH, int TS, int D, int kColour, bool kRef, bool kSwar>
 LAT_D void batch_w3_item(const View3 &v, uint32_t key0, uint32_t key1, unsigned long long sweep,
                          const TabEntry *stab, const uint32_t *st4, uint32_t item, uint32_t passes, Acc3 &acc)
 {
-    const W3ItemShape sh = w3_item_shape(v.half, v.rows, passes);
+    const ColItemShape sh = col_item_shape(v.half, v.rows, passes);
     const uint32_t L = (uint32_t)v.L;
     const int dims = D ? D : v.dims;
     const uint32_t band = item / sh.nseg, seg = item - band * sh.nseg;
@@ -648,23 +630,25 @@ bool wide3_swar(const Geom &g)
     return g.tab_strict && (g.two_S == 1 || g.two_S == 2) && (g.dims == 3 || g.two_S == 2);
 }
 
-// Rows per thread for the 3D / spin-S items of a batch phase whose lattices
-// hold chunk_rows (row, chunk column) pairs in all: at least 4 items per CTA
-// of one wave (2 CTAs on 152 SMs), 2 to 32 rows.  Long items pay their
-// set-up (Philox keys, counter reduction) once per many chunks; enough
-// items keep the SMs level.  (16 lattices of 256^3: 32 rows, 476 upd/ns,
-// against 432 at 8 rows and 464 at 16.)
-int wide3_batch_passes(uint64_t chunk_rows)
+// Rows per thread for the 3D / spin-S (or Potts) items of a batch phase
+// whose lattices of that kind hold chunk_rows (row, chunk column) pairs in
+// all: 4 to 32 rows, as many as leave at least 4 items per CTA of one wave
+// (2 CTAs on 152 SMs).  Long items pay their set-up (Philox keys, counter
+// reduction) once per many chunks and keep two chunks in flight for
+// longer; enough items keep the SMs level.  (16 lattices of 256^3: 32
+// rows, 476 upd/ns, against 432 at 8 rows and 464 at 16; 16 Potts
+// lattices of 1024^2: 4 rows, 264 upd/ns, against 226 at 2 and 257 at 8.)
+int batch_item_passes(uint64_t chunk_rows)
 {
     const uint64_t per = chunk_rows / ((uint64_t)kThreads * 4u * 2u * 152u);
-    int p = 2;
+    int p = 4;
     while (p < 32 && (uint64_t)(2 * p) <= per) p *= 2;
     return p;
 }
 
 int wide3_items(const Geom &g, int passes)
 {
-    const W3ItemShape sh = w3_item_shape(g.half, g.rows, (uint32_t)passes);
+    const ColItemShape sh = col_item_shape(g.half, g.rows, (uint32_t)passes);
     return (int)(((g.rows + sh.br - 1u) / sh.br) * sh.nseg);
 }
 

@@ -142,6 +142,27 @@ struct Ctrl {
     unsigned long long *fld;         // [series_cap] sum_i eta_i s_i (per-site field signs), same indexing
 };
 
+// Work items of the batched 8-site-chunk kernels (3D / spin-S, Potts): a
+// band of plane rows x a segment of up to 256 chunk columns of one colour of
+// one lattice.  A CTA of 256 threads covers rsb rows per pass (cpr chunks
+// each) and `passes` passes per item, so an item is br = passes * rsb rows.
+struct ColItemShape {
+    uint32_t cpr, nseg, rsb, br;   // chunks per row, column segments, rows per pass, rows per band
+};
+
+// passes: rows a thread visits per item (batch_item_passes), or 0 for 8 on
+// lattices of at least 2^16 chunks and 2 below.
+LAT_HD ColItemShape col_item_shape(uint32_t half, uint32_t rows, uint32_t passes)
+{
+    ColItemShape sh;
+    sh.cpr = half >> 3;
+    sh.nseg = (sh.cpr + 255u) / 256u;
+    sh.rsb = sh.cpr <= 256u ? 256u / sh.cpr : 1u;
+    if (passes == 0u) passes = (uint64_t)rows * sh.cpr >= 65536u ? 8u : 2u;
+    sh.br = passes * sh.rsb;
+    return sh;
+}
+
 #if defined(__CUDACC__)
 // Programmatic dependent launch.  The sweep kernels are launched so that the
 // next kernel on the stream may be scheduled while this one drains.  Each
@@ -363,18 +384,20 @@ bool wide3_supported(const Geom &g);
 // q-state Potts model, 8 sites per thread (kernels_potts.cu)
 bool potts_supported(const Geom &g);
 cudaError_t launch_sweep_potts(const Geom &g, int off, cudaStream_t st);
-int potts_items(const Geom &g);   // batch items of one colour of one lattice
+// batch items of one colour of one lattice; passes: rows a thread visits per item
+int potts_items(const Geom &g, int passes);
 int batch_potts_grid();
 cudaError_t launch_batch_potts(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
-                               int colour, int grid, cudaStream_t st);
+                               int colour, int passes, int grid, cudaStream_t st);
 cudaError_t launch_sweep_wide3(const Geom &g, int off, cudaStream_t st);
 // the byte-parallel step applies (spin-1/2 or spin-1, strict table)
 bool wide3_swar(const Geom &g);
 // batch items of one colour of one lattice; passes: rows a thread visits
 // per item (0: the size-based default)
 int wide3_items(const Geom &g, int passes);
-// rows per thread of the 3D / spin-S items of a phase with chunk_rows (row, chunk) pairs
-int wide3_batch_passes(uint64_t chunk_rows);
+// rows per thread of the 3D / spin-S or Potts items of a phase with
+// chunk_rows (row, chunk) pairs of that kind
+int batch_item_passes(uint64_t chunk_rows);
 int batch_wide3_grid(bool swar);
 cudaError_t launch_batch_wide3(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item,
                                int colour, bool swar, int passes, int grid, cudaStream_t st);

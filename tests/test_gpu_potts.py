@@ -140,6 +140,42 @@ def test_potts_batch_mixed_paths_and_overlaps():
         g.close()
 
 
+@pytest.mark.slow
+def test_potts_batch_bands_of_several_rows():
+    # eight 2D L = 2048 lattices (and a 3D one) in one batch: enough Potts
+    # work that items span several rows per thread (more than one band per
+    # lattice, a partial last one on the 3D lattice), q = 2..5, references
+    # on some, uneven sweep counts
+    cfg = [(2, 2048, 2 + i % 4, 0.8 + 0.05 * i, 50 + i, 1 + i % 2, i % 3 == 0) for i in range(8)]
+    cfg.append((3, 48, 3, 1.3, 60, 3, True))
+    lats, ors = [], []
+    for dims, L, q, T, seed, n, ref in cfg:
+        g = lt.Lattice(dims, L, q - 1, lt.POTTS, 1.0, 0.05, T, seed=seed, init=lt.INIT_RANDOM)
+        o = oracle.Lattice(dims, L, q - 1, oracle.POTTS, 1.0, 0.05, T, seed=seed, init=oracle.INIT_RANDOM)
+        if ref:
+            g.set_reference()
+            o.set_reference()
+        lats.append(g)
+        ors.append(o)
+    b = lt.Batch()
+    for g, c in zip(lats, cfg):
+        b.add(g, c[5])
+    b.run()
+    b.synchronize()
+    for g, o, c in zip(lats, ors, cfg):
+        n = c[5]
+        ser_o = o.sweep(n)
+        assert np.array_equal(g.get_spins(), o.spins), c
+        ser = g.series(0, n)
+        for k in ("bond", "mag", "up"):
+            assert np.array_equal(ser[k], ser_o[k]), (c, k)
+        if c[6]:
+            assert np.array_equal(g.autocorrelation(0, n)[0], ser_o["overlap"]), c
+    b.close()
+    for g in lats:
+        g.close()
+
+
 def test_potts_labels_and_refusals():
     g = lt.Lattice(2, 16, 2, lt.POTTS, 1.0, 0.0, 1.0, seed=1, init=lt.INIT_RANDOM)
     labels = np.random.default_rng(0).integers(0, 3, 256).astype(np.int8)
