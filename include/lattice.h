@@ -348,9 +348,8 @@ int lattice_batch_synchronize(lattice_batch_t *b);
  * thread visits per item of the pipelined 2D spin-1/2 kernel
  * (*rows_per_item; 0 = the size-based default, 8 rows on lattices with
  * L >= 1024 and 2 below; the 3D / spin-S and Potts items size themselves
- * to the phase's work of their kind, 4 to 32 rows) and the steps
- * per captured
- * CUDA graph (*steps_per_graph).  A run whose first phase (all its
+ * to the phase's work of their kind, 4 to 32 rows) and the steps per
+ * captured CUDA graph (*steps_per_graph).  A run whose first phase (all its
  * lattices) has at least 192 steps tunes both once per composition of
  * lattices (models, dimensions, spins, sizes and kernels), timing
  * candidates on its own steps (same bits whichever runs) and synchronising
