@@ -565,7 +565,11 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe(Geom g, int o
 // ---------------------------------------------------------------------
 constexpr int kNeSlots = 4 * 32;   // list entries per warp (4 groups per lane)
 
-template <int kColour, bool kRef>
+// kCMode: the c-mode rates of §III.B depend on the move alone, not on the
+// neighbour sum (every neighbour-count entry of a row of the table is the
+// same), so the index skips the neighbour-count bits (colour 0 then needs no
+// neighbour adder at all; colour 1 keeps it for the bond count).
+template <int kColour, bool kRef, bool kCMode = false>
 LAT_D void ne_col_step(bool act, const ColWalk<kColour> &c, const uint8_t *fl_c, const uint8_t *fl_o,
                        const uint32_t *sthr, uint32_t y, const WideIn &in, const PhiloxPre &pp,
                        uint32_t *gtab, uint4 *dq, Counts &cnt)
@@ -596,8 +600,9 @@ LAT_D void ne_col_step(bool act, const ColWalk<kColour> &c, const uint8_t *fl_c,
         // down: bit 6 of U | R set) indexes entries 16..31 of the table, all
         // t' = all ones, so it needs no draw; its flip is masked off below.
         locked[w] = Uw | R[w];
-        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
-                             (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u);
+        const uint32_t idx = kCMode ? (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u)
+                                    : (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
+                                          (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u);
         t[w][0] = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
         t[w][1] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
         t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
@@ -672,7 +677,7 @@ LAT_D void ne_col_step(bool act, const ColWalk<kColour> &c, const uint8_t *fl_c,
     }
 }
 
-template <int kColour, bool kRef>
+template <int kColour, bool kRef, bool kCMode = false>
 __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe_ne(Geom g, int off)
 {
     __shared__ uint32_t sthr[32];   // entries 16..31: locked sites, always accepted (then masked)
@@ -710,12 +715,12 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_wide_pipe_ne(Geom g, in
         const uint32_t y1 = y + rs;
         const bool act1 = act && y1 < L;
         if (act1) col_load<kColour>(c, y1, B);
-        ne_col_step<kColour, kRef>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab[warp], dq[warp], cnt);
+        ne_col_step<kColour, kRef, kCMode>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab[warp], dq[warp], cnt);
         if (!__any_sync(0xffffffffu, act1)) break;
         const uint32_t y2 = y1 + rs;
         const bool act2 = act1 && y2 < L;
         if (act2) col_load<kColour>(c, y2, A);
-        ne_col_step<kColour, kRef>(act1, c, fl_c, fl_o, sthr, y1, B, pp, gtab[warp], dq[warp], cnt);
+        ne_col_step<kColour, kRef, kCMode>(act1, c, fl_c, fl_o, sthr, y1, B, pp, gtab[warp], dq[warp], cnt);
         y = y2;
         act = act2;
     }
@@ -985,7 +990,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe(Geom g, int of
 // North-East at any even L: the step of ne_col_step with any-alignment
 // loads and stores, per-byte persistence updates (the groups of a row need
 // not start on a word), and the warp-compacted draws.
-template <int kColour, bool kRef, bool kAligned = false>
+template <int kColour, bool kRef, bool kAligned = false, bool kCMode = false>
 LAT_D void any_ne_step(bool act, const AnyWalk<kColour> &c, uint8_t *fl_c, const uint8_t *fl_o,
                        const uint32_t *sthr, uint32_t y, const AnyIn &in, const PhiloxPre &pp, uint32_t *gtab,
                        uint4 *dq, Counts &cnt)
@@ -1008,8 +1013,9 @@ LAT_D void any_ne_step(bool act, const AnyWalk<kColour> &c, uint8_t *fl_c, const
         // §III.B: a locked site (north or east down) indexes the all-accept
         // entries 16..31; so do the bytes past the row (masked below)
         locked[w] = Uw | R[w] | ~c.vm[w];
-        const uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
-                             (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u);
+        const uint32_t idx = kCMode ? (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u)
+                                    : (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) |
+                                          (in.S[w] & 0x20202020u) | (locked[w] & 0x40404040u);
         t[w][0] = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
         t[w][1] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
         t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
@@ -1092,7 +1098,7 @@ LAT_D void any_ne_step(bool act, const AnyWalk<kColour> &c, uint8_t *fl_c, const
     }
 }
 
-template <int kColour, bool kRef>
+template <int kColour, bool kRef, bool kCMode = false>
 __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe_ne(Geom g, int off)
 {
     __shared__ uint32_t sthr[32];   // entries 16..31: locked sites, always accepted (then masked)
@@ -1127,12 +1133,12 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_any_pipe_ne(Geom g, int
         const uint32_t y1 = y + rs;
         const bool act1 = act && y1 < L;
         if (act1) any_load<kColour>(c, y1, B);
-        any_ne_step<kColour, kRef>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab[warp], dq[warp], cnt);
+        any_ne_step<kColour, kRef, false, kCMode>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab[warp], dq[warp], cnt);
         if (!__any_sync(0xffffffffu, act1)) break;
         const uint32_t y2 = y1 + rs;
         const bool act2 = act1 && y2 < L;
         if (act2) any_load<kColour>(c, y2, A);
-        any_ne_step<kColour, kRef>(act1, c, fl_c, fl_o, sthr, y1, B, pp, gtab[warp], dq[warp], cnt);
+        any_ne_step<kColour, kRef, false, kCMode>(act1, c, fl_c, fl_o, sthr, y1, B, pp, gtab[warp], dq[warp], cnt);
         y = y2;
         act = act2;
     }
@@ -1486,10 +1492,14 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
             wave(reinterpret_cast<const void *>(k_any_pipe_ne<1, true>), res_any));
         using KG = void (*)(Geom, int);
         const bool ne = g.model == LAT_NE, ref = k.ref != nullptr;
-        const KG c0 = ne ? (ref ? k_any_pipe_ne<0, true> : k_any_pipe_ne<0, false>)
-                         : (ref ? k_any_pipe<0, true> : k_any_pipe<0, false>);
-        const KG c1 = ne ? (ref ? k_any_pipe_ne<1, true> : k_any_pipe_ne<1, false>)
-                         : (ref ? k_any_pipe<1, true> : k_any_pipe<1, false>);
+        // North-East: [c-mode][reference][colour]
+        static const KG kne[2][2][2] = {
+            {{k_any_pipe_ne<0, false>, k_any_pipe_ne<1, false>}, {k_any_pipe_ne<0, true>, k_any_pipe_ne<1, true>}},
+            {{k_any_pipe_ne<0, false, true>, k_any_pipe_ne<1, false, true>},
+             {k_any_pipe_ne<0, true, true>, k_any_pipe_ne<1, true, true>}}};
+        const int cm = g.cmode ? 1 : 0;
+        const KG c0 = ne ? kne[cm][ref][0] : (ref ? k_any_pipe<0, true> : k_any_pipe<0, false>);
+        const KG c1 = ne ? kne[cm][ref][1] : (ref ? k_any_pipe<1, true> : k_any_pipe<1, false>);
         if (ne) {   // plain launches: early-scheduled dependents measured 2% slower here
             c0<<<gb, kThreads, 0, st>>>(k, off);
             c1<<<gb, kThreads, 0, st>>>(k, off);
@@ -1504,10 +1514,13 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
             wide_chunks(g), wave(reinterpret_cast<const void *>(k_wide_pipe_ne<1, true>), res_ne));
         // plain launches: early-scheduled dependents measured no faster here
         using KG = void (*)(Geom, int);
-        const KG c0 = k.ref != nullptr ? k_wide_pipe_ne<0, true> : k_wide_pipe_ne<0, false>;
-        const KG c1 = k.ref != nullptr ? k_wide_pipe_ne<1, true> : k_wide_pipe_ne<1, false>;
-        c0<<<pb, kThreads, 0, st>>>(k, off);
-        c1<<<pb, kThreads, 0, st>>>(k, off);
+        static const KG kne[2][2][2] = {
+            {{k_wide_pipe_ne<0, false>, k_wide_pipe_ne<1, false>}, {k_wide_pipe_ne<0, true>, k_wide_pipe_ne<1, true>}},
+            {{k_wide_pipe_ne<0, false, true>, k_wide_pipe_ne<1, false, true>},
+             {k_wide_pipe_ne<0, true, true>, k_wide_pipe_ne<1, true, true>}}};
+        const int cm = g.cmode ? 1 : 0, ref = k.ref != nullptr ? 1 : 0;
+        kne[cm][ref][0]<<<pb, kThreads, 0, st>>>(k, off);
+        kne[cm][ref][1]<<<pb, kThreads, 0, st>>>(k, off);
         return cudaGetLastError();
     }
     // Ising, uniform or with per-bond couplings (and per-site field signs):
