@@ -76,20 +76,16 @@ LAT_D void store_words(int8_t *p, const uint32_t (&v)[W])
 }
 
 // Sweep colour `colour` of the chunk k (4W sites, W Philox groups) of plane
-// row y.  The two-launch kernel uses W = 4 (16 sites, one 16-byte load per
-// row); the resident kernel uses smaller W on small lattices, for more
-// threads with shorter dependency chains.  kInPlace: both buffers are the
-// same array (the resident kernel), so colour 0 does not copy the colour-1
-// sites.  kCpl: per-site disorder bytes (Eq. 1 couplings); kFld (with
-// kCpl): also per-site field signs, whose -h entries are table entries
-// 16..31, and the field sum sum_i eta_i s_i.
-template <bool kNE, bool kInPlace = false, int W = 4, bool kPre = false, bool kCpl = false, bool kFld = false>
+// row y of the resident kernel's shared-memory lattice, in place (both
+// buffer pointers of g are that array).  W = 4 is 16 sites per thread;
+// smaller W on small lattices gives more threads with shorter dependency
+// chains.  kPre: the chunk's draws come from the caller (upre).
+template <bool kNE, int W = 4, bool kPre = false>
 LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsigned long long sweep,
                       const PhiloxPre &pp, int y, int k, Counts &cnt, const U4 *upre = nullptr)
 {
-    const int8_t *src = (sweep & 1) ? g.s1 : g.s0;
-    int8_t *dst = (sweep & 1) ? g.s0 : g.s1;
-    if (colour == 1) src = dst;
+    const int8_t *src = g.s0;
+    int8_t *dst = g.s0;
     const int L = g.L;
     const uint32_t half = g.half;
     const int oc = 1 - colour;
@@ -107,18 +103,9 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         const uint32_t w = p1 ? (uint32_t)(W * k + W) : (uint32_t)(W * k - 1 + nwr);
         adj = reinterpret_cast<const uint32_t *>(row(oc, y))[wrap_once(w, nwr)];
     }
-    // Ising in the two-launch kernels: the draws do not depend on the loaded
-    // words, so they are made while the loads are in flight (a North-East
-    // item may skip them: its locked sites need none).
-    constexpr bool kEarly = !kNE && !kPre && !kInPlace;
     U4 u[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) u[w] = U4{0, 0, 0, 0};
-    if constexpr (kEarly) {
-        const uint32_t g0 = (uint32_t)y * g.G + (uint32_t)(W * k);
-#pragma unroll
-        for (int w = 0; w < W; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)colour);
-    }
     uint32_t Lf[W], R[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -128,20 +115,6 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         } else {    // x = 2j+1: west is j, east is j+1
             Lf[w] = O[w];
             R[w] = __funnelshift_r(O[w], w == W - 1 ? adj : O[w + 1], 8);
-        }
-    }
-    uint32_t C[W];   // disorder bytes of the colour-c sites (kCpl)
-    if constexpr (kCpl) {
-        // Eq. 1 couplings: a negative bond enters the energy as a flipped
-        // neighbour, so XOR 0xFE (+1 <-> -1) into that neighbour's byte
-        load_words<W>(reinterpret_cast<const int8_t *>(g.cpl) + (uint64_t)colour * g.plane + (uint64_t)y * half +
-                          4 * W * k, C);
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            Lf[w] ^= ((C[w] >> 0) & 0x01010101u) * 0xFEu;
-            R[w] ^= ((C[w] >> 1) & 0x01010101u) * 0xFEu;
-            U[w] ^= ((C[w] >> 2) & 0x01010101u) * 0xFEu;
-            D[w] ^= ((C[w] >> 3) & 0x01010101u) * 0xFEu;
         }
     }
     uint32_t t[W][4], locked[W];
@@ -156,7 +129,6 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         const uint32_t b2 = c1 & s1 & R[w];
         // byte offset into the 16-entry table (index sd<<3 | nd, 4 bytes each)
         uint32_t idx = (b0 & 0x04040404u) | (b1 & 0x08080808u) | (b2 & 0x10101010u) | (S[w] & 0x20202020u);
-        if constexpr (kFld) idx |= C[w] & 0x40404040u;   // eta_i = -1: the -h entries 16..31
         t[w][0] = *reinterpret_cast<const uint32_t *>(tb + (idx & 0xFFu));
         t[w][1] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 8) & 0xFFu));
         t[w][2] = *reinterpret_cast<const uint32_t *>(tb + ((idx >> 16) & 0xFFu));
@@ -178,7 +150,7 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
     if constexpr (kPre) {   // draws made by the caller (same groups, same counters)
 #pragma unroll
         for (int w = 0; w < W; ++w) u[w] = upre[w];
-    } else if (!kEarly && need) {
+    } else if (need) {
         const uint32_t g0 = (uint32_t)y * g.G + (uint32_t)(W * k);
 #pragma unroll
         for (int w = 0; w < W; ++w) u[w] = philox_item(pp, g0 + (uint32_t)w, (uint32_t)colour);
@@ -204,7 +176,6 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
         }
     }
     store_words<W>(dst + (uint64_t)colour * g.plane + (uint64_t)y * half + 4 * W * k, Sn);
-    if (colour == 0 && !kInPlace) store_words<W>(dst + (uint64_t)g.plane + (uint64_t)y * half + 4 * W * k, O);
     int unfl = 0;
     if constexpr (kNE) {
         // persistence bytes of the W groups (bit q = site 4m+q)
@@ -244,16 +215,6 @@ LAT_D void wide_chunk(const SweepView g, const uint32_t *sthr, int colour, unsig
             for (int w = 0; w < W; ++w) dr += ((Sn[w] ^ R1[w]) & M1) + ((O[w] ^ R0[w]) & M1);
             cnt.acf += 8 * W - byte_sum(dr);
         }
-    }
-    if constexpr (kFld) {
-        // field sum over this colour's 4W sites (final after this launch:
-        // each colour adds its own sites, so no launch reads the other
-        // plane's disorder bytes); eta_i s_i is down when exactly one of
-        // (s_i down: bit 1, eta_i = -1: bit 6) holds
-        uint32_t ed = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) ed += (Sn[w] ^ (C[w] >> 5)) & M1;
-        cnt.fld += 4 * W - byte_sum(ed);
     }
 }
 
@@ -316,8 +277,8 @@ LAT_D void flush_one(unsigned long long *dst, int v, int (*red)[5])
 // ---------------------------------------------------------------------
 // Software-pipelined two-launch Ising sweep, uniform or with per-bond
 // coupling signs (kCpl) and per-site field signs (kFld).  Same chunks,
-// draws, table and bits as wide_chunk<false>; the difference is the
-// schedule.  A chunk costs two kinds of work that load
+// draws, table and bits as the resident kernel's wide_chunk; the difference
+// is the schedule.  A chunk costs two kinds of work that load
 // different pipes: its four Philox4x32-10 calls (wide multiplies on the
 // FMA pipe) and the Metropolis step (logic on the ALU pipe).  Done one
 // after the other they keep one pipe idle while the other works, so each
@@ -1346,16 +1307,16 @@ LAT_D void resident_body(const Geom &g, int off, int n_sweeps, bool advance, uin
                     u0[w] = philox_item(pp, g0 + (uint32_t)w, 0u);
                     u1[w] = philox_item(pp, g0 + (uint32_t)w, 1u);
                 }
-                wide_chunk<kNE, true, W, true>(v, sthr, 0, sweep, pp, y1, k1, cnt, u0);
+                wide_chunk<kNE, W, true>(v, sthr, 0, sweep, pp, y1, k1, cnt, u0);
             }
             __syncthreads();
-            if (act) wide_chunk<kNE, true, W, true>(v, sthr, 1, sweep, pp, y1, k1, cnt, u1);
+            if (act) wide_chunk<kNE, W, true>(v, sthr, 1, sweep, pp, y1, k1, cnt, u1);
         } else {
             for (uint32_t t = threadIdx.x; t < total; t += blockDim.x)
-                wide_chunk<kNE, true, W>(v, sthr, 0, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+                wide_chunk<kNE, W>(v, sthr, 0, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
             __syncthreads();
             for (uint32_t t = threadIdx.x; t < total; t += blockDim.x)
-                wide_chunk<kNE, true, W>(v, sthr, 1, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
+                wide_chunk<kNE, W>(v, sthr, 1, sweep, pp, (int)(t / cpr), (int)(t % cpr), cnt);
         }
         flush_slot(slot0 + 4ull * (unsigned)s, acf0 ? acf0 + (unsigned)s : nullptr, cnt, kNE, red);  // ends with __syncthreads()
     }
