@@ -66,7 +66,9 @@ struct lattice_batch {
     // next item of: Ising tiles, NE tiles, generic colour 0 / 1, 3D/spin-S
     // per site colour 0 / 1, 2D Ising wide colour 0 / 1, 2D North-East wide
     // colour 0 / 1, Potts colour 0 / 1, any-L 2D Ising colour 0 / 1, any-L 2D
-    // North-East colour 0 / 1, 3D/spin-S byte-parallel colour 0 / 1
+    // North-East colour 0 / 1, 3D/spin-S byte-parallel colour 0 / 1, 2D
+    // c-mode North-East wide colour 0 / 1, any-L 2D c-mode North-East
+    // colour 0 / 1
     unsigned *d_counters = nullptr;
     int grid_tiled_ising = 0, grid_tiled_ne = 0, grid_generic = 0, grid_wide[2] = {0, 0}, grid_potts = 0;
     int grid_any[2] = {0, 0};     // 2D any-L, Ising / North-East
@@ -82,7 +84,7 @@ namespace {
 constexpr int kChunk = 256;       // Philox groups per generic item (one CTA)
 constexpr int kGraphSteps = 32;   // steps per captured graph
 constexpr int kGraphMinSteps = 128;
-constexpr int kCounters = 18;
+constexpr int kCounters = 22;
 constexpr int kResidentMaxL = 128;      // AUTO lattices up to this size run resident
 constexpr int kResidentChunk = 1 << 16; // sweeps per resident launch
 
@@ -147,7 +149,8 @@ int take_slot(lattice_batch *b, BatchSlot **out)
 // and of North-East lattices, any-L 2D items of Ising and of North-East
 // lattices, 3D / spin-S wide items, Potts items, generic chunks.
 struct Shape {
-    int n_lat, n_ising, n_ne, n_w2[2], n_grp[2], n_wide[2], n_potts, n_gen;
+    // n_w2 / n_grp: Ising, North-East at temperature T, North-East in c-mode
+    int n_lat, n_ising, n_ne, n_w2[3], n_grp[3], n_wide[2], n_potts, n_gen;
     int passes3, passes_p;   // rows a thread visits per 3D / spin-S item and per Potts item
     int tab_gen;   // largest table among the generic lattices
 };
@@ -183,16 +186,18 @@ int enqueue_steps(lattice_batch *b, const Phase &ph, int steps, cudaStream_t st)
             e = launch_batch_tiled(ph.geoms, ph.items + sh.n_ising, sh.n_ne, b->d_counters + 1, 0, 0,
                                    std::min(b->grid_tiled_ne, sh.n_ne), true, st);
         const uint2 *w2 = ph.items + sh.n_ising + sh.n_ne;
-        for (int m = 0; m < 2; ++m) {   // L % 32 == 0: Ising, then North-East: colour 0, then colour 1
+        // Ising, North-East at T, North-East in c-mode: colour 0, then colour 1
+        static const int kCtrW2[3] = {6, 8, 18}, kCtrGrp[3] = {12, 14, 20};
+        for (int m = 0; m < 3; ++m) {   // L % 32 == 0
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_w2[m] > 0; ++colour)
-                e = launch_batch_any(ph.geoms, w2, sh.n_w2[m], b->d_counters + 6 + 2 * m + colour, colour,
-                                     m == 1, true, ph.passes, std::min(b->grid_any[m], sh.n_w2[m]), st);
+                e = launch_batch_any(ph.geoms, w2, sh.n_w2[m], b->d_counters + kCtrW2[m] + colour, colour, m >= 1,
+                                     m == 2, true, ph.passes, std::min(b->grid_any[m ? 1 : 0], sh.n_w2[m]), st);
             w2 += sh.n_w2[m];
         }
-        for (int m = 0; m < 2; ++m) {   // other even L: Ising, then North-East
+        for (int m = 0; m < 3; ++m) {   // other even L
             for (int colour = 0; colour < 2 && e == cudaSuccess && sh.n_grp[m] > 0; ++colour)
-                e = launch_batch_any(ph.geoms, w2, sh.n_grp[m], b->d_counters + 12 + 2 * m + colour, colour,
-                                     m == 1, false, ph.passes, std::min(b->grid_any[m], sh.n_grp[m]), st);
+                e = launch_batch_any(ph.geoms, w2, sh.n_grp[m], b->d_counters + kCtrGrp[m] + colour, colour, m >= 1,
+                                     m == 2, false, ph.passes, std::min(b->grid_any[m ? 1 : 0], sh.n_grp[m]), st);
             w2 += sh.n_grp[m];
         }
         const uint2 *wide = w2;
@@ -311,7 +316,7 @@ int run_resident(lattice_batch *b, BatchSlot &sl, const std::vector<std::pair<la
 Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t n_active, int passes,
                   std::vector<Geom> &geoms, std::vector<Ctrl *> &ctrls, std::vector<uint2> &items)
 {
-    std::vector<uint2> tiled, tiled_ne, w2[2], grp[2], wide[2], potts, gen;
+    std::vector<uint2> tiled, tiled_ne, w2[3], grp[3], wide[2], potts, gen;
     int tab_gen = 0;
     // 3D / spin-S and Potts items: the rows per item follow the phase's whole
     // work of that kind (a few items per CTA), not the 2D tunable
@@ -345,7 +350,8 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
             for (int k = 0; k < nt; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && any_supported(lt->geom)) {
             const int ng = any_items(lt->geom, passes);
-            auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[lt->P.model == LAT_NE ? 1 : 0];
+            const int m = lt->P.model == LAT_NE ? (lt->geom.cmode ? 2 : 1) : 0;
+            auto &dst = (lt->geom.L % 32 == 0 ? w2 : grp)[m];
             for (int k = 0; k < ng; ++k) dst.push_back(make_uint2((unsigned)i, (unsigned)k));
         } else if (!generic && wide3_supported(lt->geom)) {
             const int nw = wide3_items(lt->geom, passes3);
@@ -361,10 +367,12 @@ Shape build_phase(const std::vector<std::pair<lattice *, int64_t>> &work, size_t
             tab_gen = std::max(tab_gen, lt->geom.tab_n);
         }
     }
-    for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &grp[0], &grp[1], &wide[0], &wide[1], &potts, &gen})
+    for (auto *v : {&tiled, &tiled_ne, &w2[0], &w2[1], &w2[2], &grp[0], &grp[1], &grp[2], &wide[0], &wide[1], &potts,
+                    &gen})
         items.insert(items.end(), v->begin(), v->end());
-    return Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(), {(int)w2[0].size(), (int)w2[1].size()},
-                 {(int)grp[0].size(), (int)grp[1].size()}, {(int)wide[0].size(), (int)wide[1].size()},
+    return Shape{(int)n_active, (int)tiled.size(), (int)tiled_ne.size(),
+                 {(int)w2[0].size(), (int)w2[1].size(), (int)w2[2].size()},
+                 {(int)grp[0].size(), (int)grp[1].size(), (int)grp[2].size()}, {(int)wide[0].size(), (int)wide[1].size()},
                  (int)potts.size(), (int)gen.size(), passes3, passes_p,
                  tab_gen};
 }

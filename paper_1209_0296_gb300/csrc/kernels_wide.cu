@@ -1131,7 +1131,7 @@ LAT_HD AnyItemShape any_item_shape(uint32_t half, uint32_t passes)
     return sh;
 }
 
-template <int kColour, bool kNE, bool kAligned>
+template <int kColour, bool kNE, bool kAligned, bool kCMode>
 LAT_D void batch_any_item(const SweepView &v, const uint32_t *sthr, uint32_t item, uint32_t passes, uint32_t *gtab,
                           uint4 *dq, Counts &cnt)
 {
@@ -1196,21 +1196,23 @@ LAT_D void batch_any_item(const SweepView &v, const uint32_t *sthr, uint32_t ite
             const uint32_t ya = y + sh.rsb;
             const bool act1 = act && ya < y1;
             if (act1) any_load<kColour, kAligned>(c, ya, B);
-            if (v.ref) any_ne_step<kColour, true, kAligned>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab, dq, cnt);
-            else any_ne_step<kColour, false, kAligned>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab, dq, cnt);
+            if (v.ref) any_ne_step<kColour, true, kAligned, kCMode>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab, dq, cnt);
+            else any_ne_step<kColour, false, kAligned, kCMode>(act, c, fl_c, fl_o, sthr, y, A, pp, gtab, dq, cnt);
             if (!__any_sync(0xffffffffu, act1)) break;
             const uint32_t yb = ya + sh.rsb;
             const bool act2 = act1 && yb < y1;
             if (act2) any_load<kColour, kAligned>(c, yb, A);
-            if (v.ref) any_ne_step<kColour, true, kAligned>(act1, c, fl_c, fl_o, sthr, ya, B, pp, gtab, dq, cnt);
-            else any_ne_step<kColour, false, kAligned>(act1, c, fl_c, fl_o, sthr, ya, B, pp, gtab, dq, cnt);
+            if (v.ref) any_ne_step<kColour, true, kAligned, kCMode>(act1, c, fl_c, fl_o, sthr, ya, B, pp, gtab, dq, cnt);
+            else any_ne_step<kColour, false, kAligned, kCMode>(act1, c, fl_c, fl_o, sthr, ya, B, pp, gtab, dq, cnt);
             y = yb;
             act = act2;
         }
     }
 }
 
-template <bool kNE, bool kAligned, int kColour>
+// kCMode: a list of c-mode North-East lattices (their steps skip the
+// neighbour-count bits of the table index).
+template <bool kNE, bool kAligned, int kColour, bool kCMode = false>
 __global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *geoms, const uint2 *items, int n_items,
                                                                   unsigned *next_item, uint32_t passes)
 {
@@ -1240,7 +1242,7 @@ __global__ void __launch_bounds__(kThreads, kPipeMinB) k_batch_any(const Geom *g
         }
         const SweepView v = sweep_view(sg);
         Counts cnt;
-        batch_any_item<kColour, kNE, kAligned>(v, sthr, w.y, passes, gtab[warp], dq[warp], cnt);
+        batch_any_item<kColour, kNE, kAligned, kCMode>(v, sthr, w.y, passes, gtab[warp], dq[warp], cnt);
         if constexpr (kColour == 1) flush(v, v.ctrl->sweep, cnt, kNE, red);   // ends with __syncthreads()
         __syncthreads();
     }
@@ -1418,16 +1420,20 @@ int batch_any_grid(bool ne)
 }
 
 cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                             bool ne, bool aligned, int passes, int grid, cudaStream_t st)
+                             bool ne, bool cmode, bool aligned, int passes, int grid, cudaStream_t st)
 {
     using K = void (*)(const Geom *, const uint2 *, int, unsigned *, uint32_t);
-    static const K kern[2][2][2] = {
+    // [Ising, North-East at T, North-East in c-mode][aligned][colour]
+    static const K kern[3][2][2] = {
         {{k_batch_any<false, false, 0>, k_batch_any<false, false, 1>},
          {k_batch_any<false, true, 0>, k_batch_any<false, true, 1>}},
         {{k_batch_any<true, false, 0>, k_batch_any<true, false, 1>},
-         {k_batch_any<true, true, 0>, k_batch_any<true, true, 1>}}};
-    return launch_pdl(kern[ne ? 1 : 0][aligned ? 1 : 0][colour ? 1 : 0], (unsigned)grid, kThreads, st, geoms, items,
-                      n_items, next_item, (uint32_t)passes);
+         {k_batch_any<true, true, 0>, k_batch_any<true, true, 1>}},
+        {{k_batch_any<true, false, 0, true>, k_batch_any<true, false, 1, true>},
+         {k_batch_any<true, true, 0, true>, k_batch_any<true, true, 1, true>}}};
+    const int m = ne ? (cmode ? 2 : 1) : 0;
+    return launch_pdl(kern[m][aligned ? 1 : 0][colour ? 1 : 0], (unsigned)grid, kThreads, st, geoms, items, n_items,
+                      next_item, (uint32_t)passes);
 }
 
 cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t st)

@@ -410,9 +410,10 @@ bool any_supported(const Geom &g);
 // per item (0: the size-based default)
 int any_items(const Geom &g, int passes);
 int batch_any_grid(bool ne);
-// aligned: every lattice of the items has L % 32 == 0 (16-byte aligned rows)
+// aligned: every lattice of the items has L % 32 == 0 (16-byte aligned
+// rows); cmode (with ne): every lattice of the items is a c-mode North-East one
 cudaError_t launch_batch_any(const Geom *geoms, const uint2 *items, int n_items, unsigned *next_item, int colour,
-                             bool ne, bool aligned, int passes, int grid, cudaStream_t st);
+                             bool ne, bool cmode, bool aligned, int passes, int grid, cudaStream_t st);
 // batched engine
 Geom tiled_geom(const Geom &g);
 int tiles_of(const Geom &g, int tile_h);
