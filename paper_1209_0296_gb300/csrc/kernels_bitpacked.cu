@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bits_pipe(Geom g, int off)
     __shared__ long long red[kThreads / 32];
     if (threadIdx.x < 16) sthr[threadIdx.x] = g.thr16[threadIdx.x];
     __syncthreads();
+    dep_wait();
     constexpr int oc = 1 - kColour;
     const unsigned long long sweep = g.ctrl->sweep + (unsigned long long)off;
     const uint32_t *old = g.bits[sweep & 1];
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bits_pipe(Geom g, int off)
             y = y2;
         }
     }
+    dep_launch();   // main work done: the next kernel may be scheduled
     if (kColour == 1) {
         unsigned long long *slot = series_slot(g.ctrl, sweep);
         long long v;
@@ -247,11 +249,8 @@ cudaError_t launch_sweep_bitpacked(const Geom &g, int off, cudaStream_t st)
     }
     const uint64_t words = (uint64_t)g.L * g.bw;
     const unsigned blocks = (unsigned)std::min<uint64_t>((words + kThreads - 1) / kThreads, (uint64_t)w);
-    // plain launches: early-scheduled dependents (programmatic dependent
-    // launch, as the int8 kernels use) measured 2% slower here
-    c0<<<blocks, kThreads, 0, st>>>(k, off);
-    c1<<<blocks, kThreads, 0, st>>>(k, off);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(c0, blocks, kThreads, st, k, off);
+    return e == cudaSuccess ? launch_pdl(c1, blocks, kThreads, st, k, off) : e;
 }
 
 bool bitpacked_supported(const Geom &g)

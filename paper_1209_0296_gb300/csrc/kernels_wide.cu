@@ -1467,11 +1467,6 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
         const int cm = g.cmode ? 1 : 0;
         const KG c0 = ne ? kne[cm][ref][0] : (ref ? k_any_pipe<0, true> : k_any_pipe<0, false>);
         const KG c1 = ne ? kne[cm][ref][1] : (ref ? k_any_pipe<1, true> : k_any_pipe<1, false>);
-        if (ne) {   // plain launches: early-scheduled dependents measured 2% slower here
-            c0<<<gb, kThreads, 0, st>>>(k, off);
-            c1<<<gb, kThreads, 0, st>>>(k, off);
-            return cudaGetLastError();
-        }
         cudaError_t e = launch_pdl(c0, gb, kThreads, st, k, off);
         return e == cudaSuccess ? launch_pdl(c1, gb, kThreads, st, k, off) : e;
     }
@@ -1479,16 +1474,14 @@ cudaError_t launch_sweep_wide(const Geom &g, bool fields, int off, cudaStream_t 
         static int res_ne = 0;
         const unsigned pb = (unsigned)std::min<long long>(
             wide_chunks(g), wave(reinterpret_cast<const void *>(k_wide_pipe_ne<1, true>), res_ne));
-        // plain launches: early-scheduled dependents measured no faster here
         using KG = void (*)(Geom, int);
         static const KG kne[2][2][2] = {
             {{k_wide_pipe_ne<0, false>, k_wide_pipe_ne<1, false>}, {k_wide_pipe_ne<0, true>, k_wide_pipe_ne<1, true>}},
             {{k_wide_pipe_ne<0, false, true>, k_wide_pipe_ne<1, false, true>},
              {k_wide_pipe_ne<0, true, true>, k_wide_pipe_ne<1, true, true>}}};
         const int cm = g.cmode ? 1 : 0, ref = k.ref != nullptr ? 1 : 0;
-        kne[cm][ref][0]<<<pb, kThreads, 0, st>>>(k, off);
-        kne[cm][ref][1]<<<pb, kThreads, 0, st>>>(k, off);
-        return cudaGetLastError();
+        cudaError_t e = launch_pdl(kne[cm][ref][0], pb, kThreads, st, k, off);
+        return e == cudaSuccess ? launch_pdl(kne[cm][ref][1], pb, kThreads, st, k, off) : e;
     }
     // Ising, uniform or with per-bond couplings (and per-site field signs):
     // the software-pipelined kernels
